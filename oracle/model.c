@@ -1,0 +1,234 @@
+/*
+ * Observation model, negative log-likelihood, gradients and the three gradient
+ * steps of the PALM iteration.  TEST INFRASTRUCTURE ONLY -- see rt3d_oracle.h.
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdlib.h>
+#include "rt3d_oracle.h"
+
+#define IDX(k, p, npix) ((int64_t)(k) * (npix) + (p))
+
+static double irf_sample(const or_irf* irf, int k)
+{
+    return (k < 0 || k >= irf->len) ? 0.0 : irf->h[k];
+}
+
+/* h(x) and h'(x): the continuous instrument response h_{i,j}(t - t_n) of the
+ * likelihood equation (Results, "Observation model").  The paper samples it per
+ * bin; a depth is real-valued, so the reading used here is the Catmull-Rom
+ * cubic (Keys, a = -1/2) interpolant of the samples, which is C^1 and
+ * reproduces constants (sum_t h(t - tau) = sum_k h_k when the support lies
+ * inside the histogram). */
+void or_irf_eval(const or_irf* irf, double x, double* h, double* dh)
+{
+    const double y = x + irf->origin;
+    if (!(y > -2.0 && y < irf->len + 1.0)) {   /* outside the 4-tap support */
+        *h = 0.0;
+        *dh = 0.0;
+        return;
+    }
+    const double kf = floor(y);
+    const int k = (int)kf;
+    const double u = y - kf;
+    const double pm = irf_sample(irf, k - 1), p0 = irf_sample(irf, k);
+    const double p1 = irf_sample(irf, k + 1), p2 = irf_sample(irf, k + 2);
+    const double c1 = p1 - pm;
+    const double c2 = 2.0 * pm - 5.0 * p0 + 4.0 * p1 - p2;
+    const double c3 = -pm + 3.0 * p0 - 3.0 * p1 + p2;
+    *h = 0.5 * (2.0 * p0 + c1 * u + c2 * u * u + c3 * u * u * u);
+    *dh = 0.5 * (c1 + 2.0 * c2 * u + 3.0 * c3 * u * u);
+}
+
+/* Mean count of pixel p in bin t (likelihood equation):
+ *   lambda = g (sum over alive points n of the pixel r_n h(t - t_n) + b),
+ * floored at lam_floor so that the logarithm and 1/lambda exist. */
+static double pixel_lambda(const or_state* s, int64_t p, int64_t npix, double g,
+                           const or_irf* irf, double tb, double lam_floor)
+{
+    double acc = s->b[p];
+    for (int k = 0; k < s->k; ++k) {
+        const int64_t n = IDX(k, p, npix);
+        if (!s->alive[n]) continue;
+        double h, dh;
+        or_irf_eval(irf, tb - s->t[n], &h, &dh);
+        acc += s->r[n] * h;
+    }
+    const double lam = g * acc;
+    return lam > lam_floor ? lam : lam_floor;
+}
+
+/* g(t, r, b) = sum_{i,j,t} (lambda - z log lambda), the negative log-likelihood
+ * of Results, "Observation model", without the constant log z! term.  Dense
+ * over every bin: the reference the sparse gradients are checked against. */
+double or_nll_dense(int h, int w, int t, const double* z, const double* gain,
+                    const or_state* s, const or_irf* irf, double lam_floor)
+{
+    const int64_t npix = (int64_t)h * w;
+    double total = 0.0;
+    for (int64_t p = 0; p < npix; ++p)
+        for (int tb = 0; tb < t; ++tb) {
+            const double lam = pixel_lambda(s, p, npix, gain[p], irf, (double)tb, lam_floor);
+            const double zz = z[p * t + tb];
+            total += lam - (zz > 0.0 ? zz * log(lam) : 0.0);
+        }
+    return total;
+}
+
+/* H_n = sum_{t in [0,T)} h(t - t_n) and H'_n = sum_t h'(t - t_n): the part of the
+ * gradient carried by the zero bins.  Summed over every bin where h can be
+ * nonzero (explicitly, also in the interior where H = 1 and H' = 0). */
+static void support_sums(const or_irf* irf, double tn, int t, double* H, double* dH)
+{
+    const int base = (int)floor(tn) - irf->origin;
+    int lo = base - 3, hi = base + irf->len + 2;
+    if (lo < 0) lo = 0;
+    if (hi > t - 1) hi = t - 1;
+    double sh = 0.0, sdh = 0.0;
+    for (int tb = lo; tb <= hi; ++tb) {
+        double hv, dv;
+        or_irf_eval(irf, tb - tn, &hv, &dv);
+        sh += hv;
+        sdh += dv;
+    }
+    *H = sh;
+    *dH = sdh;
+}
+
+/* Sums over the nonzero bins of pixel p (the cost is linear in active bins,
+ * Methods and Fig. 5):
+ *   sh[k]  = sum z h(t - t_k) / lambda,  sdh[k] = sum z h'(t - t_k) / lambda,
+ *   *sz    = sum z / lambda. */
+static void pixel_sums(const or_frame* f, const or_state* s, const or_irf* irf,
+                       double lam_floor, int64_t p, double* sh, double* sdh, double* sz)
+{
+    const int64_t npix = (int64_t)f->h * f->w;
+    const double g = f->gain[p];
+    for (int k = 0; k < s->k; ++k) sh[k] = sdh[k] = 0.0;
+    *sz = 0.0;
+    for (int64_t e = f->off[p]; e < f->off[p + 1]; ++e) {
+        const double tb = f->bin[e], zz = f->cnt[e];
+        const double lam = pixel_lambda(s, p, npix, g, irf, tb, lam_floor);
+        *sz += zz / lam;
+        for (int k = 0; k < s->k; ++k) {
+            const int64_t n = IDX(k, p, npix);
+            if (!s->alive[n]) continue;
+            double hv, dv;
+            or_irf_eval(irf, tb - s->t[n], &hv, &dv);
+            sh[k] += zz * hv / lam;
+            sdh[k] += zz * dv / lam;
+        }
+    }
+}
+
+/* Gradient of g with respect to every t_n, r_n (alive points; 0 otherwise) and
+ * b_ij.  Differentiating lambda - z log lambda:
+ *   dg/dt_n = g r_n ( -H'_n + sum_{z>0} z h'(t - t_n) / lambda )
+ *   dg/dr_n = g     (  H_n  - sum_{z>0} z h (t - t_n) / lambda )
+ *   dg/db   = g     (  T    - sum_{z>0} z / lambda ). */
+void or_gradients(const or_frame* f, const or_state* s, const or_irf* irf,
+                  const or_params* prm, double* gt, double* gr, double* gb)
+{
+    const int64_t npix = (int64_t)f->h * f->w;
+    for (int64_t p = 0; p < npix; ++p) {
+        double sh[16], sdh[16], sz;
+        pixel_sums(f, s, irf, prm->lam_floor, p, sh, sdh, &sz);
+        const double g = f->gain[p];
+        gb[p] = g * (f->t - sz);
+        for (int k = 0; k < s->k; ++k) {
+            const int64_t n = IDX(k, p, npix);
+            if (!s->alive[n]) {
+                gt[n] = gr[n] = 0.0;
+                continue;
+            }
+            double H, dH;
+            support_sums(irf, s->t[n], f->t, &H, &dH);
+            gt[n] = g * s->r[n] * (-dH + sdh[k]);
+            gr[n] = g * (H - sh[k]);
+        }
+    }
+}
+
+static double clampd(double v, double lo, double hi)
+{
+    return v < lo ? lo : (v > hi ? hi : v);
+}
+
+/* Depth update, gradient part (Results, "Reconstruction algorithm", depth
+ * update).  All points of a pixel move together from the same lambda.
+ * Step (reading; the paper's step sizes are in its supplement):
+ *   beta_t = t_step / (g r_n + eps_r)  (a Fisher-information scaling),
+ *   t_n <- clamp(t_n - clamp(beta_t dg/dt_n, +-dt_max), 0, T-1). */
+void or_t_step(const or_frame* f, const or_irf* irf, const or_params* prm, or_state* s)
+{
+    const int64_t npix = (int64_t)f->h * f->w;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < npix; ++p) {
+        const double g = f->gain[p];
+        if (!(g > 0.0)) continue;
+        double sh[16], sdh[16], sz, newt[16];
+        pixel_sums(f, s, irf, prm->lam_floor, p, sh, sdh, &sz);
+        for (int k = 0; k < s->k; ++k) {
+            const int64_t n = IDX(k, p, npix);
+            newt[k] = s->t[n];
+            if (!s->alive[n]) continue;
+            double H, dH;
+            support_sums(irf, s->t[n], f->t, &H, &dH);
+            const double grad = g * s->r[n] * (-dH + sdh[k]);
+            const double beta = prm->t_step / (g * s->r[n] + prm->eps_r);
+            const double step = clampd(-beta * grad, -prm->dt_max, prm->dt_max);
+            newt[k] = clampd(s->t[n] + step, 0.0, (double)(f->t - 1));
+        }
+        for (int k = 0; k < s->k; ++k) s->t[IDX(k, p, npix)] = newt[k];
+    }
+}
+
+/* Intensity update, gradient part.  Step (reading): beta_r = r_step (r_n + eps_r)/g,
+ *   r_n <- max(0, r_n - r_step (r_n + eps_r)(H_n - sum z h / lambda)). */
+void or_r_step(const or_frame* f, const or_irf* irf, const or_params* prm, or_state* s)
+{
+    const int64_t npix = (int64_t)f->h * f->w;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < npix; ++p) {
+        const double g = f->gain[p];
+        if (!(g > 0.0)) continue;
+        double sh[16], sdh[16], sz, newr[16];
+        pixel_sums(f, s, irf, prm->lam_floor, p, sh, sdh, &sz);
+        for (int k = 0; k < s->k; ++k) {
+            const int64_t n = IDX(k, p, npix);
+            newr[k] = s->r[n];
+            if (!s->alive[n]) continue;
+            double H, dH;
+            support_sums(irf, s->t[n], f->t, &H, &dH);
+            const double v = s->r[n] - prm->r_step * (s->r[n] + prm->eps_r) * (H - sh[k]);
+            newr[k] = v > 0.0 ? v : 0.0;
+        }
+        for (int k = 0; k < s->k; ++k) s->r[IDX(k, p, npix)] = newr[k];
+    }
+}
+
+/* Background update, gradient part.  Step (reading): beta_b = b_step (b + eps_b)/(g T),
+ *   b <- max(b_floor, b - b_step (b + eps_b)(1 - sum z/lambda / T)). */
+void or_b_step(const or_frame* f, const or_irf* irf, const or_params* prm, or_state* s)
+{
+    const int64_t npix = (int64_t)f->h * f->w;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t p = 0; p < npix; ++p) {
+        const double g = f->gain[p];
+        if (!(g > 0.0)) continue;
+        double sh[16], sdh[16], sz;
+        pixel_sums(f, s, irf, prm->lam_floor, p, sh, sdh, &sz);
+        const double v = s->b[p] - prm->b_step * (s->b[p] + prm->eps_b) * (1.0 - sz / f->t);
+        s->b[p] = v > prm->b_floor ? v : prm->b_floor;
+    }
+}
+
+int or_num_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

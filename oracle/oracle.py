@@ -1,0 +1,289 @@
+"""ctypes wrapper of the FP64 C oracle (test infrastructure only).
+
+The C sources beside this file implement, in plain loops, the observation
+model, the log-matched-filter initialisation and the PALM iteration with its
+denoisers (see rt3d_oracle.h for the paper passages).  This wrapper only
+builds the library, compacts histograms into per-pixel nonzero-bin lists and
+marshals numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "build", "liboracle.so")
+SOURCES = ["synth.c", "model.c", "init.c", "denoise.c", "palm.c"]
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (OpenMP over pixels) if it is out of date."""
+    srcs = [os.path.join(HERE, s) for s in SOURCES]
+    deps = srcs + [os.path.join(HERE, "rt3d_oracle.h")]
+    if not force and os.path.exists(LIB_PATH):
+        built = os.path.getmtime(LIB_PATH)
+        if all(os.path.getmtime(d) <= built for d in deps):
+            return LIB_PATH
+    os.makedirs(os.path.dirname(LIB_PATH), exist_ok=True)
+    tmp = LIB_PATH + f".{os.getpid()}.tmp"
+    cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-Wall",
+           "-Wno-unknown-pragmas", "-o", tmp] + srcs + ["-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class Irf(C.Structure):
+    _fields_ = [("len", C.c_int), ("origin", C.c_int), ("h", C.POINTER(C.c_double))]
+
+
+class Frame(C.Structure):
+    _fields_ = [("h", C.c_int), ("w", C.c_int), ("t", C.c_int),
+                ("off", C.POINTER(C.c_int64)), ("bin", C.POINTER(C.c_int32)),
+                ("cnt", C.POINTER(C.c_double)), ("gain", C.POINTER(C.c_double))]
+
+
+class State(C.Structure):
+    _fields_ = [("k", C.c_int), ("t", C.POINTER(C.c_double)), ("r", C.POINTER(C.c_double)),
+                ("alive", C.POINTER(C.c_uint8)), ("b", C.POINTER(C.c_double))]
+
+
+class Params(C.Structure):
+    _fields_ = [("n_iter", C.c_int), ("k_max", C.c_int),
+                ("t_step", C.c_double), ("r_step", C.c_double), ("b_step", C.c_double),
+                ("dt_max", C.c_double), ("eps_r", C.c_double), ("eps_b", C.c_double),
+                ("b_floor", C.c_double), ("lam_floor", C.c_double),
+                ("pixel_pitch", C.c_double), ("apss_radius", C.c_double),
+                ("win_r", C.c_int), ("apss_min_nb", C.c_int),
+                ("int_radius", C.c_double), ("r_min", C.c_double),
+                ("depth_denoiser", C.c_int), ("intensity_denoiser", C.c_int),
+                ("bkg_mode", C.c_int), ("bkg_sigma", C.c_double), ("bkg_radius", C.c_int),
+                ("lmf_delta_rel", C.c_double), ("lmf_frac_bits", C.c_int),
+                ("peak_min_photons", C.c_int), ("peak_sep", C.c_int)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        _lib.or_poisson_fixed.restype = C.c_uint32
+        _lib.or_nll_dense.restype = C.c_double
+        _lib.or_peaks.restype = C.c_int
+        _lib.or_num_threads.restype = C.c_int
+    return _lib
+
+
+def _ptr(a, ctype):
+    return a.ctypes.data_as(C.POINTER(ctype))
+
+
+def _f32(v):
+    """Parameters are rounded to single precision, the precision the kernels see."""
+    return float(np.float32(v))
+
+
+def make_params(d: dict) -> Params:
+    p = Params()
+    for name, ctype in Params._fields_:
+        v = d[name]
+        setattr(p, name, int(v) if ctype is C.c_int else _f32(v))
+    return p
+
+
+@dataclasses.dataclass
+class OState:
+    t: np.ndarray      # float64 [K][H][W]
+    r: np.ndarray
+    alive: np.ndarray  # uint8 [K][H][W]
+    b: np.ndarray      # float64 [H][W]
+
+    def copy(self):
+        return OState(self.t.copy(), self.r.copy(), self.alive.copy(), self.b.copy())
+
+    def c(self):
+        return State(self.t.shape[0], _ptr(self.t, C.c_double), _ptr(self.r, C.c_double),
+                     _ptr(self.alive, C.c_uint8), _ptr(self.b, C.c_double))
+
+
+def new_state(k, h, w) -> OState:
+    return OState(np.zeros((k, h, w)), np.zeros((k, h, w)), np.zeros((k, h, w), np.uint8),
+                  np.zeros((h, w)))
+
+
+class OIrf:
+    """IRF normalised in FP64 by the oracle (sum of samples in index order)."""
+
+    def __init__(self, samples, origin):
+        s = np.asarray(samples, dtype=np.float64)
+        total = 0.0
+        for v in s:
+            total += float(v)
+        self.h = np.ascontiguousarray(s / total)
+        self.origin = int(origin)
+
+    def c(self):
+        return Irf(len(self.h), self.origin, _ptr(self.h, C.c_double))
+
+
+class OFrame:
+    """Per-pixel nonzero-bin lists of a histogram (integer or expected counts)."""
+
+    def __init__(self, z, gain=None):
+        z = np.asarray(z)
+        self.hh, self.ww, self.tt = z.shape
+        flat = z.reshape(-1, self.tt)
+        rows, bins = np.nonzero(flat)
+        counts = np.bincount(rows, minlength=flat.shape[0])
+        self.off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+        self.bin = bins.astype(np.int32)
+        self.cnt = flat[rows, bins].astype(np.float64)
+        g = np.ones((self.hh, self.ww)) if gain is None else np.asarray(gain, np.float64)
+        self.gain = np.ascontiguousarray(g.reshape(self.hh, self.ww))
+
+    def c(self):
+        return Frame(self.hh, self.ww, self.tt, _ptr(self.off, C.c_int64),
+                     _ptr(self.bin, C.c_int32), _ptr(self.cnt, C.c_double),
+                     _ptr(self.gain, C.c_double))
+
+
+# ---------------------------------------------------------------------------
+# functions
+# ---------------------------------------------------------------------------
+
+def philox(ctr, key):
+    c = np.asarray(ctr, np.uint32)
+    k = np.asarray(key, np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().or_philox4x32_10(_ptr(c, C.c_uint32), _ptr(k, C.c_uint32), _ptr(out, C.c_uint32))
+    return out
+
+
+def poisson_fixed(u, p0, mu):
+    return int(lib().or_poisson_fixed(C.c_uint32(int(u)), C.c_uint64(int(p0)), C.c_uint64(int(mu))))
+
+
+def synthesize(tab: dict, seed=None) -> np.ndarray:
+    """Histogram [H][W][T] uint16 from the integer tables of scenes.sampling_tables."""
+    h, w, t = tab["h"], tab["w"], tab["t"]
+    out = np.zeros((h, w, t), np.uint16)
+    seed = tab["seed"] if seed is None else seed
+    lib().or_synthesize(h, w, t, tab["n_comp"],
+                        _ptr(tab["depth_int"], C.c_int32), _ptr(tab["depth_split"], C.c_uint32),
+                        _ptr(tab["n_parts"], C.c_uint32), _ptr(tab["p0"], C.c_uint64),
+                        _ptr(tab["mu"], C.c_uint64), _ptr(tab["irf_cdf"], C.c_uint32),
+                        tab["irf_len"], tab["irf_origin"], C.c_uint64(int(seed)),
+                        _ptr(out, C.c_uint16))
+    return out
+
+
+def irf_eval(irf: OIrf, x):
+    h = C.c_double()
+    dh = C.c_double()
+    lib().or_irf_eval(C.byref(irf.c()), C.c_double(float(x)), C.byref(h), C.byref(dh))
+    return h.value, dh.value
+
+
+def nll_dense(z, gain, st: OState, irf: OIrf, lam_floor):
+    z = np.ascontiguousarray(z, np.float64)
+    h, w, t = z.shape
+    g = np.ascontiguousarray(np.ones((h, w)) if gain is None else gain, np.float64)
+    return lib().or_nll_dense(h, w, t, _ptr(z, C.c_double), _ptr(g, C.c_double),
+                              C.byref(st.c()), C.byref(irf.c()), C.c_double(lam_floor))
+
+
+def gradients(fr: OFrame, st: OState, irf: OIrf, prm: dict):
+    k, h, w = st.t.shape
+    gt = np.zeros((k, h, w))
+    gr = np.zeros((k, h, w))
+    gb = np.zeros((h, w))
+    p = make_params(prm)
+    lib().or_gradients(C.byref(fr.c()), C.byref(st.c()), C.byref(irf.c()), C.byref(p),
+                       _ptr(gt, C.c_double), _ptr(gr, C.c_double), _ptr(gb, C.c_double))
+    return gt, gr, gb
+
+
+def lmf_kernel(irf: OIrf, delta_rel, frac_bits):
+    k = np.zeros(len(irf.h), np.int32)
+    lib().or_lmf_kernel(C.byref(irf.c()), C.c_double(_f32(delta_rel)), int(frac_bits),
+                        _ptr(k, C.c_int32))
+    return k
+
+
+def lmf(z_row, kern, origin):
+    z = np.ascontiguousarray(z_row, np.uint16)
+    kern = np.ascontiguousarray(kern, np.int32)
+    t = z.shape[0]
+    y = np.zeros(t, np.int64)
+    wc = np.zeros(t, np.int64)
+    lib().or_lmf(_ptr(z, C.c_uint16), t, _ptr(kern, C.c_int32), len(kern), int(origin),
+                 _ptr(y, C.c_int64), _ptr(wc, C.c_int64))
+    return y, wc
+
+
+def peaks(y, wc, sep, min_photons, kmax):
+    y = np.ascontiguousarray(y, np.int64)
+    wc = np.ascontiguousarray(wc, np.int64)
+    taus = np.zeros(16, np.int32)
+    n = lib().or_peaks(_ptr(y, C.c_int64), _ptr(wc, C.c_int64), len(y), int(sep),
+                       int(min_photons), int(kmax), _ptr(taus, C.c_int32))
+    return taus[:n].copy()
+
+
+def init(dense, gain, irf: OIrf, prm: dict) -> OState:
+    dense = np.ascontiguousarray(dense, np.uint16)
+    h, w, t = dense.shape
+    g = np.ascontiguousarray(np.ones((h, w)) if gain is None else gain, np.float64)
+    st = new_state(prm["k_max"], h, w)
+    p = make_params(prm)
+    lib().or_init(_ptr(dense, C.c_uint16), _ptr(g, C.c_double), h, w, t, C.byref(irf.c()),
+                  C.byref(p), C.byref(st.c()))
+    return st
+
+
+def t_step(fr, irf, prm, st):
+    lib().or_t_step(C.byref(fr.c()), C.byref(irf.c()), C.byref(make_params(prm)), C.byref(st.c()))
+
+
+def r_step(fr, irf, prm, st):
+    lib().or_r_step(C.byref(fr.c()), C.byref(irf.c()), C.byref(make_params(prm)), C.byref(st.c()))
+
+
+def b_step(fr, irf, prm, st):
+    lib().or_b_step(C.byref(fr.c()), C.byref(irf.c()), C.byref(make_params(prm)), C.byref(st.c()))
+
+
+def apss(h, w, t, prm, st):
+    lib().or_apss(h, w, t, C.byref(make_params(prm)), C.byref(st.c()))
+
+
+def int_lowpass(h, w, prm, st):
+    lib().or_int_lowpass(h, w, C.byref(make_params(prm)), C.byref(st.c()))
+
+
+def bkg_lowpass(h, w, prm, b):
+    lib().or_bkg_lowpass(h, w, C.byref(make_params(prm)), _ptr(b, C.c_double))
+
+
+def palm(fr, irf, prm, st, n_iter):
+    lib().or_palm(C.byref(fr.c()), C.byref(irf.c()), C.byref(make_params(prm)),
+                  C.byref(st.c()), int(n_iter))
+
+
+def reconstruct(dense, irf: OIrf, prm: dict, gain=None) -> OState:
+    dense = np.ascontiguousarray(dense, np.uint16)
+    h, w, t = dense.shape
+    fr = OFrame(dense, gain)
+    st = new_state(prm["k_max"], h, w)
+    lib().or_reconstruct(_ptr(dense, C.c_uint16), C.byref(fr.c()), C.byref(irf.c()),
+                         C.byref(make_params(prm)), C.byref(st.c()))
+    return st
+
+
+def num_threads() -> int:
+    return int(lib().or_num_threads())

@@ -1,0 +1,29 @@
+/*
+ * The reconstruction loop.  TEST INFRASTRUCTURE ONLY -- see rt3d_oracle.h.
+ *
+ * PALM (Bolte, Sabach & Teboulle 2014) over the blocks t, r, b as in Results,
+ * "Reconstruction algorithm" and Fig. 2: each block takes a gradient step on
+ * the negative log-likelihood and then a denoiser in the role of the proximal
+ * operator, in the order depth, intensity, background.  A fixed number of
+ * iterations is run (reading: the paper gives no stopping rule).
+ */
+#include "rt3d_oracle.h"
+
+void or_palm(const or_frame* f, const or_irf* irf, const or_params* p, or_state* s, int n_iter)
+{
+    for (int it = 0; it < n_iter; ++it) {
+        or_t_step(f, irf, p, s);                         /* depth: gradient step */
+        if (p->depth_denoiser == 1) or_apss(f->h, f->w, f->t, p, s);   /* depth: APSS */
+        or_r_step(f, irf, p, s);                         /* intensity: gradient step */
+        or_int_lowpass(f->h, f->w, p, s);                /* intensity: low-pass + pruning */
+        or_b_step(f, irf, p, s);                         /* background: gradient step */
+        or_bkg_lowpass(f->h, f->w, p, s->b);             /* background: denoiser */
+    }
+}
+
+void or_reconstruct(const uint16_t* dense, const or_frame* f, const or_irf* irf,
+                    const or_params* p, or_state* s)
+{
+    or_init(dense, f->gain, f->h, f->w, f->t, irf, p, s);
+    or_palm(f, irf, p, s, p->n_iter);
+}

@@ -1,0 +1,132 @@
+"""Pins of the oracle's denoisers: APSS, intensity low-pass, background low-pass."""
+import numpy as np
+import pytest
+
+import scenes
+
+
+def _params(**over):
+    p = scenes.make_params(scenes.small_random(4, 4, 64))
+    p.update(dict(k_max=1))
+    p.update(over)
+    return p
+
+
+def _cloud(orc, depth):
+    k = 1 if depth.ndim == 2 else depth.shape[0]
+    d = depth.reshape(k, *depth.shape[-2:])
+    st = orc.new_state(k, d.shape[1], d.shape[2])
+    st.t[:] = d
+    st.alive[:] = np.isfinite(d)
+    st.t[~np.isfinite(d)] = 0
+    st.r[:] = 1.0
+    st.b[:] = 0.01
+    return st
+
+
+@pytest.mark.parametrize("gi,gj", [(0.0, 0.0), (0.4, -0.3), (1.5, 2.0), (-4.0, 3.0)])
+def test_apss_leaves_exact_planes_fixed(orc, gi, gj):
+    """APSS reproduces planes (Guennebaud & Gross: spheres and planes are exact)."""
+    h, w = 11, 13
+    prm = _params(pixel_pitch=8.0, apss_radius=20.0, int_radius=20.0)
+    i, j = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    depth = 500.0 + gi * prm["pixel_pitch"] * i + gj * prm["pixel_pitch"] * j
+    st = _cloud(orc, depth)
+    orc.apss(h, w, 2000, prm, st)
+    np.testing.assert_allclose(st.t[0], depth, atol=1e-9)
+
+
+@pytest.mark.parametrize("radius", [60.0, 150.0])
+def test_apss_leaves_exact_spheres_fixed(orc, radius):
+    h, w = 15, 15
+    prm = _params(pixel_pitch=4.0, apss_radius=12.0)
+    i, j = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    x, y = prm["pixel_pitch"] * (j - 7.2), prm["pixel_pitch"] * (i - 6.9)
+    depth = 900.0 - np.sqrt(radius ** 2 - x ** 2 - y ** 2)
+    st = _cloud(orc, depth)
+    orc.apss(h, w, 2000, prm, st)
+    np.testing.assert_allclose(st.t[0], depth, atol=1e-9)
+
+
+def test_apss_commutes_with_depth_shift_and_smooths_noise(orc):
+    rng = np.random.default_rng(0)
+    h, w = 12, 12
+    prm = _params()
+    i, j = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    true = 300 + 3.0 * i - 2.0 * j
+    noisy = true + rng.normal(0, 2.0, (h, w))
+    a = _cloud(orc, noisy)
+    b = _cloud(orc, noisy + 123.25)
+    orc.apss(h, w, 2000, prm, a)
+    orc.apss(h, w, 2000, prm, b)
+    np.testing.assert_allclose(b.t - 123.25, a.t, atol=1e-9)
+    assert np.std(a.t[0] - true) < 0.7 * np.std(noisy - true)
+
+
+def test_apss_ignores_other_surfaces_and_degenerate_windows(orc):
+    """A second surface farther than the radius does not move the first, and a
+    one-row image (collinear neighbours) is left unchanged."""
+    h, w = 9, 9
+    prm = _params(k_max=2)
+    i, j = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    front = 400 + 2.0 * i + 1.0 * j
+    back = 400 + 200 + 0.0 * i + np.random.default_rng(1).normal(0, 3, (h, w))
+    st = _cloud(orc, np.stack([front, back]))
+    orc.apss(h, w, 2000, prm, st)
+    np.testing.assert_allclose(st.t[0], front, atol=1e-9)
+    row = _cloud(orc, np.array([[100.0, 103.0, 99.0, 101.0, 104.0, 98.0, 102.0]]))
+    before = row.t.copy()
+    orc.apss(1, 7, 2000, prm, row)
+    assert np.array_equal(row.t, before)
+
+
+def test_intensity_lowpass_constant_and_pruning(orc):
+    h, w = 6, 7
+    prm = _params(r_min=0.5)
+    st = _cloud(orc, 200 + np.random.default_rng(2).normal(0, 1, (h, w)))
+    st.r[:] = 3.25
+    orc.int_lowpass(h, w, prm, st)
+    np.testing.assert_allclose(st.r, 3.25, rtol=1e-14)
+    assert st.alive.all()
+    # an isolated low point is averaged with its neighbours; a uniformly low
+    # patch falls below r_min and is removed
+    st.r[:] = 0.4
+    orc.int_lowpass(h, w, prm, st)
+    assert not st.alive.any()
+
+
+def test_intensity_lowpass_stays_on_its_surface(orc):
+    h, w = 6, 6
+    prm = _params(k_max=2)
+    st = _cloud(orc, np.stack([np.full((h, w), 100.0), np.full((h, w), 600.0)]))
+    st.r[0] = 1.0
+    st.r[1] = 9.0
+    orc.int_lowpass(h, w, prm, st)
+    np.testing.assert_allclose(st.r[0], 1.0)
+    np.testing.assert_allclose(st.r[1], 9.0)
+
+
+@pytest.mark.parametrize("h,w,sigma,rad", [(8, 8, 1.0, 3), (5, 7, 0.8, 2), (8, 8, 2.0, 6)])
+def test_background_lowpass_equals_fft_filter(orc, h, w, sigma, rad):
+    """Periodic Gaussian filtering equals multiplying the 2-D DFT of the image by
+    the DFT of the (wrapped) kernel -- the FFT denoiser of the paper."""
+    rng = np.random.default_rng(4)
+    b = rng.uniform(0, 1, (h, w))
+    prm = _params(bkg_mode=1, bkg_sigma=sigma, bkg_radius=rad)
+    d = np.arange(-rad, rad + 1)
+    k1 = np.exp(-d.astype(float) ** 2 / (2 * np.float32(sigma) ** 2))
+    k1 /= k1.sum()
+    ker = np.zeros((h, w))
+    for a, ka in zip(d, k1):
+        for c, kc in zip(d, k1):
+            ker[a % h, c % w] += ka * kc
+    want = np.real(np.fft.ifft2(np.fft.fft2(b) * np.fft.fft2(ker)))
+    got = b.copy()
+    orc.bkg_lowpass(h, w, prm, got)
+    np.testing.assert_allclose(got, want, atol=1e-12)
+    const = np.full((h, w), 0.37)
+    orc.bkg_lowpass(h, w, prm, const)
+    np.testing.assert_allclose(const, 0.37, rtol=1e-14)
+    ident = b.copy()
+    orc.bkg_lowpass(h, w, _params(bkg_mode=0), ident)
+    assert np.array_equal(ident, b)
