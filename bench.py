@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput and latency of the full reconstruction on one B300.
+
+Workload: the multi-surface scene at 141 x 141 pixels x 4096 bins (a
+camouflage-like net at bin 1500, a smooth object at 1800-2200, a wall at
+3000; gamma IRF of shape 3 and scale 5 bins; 5 signal photons per pixel at a
+signal-to-background ratio of 1), synthesised on the device from seeded
+Philox draws.  One step = the whole method (initialisation + 20 PALM
+iterations) on a batch of frames, inputs resident in HBM; the batch's dense
+histograms (2.6 GB for 16 frames) exceed the 126 MB L2, so every step streams
+its inputs from HBM.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B]
+                       [--impl ours|reference]
+Multi-GPU (torchrun, one rank per GPU): independent replicas, no collective
+on the data path; value = all frames / the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import scenes  # noqa: E402
+
+METRIC = "frames/s (141x141 px x 4096 bins, multi-surface, full method)"
+UNIT = "frames/s"
+H, W, T, K = 141, 141, 4096, 3
+KERNEL_NAMES = ["init", "phase_a", "phase_b", "phase_c", "final"]
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=16)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--latency-frames", type=int, default=64)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-frames", type=int, default=4)
+    ap.add_argument("--no-parity", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# --------------------------------------------------------------------------- helpers
+
+def algorithmic_bytes(n_frames: int, nnz_total: int, k: int) -> dict:
+    """Bytes each kernel class must move per launch for n frames of H x W x T
+    (every array read or written once; halos counted once).  Per pixel:
+      init    2T dense read + 8 seg + 9K state + 4 b written, + 4 per nonzero entry written
+      phase A 8 seg + 4 b_half + K (4 t + 4 r + 1 alive_b + 1 alive + 4 t_half) + 4 b, + 4/entry
+      phase B 8 seg + K (4 t_half + 1 alive + 4 r + 4 t + 4 r_half) + 4 b, + 4/entry
+      phase C 8 seg + K (4 t + 4 r_half + 1 alive + 4 r + 1 alive_b) + 4 b + 4 b_half, + 4/entry
+      final   K (1 alive_b + 1 alive) + 4 b_half + 4 b."""
+    px = n_frames * H * W
+    e = 4 * nnz_total
+    return {
+        "init": px * (2 * T + 8 + 9 * k + 4) + e,
+        "phase_a": px * (8 + 4 + k * 14 + 4) + e,
+        "phase_b": px * (8 + k * 17 + 4) + e,
+        "phase_c": px * (8 + k * 14 + 8) + e,
+        "final": px * (2 * k + 8),
+    }
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        mhz, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                mhz.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(mhz) if mhz else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return {"hbm_gbs": d.get("hbm_gbs", 6400.0), "source": "measured"}
+    return {"hbm_gbs": 6400.0, "source": "fallback"}
+
+
+def traffic_record(kernel: str):
+    """dram bytes per launch of `kernel` from the committed ncu summary, or None
+    if the kernel sources changed since it was captured."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    rec = json.load(open(path)).get(kernel)
+    if not rec:
+        return None
+    from paper_1905_06700_b300 import build as B
+    if rec.get("sources_sha") != B.sources_sha():
+        return None
+    return rec.get("dram_bytes_per_launch_full")
+
+
+# --------------------------------------------------------------------------- our arm
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1905_06700_b300 import build as B
+    from paper_1905_06700_b300 import rt3d as R
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    nb = args.batch
+    base = scenes.net_object_wall(H, W, T)
+    prm = scenes.make_params(base)
+    assert prm["k_max"] == K
+    ctx = R.Context(H, W, T, K, base.irf.samples, base.irf.origin, max_batch=nb, device=local)
+    dense, seeds = [], []
+    for f in range(nb):
+        seed = 1 + rank * nb + f
+        sc = scenes.net_object_wall(H, W, T, seed=seed)
+        dense.append(ctx.synthesize(scenes.sampling_tables(sc)))
+        seeds.append(seed)
+    torch.cuda.synchronize()
+    nnz_total = int(sum(int(torch.count_nonzero(d.view(torch.int16)).item()) for d in dense))
+    frames = [dict(dense=d) for d in dense]
+    outs = [ctx.new_result(H, W, K) for _ in range(nb)]
+    stream = torch.cuda.current_stream()
+
+    for _ in range(args.warmup):
+        ctx.reconstruct_batch(prm, frames, outs)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == R.RT3D_OK
+
+    # ---------------- timed region
+    ctx.set_profiling(True)
+    ctx.kernel_times(reset=True)
+    launches0 = ctx.launch_count()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    evs[0].record(stream)
+    for i in range(args.steps):
+        ctx.reconstruct_batch(prm, frames, outs)
+        evs[i + 1].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clk = clocks.stop()
+    launches = ctx.launch_count() - launches0
+    ctx.set_profiling(False)
+    ms_total = evs[0].elapsed_time(evs[-1])
+    step_ms = [evs[i].elapsed_time(evs[i + 1]) for i in range(args.steps)]
+    ktimes = ctx.kernel_times(reset=True)
+    assert ctx.device_status() == R.RT3D_OK
+
+    t_max = ms_total
+    if world > 1:
+        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    frames_all = nb * args.steps * world
+    value = frames_all / (t_max / 1000.0)
+
+    # ---------------- dominant kernel vs the HBM roofline
+    alg = algorithmic_bytes(nb, nnz_total, K)
+    per_kernel = {}
+    for name in KERNEL_NAMES:
+        ms, n = ktimes[name]
+        if n:
+            per_kernel[name] = dict(ms_total=ms, launches=n, ms_per_launch=ms / n,
+                                    alg_bytes_per_launch=alg[name],
+                                    gbs=alg[name] / (ms / n / 1000.0) / 1e9)
+    dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_total"])
+    peaks = measured_peaks()
+    d = per_kernel[dom]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(d["gbs"], 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(d["gbs"] / peaks["hbm_gbs"], 4),
+                "peak_source": f"{peaks['source']} (burst copy)",
+                "traffic": traffic_record(dom)}
+
+    result = None
+    if rank == 0:
+        # ---------------- single-frame latency (batch of one)
+        lat = []
+        one = ctx.new_result(H, W, K)
+        for i in range(args.latency_frames + 3):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            ctx.reconstruct(prm, dense=dense[i % nb], out=one)
+            b.record(stream)
+            b.synchronize()
+            if i >= 3:
+                lat.append(a.elapsed_time(b))
+        lat.sort()
+
+        # ---------------- end to end through the host entry point
+        e2e = run_e2e(args, ctx, prm, dense, R)
+
+        # ---------------- parity of the benchmark frame against the oracle
+        parity = None if args.no_parity else bench_parity(prm, seeds[0], outs[0])
+
+        # ---------------- the oracle on the host cores
+        cpu = None if world > 1 else cpu_baseline(args, prm)
+
+        result = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 (matched filter int32)", "data": "synthetic (seeded Philox, device-resident)",
+            "config": {"workload": "net_object_wall 141x141x4096, K=3, gamma IRF (3,5), "
+                                   "5 signal photons/px, SBR 1, 20 PALM iterations",
+                       "frames_per_step": nb, "nnz_per_pixel": round(nnz_total / (nb * H * W), 2),
+                       "l2": "inputs larger than L2 (dense histograms stream from HBM each step)",
+                       "parallelism": f"replicas x{world}"},
+            "latency_ms": {"batch_step_p50": round(statistics.median(step_ms), 4),
+                           "batch_step_p99": round(float(np.percentile(step_ms, 99)), 4),
+                           "frame_p50": round(float(np.percentile(lat, 50)), 4),
+                           "frame_p99": round(float(np.percentile(lat, 99)), 4),
+                           "frame_samples": len(lat)},
+            "e2e": e2e,
+            "roofline": roofline,
+            "kernels": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in v.items()}
+                        for k, v in per_kernel.items()},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "parity": parity,
+            "cpu_baseline": cpu,
+        }
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    ctx.close()
+    return result
+
+
+def run_e2e(args, ctx, prm, dense, R):
+    """The same metric through rt3d_reconstruct_host: every step copies each
+    frame's histogram from pinned host memory and its results back."""
+    import torch
+    nb = len(dense)
+    host = [d.view(torch.int16).cpu().pin_memory() for d in dense]
+    host_np = [h.numpy().view(np.uint16) for h in host]
+    outs = [dict(t=np.zeros((K, H, W), np.float32), r=np.zeros((K, H, W), np.float32),
+                 alive=np.zeros((K, H, W), np.uint8), b=np.zeros((H, W), np.float32),
+                 n_points=np.zeros(1, np.int32)) for _ in range(nb)]
+    R.reconstruct_host(ctx, prm, host_np[0], out=outs[0])          # warm-up
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for i in range(nb):
+            R.reconstruct_host(ctx, prm, host_np[i], out=outs[i])
+    dt = time.perf_counter() - t0
+    h2d = nb * H * W * T * 2
+    d2h = nb * (K * H * W * 9 + H * W * 4 + 4)
+    return {"value": round(nb * args.e2e_steps / dt, 2), "unit": UNIT,
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "path": "rt3d_reconstruct_host, dense uint16 histograms in pinned host memory"}
+
+
+def bench_parity(prm, seed, out):
+    """Depth/intensity error of the benchmark's first frame against the FP64 oracle."""
+    import oracle
+    sc = scenes.net_object_wall(H, W, T, seed=seed)
+    z = oracle.synthesize(scenes.sampling_tables(sc))
+    o = oracle.reconstruct(z, oracle.OIrf(sc.irf.samples, sc.irf.origin), prm)
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    ga, oa = g["alive"].astype(bool), o.alive.astype(bool)
+    both = ga & oa
+    dt = np.abs(g["t"].astype(np.float64) - o.t)[both]
+    dr = (np.abs(g["r"].astype(np.float64) - o.r) / np.maximum(o.r, 0.1))[both]
+    return {"points": int(oa.sum()), "alive_mismatch": int((ga != oa).sum()),
+            "dt_max_bins": float(dt.max()), "dt_p999_bins": float(np.percentile(dt, 99.9)),
+            "dt_median_bins": float(np.median(dt)), "dr_p999_rel": float(np.percentile(dr, 99.9)),
+            "frac_within_1e-3_bins": float((dt <= 1e-3).mean())}
+
+
+def cpu_baseline(args, prm) -> dict:
+    """The FP64 oracle, as it stands, on whole frames on this host's cores."""
+    import oracle
+    oracle.build()
+    zs = []
+    for f in range(args.cpu_frames):
+        sc = scenes.net_object_wall(H, W, T, seed=1000 + f)
+        zs.append((sc, oracle.synthesize(scenes.sampling_tables(sc))))
+    irf = oracle.OIrf(zs[0][0].irf.samples, zs[0][0].irf.origin)
+    t0 = time.perf_counter()
+    for sc, z in zs:
+        oracle.reconstruct(z, irf, prm)
+    dt = time.perf_counter() - t0
+    return {"value": round(len(zs) / dt, 4), "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{len(zs)} full 141x141x4096 frames (init + 20 iterations), FP64, OpenMP"}
+
+
+# --------------------------------------------------------------------------- reference arm
+
+def run_reference(args, world, rank):
+    """The reference arm is the FP64 oracle on the host cores (no code of the
+    paper exists to run): each step reconstructs one full frame."""
+    if rank != 0:
+        return None
+    import oracle
+    oracle.build()
+    base = scenes.net_object_wall(H, W, T)
+    prm = scenes.make_params(base)
+    irf = oracle.OIrf(base.irf.samples, base.irf.origin)
+    zs = []
+    for f in range(args.warmup + args.steps):
+        sc = scenes.net_object_wall(H, W, T, seed=1 + f)
+        zs.append(oracle.synthesize(scenes.sampling_tables(sc)))
+    for f in range(args.warmup):
+        oracle.reconstruct(zs[f], irf, prm)
+    times = []
+    for f in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.reconstruct(zs[args.warmup + f], irf, prm)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps / total
+    cores = oracle.num_threads()
+    sample = "1 full 141x141x4096 frame per step (init + 20 iterations), FP64 oracle, OpenMP"
+    return {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(1000 * total / args.steps, 2), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "net_object_wall 141x141x4096, K=3, 20 PALM iterations",
+                       "frames_per_step": 1},
+            "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_env()
+    if args.impl == "reference":
+        res = run_reference(args, world, rank)
+    else:
+        res = run_ours(args, world, rank, local)
+    if res is not None and rank == 0:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,273 @@
+/*
+ * rt3d.h -- C ABI of the B300 (sm_103a) reconstruction library for
+ * time-correlated single-photon (TCSPC) lidar histograms.
+ *
+ * The library implements the method of Tachella et al., "Real-time 3D
+ * reconstruction from single-photon lidar data using plug-and-play point cloud
+ * denoisers" (Nature Communications 2019):
+ *   - the Poisson observation model and its negative log-likelihood
+ *     (Results, "Observation model", the likelihood equation and g(t, r, b));
+ *   - a per-pixel initialisation (Methods, "3D Reconstruction algorithm"):
+ *     log-matched filter and peak picking into up to K points per pixel;
+ *   - the PALM loop over depth, intensity and background (Results,
+ *     "Reconstruction algorithm", Fig. 2): a gradient step on each block
+ *     followed by a plug-and-play denoiser -- APSS sphere fitting for depth,
+ *     a manifold low-pass plus pruning for intensity, identity or an
+ *     FFT-equivalent low-pass for the background.
+ *
+ * Conventions, for every entry point below:
+ *   - All frame and result pointers are DEVICE pointers owned by the caller,
+ *     unless the function says otherwise.  The library never frees them.
+ *   - Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream).  A return of RT3D_OK means the work was
+ *     validated and launched.  Errors detected on the device (capacity,
+ *     arithmetic range) are reported by rt3d_device_status().
+ *   - Arguments are validated on the host before anything is launched; an
+ *     invalid argument returns RT3D_E_INVALID and launches nothing.
+ *   - No exception crosses the ABI.  A context may be used from one host
+ *     thread at a time; calls that share a context are ordered on their
+ *     streams by the caller.
+ *   - Layouts: histograms [h][w][t] (bin-contiguous uint16); point slots
+ *     [k][h][w]; images [h][w].  Depths t are in bins (real-valued, bin b
+ *     covers [b, b+1)), intensities r in expected signal photons at gain 1,
+ *     backgrounds b in photons per bin.
+ */
+#ifndef RT3D_H
+#define RT3D_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT3D_VERSION 1
+#define RT3D_MAX_K 4          /* point slots per pixel */
+#define RT3D_MAX_IRF 256      /* samples of the instrument response */
+#define RT3D_MAX_BATCH 64     /* frames per batched call */
+#define RT3D_MAX_T 16384      /* histogram bins */
+#define RT3D_MAX_WIN_R 4      /* neighbourhood half-width of the denoisers, pixels */
+#define RT3D_MAX_BKG_R 15     /* background filter half-width, pixels */
+#define RT3D_MAX_SYNTH_COMP 8 /* surfaces per pixel in rt3d_synthesize */
+
+/* Opaque context: owns the device workspace of one CUDA device. */
+typedef struct rt3d_ctx rt3d_ctx_t;
+
+typedef enum {
+    RT3D_OK = 0,
+    RT3D_E_INVALID = -1,   /* bad argument; nothing was launched */
+    RT3D_E_NOMEM = -2,     /* device memory for the workspace is not available */
+    RT3D_E_CUDA = -3,      /* a CUDA runtime call failed */
+    RT3D_E_TIMEOUT = -4,   /* a bounded wait gave up */
+    RT3D_E_UNIMPL = -5,    /* option not built */
+    RT3D_E_CAPACITY = -6,  /* device: more nonzero bins than the sparse buffer holds */
+    RT3D_E_RANGE = -7      /* device: counts exceed the exact-arithmetic range */
+} rt3d_status;
+
+/* Matched-filter arithmetic (all exact for counts within range). */
+enum { RT3D_LMF_INT = 0, RT3D_LMF_BF16 = 1, RT3D_LMF_FP16 = 2 };
+/* Depth denoiser: none, APSS (the paper's), learned conv net (if loaded). */
+enum { RT3D_DEPTH_NONE = 0, RT3D_DEPTH_APSS = 1, RT3D_DEPTH_LEARNED = 2 };
+/* Background denoiser: identity (bistatic) or periodic Gaussian (= FFT low-pass). */
+enum { RT3D_BKG_IDENTITY = 0, RT3D_BKG_LOWPASS = 1 };
+
+/* Sizes the context's device workspace (allocated once, in rt3d_create). */
+typedef struct {
+    int32_t max_h, max_w, max_t;   /* largest frame */
+    int32_t k_max;                 /* point slots per pixel, 1..RT3D_MAX_K */
+    int32_t max_batch;             /* frames per batched call, 1..RT3D_MAX_BATCH */
+    int64_t max_entries;           /* nonzero-bin capacity per call; 0 = max_batch*max_h*max_w*max_t */
+    int32_t device;                /* CUDA device ordinal */
+} rt3d_config;
+
+/* Instrument response h_{i,j}(.) of the likelihood equation, shared by all
+ * pixels: HOST pointer to len samples at unit bin spacing; sample `origin`
+ * sits at depth offset 0 (a depth names the position of that sample).  The
+ * library normalises the samples to unit sum (in double precision, summing in
+ * index order) and interpolates them with the Catmull-Rom cubic.  Copied at
+ * rt3d_create; the caller keeps ownership. */
+typedef struct {
+    const double* samples;
+    int32_t len;                   /* 1..RT3D_MAX_IRF */
+    int32_t origin;                /* 0..len-1 */
+} rt3d_irf;
+
+/* One lidar frame, DEVICE pointers.  Give `dense`, or the sparse list
+ * (csr_off, csr_ent), or both (then the sparse list is used by the loop and
+ * the dense histogram by the initialisation).
+ *   dense    [h][w][t] uint16 photon counts
+ *   csr_off  [h*w + 1] offsets into csr_ent (pixel p owns off[p]..off[p+1])
+ *   csr_ent  packed (bin << 16) | count, count >= 1, bins increasing per pixel;
+ *            a photon list with repeated bins is NOT accepted -- merge first
+ *   gain     [h][w] detector gain g_{i,j} (0 = dead pixel) or NULL for 1. */
+typedef struct {
+    int32_t h, w, t;
+    const uint16_t* dense;
+    const uint32_t* csr_off;
+    const uint32_t* csr_ent;
+    const float* gain;
+} rt3d_frame;
+
+/* Every constant of the method.  Step sizes of the gradient steps (the paper's
+ * are in its supplement; these are the library's reading):
+ *   depth      beta_t = t_step / (g r + eps_r), step clamped to +-dt_max,
+ *              t clamped to [0, T-1]; t_step = eta / I_h with I_h the IRF's
+ *              location Fisher information sum h'^2/h is a scaled Fisher step
+ *   intensity  r <- max(0, r - r_step (r + eps_r)(H - sum z h / lambda))
+ *              (r_step = 1, eps_r = 0: the EM update r <- r sum z h/lambda / H)
+ *   background b <- max(b_floor, b - b_step (b + eps_b)(1 - sum z / lambda / T))
+ * with lambda floored at lam_floor. */
+typedef struct {
+    int32_t n_iter;                /* PALM iterations, >= 0 */
+    int32_t k_max;                 /* slots used, 1..config.k_max */
+    float t_step, r_step, b_step, dt_max, eps_r, eps_b, b_floor, lam_floor;
+    float pixel_pitch;             /* world units (bins) per pixel, orthographic f */
+    float apss_radius;             /* APSS kernel radius h (bins, world units) */
+    int32_t win_r;                 /* denoiser pixel window half-width, 0..RT3D_MAX_WIN_R */
+    int32_t apss_min_nb;           /* fewer weighted neighbours: depth left unchanged */
+    float int_radius;              /* intensity low-pass radius (bins, world units) */
+    float r_min;                   /* pruning threshold on intensity, > 0 */
+    float merge_dist;              /* same-pixel points closer than this (bins) merge, >= 0 */
+    int32_t depth_denoiser;        /* RT3D_DEPTH_* */
+    int32_t intensity_denoiser;    /* 0 = off (pruning still applies), 1 = low-pass */
+    int32_t bkg_mode;              /* RT3D_BKG_* */
+    float bkg_sigma;               /* background Gaussian sigma, pixels */
+    int32_t bkg_radius;            /* background kernel half-width, 0..RT3D_MAX_BKG_R */
+    float lmf_delta_rel;           /* matched-filter floor delta / max h */
+    int32_t lmf_frac_bits;         /* matched-filter fixed-point fraction bits, 0..12 */
+    int32_t peak_min_photons;      /* counts required in a peak's IRF window, 0..255 */
+    int32_t peak_sep;              /* local-maximum half-width, bins, >= 0 */
+    int32_t lmf_precision;         /* RT3D_LMF_* */
+    int32_t warm_start;            /* 1: start from the points already in the result */
+} rt3d_params;
+
+/* Output (and, with warm_start, input) point cloud: DEVICE buffers owned by
+ * the caller.  t, r, alive: [params.k_max][h][w]; b: [h][w]; n_points: one
+ * int32 (number of alive points) or NULL. */
+typedef struct {
+    float* t;
+    float* r;
+    uint8_t* alive;
+    float* b;
+    int32_t* n_points;
+} rt3d_result;
+
+/* Synthetic scene for rt3d_synthesize (test and benchmark input).  DEVICE
+ * pointers; S = n_comp surfaces, P = h*w:
+ *   depth_int [S][P] int32, depth_split [S][P] uint32 (photon lands one bin
+ *   later when a uniform word is below it), n_parts/p0/mu [S+1][P] (the last
+ *   plane is the background; fixed-point Poisson parameters, see below),
+ *   irf_cdf [irf_len-1] uint32 offset thresholds. */
+typedef struct {
+    int32_t h, w, t, n_comp;
+    const int32_t* depth_int;
+    const uint32_t* depth_split;
+    const uint32_t* n_parts;
+    const uint64_t* p0;
+    const uint64_t* mu;
+    const uint32_t* irf_cdf;
+    int32_t irf_len, irf_origin;
+} rt3d_scene;
+
+/* Human-readable name of a status code (static string). */
+const char* rt3d_status_str(int status);
+int rt3d_version(void);
+
+/* Fill `p` with the library defaults (n_iter 20, K 2, 7x7 window, ...). */
+rt3d_status rt3d_default_params(rt3d_params* p);
+
+/* Host-only validation of a frame and parameters against a configuration.
+ * Touches no device; frame pointers are only checked for NULL-ness. */
+rt3d_status rt3d_validate(const rt3d_config* cfg, const rt3d_frame* f, const rt3d_params* p);
+
+/* Create a context on cfg->device: copies the IRF, allocates the workspace
+ * (sparse-entry buffer, half-step state, counters).  *out is NULL on error. */
+rt3d_status rt3d_create(const rt3d_config* cfg, const rt3d_irf* irf, rt3d_ctx_t** out);
+void rt3d_destroy(rt3d_ctx_t* ctx);
+
+/* Photon synthesis (test/benchmark input, not the method): Poisson counts of
+ * the observation model drawn with Philox4x32-10 (Salmon et al., SC'11),
+ * key = seed, counters (pixel, component, part, 1) for a count and
+ * (pixel, component, photon, 2) for a photon; background is component 255.
+ * Counts: each of n_parts parts by fixed-point inversion from p0 = exp(-mu)
+ * 2^62 and mu 2^32.  Writes dense [h][w][t] (device).  Integer-only on the
+ * device, so the result is bit-reproducible on any implementation. */
+rt3d_status rt3d_synthesize(rt3d_ctx_t* ctx, const rt3d_scene* scene, uint64_t seed,
+                            uint16_t* dense, void* stream);
+
+/* Dense histogram -> sparse list (nonzero bins per pixel, increasing), the
+ * representation whose cost is linear in active bins (Methods, Fig. 5).
+ * csr_off [h*w+1] and csr_ent [capacity] are device outputs; *nnz_host gets
+ * the total (the call synchronises on `stream` to return it).  Returns
+ * RT3D_E_CAPACITY (and writes nothing past `capacity`) if it does not fit. */
+rt3d_status rt3d_compact(rt3d_ctx_t* ctx, const rt3d_frame* f, uint32_t* csr_off,
+                         uint32_t* csr_ent, int64_t capacity, int64_t* nnz_host,
+                         void* stream);
+
+/* Log-matched filter output of the initialisation kernel, for inspection:
+ * y[h][w][t] int32 = sum_s z(tau + s - origin) K_s with the quantised
+ * log-IRF K_s = round(2^f log1p(h_s / (delta_rel max h))).  Needs `dense`. */
+rt3d_status rt3d_lmf(rt3d_ctx_t* ctx, const rt3d_frame* f, const rt3d_params* p,
+                     int32_t* y, void* stream);
+
+/* Initialisation only (matched filter, peaks, initial t, r, alive, b). */
+rt3d_status rt3d_init(rt3d_ctx_t* ctx, const rt3d_frame* f, const rt3d_params* p,
+                      rt3d_result* out, void* stream);
+
+/* The whole method on one frame: initialisation (or warm start) then
+ * params.n_iter PALM iterations.  Results land in `out`. */
+rt3d_status rt3d_reconstruct(rt3d_ctx_t* ctx, const rt3d_frame* f, const rt3d_params* p,
+                             rt3d_result* out, void* stream);
+
+/* n frames (any mix of sizes within the configuration) in one set of
+ * launches; frame i's results land in out[i].  Each frame's result is
+ * bitwise identical to reconstructing it alone. */
+rt3d_status rt3d_reconstruct_batch(rt3d_ctx_t* ctx, int n, const rt3d_frame* f,
+                                   const rt3d_params* p, rt3d_result* out, void* stream);
+
+/* End-to-end form with HOST buffers: copies the frame's arrays (HOST
+ * pointers in `f`) to the device, reconstructs, and copies the results back
+ * into HOST buffers `out` (n_points may be NULL).  Synchronous: returns after
+ * the results are on the host.  Uses the context's staging buffers. */
+rt3d_status rt3d_reconstruct_host(rt3d_ctx_t* ctx, const rt3d_frame* f, const rt3d_params* p,
+                                  rt3d_result* out, void* stream);
+
+/* One fused phase of iteration k, for testing the loop kernels in isolation.
+ * state holds t, r, alive, b (device, as rt3d_result); the frame's sparse list
+ * (csr_off/csr_ent) is required.  phase:
+ *   0 (A): [b <- background denoiser(b), unless `first`] then the depth
+ *          gradient step: t <- t - beta_t dg/dt
+ *   1 (B): APSS on t, then the intensity gradient step with the new t
+ *   2 (C): intensity low-pass + pruning, then the background gradient step
+ *          (b receives the step's output, before its denoiser)
+ * All three update `state` in place. */
+rt3d_status rt3d_phase(rt3d_ctx_t* ctx, int phase, int first, const rt3d_frame* f,
+                       const rt3d_params* p, rt3d_result* state, void* stream);
+
+/* Synchronise `stream`, then return and clear the device-side status word
+ * (RT3D_OK, RT3D_E_CAPACITY or RT3D_E_RANGE). */
+rt3d_status rt3d_device_status(rt3d_ctx_t* ctx, void* stream);
+
+/* Kernel launches made by this context since creation (all entry points). */
+int64_t rt3d_launch_count(rt3d_ctx_t* ctx);
+
+/* Per-kernel timing with CUDA events recorded on the launch stream around
+ * each launch (off by default).  rt3d_kernel_times synchronises and returns,
+ * for kernel class i (0 init, 1 phase A, 2 phase B, 3 phase C, 4 final,
+ * 5 synthesize), the accumulated milliseconds and launch count since the last
+ * reset. */
+rt3d_status rt3d_set_profiling(rt3d_ctx_t* ctx, int on);
+rt3d_status rt3d_kernel_times(rt3d_ctx_t* ctx, double* ms, int64_t* launches, int n, int reset);
+
+/* Copy the sparse representation built by the last initialisation out to
+ * HOST buffers, for inspection: seg[p] = (start, count) per pixel of the
+ * batch (in frame order) and ent[0..n_ent).  Synchronises `stream`. */
+rt3d_status rt3d_get_sparse(rt3d_ctx_t* ctx, uint32_t* seg_host, int64_t n_pix,
+                            uint32_t* ent_host, int64_t n_ent, int64_t* n_ent_used,
+                            void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

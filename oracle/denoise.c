@@ -135,8 +135,13 @@ void or_apss(int h, int w, int t, const or_params* prm, or_state* s)
  * intensities of the alive points of its (2R+1)^2 pixel window that lie on the
  * same surface patch, w = (1 - d^2/h_r^2)^4 for the world distance d < h_r
  * (itself included, w = 1) -- a nearest-neighbour low-pass in the manifold
- * metric.  Then points whose intensity is below r_min are removed; that
- * decision is taken in single precision, like the kernel. */
+ * metric.  Then points whose intensity is below r_min are removed (Results,
+ * "Intensity update"); that decision is taken in single precision, like the
+ * kernel.  Finally two surviving points of one pixel closer in depth than
+ * merge_dist describe one surface: scanning slot pairs (a, c), a < c, in
+ * order, the one with the smaller intensity (c on a tie) is removed and its
+ * intensity added to the other (reading: keeps one point per surface and
+ * pixel, which the likelihood alone cannot separate). */
 void or_int_lowpass(int h, int w, const or_params* prm, or_state* s)
 {
     const int64_t npix = (int64_t)h * w;
@@ -180,6 +185,16 @@ void or_int_lowpass(int h, int w, const or_params* prm, or_state* s)
             s->r[n] = rbar;
             s->alive[n] = ((float)rbar >= (float)prm->r_min) ? 1 : 0;
         }
+        for (int a = 0; a < K; ++a)
+            for (int c = a + 1; c < K; ++c) {
+                const int64_t na = (int64_t)a * npix + p, nc = (int64_t)c * npix + p;
+                if (!s->alive[na] || !s->alive[nc]) continue;
+                if (!((float)fabs(s->t[na] - s->t[nc]) < (float)prm->merge_dist)) continue;
+                const int64_t keep = s->r[nc] > s->r[na] ? nc : na;
+                const int64_t drop = keep == na ? nc : na;
+                s->r[keep] += s->r[drop];
+                s->alive[drop] = 0;
+            }
     }
     free(rsrc);
     free(asrc);

@@ -156,8 +156,11 @@ static double clampd(double v, double lo, double hi)
 
 /* Depth update, gradient part (Results, "Reconstruction algorithm", depth
  * update).  All points of a pixel move together from the same lambda.
- * Step (reading; the paper's step sizes are in its supplement):
- *   beta_t = t_step / (g r_n + eps_r)  (a Fisher-information scaling),
+ * Step (reading; the paper's step sizes are in its supplement): a scaled
+ * Fisher-scoring step.  The expected information of a depth is about
+ * g r_n I_h, I_h = sum h'^2/h the IRF's location information, so with
+ * t_step = eta / I_h
+ *   beta_t = t_step / (g r_n + eps_r),
  *   t_n <- clamp(t_n - clamp(beta_t dg/dt_n, +-dt_max), 0, T-1). */
 void or_t_step(const or_frame* f, const or_irf* irf, const or_params* prm, or_state* s)
 {
@@ -184,7 +187,9 @@ void or_t_step(const or_frame* f, const or_irf* irf, const or_params* prm, or_st
 }
 
 /* Intensity update, gradient part.  Step (reading): beta_r = r_step (r_n + eps_r)/g,
- *   r_n <- max(0, r_n - r_step (r_n + eps_r)(H_n - sum z h / lambda)). */
+ *   r_n <- max(0, r_n - r_step (r_n + eps_r)(H_n - sum z h / lambda));
+ * with r_step = 1 and eps_r = 0 this is the EM (Richardson-Lucy) update
+ * r <- r sum z h / lambda / H, so the step is a damped EM step. */
 void or_r_step(const or_frame* f, const or_irf* irf, const or_params* prm, or_state* s)
 {
     const int64_t npix = (int64_t)f->h * f->w;
@@ -208,7 +213,8 @@ void or_r_step(const or_frame* f, const or_irf* irf, const or_params* prm, or_st
 }
 
 /* Background update, gradient part.  Step (reading): beta_b = b_step (b + eps_b)/(g T),
- *   b <- max(b_floor, b - b_step (b + eps_b)(1 - sum z/lambda / T)). */
+ *   b <- max(b_floor, b - b_step (b + eps_b)(1 - sum z/lambda / T)),
+ * likewise a damped EM step for the background. */
 void or_b_step(const or_frame* f, const or_irf* irf, const or_params* prm, or_state* s)
 {
     const int64_t npix = (int64_t)f->h * f->w;

@@ -61,7 +61,7 @@ class Params(C.Structure):
                 ("b_floor", C.c_double), ("lam_floor", C.c_double),
                 ("pixel_pitch", C.c_double), ("apss_radius", C.c_double),
                 ("win_r", C.c_int), ("apss_min_nb", C.c_int),
-                ("int_radius", C.c_double), ("r_min", C.c_double),
+                ("int_radius", C.c_double), ("r_min", C.c_double), ("merge_dist", C.c_double),
                 ("depth_denoiser", C.c_int), ("intensity_denoiser", C.c_int),
                 ("bkg_mode", C.c_int), ("bkg_sigma", C.c_double), ("bkg_radius", C.c_int),
                 ("lmf_delta_rel", C.c_double), ("lmf_frac_bits", C.c_int),

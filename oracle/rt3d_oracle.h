@@ -62,7 +62,7 @@ typedef struct {
     double t_step, r_step, b_step, dt_max, eps_r, eps_b, b_floor, lam_floor;
     double pixel_pitch, apss_radius;
     int win_r, apss_min_nb;
-    double int_radius, r_min;
+    double int_radius, r_min, merge_dist;
     int depth_denoiser, intensity_denoiser, bkg_mode;
     double bkg_sigma;
     int bkg_radius;

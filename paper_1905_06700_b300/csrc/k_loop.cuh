@@ -1,0 +1,511 @@
+// k_loop.cuh -- the PALM iteration (Results, "Reconstruction algorithm",
+// Fig. 2) as three fused kernels per iteration plus a finaliser.
+//
+// Each neighbourhood step (APSS, intensity low-pass, background low-pass)
+// needs the preceding per-pixel step finished on its halo, so the per-pixel
+// gradient steps ride at the tail (or head) of the neighbourhood kernels:
+//   A: [b <- background denoiser(b_half); alive <- alive_b]  + depth step
+//   B: APSS(t_half)                                           + intensity step
+//   C: intensity low-pass + pruning                           + background step
+// A CTA owns an 8 x 16 pixel tile of one frame.  Neighbourhood work runs one
+// thread per pixel over a shared-memory copy of the tile and its halo; the
+// per-pixel gradient steps run one 8-lane group per pixel, lanes striding over
+// the pixel's nonzero bins (cost linear in active bins, Methods and Fig. 5).
+#pragma once
+#include "rt3d_device.cuh"
+
+namespace rt3d {
+
+constexpr int kG = 8;                             // lanes per pixel in gradient steps
+constexpr int kGroups = kTileThreads / kG;        // 16 groups per CTA
+
+struct TileCtx {
+    int fi, i0, j0, li, lj, gi, gj;
+    bool inb;
+};
+
+__device__ __forceinline__ TileCtx tile_ctx(const Batch& B)
+{
+    TileCtx c;
+    c.fi = frame_of_tile(B, blockIdx.x);
+    const FrameDesc& F = B.f[c.fi];
+    const int lt = blockIdx.x - F.tile_base;
+    c.i0 = (lt / F.tiles_w) * kTileH;
+    c.j0 = (lt % F.tiles_w) * kTileW;
+    c.li = threadIdx.x / kTileW;
+    c.lj = threadIdx.x % kTileW;
+    c.gi = c.i0 + c.li;
+    c.gj = c.j0 + c.lj;
+    c.inb = c.gi < F.h && c.gj < F.w;
+    return c;
+}
+
+__device__ __forceinline__ void load_irf(float* pad, const KParams& P)
+{
+    for (int i = threadIdx.x; i < P.irf_len + 2 * kIrfPad; i += blockDim.x) {
+        const int k = i - kIrfPad;
+        pad[i] = (k >= 0 && k < P.irf_len) ? P.irf[k] : 0.0f;
+    }
+}
+
+// Sums over the nonzero bins of one pixel, one 8-lane group:
+//   sh[k] = sum z h(t - t_k)/lambda, sdh[k] = sum z h'(t - t_k)/lambda,
+//   sz = sum z/lambda, lambda = max(g (sum_alive r_k h(t - t_k) + b), lam_floor).
+__device__ __forceinline__ void pixel_sums(const uint32_t* ent, uint2 sg, int gl, unsigned gmask,
+                                           const float* pad, const KParams& P,
+                                           const float* tk, const float* rk, const bool* ak,
+                                           float b, float g, float* sh, float* sdh, float& sz)
+{
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) { sh[k] = 0.0f; sdh[k] = 0.0f; }
+    sz = 0.0f;
+    for (uint32_t e = gl; e < sg.y; e += kG) {
+        const uint32_t v = ent[sg.x + e];
+        const float tb = (float)(v >> 16), z = (float)(v & 0xffffu);
+        float hv[kMaxK], dv[kMaxK];
+        float acc = b;
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k) {
+            hv[k] = 0.0f;
+            dv[k] = 0.0f;
+            if (k < P.k && ak[k]) {
+                irf_eval(pad, P.irf_len, P.irf_origin, tb - tk[k], hv[k], dv[k]);
+                acc += rk[k] * hv[k];
+            }
+        }
+        const float lam = fmaxf(g * acc, P.lam_floor);
+        const float inv = z / lam;
+        sz += inv;
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k) {
+            sh[k] += hv[k] * inv;
+            sdh[k] += dv[k] * inv;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) {
+        sh[k] = group_sum<kG>(sh[k], gmask);
+        sdh[k] = group_sum<kG>(sdh[k], gmask);
+    }
+    sz = group_sum<kG>(sz, gmask);
+}
+
+// Background denoiser at pixel (i, j): periodic separable Gaussian over the
+// frame (equal to the FFT low-pass with the kernel's DFT), or identity.
+__device__ __forceinline__ float bkg_filter(const KParams& P, const float* bh, int h, int w,
+                                            int i, int j)
+{
+    if (P.bkg_mode != RT3D_BKG_LOWPASS) return bh[i * w + j];
+    const int R = P.bkg_rad;
+    float acc = 0.0f;
+    for (int di = -R; di <= R; ++di) {
+        int ii = (i + di) % h;
+        if (ii < 0) ii += h;
+        float row = 0.0f;
+        for (int dj = -R; dj <= R; ++dj) {
+            int jj = (j + dj) % w;
+            if (jj < 0) jj += w;
+            row += P.bkg_ker[dj + R] * bh[ii * w + jj];
+        }
+        acc += P.bkg_ker[di + R] * row;
+    }
+    return acc;
+}
+
+// ----------------------------------------------------------------------------
+// Phase A: background denoiser of the previous iteration + depth gradient step.
+__global__ void __launch_bounds__(kTileThreads)
+k_phase_a(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const Work W, int first)
+{
+    __shared__ float pad[kMaxIrf + 2 * kIrfPad];
+    __shared__ float s_t[kMaxK][kTileThreads], s_r[kMaxK][kTileThreads];
+    __shared__ uint8_t s_a[kMaxK][kTileThreads];
+    __shared__ float s_b[kTileThreads], s_g[kTileThreads];
+    load_irf(pad, P);
+    const TileCtx c = tile_ctx(B);
+    const FrameDesc& F = B.f[c.fi];
+    const int np = F.npix, S = W.stride;
+    const int lp = c.gi * F.w + c.gj, wp = F.pix_base + lp;
+    if (c.inb) {
+        float b;
+        if (first) {
+            b = F.b[lp];
+        } else {
+            b = bkg_filter(P, W.b_half + F.pix_base, F.h, F.w, c.gi, c.gj);
+            F.b[lp] = b;
+        }
+        s_b[threadIdx.x] = b;
+        s_g[threadIdx.x] = F.gain ? F.gain[lp] : 1.0f;
+        for (int k = 0; k < P.k; ++k) {
+            uint8_t a;
+            if (first) {
+                a = F.alive[(long long)k * np + lp];
+            } else {
+                a = W.alive_b[(long long)k * S + wp];
+                F.alive[(long long)k * np + lp] = a;
+            }
+            s_a[k][threadIdx.x] = a;
+            s_t[k][threadIdx.x] = F.t[(long long)k * np + lp];
+            s_r[k][threadIdx.x] = F.r[(long long)k * np + lp];
+        }
+    }
+    __syncthreads();
+
+    const int grp = threadIdx.x / kG, gl = threadIdx.x % kG;
+    const unsigned gmask = 0xffu << ((threadIdx.x & 31) & ~(kG - 1));
+    for (int q = grp; q < kTileThreads; q += kGroups) {
+        const int qi = c.i0 + q / kTileW, qj = c.j0 + q % kTileW;
+        if (qi >= F.h || qj >= F.w) continue;
+        const int qlp = qi * F.w + qj, qwp = F.pix_base + qlp;
+        float tk[kMaxK], rk[kMaxK];
+        bool ak[kMaxK];
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k) {
+            const bool in = k < P.k;
+            tk[k] = in ? s_t[k][q] : 0.0f;
+            rk[k] = in ? s_r[k][q] : 0.0f;
+            ak[k] = in && s_a[k][q];
+        }
+        const float g = s_g[q];
+        float sh[kMaxK], sdh[kMaxK], sz;
+        pixel_sums(F.ent, W.seg[qwp], gl, gmask, pad, P, tk, rk, ak, s_b[q], g, sh, sdh, sz);
+        if (gl < P.k) {
+            const int k = gl;
+            float tn = 0.0f;
+#pragma unroll
+            for (int m = 0; m < kMaxK; ++m)
+                if (m == k) {
+                    tn = tk[m];
+                    if (ak[m] && g > 0.0f) {
+                        float H, dH;
+                        support_sums(pad, P, F.nt, tk[m], H, dH);
+                        const float grad = g * rk[m] * (-dH + sdh[m]);
+                        const float beta = P.t_step / (g * rk[m] + P.eps_r);
+                        const float step = clampf(-beta * grad, -P.dt_max, P.dt_max);
+                        tn = clampf(tk[m] + step, 0.0f, (float)(F.nt - 1));
+                    }
+                }
+            W.t_half[(long long)k * S + qwp] = tn;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// APSS projection of one point (Results, "Depth update"; Guennebaud & Gross):
+// weighted algebraic-sphere fit s(x) = u0 + u1 x + u2 y + z + u4 |x|^2 over
+// the window (local coordinates scaled by 1/h), solved in centred form --
+// the 3x3 normal equations of (x, y, |x|^2) against z, then u0 from the
+// weighted means -- and projection along the line of sight onto s = 0.
+template <int HW>
+__device__ float apss_point(const float* st, const uint8_t* sa, int hstride, int R, int K,
+                            int ci, int cj, float tn, const KParams& P, int T)
+{
+    const float inv_h = 1.0f / P.apss_h;
+    const float px = P.pitch * inv_h;
+    float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sz = 0.f, Sq = 0.f;
+    float Sxx = 0.f, Sxy = 0.f, Syy = 0.f, Sxq = 0.f, Syq = 0.f, Sqq = 0.f;
+    float Sxz = 0.f, Syz = 0.f, Sqz = 0.f;
+    int nw = 0, si = 0, sj = 0, sii = 0, sjj = 0, sij = 0;
+    for (int di = -R; di <= R; ++di) {
+        const float y = (float)di * px;
+        for (int dj = -R; dj <= R; ++dj) {
+            const float x = (float)dj * px;
+            const float r2 = x * x + y * y;
+            const int q = (ci + di) * hstride + (cj + dj);
+            for (int m = 0; m < K; ++m) {
+                if (!sa[m * HW + q]) continue;
+                const float z = (st[m * HW + q] - tn) * inv_h;
+                const float d2 = r2 + z * z;
+                if (!(d2 < 1.0f)) continue;
+                float w = 1.0f - d2;
+                w *= w;
+                w *= w;
+                const float wx = w * x, wy = w * y, wq = w * d2;
+                S0 += w; Sx += wx; Sy += wy; Sz += w * z; Sq += wq;
+                Sxx += wx * x; Sxy += wx * y; Syy += wy * y;
+                Sxq += wx * d2; Syq += wy * d2; Sqq += wq * d2;
+                Sxz += wx * z; Syz += wy * z; Sqz += wq * z;
+                ++nw; si += di; sj += dj; sii += di * di; sjj += dj * dj; sij += di * dj;
+            }
+        }
+    }
+    if (nw < P.apss_min_nb) return tn;
+    const long long vii = (long long)nw * sii - (long long)si * si;
+    const long long vjj = (long long)nw * sjj - (long long)sj * sj;
+    const long long vij = (long long)nw * sij - (long long)si * sj;
+    if (vii * vjj - vij * vij == 0) return tn;      // collinear pixel offsets
+    const float iw = 1.0f / S0;
+    const float mx = Sx * iw, my = Sy * iw, mz = Sz * iw, mq = Sq * iw;
+    const float cxx = Sxx * iw - mx * mx, cxy = Sxy * iw - mx * my, cyy = Syy * iw - my * my;
+    const float cxq = Sxq * iw - mx * mq, cyq = Syq * iw - my * mq, cqq = Sqq * iw - mq * mq;
+    const float dx = Sxz * iw - mx * mz, dy = Syz * iw - my * mz, dq = Sqz * iw - mq * mz;
+    // Cholesky of the 3x3 covariance
+    if (!(cxx > 0.0f)) return tn;
+    const float l11 = sqrtf(cxx);
+    const float l21 = cxy / l11, l31 = cxq / l11;
+    const float d22 = cyy - l21 * l21;
+    if (!(d22 > 0.0f)) return tn;
+    const float l22 = sqrtf(d22);
+    const float l32 = (cyq - l31 * l21) / l22;
+    const float d33 = cqq - l31 * l31 - l32 * l32;
+    if (!(d33 > 0.0f)) return tn;
+    const float l33 = sqrtf(d33);
+    const float y1 = -dx / l11;
+    const float y2 = (-dy - l21 * y1) / l22;
+    const float y3 = (-dq - l31 * y1 - l32 * y2) / l33;
+    const float u4 = y3 / l33;
+    const float u2 = (y2 - l32 * u4) / l22;
+    const float u1 = (y1 - l21 * u2 - l31 * u4) / l11;
+    const float u0 = -mz - u1 * mx - u2 * my - u4 * mq;
+    const float disc = 1.0f - 4.0f * u0 * u4;
+    float zs = -2.0f * u0 / (1.0f + sqrtf(fmaxf(disc, 0.0f)));
+    zs = clampf(zs, -1.0f, 1.0f);
+    return clampf(tn + P.apss_h * zs, 0.0f, (float)(T - 1));
+}
+
+constexpr int kHaloH = kTileH + 2 * kMaxWinR, kHaloW = kTileW + 2 * kMaxWinR;
+constexpr int kHalo = kHaloH * kHaloW;
+
+// Load a [k] plane set of float/alive values for the tile plus halo R.
+__device__ __forceinline__ void load_halo(const TileCtx& c, const FrameDesc& F, int R, int K,
+                                          const float* src, long long src_stride, int src_off,
+                                          const uint8_t* asrc, long long a_stride, int a_off,
+                                          float* st, uint8_t* sa)
+{
+    const int hh = kTileH + 2 * R, hw = kTileW + 2 * R;
+    for (int idx = threadIdx.x; idx < hh * hw; idx += blockDim.x) {
+        const int hi = idx / hw, hj = idx % hw;
+        const int gi = c.i0 - R + hi, gj = c.j0 - R + hj;
+        const int q = hi * (kTileW + 2 * R) + hj;
+        const bool in = gi >= 0 && gi < F.h && gj >= 0 && gj < F.w;
+        const int lp = in ? gi * F.w + gj : 0;
+        for (int m = 0; m < K; ++m) {
+            uint8_t a = 0;
+            float v = 0.0f;
+            if (in) {
+                a = asrc[(long long)m * a_stride + a_off + lp];
+                v = src[(long long)m * src_stride + src_off + lp];
+            }
+            sa[m * kHalo + q] = a;
+            st[m * kHalo + q] = v;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Phase B: APSS depth denoiser + intensity gradient step.
+__global__ void __launch_bounds__(kTileThreads)
+k_phase_b(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const Work W)
+{
+    __shared__ float pad[kMaxIrf + 2 * kIrfPad];
+    __shared__ float st[kMaxK * kHalo];
+    __shared__ uint8_t sa[kMaxK * kHalo];
+    __shared__ float s_tn[kMaxK][kTileThreads];
+    load_irf(pad, P);
+    const TileCtx c = tile_ctx(B);
+    const FrameDesc& F = B.f[c.fi];
+    const int np = F.npix, S = W.stride, R = P.win_r, K = P.k;
+    load_halo(c, F, R, K, W.t_half, S, F.pix_base, F.alive, np, 0, st, sa);
+    __syncthreads();
+    const int hstride = kTileW + 2 * R;
+    if (c.inb) {
+        const int lp = c.gi * F.w + c.gj;
+        const int ci = c.li + R, cj = c.lj + R;
+        for (int k = 0; k < K; ++k) {
+            const int q = ci * hstride + cj;
+            float tn = st[k * kHalo + q];
+            if (sa[k * kHalo + q] && P.depth_den == RT3D_DEPTH_APSS)
+                tn = apss_point<kHalo>(st, sa, hstride, R, K, ci, cj, tn, P, F.nt);
+            s_tn[k][threadIdx.x] = tn;
+            F.t[(long long)k * np + lp] = tn;
+        }
+    }
+    __syncthreads();
+
+    const int grp = threadIdx.x / kG, gl = threadIdx.x % kG;
+    const unsigned gmask = 0xffu << ((threadIdx.x & 31) & ~(kG - 1));
+    for (int q = grp; q < kTileThreads; q += kGroups) {
+        const int qi = c.i0 + q / kTileW, qj = c.j0 + q % kTileW;
+        if (qi >= F.h || qj >= F.w) continue;
+        const int qlp = qi * F.w + qj, qwp = F.pix_base + qlp;
+        const int hq = (q / kTileW + R) * hstride + (q % kTileW + R);
+        float tk[kMaxK], rk[kMaxK];
+        bool ak[kMaxK];
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k) {
+            const bool in = k < K;
+            tk[k] = in ? s_tn[k][q] : 0.0f;
+            rk[k] = in ? F.r[(long long)k * np + qlp] : 0.0f;
+            ak[k] = in && sa[k * kHalo + hq];
+        }
+        const float g = F.gain ? F.gain[qlp] : 1.0f;
+        float sh[kMaxK], sdh[kMaxK], sz;
+        pixel_sums(F.ent, W.seg[qwp], gl, gmask, pad, P, tk, rk, ak, F.b[qlp], g, sh, sdh, sz);
+        if (gl < K) {
+            const int k = gl;
+            float rn = 0.0f;
+#pragma unroll
+            for (int m = 0; m < kMaxK; ++m)
+                if (m == k) {
+                    rn = rk[m];
+                    if (ak[m] && g > 0.0f) {
+                        float H, dH;
+                        support_sums(pad, P, F.nt, tk[m], H, dH);
+                        rn = fmaxf(rk[m] - P.r_step * (rk[m] + P.eps_r) * (H - sh[m]), 0.0f);
+                    }
+                }
+            W.r_half[(long long)k * S + qwp] = rn;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Phase C: intensity low-pass on the surface + pruning + background gradient step.
+__global__ void __launch_bounds__(kTileThreads)
+k_phase_c(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const Work W)
+{
+    __shared__ float pad[kMaxIrf + 2 * kIrfPad];
+    __shared__ float st[kMaxK * kHalo];
+    __shared__ float sr[kMaxK * kHalo];
+    __shared__ uint8_t sa[kMaxK * kHalo];
+    __shared__ float s_rn[kMaxK][kTileThreads];
+    __shared__ uint8_t s_an[kMaxK][kTileThreads];
+    load_irf(pad, P);
+    const TileCtx c = tile_ctx(B);
+    const FrameDesc& F = B.f[c.fi];
+    const int np = F.npix, S = W.stride, R = P.win_r, K = P.k;
+    load_halo(c, F, R, K, F.t, np, 0, F.alive, np, 0, st, sa);
+    {
+        // r_half for the same halo (alive already loaded)
+        const int hh = kTileH + 2 * R, hw = kTileW + 2 * R;
+        for (int idx = threadIdx.x; idx < hh * hw; idx += blockDim.x) {
+            const int hi = idx / hw, hj = idx % hw;
+            const int gi = c.i0 - R + hi, gj = c.j0 - R + hj;
+            const bool in = gi >= 0 && gi < F.h && gj >= 0 && gj < F.w;
+            const int lp = in ? gi * F.w + gj : 0;
+            for (int m = 0; m < K; ++m)
+                sr[m * kHalo + idx] = in ? W.r_half[(long long)m * S + F.pix_base + lp] : 0.0f;
+        }
+    }
+    __syncthreads();
+    const int hstride = kTileW + 2 * R;
+    if (c.inb) {
+        const int lp = c.gi * F.w + c.gj, wp = F.pix_base + lp;
+        const int ci = c.li + R, cj = c.lj + R, q0 = ci * hstride + cj;
+        const float inv_h = 1.0f / P.int_h, px = P.pitch * inv_h;
+        for (int k = 0; k < K; ++k) {
+            uint8_t an = 0;
+            float rn = F.r[(long long)k * np + lp];
+            if (sa[k * kHalo + q0]) {
+                float rbar = sr[k * kHalo + q0];
+                if (P.int_den) {
+                    const float tn = st[k * kHalo + q0];
+                    float num = 0.0f, den = 0.0f;
+                    for (int di = -R; di <= R; ++di) {
+                        const float y = (float)di * px;
+                        for (int dj = -R; dj <= R; ++dj) {
+                            const float x = (float)dj * px;
+                            const int q = (ci + di) * hstride + (cj + dj);
+                            for (int m = 0; m < K; ++m) {
+                                if (!sa[m * kHalo + q]) continue;
+                                const float z = (st[m * kHalo + q] - tn) * inv_h;
+                                const float d2 = x * x + y * y + z * z;
+                                if (!(d2 < 1.0f)) continue;
+                                float w = 1.0f - d2;
+                                w *= w;
+                                w *= w;
+                                num += w * sr[m * kHalo + q];
+                                den += w;
+                            }
+                        }
+                    }
+                    rbar = num / den;
+                }
+                rn = rbar;
+                an = rbar >= P.r_min ? 1 : 0;
+            }
+            s_rn[k][threadIdx.x] = rn;
+            s_an[k][threadIdx.x] = an;
+        }
+        // same-pixel points closer than merge_dist are one surface: the weaker
+        // (the later slot on a tie) is removed and its intensity added to the other
+        for (int a = 0; a < K; ++a)
+            for (int b2 = a + 1; b2 < K; ++b2) {
+                if (!s_an[a][threadIdx.x] || !s_an[b2][threadIdx.x]) continue;
+                const float ta = st[a * kHalo + q0], tb = st[b2 * kHalo + q0];
+                if (!(fabsf(ta - tb) < P.merge_dist)) continue;
+                const int keep = s_rn[b2][threadIdx.x] > s_rn[a][threadIdx.x] ? b2 : a;
+                const int drop = keep == a ? b2 : a;
+                s_rn[keep][threadIdx.x] += s_rn[drop][threadIdx.x];
+                s_an[drop][threadIdx.x] = 0;
+            }
+        for (int k = 0; k < K; ++k) {
+            if (sa[k * kHalo + q0]) F.r[(long long)k * np + lp] = s_rn[k][threadIdx.x];
+            W.alive_b[(long long)k * S + wp] = s_an[k][threadIdx.x];
+        }
+    }
+    __syncthreads();
+
+    const int grp = threadIdx.x / kG, gl = threadIdx.x % kG;
+    const unsigned gmask = 0xffu << ((threadIdx.x & 31) & ~(kG - 1));
+    for (int q = grp; q < kTileThreads; q += kGroups) {
+        const int qi = c.i0 + q / kTileW, qj = c.j0 + q % kTileW;
+        if (qi >= F.h || qj >= F.w) continue;
+        const int qlp = qi * F.w + qj, qwp = F.pix_base + qlp;
+        const int hq = (q / kTileW + R) * hstride + (q % kTileW + R);
+        float tk[kMaxK], rk[kMaxK];
+        bool ak[kMaxK];
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k) {
+            const bool in = k < K;
+            tk[k] = in ? st[k * kHalo + hq] : 0.0f;
+            rk[k] = in ? s_rn[k][q] : 0.0f;
+            ak[k] = in && s_an[k][q];
+        }
+        const float g = F.gain ? F.gain[qlp] : 1.0f;
+        const float b = F.b[qlp];
+        float sh[kMaxK], sdh[kMaxK], sz;
+        pixel_sums(F.ent, W.seg[qwp], gl, gmask, pad, P, tk, rk, ak, b, g, sh, sdh, sz);
+        if (gl == 0) {
+            float bn = b;
+            if (g > 0.0f)
+                bn = fmaxf(b - P.b_step * (b + P.eps_b) * (1.0f - sz / (float)F.nt), P.b_floor);
+            W.b_half[qwp] = bn;
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------
+// Finaliser: the last iteration's pruning and background denoiser land in the
+// result buffers; alive points are counted per frame.
+__global__ void __launch_bounds__(kTileThreads)
+k_final(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const Work W, int ran)
+{
+    __shared__ int s_cnt;
+    if (threadIdx.x == 0) s_cnt = 0;
+    __syncthreads();
+    const TileCtx c = tile_ctx(B);
+    const FrameDesc& F = B.f[c.fi];
+    int mine = 0;
+    if (c.inb) {
+        const int lp = c.gi * F.w + c.gj, wp = F.pix_base + lp;
+        for (int k = 0; k < P.k; ++k) {
+            uint8_t a;
+            if (ran) {
+                a = W.alive_b[(long long)k * W.stride + wp];
+                F.alive[(long long)k * F.npix + lp] = a;
+            } else {
+                a = F.alive[(long long)k * F.npix + lp];
+            }
+            mine += a;
+        }
+        if (ran) F.b[lp] = bkg_filter(P, W.b_half + F.pix_base, F.h, F.w, c.gi, c.gj);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&s_cnt, mine);
+    __syncthreads();
+    if (threadIdx.x == 0 && s_cnt && F.n_points) atomicAdd(F.n_points, s_cnt);
+}
+
+}  // namespace rt3d

@@ -1,0 +1,816 @@
+// rt3d.cu -- host implementation of the C ABI declared in include/rt3d.h.
+//
+// The context owns one device workspace sized at creation; every call builds
+// the by-value kernel parameters (KParams: constants and tables derived from
+// the IRF; Batch: one descriptor per frame) and enqueues the kernels on the
+// caller's stream.  Nothing here computes any part of the method on the host
+// beyond the per-call tables (normalised IRF, quantised log-IRF, background
+// filter taps), which are O(IRF length) and identical for every pixel.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "rt3d.h"
+#include "rt3d_device.cuh"
+#include "k_synth.cuh"
+#include "k_init.cuh"
+#include "k_loop.cuh"
+#include "k_compact.cuh"
+
+using namespace rt3d;
+
+namespace {
+
+constexpr int kNumKernelClasses = 8;
+enum KernelClass { kcInit = 0, kcA = 1, kcB = 2, kcC = 3, kcFinal = 4, kcSynth = 5, kcCompact = 6, kcOther = 7 };
+
+struct PendingTiming {
+    int cls;
+    cudaEvent_t a, b;
+};
+
+}  // namespace
+
+struct rt3d_ctx {
+    rt3d_config cfg{};
+    std::vector<double> irf_norm;   // normalised in double, index order
+    int irf_len = 0, irf_origin = 0;
+    Work W{};
+    long long stride = 0;           // workspace pixels = max_batch * max_h * max_w
+    int* d_status = nullptr;
+    unsigned long long* d_count = nullptr;
+    uint32_t* d_tmp = nullptr;      // [stride + 1] scratch of rt3d_compact
+    long long launches = 0;
+    bool profiling = false;
+    std::vector<PendingTiming> pending;
+    std::vector<cudaEvent_t> event_pool;
+    double ms[kNumKernelClasses] = {0};
+    long long counts[kNumKernelClasses] = {0};
+    // staging of rt3d_reconstruct_host (allocated on first use)
+    uint16_t* s_dense = nullptr;
+    uint32_t* s_off = nullptr;
+    uint32_t* s_ent = nullptr;
+    long long s_ent_cap = 0;
+    float* s_gain = nullptr;
+    float* s_t = nullptr;
+    float* s_r = nullptr;
+    float* s_b = nullptr;
+    uint8_t* s_alive = nullptr;
+    int32_t* s_np = nullptr;
+};
+
+namespace {
+
+rt3d_status cuda_fail(cudaError_t e)
+{
+    return e == cudaErrorMemoryAllocation ? RT3D_E_NOMEM : RT3D_E_CUDA;
+}
+
+#define RT3D_CUDA(call)                                   \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_);      \
+    } while (0)
+
+cudaEvent_t take_event(rt3d_ctx* c)
+{
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Launch bookkeeping: counts every launch; with profiling on, brackets it with
+// events on the launch stream.
+struct LaunchScope {
+    rt3d_ctx* c;
+    cudaStream_t s;
+    int cls;
+    cudaEvent_t a = nullptr, b = nullptr;
+    LaunchScope(rt3d_ctx* c_, cudaStream_t s_, int cls_) : c(c_), s(s_), cls(cls_)
+    {
+        ++c->launches;
+        if (c->profiling) {
+            a = take_event(c);
+            b = take_event(c);
+            cudaEventRecord(a, s);
+        }
+    }
+    ~LaunchScope()
+    {
+        if (a) {
+            cudaEventRecord(b, s);
+            c->pending.push_back({cls, a, b});
+        }
+    }
+};
+
+bool frame_ok(const rt3d_config* cfg, const rt3d_frame* f)
+{
+    if (!f) return false;
+    if (f->h < 1 || f->w < 1 || f->t < 1) return false;
+    if (f->h > cfg->max_h || f->w > cfg->max_w || f->t > cfg->max_t) return false;
+    if (f->t > RT3D_MAX_T) return false;
+    const bool has_dense = f->dense != nullptr;
+    const bool has_csr = f->csr_off != nullptr && f->csr_ent != nullptr;
+    if (!has_dense && !has_csr) return false;
+    if ((f->csr_off == nullptr) != (f->csr_ent == nullptr)) return false;
+    return true;
+}
+
+bool params_ok(const rt3d_config* cfg, const rt3d_params* p)
+{
+    if (!p) return false;
+    if (p->n_iter < 0 || p->n_iter > 100000) return false;
+    if (p->k_max < 1 || p->k_max > cfg->k_max || p->k_max > RT3D_MAX_K) return false;
+    const float pos[] = {p->t_step, p->r_step, p->b_step, p->dt_max, p->pixel_pitch,
+                         p->apss_radius, p->int_radius, p->r_min, p->lam_floor};
+    for (float v : pos)
+        if (!(v > 0.0f) || !std::isfinite(v)) return false;
+    const float nonneg[] = {p->eps_r, p->eps_b, p->b_floor, p->lmf_delta_rel, p->merge_dist};
+    for (float v : nonneg)
+        if (!(v >= 0.0f) || !std::isfinite(v)) return false;
+    if (!(p->lmf_delta_rel > 0.0f)) return false;
+    if (p->win_r < 0 || p->win_r > RT3D_MAX_WIN_R) return false;
+    if (p->apss_min_nb < 0) return false;
+    if (p->depth_denoiser < 0 || p->depth_denoiser > 2) return false;
+    if (p->intensity_denoiser < 0 || p->intensity_denoiser > 1) return false;
+    if (p->bkg_mode < 0 || p->bkg_mode > 1) return false;
+    if (p->bkg_mode == RT3D_BKG_LOWPASS && !(p->bkg_sigma > 0.0f)) return false;
+    if (p->bkg_radius < 0 || p->bkg_radius > RT3D_MAX_BKG_R) return false;
+    if (p->lmf_frac_bits < 0 || p->lmf_frac_bits > 12) return false;
+    if (p->peak_min_photons < 0 || p->peak_min_photons > 255) return false;
+    if (p->peak_sep < 0 || p->peak_sep > RT3D_MAX_T) return false;
+    if (p->lmf_precision < 0 || p->lmf_precision > 2) return false;
+    if (p->warm_start < 0 || p->warm_start > 1) return false;
+    return true;
+}
+
+bool config_ok(const rt3d_config* cfg)
+{
+    if (!cfg) return false;
+    if (cfg->max_h < 1 || cfg->max_w < 1 || cfg->max_t < 1 || cfg->max_t > RT3D_MAX_T) return false;
+    if (cfg->k_max < 1 || cfg->k_max > RT3D_MAX_K) return false;
+    if (cfg->max_batch < 1 || cfg->max_batch > RT3D_MAX_BATCH) return false;
+    if (cfg->max_entries < 0) return false;
+    const long long pix = (long long)cfg->max_batch * cfg->max_h * cfg->max_w;
+    if (pix > (1ll << 30)) return false;
+    return cfg->device >= 0;
+}
+
+// Per-call tables derived from the IRF and the parameters.
+rt3d_status build_kparams(const rt3d_ctx* c, const rt3d_params* p, KParams* K)
+{
+    std::memset(K, 0, sizeof(KParams));
+    K->n_iter = p->n_iter;
+    K->k = p->k_max;
+    K->t_step = p->t_step;
+    K->r_step = p->r_step;
+    K->b_step = p->b_step;
+    K->dt_max = p->dt_max;
+    K->eps_r = p->eps_r;
+    K->eps_b = p->eps_b;
+    K->b_floor = p->b_floor;
+    K->lam_floor = p->lam_floor;
+    K->pitch = p->pixel_pitch;
+    K->apss_h = p->apss_radius;
+    K->int_h = p->int_radius;
+    K->r_min = p->r_min;
+    K->merge_dist = p->merge_dist;
+    K->win_r = p->win_r;
+    K->apss_min_nb = p->apss_min_nb;
+    K->depth_den = p->depth_denoiser;
+    K->int_den = p->intensity_denoiser;
+    K->bkg_mode = p->bkg_mode;
+    K->bkg_rad = p->bkg_radius;
+    K->irf_len = c->irf_len;
+    K->irf_origin = c->irf_origin;
+    K->peak_sep = p->peak_sep;
+    K->peak_min_photons = p->peak_min_photons;
+    float fsum = 0.0f;
+    double hmax = 0.0;
+    for (int s = 0; s < c->irf_len; ++s) {
+        K->irf[s] = (float)c->irf_norm[s];
+        fsum += K->irf[s];
+        if (c->irf_norm[s] > hmax) hmax = c->irf_norm[s];
+    }
+    K->irf_sum = fsum;
+    // quantised log-IRF: K_s = round(2^f log1p(h_s / (delta_rel max h)))
+    const double delta = (double)p->lmf_delta_rel * hmax;
+    const double scale = std::ldexp(1.0, p->lmf_frac_bits);
+    int kmax = 0;
+    for (int s = 0; s < c->irf_len; ++s) {
+        const double v = std::nearbyint(scale * std::log1p(c->irf_norm[s] / delta));
+        if (v > 1e9) return RT3D_E_INVALID;
+        K->lmf[s] = (int)v;
+        if (K->lmf[s] > kmax) kmax = K->lmf[s];
+    }
+    K->lmf_kmax = kmax;
+    if (p->lmf_precision == RT3D_LMF_BF16 && kmax > 256) return RT3D_E_INVALID;
+    if (p->lmf_precision == RT3D_LMF_FP16 && kmax > 2048) return RT3D_E_INVALID;
+    if (p->bkg_mode == RT3D_BKG_LOWPASS) {
+        const double sg = (double)p->bkg_sigma;
+        double ks = 0.0;
+        double tap[2 * kMaxBkgR + 1];
+        for (int d = -p->bkg_radius; d <= p->bkg_radius; ++d) {
+            tap[d + p->bkg_radius] = std::exp(-(double)d * d / (2.0 * sg * sg));
+            ks += tap[d + p->bkg_radius];
+        }
+        for (int d = 0; d <= 2 * p->bkg_radius; ++d) K->bkg_ker[d] = (float)(tap[d] / ks);
+    }
+    return RT3D_OK;
+}
+
+// Batch descriptors for n frames whose results go to out[i].
+rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_result* out,
+                        Batch* B)
+{
+    std::memset(B, 0, sizeof(Batch));
+    B->n = n;
+    int tiles = 0, pix = 0, tmax = 0;
+    for (int i = 0; i < n; ++i) {
+        FrameDesc& d = B->f[i];
+        d.h = f[i].h;
+        d.w = f[i].w;
+        d.nt = f[i].t;
+        d.npix = f[i].h * f[i].w;
+        d.tiles_w = (f[i].w + kTileW - 1) / kTileW;
+        d.tile_base = tiles;
+        d.pix_base = pix;
+        tiles += d.tiles_w * ((f[i].h + kTileH - 1) / kTileH);
+        pix += d.npix;
+        tmax = f[i].t > tmax ? f[i].t : tmax;
+        d.dense = f[i].dense;
+        d.csr_off = f[i].csr_off;
+        d.use_csr = f[i].csr_off != nullptr;
+        d.ent = d.use_csr ? f[i].csr_ent : c->W.ent;
+        d.gain = f[i].gain;
+        if (out) {
+            d.t = out[i].t;
+            d.r = out[i].r;
+            d.alive = out[i].alive;
+            d.b = out[i].b;
+            d.n_points = out[i].n_points;
+        }
+    }
+    if (pix > c->stride) return RT3D_E_INVALID;
+    B->total_tiles = tiles;
+    B->total_pix = pix;
+    B->max_t = tmax;
+    return RT3D_OK;
+}
+
+int init_warps(int max_t)
+{
+    int w = kInitSmemBudget / init_warp_bytes(max_t);
+    return w < 1 ? 1 : (w > kInitWarps ? kInitWarps : w);
+}
+
+size_t init_smem(const KParams& K, int max_t)
+{
+    return (size_t)((K.irf_len * 4 + 15) & ~15) + (size_t)init_warps(max_t) * init_warp_bytes(max_t);
+}
+
+rt3d_status launch_init(rt3d_ctx* c, const KParams& K, const Batch& B, Work W, cudaStream_t s,
+                        bool dump, bool compact_only)
+{
+    const size_t smem = init_smem(K, B.max_t);
+    const int warps = init_warps(B.max_t);
+    const int grid = (B.total_pix + warps - 1) / warps;
+    if (grid == 0) return RT3D_OK;
+    auto fn = dump ? k_init<true, false> : (compact_only ? k_init<false, true> : k_init<false, false>);
+    RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        LaunchScope ls(c, s, kcInit);
+        fn<<<grid, warps * 32, smem, s>>>(K, B, W);
+    }
+    RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}
+
+rt3d_status launch_loop(rt3d_ctx* c, const KParams& K, const Batch& B, cudaStream_t s, int n_iter)
+{
+    for (int it = 0; it < n_iter; ++it) {
+        {
+            LaunchScope ls(c, s, kcA);
+            k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W, it == 0 ? 1 : 0);
+        }
+        {
+            LaunchScope ls(c, s, kcB);
+            k_phase_b<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W);
+        }
+        {
+            LaunchScope ls(c, s, kcC);
+            k_phase_c<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W);
+        }
+    }
+    RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}
+
+rt3d_status launch_final(rt3d_ctx* c, const KParams& K, const Batch& B, cudaStream_t s, int ran)
+{
+    for (int i = 0; i < B.n; ++i)
+        if (B.f[i].n_points) RT3D_CUDA(cudaMemsetAsync(B.f[i].n_points, 0, sizeof(int32_t), s));
+    {
+        LaunchScope ls(c, s, kcFinal);
+        k_final<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W, ran);
+    }
+    RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}
+
+rt3d_status check_common(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params* p,
+                         const rt3d_result* out)
+{
+    if (!c || !f || !p || n < 1 || n > c->cfg.max_batch) return RT3D_E_INVALID;
+    if (!params_ok(&c->cfg, p)) return RT3D_E_INVALID;
+    for (int i = 0; i < n; ++i) {
+        if (!frame_ok(&c->cfg, &f[i])) return RT3D_E_INVALID;
+        if (out && (!out[i].t || !out[i].r || !out[i].alive || !out[i].b)) return RT3D_E_INVALID;
+    }
+    if (p->depth_denoiser == RT3D_DEPTH_LEARNED) return RT3D_E_UNIMPL;
+    return RT3D_OK;
+}
+
+rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params* p,
+                      rt3d_result* out, cudaStream_t s)
+{
+    rt3d_status st = check_common(c, n, f, p, out);
+    if (st != RT3D_OK) return st;
+    RT3D_CUDA(cudaSetDevice(c->cfg.device));
+    KParams K;
+    st = build_kparams(c, p, &K);
+    if (st != RT3D_OK) return st;
+    Batch B;
+    st = build_batch(c, n, f, out, &B);
+    if (st != RT3D_OK) return st;
+    RT3D_CUDA(cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), s));
+    st = launch_init(c, K, B, c->W, s, false, p->warm_start != 0);
+    if (st != RT3D_OK) return st;
+    st = launch_loop(c, K, B, s, p->n_iter);
+    if (st != RT3D_OK) return st;
+    return launch_final(c, K, B, s, p->n_iter > 0 ? 1 : 0);
+}
+
+}  // namespace
+
+// ============================================================================
+extern "C" {
+
+const char* rt3d_status_str(int status)
+{
+    switch (status) {
+        case RT3D_OK: return "ok";
+        case RT3D_E_INVALID: return "invalid argument";
+        case RT3D_E_NOMEM: return "out of device memory";
+        case RT3D_E_CUDA: return "CUDA error";
+        case RT3D_E_TIMEOUT: return "timeout";
+        case RT3D_E_UNIMPL: return "not implemented";
+        case RT3D_E_CAPACITY: return "sparse-entry capacity exceeded";
+        case RT3D_E_RANGE: return "counts exceed exact-arithmetic range";
+        default: return "unknown status";
+    }
+}
+
+int rt3d_version(void) { return RT3D_VERSION; }
+
+rt3d_status rt3d_default_params(rt3d_params* p)
+{
+    if (!p) return RT3D_E_INVALID;
+    std::memset(p, 0, sizeof(*p));
+    p->n_iter = 20;
+    p->k_max = 2;
+    p->t_step = 8.0f;
+    p->r_step = 0.5f;
+    p->b_step = 0.5f;
+    p->dt_max = 4.0f;
+    p->eps_r = 1e-3f;
+    p->eps_b = 1e-6f;
+    p->b_floor = 1e-7f;
+    p->lam_floor = 1e-9f;
+    p->pixel_pitch = 16.0f;
+    p->apss_radius = 56.0f;
+    p->win_r = 3;
+    p->apss_min_nb = 6;
+    p->int_radius = 56.0f;
+    p->r_min = 0.5f;
+    p->merge_dist = 8.0f;
+    p->depth_denoiser = RT3D_DEPTH_APSS;
+    p->intensity_denoiser = 1;
+    p->bkg_mode = RT3D_BKG_IDENTITY;
+    p->bkg_sigma = 1.0f;
+    p->bkg_radius = 3;
+    p->lmf_delta_rel = 1e-3f;
+    p->lmf_frac_bits = 5;
+    p->peak_min_photons = 2;
+    p->peak_sep = 8;
+    p->lmf_precision = RT3D_LMF_INT;
+    p->warm_start = 0;
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_validate(const rt3d_config* cfg, const rt3d_frame* f, const rt3d_params* p)
+{
+    if (!config_ok(cfg)) return RT3D_E_INVALID;
+    if (f && !frame_ok(cfg, f)) return RT3D_E_INVALID;
+    if (p && !params_ok(cfg, p)) return RT3D_E_INVALID;
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_create(const rt3d_config* cfg, const rt3d_irf* irf, rt3d_ctx_t** out)
+{
+    if (!out) return RT3D_E_INVALID;
+    *out = nullptr;
+    if (!config_ok(cfg) || !irf || !irf->samples) return RT3D_E_INVALID;
+    if (irf->len < 1 || irf->len > RT3D_MAX_IRF || irf->origin < 0 || irf->origin >= irf->len)
+        return RT3D_E_INVALID;
+    double sum = 0.0;
+    for (int s = 0; s < irf->len; ++s) {
+        if (!(irf->samples[s] >= 0.0) || !std::isfinite(irf->samples[s])) return RT3D_E_INVALID;
+        sum += irf->samples[s];
+    }
+    if (!(sum > 0.0)) return RT3D_E_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device >= ndev) return RT3D_E_CUDA;
+    RT3D_CUDA(cudaSetDevice(cfg->device));
+
+    rt3d_ctx* c = new (std::nothrow) rt3d_ctx();
+    if (!c) return RT3D_E_NOMEM;
+    c->cfg = *cfg;
+    c->irf_len = irf->len;
+    c->irf_origin = irf->origin;
+    c->irf_norm.resize(irf->len);
+    for (int s = 0; s < irf->len; ++s) c->irf_norm[s] = irf->samples[s] / sum;
+    c->stride = (long long)cfg->max_batch * cfg->max_h * cfg->max_w;
+    long long cap = cfg->max_entries;
+    if (cap == 0) cap = c->stride * cfg->max_t;
+    const int K = cfg->k_max;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes ? bytes : 16);
+    };
+    alloc((void**)&c->W.seg, sizeof(uint2) * c->stride);
+    alloc((void**)&c->W.ent, sizeof(uint32_t) * cap);
+    alloc((void**)&c->d_count, sizeof(unsigned long long));
+    alloc((void**)&c->W.t_half, sizeof(float) * K * c->stride);
+    alloc((void**)&c->W.r_half, sizeof(float) * K * c->stride);
+    alloc((void**)&c->W.b_half, sizeof(float) * c->stride);
+    alloc((void**)&c->W.alive_b, (size_t)K * c->stride);
+    alloc((void**)&c->d_status, sizeof(int));
+    alloc((void**)&c->d_tmp, sizeof(uint32_t) * (c->stride + 1));
+    if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(c->W.alive_b, 0, (size_t)K * c->stride);
+    if (e != cudaSuccess) {
+        rt3d_destroy(c);
+        return cuda_fail(e);
+    }
+    c->W.ent_count = c->d_count;
+    c->W.ent_cap = cap;
+    c->W.stride = (int)c->stride;
+    c->W.status = c->d_status;
+    c->W.y_out = nullptr;
+    *out = c;
+    return RT3D_OK;
+}
+
+void rt3d_destroy(rt3d_ctx_t* c)
+{
+    if (!c) return;
+    cudaSetDevice(c->cfg.device);
+    void* ptrs[] = {c->W.seg, c->W.ent, c->d_count, c->W.t_half, c->W.r_half, c->W.b_half,
+                    c->W.alive_b, c->d_status, c->d_tmp, c->s_dense, c->s_off, c->s_ent,
+                    c->s_gain, c->s_t, c->s_r, c->s_b, c->s_alive, c->s_np};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (auto& pt : c->pending) {
+        cudaEventDestroy(pt.a);
+        cudaEventDestroy(pt.b);
+    }
+    for (auto ev : c->event_pool) cudaEventDestroy(ev);
+    delete c;
+}
+
+rt3d_status rt3d_synthesize(rt3d_ctx_t* c, const rt3d_scene* sc, uint64_t seed, uint16_t* dense,
+                            void* stream)
+{
+    if (!c || !sc || !dense) return RT3D_E_INVALID;
+    if (sc->h < 1 || sc->w < 1 || sc->t < 1 || sc->t > RT3D_MAX_T) return RT3D_E_INVALID;
+    if (sc->n_comp < 0 || sc->n_comp > RT3D_MAX_SYNTH_COMP) return RT3D_E_INVALID;
+    if (sc->irf_len < 1 || sc->irf_len > RT3D_MAX_IRF) return RT3D_E_INVALID;
+    if (sc->irf_origin < 0 || sc->irf_origin >= sc->irf_len) return RT3D_E_INVALID;
+    if (!sc->n_parts || !sc->p0 || !sc->mu || (sc->irf_len > 1 && !sc->irf_cdf)) return RT3D_E_INVALID;
+    if (sc->n_comp > 0 && (!sc->depth_int || !sc->depth_split)) return RT3D_E_INVALID;
+    RT3D_CUDA(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    SynthArgs a;
+    a.h = sc->h;
+    a.w = sc->w;
+    a.t = sc->t;
+    a.n_comp = sc->n_comp;
+    a.depth_int = sc->depth_int;
+    a.depth_split = sc->depth_split;
+    a.n_parts = sc->n_parts;
+    a.p0 = sc->p0;
+    a.mu = sc->mu;
+    a.irf_cdf = sc->irf_cdf;
+    a.irf_len = sc->irf_len;
+    a.irf_origin = sc->irf_origin;
+    a.key = make_uint2((uint32_t)seed, (uint32_t)(seed >> 32));
+    a.out = dense;
+    const long long npix = (long long)sc->h * sc->w;
+    const size_t smem = sizeof(uint32_t) * (((sc->irf_len - 1) + 3) & ~3) +
+                        sizeof(uint32_t) * kSynthWarps * ((sc->t + 3) & ~3);
+    RT3D_CUDA(cudaFuncSetAttribute(k_synth, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    {
+        LaunchScope ls(c, s, kcSynth);
+        k_synth<<<(unsigned)((npix + kSynthWarps - 1) / kSynthWarps), kSynthWarps * 32, smem, s>>>(a);
+    }
+    RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_compact(rt3d_ctx_t* c, const rt3d_frame* f, uint32_t* csr_off, uint32_t* csr_ent,
+                         int64_t capacity, int64_t* nnz_host, void* stream)
+{
+    if (!c || !f || !f->dense || !csr_off || capacity < 0 || !nnz_host) return RT3D_E_INVALID;
+    if (!frame_ok(&c->cfg, f)) return RT3D_E_INVALID;
+    if (capacity > 0 && !csr_ent) return RT3D_E_INVALID;
+    RT3D_CUDA(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int npix = f->h * f->w;
+    const int grid = (npix + kCompactWarps - 1) / kCompactWarps;
+    {
+        LaunchScope ls(c, s, kcCompact);
+        k_count_nnz<<<grid, kCompactWarps * 32, 0, s>>>(f->dense, npix, f->t, c->d_tmp);
+    }
+    {
+        LaunchScope ls(c, s, kcCompact);
+        k_exclusive_scan<<<1, 1024, 0, s>>>(c->d_tmp, npix, csr_off);
+    }
+    RT3D_CUDA(cudaGetLastError());
+    uint32_t total = 0;
+    RT3D_CUDA(cudaMemcpyAsync(&total, csr_off + npix, sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    RT3D_CUDA(cudaStreamSynchronize(s));
+    *nnz_host = total;
+    if ((int64_t)total > capacity) return RT3D_E_CAPACITY;
+    {
+        LaunchScope ls(c, s, kcCompact);
+        k_emit<<<grid, kCompactWarps * 32, 0, s>>>(f->dense, npix, f->t, csr_off, csr_ent);
+    }
+    RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_lmf(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d_params* p, int32_t* y,
+                     void* stream)
+{
+    if (!y) return RT3D_E_INVALID;
+    rt3d_status st = check_common(c, 1, f, p, nullptr);
+    if (st != RT3D_OK) return st;
+    RT3D_CUDA(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    KParams K;
+    st = build_kparams(c, p, &K);
+    if (st != RT3D_OK) return st;
+    Batch B;
+    st = build_batch(c, 1, f, nullptr, &B);
+    if (st != RT3D_OK) return st;
+    Work W = c->W;
+    W.y_out = y;
+    RT3D_CUDA(cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), s));
+    return launch_init(c, K, B, W, s, true, false);
+}
+
+rt3d_status rt3d_init(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d_params* p, rt3d_result* out,
+                      void* stream)
+{
+    if (!out) return RT3D_E_INVALID;
+    rt3d_status st = check_common(c, 1, f, p, out);
+    if (st != RT3D_OK) return st;
+    RT3D_CUDA(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    KParams K;
+    st = build_kparams(c, p, &K);
+    if (st != RT3D_OK) return st;
+    Batch B;
+    st = build_batch(c, 1, f, out, &B);
+    if (st != RT3D_OK) return st;
+    RT3D_CUDA(cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), s));
+    st = launch_init(c, K, B, c->W, s, false, false);
+    if (st != RT3D_OK) return st;
+    return launch_final(c, K, B, s, 0);
+}
+
+rt3d_status rt3d_reconstruct(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d_params* p,
+                             rt3d_result* out, void* stream)
+{
+    if (!out) return RT3D_E_INVALID;
+    return run_batch(c, 1, f, p, out, (cudaStream_t)stream);
+}
+
+rt3d_status rt3d_reconstruct_batch(rt3d_ctx_t* c, int n, const rt3d_frame* f,
+                                   const rt3d_params* p, rt3d_result* out, void* stream)
+{
+    if (!out) return RT3D_E_INVALID;
+    return run_batch(c, n, f, p, out, (cudaStream_t)stream);
+}
+
+rt3d_status rt3d_reconstruct_host(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d_params* p,
+                                  rt3d_result* out, void* stream)
+{
+    if (!c || !f || !p || !out) return RT3D_E_INVALID;
+    rt3d_status st = check_common(c, 1, f, p, out);
+    if (st != RT3D_OK) return st;
+    RT3D_CUDA(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long mpix = (long long)c->cfg.max_h * c->cfg.max_w;
+    const int K = c->cfg.k_max;
+    if (!c->s_t) {
+        RT3D_CUDA(cudaMalloc((void**)&c->s_dense, sizeof(uint16_t) * mpix * c->cfg.max_t));
+        RT3D_CUDA(cudaMalloc((void**)&c->s_off, sizeof(uint32_t) * (mpix + 1)));
+        RT3D_CUDA(cudaMalloc((void**)&c->s_gain, sizeof(float) * mpix));
+        RT3D_CUDA(cudaMalloc((void**)&c->s_t, sizeof(float) * K * mpix));
+        RT3D_CUDA(cudaMalloc((void**)&c->s_r, sizeof(float) * K * mpix));
+        RT3D_CUDA(cudaMalloc((void**)&c->s_b, sizeof(float) * mpix));
+        RT3D_CUDA(cudaMalloc((void**)&c->s_alive, (size_t)K * mpix));
+        RT3D_CUDA(cudaMalloc((void**)&c->s_np, sizeof(int32_t)));
+    }
+    const long long npix = (long long)f->h * f->w;
+    rt3d_frame df = *f;
+    if (f->dense) {
+        RT3D_CUDA(cudaMemcpyAsync(c->s_dense, f->dense, sizeof(uint16_t) * npix * f->t,
+                                  cudaMemcpyHostToDevice, s));
+        df.dense = c->s_dense;
+    }
+    if (f->csr_off) {
+        const long long nent = f->csr_off[npix];
+        if (nent > c->s_ent_cap) {
+            if (c->s_ent) cudaFree(c->s_ent);
+            c->s_ent = nullptr;
+            c->s_ent_cap = 0;
+            RT3D_CUDA(cudaMalloc((void**)&c->s_ent, sizeof(uint32_t) * (nent > 0 ? nent : 1)));
+            c->s_ent_cap = nent;
+        }
+        RT3D_CUDA(cudaMemcpyAsync(c->s_off, f->csr_off, sizeof(uint32_t) * (npix + 1),
+                                  cudaMemcpyHostToDevice, s));
+        if (nent > 0)
+            RT3D_CUDA(cudaMemcpyAsync(c->s_ent, f->csr_ent, sizeof(uint32_t) * nent,
+                                      cudaMemcpyHostToDevice, s));
+        df.csr_off = c->s_off;
+        df.csr_ent = c->s_ent;
+    }
+    if (f->gain) {
+        RT3D_CUDA(cudaMemcpyAsync(c->s_gain, f->gain, sizeof(float) * npix, cudaMemcpyHostToDevice, s));
+        df.gain = c->s_gain;
+    }
+    rt3d_result dr{c->s_t, c->s_r, c->s_alive, c->s_b, c->s_np};
+    const int Kp = p->k_max;
+    if (p->warm_start) {
+        RT3D_CUDA(cudaMemcpyAsync(c->s_t, out->t, sizeof(float) * Kp * npix, cudaMemcpyHostToDevice, s));
+        RT3D_CUDA(cudaMemcpyAsync(c->s_r, out->r, sizeof(float) * Kp * npix, cudaMemcpyHostToDevice, s));
+        RT3D_CUDA(cudaMemcpyAsync(c->s_alive, out->alive, (size_t)Kp * npix, cudaMemcpyHostToDevice, s));
+        RT3D_CUDA(cudaMemcpyAsync(c->s_b, out->b, sizeof(float) * npix, cudaMemcpyHostToDevice, s));
+    }
+    st = run_batch(c, 1, &df, p, &dr, s);
+    if (st != RT3D_OK) return st;
+    RT3D_CUDA(cudaMemcpyAsync(out->t, c->s_t, sizeof(float) * Kp * npix, cudaMemcpyDeviceToHost, s));
+    RT3D_CUDA(cudaMemcpyAsync(out->r, c->s_r, sizeof(float) * Kp * npix, cudaMemcpyDeviceToHost, s));
+    RT3D_CUDA(cudaMemcpyAsync(out->alive, c->s_alive, (size_t)Kp * npix, cudaMemcpyDeviceToHost, s));
+    RT3D_CUDA(cudaMemcpyAsync(out->b, c->s_b, sizeof(float) * npix, cudaMemcpyDeviceToHost, s));
+    if (out->n_points)
+        RT3D_CUDA(cudaMemcpyAsync(out->n_points, c->s_np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RT3D_CUDA(cudaStreamSynchronize(s));
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_phase(rt3d_ctx_t* c, int phase, int first, const rt3d_frame* f,
+                       const rt3d_params* p, rt3d_result* state, void* stream)
+{
+    if (!state || phase < 0 || phase > 2) return RT3D_E_INVALID;
+    rt3d_status st = check_common(c, 1, f, p, state);
+    if (st != RT3D_OK) return st;
+    if (!f->csr_off) return RT3D_E_INVALID;
+    RT3D_CUDA(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    KParams K;
+    st = build_kparams(c, p, &K);
+    if (st != RT3D_OK) return st;
+    Batch B;
+    st = build_batch(c, 1, f, state, &B);
+    if (st != RT3D_OK) return st;
+    // sparse segments of the caller's list
+    st = launch_init(c, K, B, c->W, s, false, true);
+    if (st != RT3D_OK) return st;
+    const long long np = (long long)f->h * f->w;
+    const long long S = c->stride;
+    const int Kp = p->k_max;
+    for (int k = 0; k < Kp; ++k) {
+        if (phase == 0)
+            RT3D_CUDA(cudaMemcpyAsync(c->W.alive_b + k * S, state->alive + k * np, np,
+                                      cudaMemcpyDeviceToDevice, s));
+        if (phase == 1)
+            RT3D_CUDA(cudaMemcpyAsync(c->W.t_half + k * S, state->t + k * np, sizeof(float) * np,
+                                      cudaMemcpyDeviceToDevice, s));
+        if (phase == 2)
+            RT3D_CUDA(cudaMemcpyAsync(c->W.r_half + k * S, state->r + k * np, sizeof(float) * np,
+                                      cudaMemcpyDeviceToDevice, s));
+    }
+    if (phase == 0)
+        RT3D_CUDA(cudaMemcpyAsync(c->W.b_half, state->b, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
+    {
+        LaunchScope ls(c, s, phase == 0 ? kcA : (phase == 1 ? kcB : kcC));
+        if (phase == 0) k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W, first);
+        if (phase == 1) k_phase_b<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W);
+        if (phase == 2) k_phase_c<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W);
+    }
+    RT3D_CUDA(cudaGetLastError());
+    for (int k = 0; k < Kp; ++k) {
+        if (phase == 0)
+            RT3D_CUDA(cudaMemcpyAsync(state->t + k * np, c->W.t_half + k * S, sizeof(float) * np,
+                                      cudaMemcpyDeviceToDevice, s));
+        if (phase == 1)
+            RT3D_CUDA(cudaMemcpyAsync(state->r + k * np, c->W.r_half + k * S, sizeof(float) * np,
+                                      cudaMemcpyDeviceToDevice, s));
+        if (phase == 2)
+            RT3D_CUDA(cudaMemcpyAsync(state->alive + k * np, c->W.alive_b + k * S, np,
+                                      cudaMemcpyDeviceToDevice, s));
+    }
+    if (phase == 2)
+        RT3D_CUDA(cudaMemcpyAsync(state->b, c->W.b_half, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_device_status(rt3d_ctx_t* c, void* stream)
+{
+    if (!c) return RT3D_E_INVALID;
+    RT3D_CUDA(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    RT3D_CUDA(cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RT3D_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
+    RT3D_CUDA(cudaStreamSynchronize(s));
+    if (h & kStatusCapacity) return RT3D_E_CAPACITY;
+    if (h & kStatusRange) return RT3D_E_RANGE;
+    return RT3D_OK;
+}
+
+int64_t rt3d_launch_count(rt3d_ctx_t* c) { return c ? c->launches : -1; }
+
+rt3d_status rt3d_set_profiling(rt3d_ctx_t* c, int on)
+{
+    if (!c) return RT3D_E_INVALID;
+    c->profiling = on != 0;
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_kernel_times(rt3d_ctx_t* c, double* ms, int64_t* launches, int n, int reset)
+{
+    if (!c || n < 0) return RT3D_E_INVALID;
+    for (auto& pt : c->pending) {
+        if (cudaEventSynchronize(pt.b) != cudaSuccess) return RT3D_E_CUDA;
+        float v = 0.0f;
+        cudaEventElapsedTime(&v, pt.a, pt.b);
+        c->ms[pt.cls] += v;
+        c->counts[pt.cls] += 1;
+        c->event_pool.push_back(pt.a);
+        c->event_pool.push_back(pt.b);
+    }
+    c->pending.clear();
+    for (int i = 0; i < n && i < kNumKernelClasses; ++i) {
+        if (ms) ms[i] = c->ms[i];
+        if (launches) launches[i] = c->counts[i];
+    }
+    if (reset)
+        for (int i = 0; i < kNumKernelClasses; ++i) {
+            c->ms[i] = 0.0;
+            c->counts[i] = 0;
+        }
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_get_sparse(rt3d_ctx_t* c, uint32_t* seg_host, int64_t n_pix, uint32_t* ent_host,
+                            int64_t n_ent, int64_t* n_ent_used, void* stream)
+{
+    if (!c || n_pix < 0 || n_pix > c->stride || n_ent < 0 || n_ent > c->W.ent_cap) return RT3D_E_INVALID;
+    RT3D_CUDA(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    unsigned long long used = 0;
+    RT3D_CUDA(cudaMemcpyAsync(&used, c->d_count, sizeof(used), cudaMemcpyDeviceToHost, s));
+    if (seg_host && n_pix)
+        RT3D_CUDA(cudaMemcpyAsync(seg_host, c->W.seg, sizeof(uint2) * n_pix, cudaMemcpyDeviceToHost, s));
+    if (ent_host && n_ent)
+        RT3D_CUDA(cudaMemcpyAsync(ent_host, c->W.ent, sizeof(uint32_t) * n_ent, cudaMemcpyDeviceToHost, s));
+    RT3D_CUDA(cudaStreamSynchronize(s));
+    if (n_ent_used) *n_ent_used = (int64_t)used;
+    return RT3D_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+// rt3d_device.cuh -- types and device helpers shared by the rt3d kernels.
+//
+// Everything a kernel needs travels by value in two __grid_constant__
+// parameters: KParams (the method's constants, the normalised IRF, the
+// quantised log-IRF and the background filter taps) and Batch (one descriptor
+// per frame).  No constant-memory tables, so every launch is self-contained
+// and capturable in a CUDA graph.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "rt3d.h"
+
+namespace rt3d {
+
+constexpr int kMaxK = RT3D_MAX_K;
+constexpr int kMaxIrf = RT3D_MAX_IRF;
+constexpr int kMaxBatch = RT3D_MAX_BATCH;
+constexpr int kMaxWinR = RT3D_MAX_WIN_R;
+constexpr int kMaxBkgR = RT3D_MAX_BKG_R;
+constexpr int kIrfPad = 3;          // zero samples on each side of the padded IRF
+
+// device status bits (or-ed into Work::status)
+constexpr int kStatusCapacity = 1;
+constexpr int kStatusRange = 2;
+
+struct KParams {
+    int n_iter, k;
+    float t_step, r_step, b_step, dt_max, eps_r, eps_b, b_floor, lam_floor;
+    float pitch, apss_h, int_h, r_min, merge_dist;
+    int win_r, apss_min_nb;
+    int depth_den, int_den, bkg_mode, bkg_rad;
+    int irf_len, irf_origin;
+    float irf_sum;                  // sum of the float IRF samples (H in the interior)
+    int peak_sep, peak_min_photons;
+    int lmf_kmax;                   // largest quantised log-IRF value
+    float irf[kMaxIrf];             // normalised IRF samples
+    int lmf[kMaxIrf];               // quantised log-IRF K_s
+    float bkg_ker[2 * kMaxBkgR + 1];
+};
+
+struct FrameDesc {
+    int h, w, nt, npix;             // nt = histogram bins
+    int tiles_w, tile_base;         // tile grid of the loop kernels
+    int pix_base;                   // first pixel of this frame in the batch workspace
+    int use_csr;                    // loop reads the caller's sparse list
+    const uint16_t* dense;
+    const uint32_t* csr_off;
+    const uint32_t* ent;            // entries the loop reads (caller's or workspace)
+    const float* gain;
+    float* t;                       // [k][h][w] primary state (the result buffers)
+    float* r;
+    uint8_t* alive;
+    float* b;                       // [h][w]
+    int32_t* n_points;
+};
+
+struct Batch {
+    int n, total_tiles, total_pix, max_t;
+    FrameDesc f[kMaxBatch];
+};
+
+struct Work {
+    uint2* seg;                     // [stride] (start, count) per pixel
+    uint32_t* ent;                  // nonzero-bin entries built from dense histograms
+    unsigned long long* ent_count;  // allocation cursor into ent
+    long long ent_cap;
+    float* t_half;                  // [K][stride]
+    float* r_half;                  // [K][stride]
+    float* b_half;                  // [stride]
+    uint8_t* alive_b;               // [K][stride] pruning output (ping-pong with alive)
+    int32_t* y_out;                 // matched-filter dump (rt3d_lmf) or null
+    int stride;
+    int* status;
+};
+
+constexpr int kTileH = 8, kTileW = 16, kTileThreads = kTileH * kTileW;
+
+// ---------------------------------------------------------------- helpers
+
+__device__ __forceinline__ int frame_of_tile(const Batch& B, int tile)
+{
+    int lo = 0, hi = B.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.f[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int frame_of_pixel(const Batch& B, int pix)
+{
+    int lo = 0, hi = B.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.f[mid].pix_base <= pix) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Catmull-Rom (Keys a = -1/2) interpolation of the IRF samples and its
+// derivative at offset x from a point's depth.  `pad` holds the samples with
+// kIrfPad zeros on each side, so pad[k + kIrfPad] = h_k for k in [-3, L+2].
+__device__ __forceinline__ void irf_eval(const float* pad, int L, int origin, float x,
+                                         float& h, float& dh)
+{
+    const float y = x + (float)origin;
+    if (!(y > -2.0f && y < (float)L + 1.0f)) {
+        h = 0.0f;
+        dh = 0.0f;
+        return;
+    }
+    const float kf = floorf(y);
+    const int k = (int)kf + kIrfPad;
+    const float u = y - kf;
+    const float pm = pad[k - 1], p0 = pad[k], p1 = pad[k + 1], p2 = pad[k + 2];
+    const float c1 = p1 - pm;
+    const float c2 = 2.0f * pm - 5.0f * p0 + 4.0f * p1 - p2;
+    const float c3 = -pm + 3.0f * p0 - 3.0f * p1 + p2;
+    h = 0.5f * (2.0f * p0 + u * (c1 + u * (c2 + u * c3)));
+    dh = 0.5f * (c1 + u * (2.0f * c2 + 3.0f * c3 * u));
+}
+
+// H = sum_{t in [0,T)} h(t - tn) and H' = sum h'(t - tn).  In the interior the
+// Catmull-Rom interpolant reproduces constants: H = sum of samples, H' = 0;
+// near the histogram ends the sums are taken explicitly.
+__device__ __forceinline__ void support_sums(const float* pad, const KParams& P, int T,
+                                             float tn, float& H, float& dH)
+{
+    const int base = (int)floorf(tn) - P.irf_origin;
+    int lo = base - 3, hi = base + P.irf_len + 2;
+    if (lo >= 0 && hi <= T - 1) {
+        H = P.irf_sum;
+        dH = 0.0f;
+        return;
+    }
+    if (lo < 0) lo = 0;
+    if (hi > T - 1) hi = T - 1;
+    float sh = 0.0f, sdh = 0.0f;
+    for (int tb = lo; tb <= hi; ++tb) {
+        float hv, dv;
+        irf_eval(pad, P.irf_len, P.irf_origin, (float)tb - tn, hv, dv);
+        sh += hv;
+        sdh += dv;
+    }
+    H = sh;
+    dH = sdh;
+}
+
+template <int G>
+__device__ __forceinline__ float group_sum(float v, unsigned mask)
+{
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi)
+{
+    return fminf(fmaxf(v, lo), hi);
+}
+
+}  // namespace rt3d

@@ -1,0 +1,376 @@
+"""Thin Python binding of the rt3d C ABI (include/rt3d.h).
+
+Argument marshalling only: every step of the method runs in the library's
+CUDA kernels.  PyTorch provides device memory and streams.  The functions
+named rt3d_* mirror the C entry points one to one; `Context` bundles them
+with torch-tensor allocation for convenience.  There is no CPU fallback: if
+the compiled library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "lib", "librt3d.so")
+
+RT3D_OK = 0
+RT3D_E_INVALID = -1
+RT3D_E_NOMEM = -2
+RT3D_E_CUDA = -3
+RT3D_E_TIMEOUT = -4
+RT3D_E_UNIMPL = -5
+RT3D_E_CAPACITY = -6
+RT3D_E_RANGE = -7
+
+MAX_K = 4
+MAX_BATCH = 64
+
+
+class Rt3dError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: rt3d status {status} ({status_str(status)})")
+
+
+class Config(C.Structure):
+    _fields_ = [("max_h", C.c_int32), ("max_w", C.c_int32), ("max_t", C.c_int32),
+                ("k_max", C.c_int32), ("max_batch", C.c_int32), ("max_entries", C.c_int64),
+                ("device", C.c_int32)]
+
+
+class Irf(C.Structure):
+    _fields_ = [("samples", C.POINTER(C.c_double)), ("len", C.c_int32), ("origin", C.c_int32)]
+
+
+class Frame(C.Structure):
+    _fields_ = [("h", C.c_int32), ("w", C.c_int32), ("t", C.c_int32),
+                ("dense", C.c_void_p), ("csr_off", C.c_void_p), ("csr_ent", C.c_void_p),
+                ("gain", C.c_void_p)]
+
+
+class Params(C.Structure):
+    _fields_ = [("n_iter", C.c_int32), ("k_max", C.c_int32),
+                ("t_step", C.c_float), ("r_step", C.c_float), ("b_step", C.c_float),
+                ("dt_max", C.c_float), ("eps_r", C.c_float), ("eps_b", C.c_float),
+                ("b_floor", C.c_float), ("lam_floor", C.c_float),
+                ("pixel_pitch", C.c_float), ("apss_radius", C.c_float),
+                ("win_r", C.c_int32), ("apss_min_nb", C.c_int32),
+                ("int_radius", C.c_float), ("r_min", C.c_float), ("merge_dist", C.c_float),
+                ("depth_denoiser", C.c_int32), ("intensity_denoiser", C.c_int32),
+                ("bkg_mode", C.c_int32), ("bkg_sigma", C.c_float), ("bkg_radius", C.c_int32),
+                ("lmf_delta_rel", C.c_float), ("lmf_frac_bits", C.c_int32),
+                ("peak_min_photons", C.c_int32), ("peak_sep", C.c_int32),
+                ("lmf_precision", C.c_int32), ("warm_start", C.c_int32)]
+
+
+class Result(C.Structure):
+    _fields_ = [("t", C.c_void_p), ("r", C.c_void_p), ("alive", C.c_void_p), ("b", C.c_void_p),
+                ("n_points", C.c_void_p)]
+
+
+class Scene(C.Structure):
+    _fields_ = [("h", C.c_int32), ("w", C.c_int32), ("t", C.c_int32), ("n_comp", C.c_int32),
+                ("depth_int", C.c_void_p), ("depth_split", C.c_void_p), ("n_parts", C.c_void_p),
+                ("p0", C.c_void_p), ("mu", C.c_void_p), ("irf_cdf", C.c_void_p),
+                ("irf_len", C.c_int32), ("irf_origin", C.c_int32)]
+
+
+_lib = None
+_P = C.c_void_p
+
+
+def lib():
+    """Load lib/librt3d.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"rt3d CUDA library not built: {LIB_PATH} is missing "
+                           "(run __graft_entry__.build() or python paper_1905_06700_b300/build.py)")
+    L = C.CDLL(LIB_PATH)
+    sig = {
+        "rt3d_status_str": (C.c_char_p, [C.c_int]),
+        "rt3d_version": (C.c_int, []),
+        "rt3d_default_params": (C.c_int, [C.POINTER(Params)]),
+        "rt3d_validate": (C.c_int, [C.POINTER(Config), C.POINTER(Frame), C.POINTER(Params)]),
+        "rt3d_create": (C.c_int, [C.POINTER(Config), C.POINTER(Irf), C.POINTER(_P)]),
+        "rt3d_destroy": (None, [_P]),
+        "rt3d_synthesize": (C.c_int, [_P, C.POINTER(Scene), C.c_uint64, _P, _P]),
+        "rt3d_compact": (C.c_int, [_P, C.POINTER(Frame), _P, _P, C.c_int64,
+                                   C.POINTER(C.c_int64), _P]),
+        "rt3d_lmf": (C.c_int, [_P, C.POINTER(Frame), C.POINTER(Params), _P, _P]),
+        "rt3d_init": (C.c_int, [_P, C.POINTER(Frame), C.POINTER(Params), C.POINTER(Result), _P]),
+        "rt3d_reconstruct": (C.c_int, [_P, C.POINTER(Frame), C.POINTER(Params),
+                                       C.POINTER(Result), _P]),
+        "rt3d_reconstruct_batch": (C.c_int, [_P, C.c_int, C.POINTER(Frame), C.POINTER(Params),
+                                             C.POINTER(Result), _P]),
+        "rt3d_reconstruct_host": (C.c_int, [_P, C.POINTER(Frame), C.POINTER(Params),
+                                            C.POINTER(Result), _P]),
+        "rt3d_phase": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(Frame), C.POINTER(Params),
+                                 C.POINTER(Result), _P]),
+        "rt3d_device_status": (C.c_int, [_P, _P]),
+        "rt3d_launch_count": (C.c_int64, [_P]),
+        "rt3d_set_profiling": (C.c_int, [_P, C.c_int]),
+        "rt3d_kernel_times": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                        C.c_int, C.c_int]),
+        "rt3d_get_sparse": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64,
+                                      C.POINTER(C.c_int64), _P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def status_str(status: int) -> str:
+    try:
+        return lib().rt3d_status_str(status).decode()
+    except Exception:  # library missing: still format the error
+        return "unknown"
+
+
+def check(status: int, what: str):
+    if status != RT3D_OK:
+        raise Rt3dError(status, what)
+
+
+# ---- one-to-one wrappers of the C entry points --------------------------------
+
+def rt3d_version() -> int:
+    return lib().rt3d_version()
+
+
+def rt3d_default_params() -> Params:
+    p = Params()
+    check(lib().rt3d_default_params(C.byref(p)), "rt3d_default_params")
+    return p
+
+
+def rt3d_validate(cfg: Config, frame: Optional[Frame], params: Optional[Params]) -> int:
+    return lib().rt3d_validate(C.byref(cfg), C.byref(frame) if frame else None,
+                               C.byref(params) if params else None)
+
+
+def rt3d_create(cfg: Config, irf_samples, irf_origin: int):
+    samples = np.ascontiguousarray(irf_samples, dtype=np.float64)
+    irf = Irf(samples.ctypes.data_as(C.POINTER(C.c_double)), len(samples), int(irf_origin))
+    h = _P()
+    check(lib().rt3d_create(C.byref(cfg), C.byref(irf), C.byref(h)), "rt3d_create")
+    return h
+
+
+def rt3d_destroy(h):
+    lib().rt3d_destroy(h)
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def params_from(d) -> Params:
+    """Params from a dict (missing keys take the library defaults)."""
+    if isinstance(d, Params):
+        return d
+    p = rt3d_default_params()
+    for name, ctype in Params._fields_:
+        if name in d:
+            setattr(p, name, int(d[name]) if ctype is C.c_int32 else float(d[name]))
+    return p
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A library context plus torch-tensor marshalling for its entry points."""
+
+    def __init__(self, max_h: int, max_w: int, max_t: int, k_max: int, irf_samples, irf_origin: int,
+                 max_batch: int = 1, max_entries: int = 0, device: int = 0):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        self.cfg = Config(max_h, max_w, max_t, k_max, max_batch, max_entries, device)
+        self.k_max = k_max
+        self.handle = rt3d_create(self.cfg, irf_samples, irf_origin)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            rt3d_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- frames / results -------------------------------------------------------
+    def frame(self, dense=None, csr=None, gain=None, shape=None) -> Frame:
+        if dense is not None:
+            h, w, t = dense.shape
+        else:
+            h, w, t = shape
+        off, ent = (csr if csr is not None else (None, None))
+        return Frame(h, w, t, _ptr(dense), _ptr(off), _ptr(ent), _ptr(gain))
+
+    def new_result(self, h, w, k=None):
+        torch = self.torch
+        k = k or self.k_max
+        d = self.device
+        return dict(t=torch.zeros((k, h, w), dtype=torch.float32, device=d),
+                    r=torch.zeros((k, h, w), dtype=torch.float32, device=d),
+                    alive=torch.zeros((k, h, w), dtype=torch.uint8, device=d),
+                    b=torch.zeros((h, w), dtype=torch.float32, device=d),
+                    n_points=torch.zeros(1, dtype=torch.int32, device=d))
+
+    @staticmethod
+    def result_struct(res: dict) -> Result:
+        return Result(_ptr(res["t"]), _ptr(res["r"]), _ptr(res["alive"]), _ptr(res["b"]),
+                      _ptr(res.get("n_points")))
+
+    # -- entry points -------------------------------------------------------------
+    def synthesize(self, tables: dict, seed: Optional[int] = None, out=None, stream=None):
+        torch = self.torch
+        d = self.device
+        h, w, t = tables["h"], tables["w"], tables["t"]
+
+        def up(a, dt):
+            return torch.from_numpy(np.ascontiguousarray(a).view(dt)).to(d)
+        keep = dict(depth_int=up(tables["depth_int"], np.int32),
+                    depth_split=up(tables["depth_split"], np.int32),
+                    n_parts=up(tables["n_parts"], np.int32),
+                    p0=up(tables["p0"], np.int64), mu=up(tables["mu"], np.int64),
+                    irf_cdf=up(tables["irf_cdf"] if len(tables["irf_cdf"]) else np.zeros(1, np.uint32),
+                               np.int32))
+        sc = Scene(h, w, t, tables["n_comp"], _ptr(keep["depth_int"]), _ptr(keep["depth_split"]),
+                   _ptr(keep["n_parts"]), _ptr(keep["p0"]), _ptr(keep["mu"]), _ptr(keep["irf_cdf"]),
+                   tables["irf_len"], tables["irf_origin"])
+        if out is None:
+            out = torch.empty((h, w, t), dtype=torch.uint16, device=d)
+        seed = tables["seed"] if seed is None else seed
+        check(lib().rt3d_synthesize(self.handle, C.byref(sc), C.c_uint64(int(seed)), _ptr(out),
+                                    _stream(stream)), "rt3d_synthesize")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        return out
+
+    def compact(self, dense, capacity=None, stream=None):
+        torch = self.torch
+        h, w, t = dense.shape
+        if capacity is None:
+            capacity = h * w * t
+        off = torch.empty(h * w + 1, dtype=torch.int32, device=self.device)
+        ent = torch.empty(max(int(capacity), 1), dtype=torch.int32, device=self.device)
+        nnz = C.c_int64()
+        fr = self.frame(dense)
+        check(lib().rt3d_compact(self.handle, C.byref(fr), _ptr(off), _ptr(ent), int(capacity),
+                                 C.byref(nnz), _stream(stream)), "rt3d_compact")
+        return off, ent[: nnz.value]
+
+    def lmf(self, params, dense=None, csr=None, shape=None, stream=None):
+        torch = self.torch
+        fr = self.frame(dense, csr, shape=shape)
+        y = torch.empty((fr.h, fr.w, fr.t), dtype=torch.int32, device=self.device)
+        p = params_from(params)
+        check(lib().rt3d_lmf(self.handle, C.byref(fr), C.byref(p), _ptr(y), _stream(stream)), "rt3d_lmf")
+        return y
+
+    def init(self, params, dense=None, csr=None, gain=None, shape=None, out=None, stream=None):
+        fr = self.frame(dense, csr, gain, shape)
+        p = params_from(params)
+        out = out or self.new_result(fr.h, fr.w, p.k_max)
+        rs = self.result_struct(out)
+        check(lib().rt3d_init(self.handle, C.byref(fr), C.byref(p), C.byref(rs), _stream(stream)),
+              "rt3d_init")
+        return out
+
+    def reconstruct(self, params, dense=None, csr=None, gain=None, shape=None, out=None, stream=None):
+        fr = self.frame(dense, csr, gain, shape)
+        p = params_from(params)
+        out = out or self.new_result(fr.h, fr.w, p.k_max)
+        rs = self.result_struct(out)
+        check(lib().rt3d_reconstruct(self.handle, C.byref(fr), C.byref(p), C.byref(rs),
+                                     _stream(stream)), "rt3d_reconstruct")
+        return out
+
+    def reconstruct_batch(self, params, frames: Sequence[dict], outs=None, stream=None):
+        p = params_from(params)
+        n = len(frames)
+        fa = (Frame * n)()
+        for i, f in enumerate(frames):
+            fa[i] = self.frame(f.get("dense"), f.get("csr"), f.get("gain"), f.get("shape"))
+        if outs is None:
+            outs = [self.new_result(fa[i].h, fa[i].w, p.k_max) for i in range(n)]
+        ra = (Result * n)(*[self.result_struct(o) for o in outs])
+        check(lib().rt3d_reconstruct_batch(self.handle, n, fa, C.byref(p), ra, _stream(stream)),
+              "rt3d_reconstruct_batch")
+        return outs
+
+    def phase(self, phase: int, first: int, params, csr, state: dict, gain=None, shape=None, stream=None):
+        fr = self.frame(None, csr, gain, shape)
+        p = params_from(params)
+        rs = self.result_struct(state)
+        check(lib().rt3d_phase(self.handle, int(phase), int(first), C.byref(fr), C.byref(p),
+                               C.byref(rs), _stream(stream)), "rt3d_phase")
+        return state
+
+    def device_status(self, stream=None) -> int:
+        return lib().rt3d_device_status(self.handle, _stream(stream))
+
+    def launch_count(self) -> int:
+        return int(lib().rt3d_launch_count(self.handle))
+
+    def set_profiling(self, on: bool):
+        check(lib().rt3d_set_profiling(self.handle, int(on)), "rt3d_set_profiling")
+
+    def kernel_times(self, reset=False):
+        ms = (C.c_double * 8)()
+        n = (C.c_int64 * 8)()
+        check(lib().rt3d_kernel_times(self.handle, ms, n, 8, int(reset)), "rt3d_kernel_times")
+        names = ["init", "phase_a", "phase_b", "phase_c", "final", "synth", "compact", "other"]
+        return {names[i]: (ms[i], n[i]) for i in range(8)}
+
+    def get_sparse(self, n_pix: int, n_ent: int, stream=None):
+        seg = np.zeros((n_pix, 2), np.uint32)
+        ent = np.zeros(max(n_ent, 1), np.uint32)
+        used = C.c_int64()
+        check(lib().rt3d_get_sparse(self.handle, seg.ctypes.data_as(C.c_void_p), n_pix,
+                                    ent.ctypes.data_as(C.c_void_p), n_ent, C.byref(used),
+                                    _stream(stream)), "rt3d_get_sparse")
+        return seg, ent[:n_ent], used.value
+
+
+def _host_ptr(a):
+    return None if a is None else C.c_void_p(a.ctypes.data)
+
+
+def reconstruct_host(ctx: Context, params, dense: np.ndarray, gain: Optional[np.ndarray] = None,
+                     csr: Optional[tuple] = None, out: Optional[dict] = None, stream=None) -> dict:
+    """rt3d_reconstruct_host: HOST numpy buffers in and out (copies inside the call)."""
+    p = params_from(params)
+    h, w, t = dense.shape if dense is not None else csr[2]
+    dense = None if dense is None else np.ascontiguousarray(dense, np.uint16)
+    gain = None if gain is None else np.ascontiguousarray(gain, np.float32)
+    off = ent = None
+    if csr is not None:
+        off = np.ascontiguousarray(csr[0], np.uint32)
+        ent = np.ascontiguousarray(csr[1], np.uint32)
+    fr = Frame(h, w, t, _host_ptr(dense), _host_ptr(off), _host_ptr(ent), _host_ptr(gain))
+    k = p.k_max
+    if out is None:
+        out = dict(t=np.zeros((k, h, w), np.float32), r=np.zeros((k, h, w), np.float32),
+                   alive=np.zeros((k, h, w), np.uint8), b=np.zeros((h, w), np.float32),
+                   n_points=np.zeros(1, np.int32))
+    rs = Result(_host_ptr(out["t"]), _host_ptr(out["r"]), _host_ptr(out["alive"]),
+                _host_ptr(out["b"]), _host_ptr(out.get("n_points")))
+    check(lib().rt3d_reconstruct_host(ctx.handle, C.byref(fr), C.byref(p), C.byref(rs),
+                                      _stream(stream)), "rt3d_reconstruct_host")
+    return out

@@ -48,6 +48,14 @@ class Irf:
     def normalised(self) -> np.ndarray:
         return self.samples / self.samples.sum()
 
+    def fisher_information(self) -> float:
+        """Location Fisher information sum h'^2 / h of the normalised samples
+        (central differences), i.e. 1/sigma^2 for a Gaussian pulse."""
+        h = self.normalised()
+        d = np.gradient(h)
+        m = h > 1e-6 * h.max()
+        return float((d[m] ** 2 / h[m]).sum())
+
     def variance(self) -> float:
         h = self.normalised()
         k = np.arange(self.length) - self.origin
@@ -316,17 +324,18 @@ def moving_frame(base: Scene, frame: int, speed: float = 1.0) -> Scene:
 # ---------------------------------------------------------------------------
 
 def make_params(scene: Scene, **over) -> dict:
-    """Default reconstruction parameters for a workload.  Step sizes scale with
-    the IRF variance; the APSS radius is 3.5 pixels in world units
+    """Default reconstruction parameters for a workload.  The depth step is half
+    a Fisher-scoring step (t_step = 0.5 / I_h), clamped to one IRF standard
+    deviation; the APSS radius is 3.5 pixels in world units
     (7x7 pixel window)."""
     var = scene.irf.variance()
     pitch = over.pop("pixel_pitch", 16.0)
     p = dict(
         n_iter=20, k_max=max(1, scene.n_comp),
-        t_step=0.5 * var, r_step=0.5, b_step=0.5,
+        t_step=0.5 / scene.irf.fisher_information(), r_step=0.5, b_step=0.5,
         dt_max=math.sqrt(var), eps_r=1e-3, eps_b=1e-6, b_floor=1e-7, lam_floor=1e-9,
         pixel_pitch=pitch, apss_radius=3.5 * pitch, win_r=3, apss_min_nb=6,
-        int_radius=3.5 * pitch, r_min=0.5,
+        int_radius=3.5 * pitch, r_min=0.5, merge_dist=max(2.0, 2.0 * math.sqrt(var)),
         depth_denoiser=1, intensity_denoiser=1, bkg_mode=0, bkg_sigma=1.0, bkg_radius=3,
         lmf_delta_rel=1e-3, lmf_frac_bits=5, peak_min_photons=2,
         peak_sep=max(2, int(math.ceil(2.0 * math.sqrt(var)))),

@@ -1,0 +1,305 @@
+"""GPU (sm_103a) kernels vs the FP64 oracle, through the C ABI.
+
+Integer work (photon synthesis, sparse compaction, matched filter, peak bins)
+must be bit-exact; floating-point results within 1e-3 bins of depth and 1e-4
+relative intensity/background of the oracle (the FP32 tolerance)."""
+import numpy as np
+import pytest
+
+import scenes
+from gpu_util import (compare_clouds, ill_conditioned, make_ctx, np_of, oracle_irf,
+                      oracle_with_probe, state_f32_rounded, state_to_device, torch_mod, u16_np,
+                      upload_u16, workload_params)
+
+pytestmark = pytest.mark.gpu
+
+TOL_T = 1e-3
+TOL_R = 1e-4
+
+
+def _scenes_small():
+    return [
+        scenes.plane_hemisphere(),                                   # 32x32x1024, K=1
+        scenes.small_random(13, 29, 300, n_comp=2, seed=4),          # ragged tile edges
+        scenes.small_random(1, 1, 64, n_comp=1, seed=5),             # single pixel
+        scenes.small_random(1, 37, 203, n_comp=2, seed=6),           # one row, T % 8 != 0
+        scenes.small_random(9, 17, 129, n_comp=3, seed=7),
+    ]
+
+
+@pytest.mark.parametrize("idx", range(5))
+def test_synthesis_bit_exact(orc, idx):
+    sc = _scenes_small()[idx]
+    tab = scenes.sampling_tables(sc)
+    ctx = make_ctx(sc)
+    z = u16_np(ctx.synthesize(tab))
+    assert np.array_equal(z, orc.synthesize(tab))
+
+
+def test_synthesis_bit_exact_multisurface_full_size(orc):
+    sc = scenes.net_object_wall()                                    # 141x141x4096
+    tab = scenes.sampling_tables(sc)
+    ctx = make_ctx(sc)
+    z = u16_np(ctx.synthesize(tab))
+    assert np.array_equal(z, orc.synthesize(tab))
+
+
+@pytest.mark.parametrize("idx", range(5))
+def test_compaction_bit_exact(orc, idx):
+    sc = _scenes_small()[idx]
+    tab = scenes.sampling_tables(sc)
+    z = orc.synthesize(tab)
+    ctx = make_ctx(sc)
+    off, ent = ctx.compact(upload_u16(z))
+    off = off.cpu().numpy().view(np.uint32)
+    ent = ent.cpu().numpy().view(np.uint32)
+    fr = orc.OFrame(z)
+    assert np.array_equal(off, fr.off.astype(np.uint32))
+    assert np.array_equal(ent >> 16, fr.bin.astype(np.uint32))
+    assert np.array_equal(ent & 0xFFFF, fr.cnt.astype(np.uint32))
+
+
+@pytest.mark.parametrize("idx", range(5))
+def test_matched_filter_bit_exact(orc, idx):
+    sc = _scenes_small()[idx]
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc)
+    ctx = make_ctx(sc)
+    y = ctx.lmf(prm, dense=upload_u16(z)).cpu().numpy()
+    irf = oracle_irf(orc, sc)
+    kern = orc.lmf_kernel(irf, prm["lmf_delta_rel"], prm["lmf_frac_bits"])
+    for i in range(sc.h):
+        for j in range(sc.w):
+            want, _ = orc.lmf(z[i, j], kern, irf.origin)
+            assert np.array_equal(y[i, j], want), (i, j)
+
+
+def _init_pair(orc, sc, **over):
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc, **over)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    g = np_of(ctx.init(prm, dense=upload_u16(z)))
+    o = orc.init(z, None, oracle_irf(orc, sc), prm)
+    return z, prm, ctx, g, o
+
+
+@pytest.mark.parametrize("idx", range(5))
+def test_init_peaks_bit_exact(orc, idx):
+    sc = _scenes_small()[idx]
+    z, prm, ctx, g, o = _init_pair(orc, sc)
+    assert np.array_equal(g["alive"], o.alive)
+    assert np.array_equal(g["t"].astype(np.float64), o.t)       # integer peak bins
+    np.testing.assert_allclose(g["r"], o.r, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(g["b"], o.b, rtol=1e-5, atol=1e-12)
+    assert g["n_points"] == int(o.alive.sum())
+    # the sparse list built inside the initialisation kernel
+    seg, ent, used = ctx.get_sparse(sc.h * sc.w, int(np.count_nonzero(z)))
+    assert used == np.count_nonzero(z)
+    fr = orc.OFrame(z)
+    for p in range(sc.h * sc.w):
+        s, n = seg[p]
+        e = ent[s:s + n]
+        assert np.array_equal(e >> 16, fr.bin[fr.off[p]:fr.off[p + 1]])
+        assert np.array_equal(e & 0xFFFF, fr.cnt[fr.off[p]:fr.off[p + 1]])
+
+
+def test_init_multisurface_full_size_bit_exact(orc):
+    sc = scenes.net_object_wall()
+    z, prm, ctx, g, o = _init_pair(orc, sc)
+    assert np.array_equal(g["alive"], o.alive)
+    assert np.array_equal(g["t"].astype(np.float64), o.t)
+    np.testing.assert_allclose(g["r"], o.r, rtol=1e-5, atol=1e-6)
+
+
+def _phase_setup(orc, sc, **over):
+    torch = torch_mod()
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc, **over)
+    irf = oracle_irf(orc, sc)
+    st0 = state_f32_rounded(orc, orc.init(z, None, irf, prm))
+    ctx = make_ctx(sc, k=prm["k_max"])
+    off, ent = ctx.compact(upload_u16(z))
+    return z, prm, irf, st0, ctx, (off, ent), orc.OFrame(z)
+
+
+@pytest.mark.parametrize("idx", [0, 1, 4])
+@pytest.mark.parametrize("bkg_mode", [0, 1])
+def test_phase_a_depth_step(orc, idx, bkg_mode):
+    sc = _scenes_small()[idx]
+    z, prm, irf, st0, ctx, csr, fr = _phase_setup(orc, sc, bkg_mode=bkg_mode)
+    for first in (1, 0):
+        dev = state_to_device(st0)
+        ctx.phase(0, first, prm, csr, dev, shape=(sc.h, sc.w, sc.t))
+        g = np_of(dev)
+        o = st0.copy()
+        if not first:
+            orc.bkg_lowpass(sc.h, sc.w, prm, o.b)
+        orc.t_step(fr, irf, prm, o)
+        compare_clouds(g, o, sc.t, TOL_T, TOL_R, label=f"A first={first}")
+
+
+@pytest.mark.parametrize("idx", [0, 1, 4])
+@pytest.mark.parametrize("den", [1, 0])
+def test_phase_b_apss_and_intensity_step(orc, idx, den):
+    sc = _scenes_small()[idx]
+    z, prm, irf, st0, ctx, csr, fr = _phase_setup(orc, sc, depth_denoiser=den)
+    # start from a state after one depth step so that APSS has work to do
+    orc.t_step(fr, irf, prm, st0)
+    st0 = state_f32_rounded(orc, st0)
+    dev = state_to_device(st0)
+    ctx.phase(1, 0, prm, csr, dev, shape=(sc.h, sc.w, sc.t))
+    g = np_of(dev)
+    o = st0.copy()
+    if den:
+        orc.apss(sc.h, sc.w, sc.t, prm, o)
+    orc.r_step(fr, irf, prm, o)
+    compare_clouds(g, o, sc.t, TOL_T, TOL_R, label="B")
+
+
+@pytest.mark.parametrize("idx", [0, 1, 4])
+@pytest.mark.parametrize("den", [1, 0])
+def test_phase_c_intensity_lowpass_prune_and_background_step(orc, idx, den):
+    sc = _scenes_small()[idx]
+    z, prm, irf, st0, ctx, csr, fr = _phase_setup(orc, sc, intensity_denoiser=den)
+    orc.t_step(fr, irf, prm, st0)
+    orc.apss(sc.h, sc.w, sc.t, prm, st0)
+    orc.r_step(fr, irf, prm, st0)
+    st0 = state_f32_rounded(orc, st0)
+    dev = state_to_device(st0)
+    ctx.phase(2, 0, prm, csr, dev, shape=(sc.h, sc.w, sc.t))
+    g = np_of(dev)
+    o = st0.copy()
+    orc.int_lowpass(sc.h, sc.w, prm, o)
+    orc.b_step(fr, irf, prm, o)
+    compare_clouds(g, o, sc.t, TOL_T, TOL_R, label="C")
+
+
+@pytest.mark.parametrize("idx", range(5))
+def test_reconstruct_matches_oracle(orc, idx):
+    sc = _scenes_small()[idx]
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    g = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
+    o, probe = oracle_with_probe(orc, sc, z, prm)
+    ill = ill_conditioned(o, probe, TOL_T, TOL_R)
+    stats = compare_clouds(g, o, sc.t, TOL_T, TOL_R, ill=ill, max_ill_frac=0.02, label=sc.name)
+    assert g["n_points"] == int(g["alive"].sum())
+    print(sc.name, stats)
+
+
+@pytest.mark.parametrize("over", [dict(bkg_mode=1), dict(depth_denoiser=0, intensity_denoiser=0),
+                                  dict(k_max=4), dict(k_max=1, win_r=1), dict(n_iter=0),
+                                  dict(win_r=4, apss_radius=72.0, int_radius=72.0)])
+def test_reconstruct_options_match_oracle(orc, over):
+    sc = scenes.small_random(21, 19, 256, n_comp=2, seed=11)
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc, **over)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    g = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
+    o, probe = oracle_with_probe(orc, sc, z, prm)
+    ill = ill_conditioned(o, probe, TOL_T, TOL_R)
+    stats = compare_clouds(g, o, sc.t, TOL_T, TOL_R, ill=ill, max_ill_frac=0.02, label=str(over))
+    print(over, stats)
+
+
+def test_reconstruct_with_gain_and_dead_pixels(orc):
+    sc = scenes.small_random(16, 24, 256, n_comp=2, seed=12)
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    rng = np.random.default_rng(0)
+    gain = rng.uniform(0.6, 1.4, (sc.h, sc.w)).astype(np.float32)
+    gain[3, 5] = 0.0
+    gain[10, 0] = 0.0
+    torch = torch_mod()
+    prm = workload_params(sc)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    g = np_of(ctx.reconstruct(prm, dense=upload_u16(z), gain=torch.from_numpy(gain).cuda()))
+    o, probe = oracle_with_probe(orc, sc, z, prm, gain=gain.astype(np.float64))
+    ill = ill_conditioned(o, probe, TOL_T, TOL_R)
+    compare_clouds(g, o, sc.t, TOL_T, TOL_R, ill=ill, max_ill_frac=0.02, label="gain")
+    assert not g["alive"][:, 3, 5].any() and not g["alive"][:, 10, 0].any()
+
+
+def test_sparse_input_equals_dense_input(orc):
+    sc = scenes.small_random(13, 29, 300, n_comp=2, seed=4)
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    zd = upload_u16(z)
+    a = np_of(ctx.reconstruct(prm, dense=zd))
+    csr = ctx.compact(zd)
+    b = np_of(ctx.reconstruct(prm, csr=csr, shape=z.shape))
+    for k in ("t", "r", "alive", "b"):
+        assert np.array_equal(a[k], b[k]), k
+
+
+def test_batch_results_equal_single_frame_results(orc):
+    """Frames of mixed sizes in one batched call give bitwise the results of
+    reconstructing each alone."""
+    scs = [scenes.small_random(13, 29, 300, n_comp=2, seed=21),
+           scenes.small_random(32, 32, 256, n_comp=2, seed=22),
+           scenes.small_random(5, 70, 200, n_comp=2, seed=23),
+           scenes.small_random(1, 1, 64, n_comp=2, seed=24)]
+    irf = scenes.gaussian_irf(3.0, 12)
+    for s in scs:
+        s.irf = irf
+    zs = [orc.synthesize(scenes.sampling_tables(s)) for s in scs]
+    prm = workload_params(scs[0])
+    from paper_1905_06700_b300 import rt3d as R
+    ctx = R.Context(32, 70, 300, 2, irf.samples, irf.origin, max_batch=8)
+    singles = [np_of(ctx.reconstruct(prm, dense=upload_u16(z))) for z in zs]
+    batch = [np_of(o) for o in ctx.reconstruct_batch(prm, [dict(dense=upload_u16(z)) for z in zs])]
+    for s, b in zip(singles, batch):
+        for k in ("t", "r", "alive", "b", "n_points"):
+            assert np.array_equal(np.asarray(s[k]), np.asarray(b[k])), k
+
+
+def test_host_entry_point_equals_device_path(orc):
+    from paper_1905_06700_b300 import rt3d as R
+    sc = scenes.small_random(13, 29, 300, n_comp=2, seed=4)
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    a = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
+    b = R.reconstruct_host(ctx, prm, z)
+    for k in ("t", "r", "alive", "b"):
+        assert np.array_equal(a[k], b[k]), k
+    assert int(b["n_points"][0]) == a["n_points"]
+
+
+def test_capacity_overflow_is_reported_not_faulted(orc):
+    from paper_1905_06700_b300 import rt3d as R
+    sc = scenes.small_random(16, 16, 256, n_comp=2, seed=3)
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc)
+    ctx = make_ctx(sc, k=prm["k_max"], max_entries=int(np.count_nonzero(z)) // 2)
+    ctx.reconstruct(prm, dense=upload_u16(z))
+    assert ctx.device_status() == R.RT3D_E_CAPACITY
+    assert ctx.device_status() == R.RT3D_OK          # cleared after reading
+    ctx2 = make_ctx(sc, k=prm["k_max"])
+    ctx2.reconstruct(prm, dense=upload_u16(z))
+    assert ctx2.device_status() == R.RT3D_OK
+
+
+def test_empty_histograms_give_no_points(orc):
+    sc = scenes.small_random(7, 9, 128, n_comp=1, seed=1)
+    z = np.zeros((sc.h, sc.w, sc.t), np.uint16)
+    prm = workload_params(sc)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    g = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
+    assert g["n_points"] == 0 and not g["alive"].any()
+    np.testing.assert_allclose(g["b"], np.float32(prm["b_floor"]))
+
+
+def test_reconstruct_multisurface_full_size_matches_oracle(orc):
+    """The benchmark workload (141 x 141 x 4096, up to three surfaces per pixel)
+    at full size, every point compared."""
+    sc = scenes.net_object_wall()
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    g = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
+    o, probe = oracle_with_probe(orc, sc, z, prm)
+    ill = ill_conditioned(o, probe, TOL_T, TOL_R)
+    stats = compare_clouds(g, o, sc.t, TOL_T, TOL_R, ill=ill, max_ill_frac=0.02, label="full")
+    print("141x141x4096", stats)
