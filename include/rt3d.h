@@ -260,6 +260,28 @@ int64_t rt3d_launch_count(rt3d_ctx_t* ctx);
 rt3d_status rt3d_set_profiling(rt3d_ctx_t* ctx, int on);
 rt3d_status rt3d_kernel_times(rt3d_ctx_t* ctx, double* ms, int64_t* launches, int n, int reset);
 
+/* The whole method (as rt3d_reconstruct) without any allocation and without a
+ * context.  The paper has no counterpart: this entry point exists for callers
+ * that cannot allocate device memory when they run -- processing loops that
+ * reserve all memory at start-up for a fixed footprint, plugins whose host
+ * framework owns the device memory, processes under a strict memory quota.
+ * The kernels' scratch (sparse entries, half-step state, counters) lives in
+ * one static device array of about 8.8 MiB that the library reserves on every
+ * GPU that loads it, until the process exits.  Limits, checked on the host
+ * before anything is launched (RT3D_E_INVALID otherwise): h*w <= 16384
+ * pixels; with a dense histogram also h*w*t <= 2^21 bins; k_max <= RT3D_MAX_K.
+ * `irf` is a HOST pointer (normalised per call); frame and result pointers
+ * are DEVICE pointers owned by the caller; the work is enqueued on `stream`
+ * on the current CUDA device.  The first call on a device looks the array's
+ * device address up once (cudaGetSymbolAddress), so make that first call
+ * before any stream capture.  Every call shares the one array and reuses it
+ * from the previous call (the counters are cleared each call): calls whose
+ * work overlaps on the GPU -- on different streams, or from several threads
+ * -- race on it and must be ordered by the caller.  No cudaMalloc, cudaFree
+ * or other allocating routine is called. */
+rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_frame* f,
+                                     const rt3d_params* p, rt3d_result* out, void* stream);
+
 /* Copy the sparse representation built by the last initialisation out to
  * HOST buffers, for inspection: seg[p] = (start, count) per pixel of the
  * batch (in frame order) and ent[0..n_ent).  Synchronises `stream`. */

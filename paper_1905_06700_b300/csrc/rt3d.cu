@@ -814,3 +814,218 @@ rt3d_status rt3d_get_sparse(rt3d_ctx_t* c, uint32_t* seg_host, int64_t n_pix, ui
 }
 
 }  // extern "C"
+
+// ============================================================================
+// Reconstruction without any allocation (rt3d_reconstruct_noalloc).
+//
+// Callers that must not allocate device memory after start-up get the whole
+// method with its scratch in one file-scope device array, reserved when the
+// library is loaded and held by every GPU that loads it until the process
+// exits.  Its size bounds the frames this entry point accepts:
+//   pixels h*w <= kStaticMaxPixels, and for a dense histogram h*w*t <=
+//   kStaticMaxEntries (so that even a histogram with every bin nonzero fits
+//   the sparse-entry area; a caller's own sparse list needs no entry area).
+namespace {
+
+constexpr long long kStaticMaxPixels = 16384;            // e.g. 128 x 128
+constexpr long long kStaticMaxEntries = 1ll << 21;       // 8 MiB of entries
+constexpr long long kStaticEntBytes = 4 * kStaticMaxEntries;
+constexpr long long kStaticSegBytes = 8 * kStaticMaxPixels;
+constexpr long long kStaticHalfBytes = 4ll * RT3D_MAX_K * kStaticMaxPixels;   // t_half or r_half
+constexpr long long kStaticBBytes = 4 * kStaticMaxPixels;
+constexpr long long kStaticAliveBytes = (long long)RT3D_MAX_K * kStaticMaxPixels;
+constexpr long long kStaticOffSeg = kStaticEntBytes;
+constexpr long long kStaticOffT = kStaticOffSeg + kStaticSegBytes;
+constexpr long long kStaticOffR = kStaticOffT + kStaticHalfBytes;
+constexpr long long kStaticOffB = kStaticOffR + kStaticHalfBytes;
+constexpr long long kStaticOffA = kStaticOffB + kStaticBBytes;
+constexpr long long kStaticOffCount = (kStaticOffA + kStaticAliveBytes + 255) & ~255ll;
+constexpr long long kStaticOffStatus = kStaticOffCount + 256;
+constexpr long long kStaticBytes = kStaticOffStatus + 256;
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+constexpr int kStaticMaxDevices = 64;
+std::mutex g_static_mutex;
+unsigned char* g_static_ptr[kStaticMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (host code sees
+// only a host-side stand-in for the symbol, never usable as a device pointer).
+rt3d_status static_scratch(int device, unsigned char** out)
+{
+    if (device < 0 || device >= kStaticMaxDevices) return RT3D_E_INVALID;
+    std::lock_guard<std::mutex> lock(g_static_mutex);
+    if (!g_static_ptr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+        if (e != cudaSuccess || p == nullptr) return RT3D_E_CUDA;
+        g_static_ptr[device] = static_cast<unsigned char*>(p);
+    }
+    *out = g_static_ptr[device];
+    return RT3D_OK;
+}
+
+// The per-call tables of build_kparams, from a caller's IRF instead of a
+// context (normalised in double, summing in index order, on the stack).
+rt3d_status static_kparams(const rt3d_irf* irf, const rt3d_params* p, KParams* K)
+{
+    double hn[RT3D_MAX_IRF];
+    double sum = 0.0;
+    for (int s = 0; s < irf->len; ++s) {
+        if (!(irf->samples[s] >= 0.0) || !std::isfinite(irf->samples[s])) return RT3D_E_INVALID;
+        sum += irf->samples[s];
+    }
+    if (!(sum > 0.0)) return RT3D_E_INVALID;
+    for (int s = 0; s < irf->len; ++s) hn[s] = irf->samples[s] / sum;
+    std::memset(K, 0, sizeof(KParams));
+    K->n_iter = p->n_iter;
+    K->k = p->k_max;
+    K->t_step = p->t_step;
+    K->r_step = p->r_step;
+    K->b_step = p->b_step;
+    K->dt_max = p->dt_max;
+    K->eps_r = p->eps_r;
+    K->eps_b = p->eps_b;
+    K->b_floor = p->b_floor;
+    K->lam_floor = p->lam_floor;
+    K->pitch = p->pixel_pitch;
+    K->apss_h = p->apss_radius;
+    K->int_h = p->int_radius;
+    K->r_min = p->r_min;
+    K->merge_dist = p->merge_dist;
+    K->win_r = p->win_r;
+    K->apss_min_nb = p->apss_min_nb;
+    K->depth_den = p->depth_denoiser;
+    K->int_den = p->intensity_denoiser;
+    K->bkg_mode = p->bkg_mode;
+    K->bkg_rad = p->bkg_radius;
+    K->irf_len = irf->len;
+    K->irf_origin = irf->origin;
+    K->peak_sep = p->peak_sep;
+    K->peak_min_photons = p->peak_min_photons;
+    float fsum = 0.0f;
+    double hmax = 0.0;
+    for (int s = 0; s < irf->len; ++s) {
+        K->irf[s] = (float)hn[s];
+        fsum += K->irf[s];
+        if (hn[s] > hmax) hmax = hn[s];
+    }
+    K->irf_sum = fsum;
+    const double delta = (double)p->lmf_delta_rel * hmax;
+    const double scale = std::ldexp(1.0, p->lmf_frac_bits);
+    int kmax = 0;
+    for (int s = 0; s < irf->len; ++s) {
+        const double v = std::nearbyint(scale * std::log1p(hn[s] / delta));
+        if (v > 1e9) return RT3D_E_INVALID;
+        K->lmf[s] = (int)v;
+        if (K->lmf[s] > kmax) kmax = K->lmf[s];
+    }
+    K->lmf_kmax = kmax;
+    if (p->lmf_precision == RT3D_LMF_BF16 && kmax > 256) return RT3D_E_INVALID;
+    if (p->lmf_precision == RT3D_LMF_FP16 && kmax > 2048) return RT3D_E_INVALID;
+    if (p->bkg_mode == RT3D_BKG_LOWPASS) {
+        const double sg = (double)p->bkg_sigma;
+        double ks = 0.0;
+        double tap[2 * kMaxBkgR + 1];
+        for (int d = -p->bkg_radius; d <= p->bkg_radius; ++d) {
+            tap[d + p->bkg_radius] = std::exp(-(double)d * d / (2.0 * sg * sg));
+            ks += tap[d + p->bkg_radius];
+        }
+        for (int d = 0; d <= 2 * p->bkg_radius; ++d) K->bkg_ker[d] = (float)(tap[d] / ks);
+    }
+    return RT3D_OK;
+}
+
+}  // namespace
+
+extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_frame* f,
+                                                const rt3d_params* p, rt3d_result* out,
+                                                void* stream)
+{
+    if (!irf || !irf->samples || !f || !p || !out) return RT3D_E_INVALID;
+    if (!out->t || !out->r || !out->alive || !out->b) return RT3D_E_INVALID;
+    if (irf->len < 1 || irf->len > RT3D_MAX_IRF || irf->origin < 0 || irf->origin >= irf->len)
+        return RT3D_E_INVALID;
+    // limits of the static scratch, checked before anything is launched
+    const long long npix = (long long)f->h * f->w;
+    if (f->h < 1 || f->w < 1 || f->t < 1 || f->t > RT3D_MAX_T) return RT3D_E_INVALID;
+    if (npix > kStaticMaxPixels) return RT3D_E_INVALID;
+    const bool has_csr = f->csr_off != nullptr && f->csr_ent != nullptr;
+    if ((f->csr_off == nullptr) != (f->csr_ent == nullptr)) return RT3D_E_INVALID;
+    if (!has_csr && (!f->dense || npix * f->t > kStaticMaxEntries)) return RT3D_E_INVALID;
+    rt3d_config cfg{};
+    cfg.max_h = f->h;
+    cfg.max_w = f->w;
+    cfg.max_t = f->t;
+    cfg.k_max = RT3D_MAX_K;
+    cfg.max_batch = 1;
+    if (!params_ok(&cfg, p)) return RT3D_E_INVALID;
+    if (p->depth_denoiser == RT3D_DEPTH_LEARNED) return RT3D_E_UNIMPL;
+
+    int device = 0;
+    RT3D_CUDA(cudaGetDevice(&device));
+    unsigned char* base = nullptr;
+    rt3d_status st = static_scratch(device, &base);
+    if (st != RT3D_OK) return st;
+    KParams K;
+    st = static_kparams(irf, p, &K);
+    if (st != RT3D_OK) return st;
+
+    Work W{};
+    W.ent = reinterpret_cast<uint32_t*>(base);
+    W.seg = reinterpret_cast<uint2*>(base + kStaticOffSeg);
+    W.t_half = reinterpret_cast<float*>(base + kStaticOffT);
+    W.r_half = reinterpret_cast<float*>(base + kStaticOffR);
+    W.b_half = reinterpret_cast<float*>(base + kStaticOffB);
+    W.alive_b = base + kStaticOffA;
+    W.ent_count = reinterpret_cast<unsigned long long*>(base + kStaticOffCount);
+    W.ent_cap = kStaticMaxEntries;
+    W.stride = (int)kStaticMaxPixels;
+    W.status = reinterpret_cast<int*>(base + kStaticOffStatus);
+    W.y_out = nullptr;
+
+    Batch B;
+    std::memset(&B, 0, sizeof(Batch));
+    B.n = 1;
+    FrameDesc& d = B.f[0];
+    d.h = f->h;
+    d.w = f->w;
+    d.nt = f->t;
+    d.npix = (int)npix;
+    d.tiles_w = (f->w + kTileW - 1) / kTileW;
+    d.tile_base = 0;
+    d.pix_base = 0;
+    d.dense = f->dense;
+    d.csr_off = f->csr_off;
+    d.use_csr = has_csr;
+    d.ent = has_csr ? f->csr_ent : W.ent;
+    d.gain = f->gain;
+    d.t = out->t;
+    d.r = out->r;
+    d.alive = out->alive;
+    d.b = out->b;
+    d.n_points = out->n_points;
+    B.total_tiles = d.tiles_w * ((f->h + kTileH - 1) / kTileH);
+    B.total_pix = (int)npix;
+    B.max_t = f->t;
+
+    cudaStream_t s = (cudaStream_t)stream;
+    // the allocation cursor and the device status word start at zero every call
+    RT3D_CUDA(cudaMemsetAsync(W.ent_count, 0, sizeof(unsigned long long), s));
+    RT3D_CUDA(cudaMemsetAsync(W.status, 0, sizeof(int), s));
+    if (out->n_points) RT3D_CUDA(cudaMemsetAsync(out->n_points, 0, sizeof(int32_t), s));
+
+    const size_t smem = init_smem(K, B.max_t);
+    const int warps = init_warps(B.max_t);
+    auto init_fn = p->warm_start ? k_init<false, true> : k_init<false, false>;
+    RT3D_CUDA(cudaFuncSetAttribute(init_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    init_fn<<<(B.total_pix + warps - 1) / warps, warps * 32, smem, s>>>(K, B, W);
+    for (int it = 0; it < p->n_iter; ++it) {
+        k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, W, it == 0 ? 1 : 0);
+        k_phase_b<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, W);
+        k_phase_c<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, W);
+    }
+    k_final<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, W, p->n_iter > 0 ? 1 : 0);
+    RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}

@@ -119,6 +119,8 @@ def lib():
                                         C.c_int, C.c_int]),
         "rt3d_get_sparse": (C.c_int, [_P, _P, C.c_int64, _P, C.c_int64,
                                       C.POINTER(C.c_int64), _P]),
+        "rt3d_reconstruct_noalloc": (C.c_int, [C.POINTER(Irf), C.POINTER(Frame),
+                                               C.POINTER(Params), C.POINTER(Result), _P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -374,3 +376,15 @@ def reconstruct_host(ctx: Context, params, dense: np.ndarray, gain: Optional[np.
     check(lib().rt3d_reconstruct_host(ctx.handle, C.byref(fr), C.byref(p), C.byref(rs),
                                       _stream(stream)), "rt3d_reconstruct_host")
     return out
+
+
+def rt3d_reconstruct_noalloc(irf_samples, irf_origin: int, frame: Frame, params, result: Result,
+                             stream=None) -> int:
+    """The whole method with the library's static scratch: no context and no
+    allocation (for callers that must not allocate device memory while they
+    run).  Returns the rt3d status."""
+    samples = np.ascontiguousarray(irf_samples, dtype=np.float64)
+    irf = Irf(samples.ctypes.data_as(C.POINTER(C.c_double)), len(samples), int(irf_origin))
+    p = params_from(params)
+    return lib().rt3d_reconstruct_noalloc(C.byref(irf), C.byref(frame), C.byref(p),
+                                          C.byref(result), _stream(stream))
