@@ -235,7 +235,7 @@ def run_ours(args, world, rank, local):
         # ---------------- single-frame latency (batch of one)
         lat = []
         one = ctx.new_result(H, W, K)
-        for i in range(args.latency_frames + 3):
+        for i in range(args.latency_frames + 3 if args.latency_frames > 0 else 0):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -245,15 +245,17 @@ def run_ours(args, world, rank, local):
             if i >= 3:
                 lat.append(a.elapsed_time(b))
         lat.sort()
+        if not lat:
+            lat = [float("nan")]
 
         # ---------------- end to end through the host entry point
-        e2e = run_e2e(args, ctx, prm, dense, R)
+        e2e = run_e2e(args, ctx, prm, dense, R) if args.e2e_steps > 0 else None
 
         # ---------------- parity of the benchmark frame against the oracle
         parity = None if args.no_parity else bench_parity(prm, seeds[0], outs[0])
 
         # ---------------- the oracle on the host cores
-        cpu = None if world > 1 else cpu_baseline(args, prm)
+        cpu = None if (world > 1 or args.cpu_frames < 1) else cpu_baseline(args, prm)
 
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,

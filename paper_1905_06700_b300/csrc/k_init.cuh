@@ -1,31 +1,46 @@
 // k_init.cuh -- per-pixel initialisation (Methods, "3D Reconstruction
 // algorithm": the initialisation processes each pixel independently).
 //
-// One warp per pixel:
-//   1. dense histogram: stream the row (16-byte loads), count nonzero bins,
-//      reserve space in the workspace entry buffer with one atomic, re-read the
-//      row (L2-resident by then) and emit packed (bin << 16 | count) entries in
-//      bin order -- the sparse form the PALM loop iterates over;
-//      sparse input: take the caller's list as is;
-//   2. log-matched filter by scatter: every nonzero bin adds count * K_s to
-//      y(bin + origin - s) for the L taps (lanes over taps), together with a
-//      saturating window count; integer arithmetic, so exact;
+// One warp per pixel, bounded by the dense read (2 T bytes per pixel):
+//   1. stream the histogram row once with 16-byte loads; one vote per load
+//      finds the few 16-byte words holding a nonzero bin, which 8 lanes unpack
+//      into packed (bin << 16 | count) entries in a per-warp shared staging
+//      list, in bin order; one atomic reserves the pixel's span of the
+//      workspace entry buffer -- the sparse form the PALM loop iterates over.
+//      Rows with more nonzero bins than the staging list holds are re-read
+//      and emitted straight to global memory.  A caller's sparse list is used
+//      as is;
+//   2. log-matched filter by scatter, cluster by cluster: entries more than
+//      L - 1 + 2 sep bins apart cannot affect each other's filter values,
+//      peak tests or window counts, so the sorted entries split into
+//      independent clusters; a cluster with fewer photons than the peak
+//      threshold cannot hold a peak and is skipped (most isolated background
+//      photons).  For the others, the filter output of up to 256 positions
+//      plus a +-sep halo lives in shared memory; each entry adds count * K_s
+//      at bin + origin - s for the L taps (lanes over taps).  Integer
+//      arithmetic, so the output is exact;
 //   3. peak picking: strict-left / non-strict-right local maxima over +-sep
-//      with enough photons in the IRF window; the K largest (ties to the
-//      earlier bin) by a K-round warp arg-max; slots by increasing depth;
+//      (immediate neighbours first, then the window) with enough photons in
+//      the IRF window (summed from the chunk's entries); each lane keeps its K
+//      best, a K-round warp arg-max keeps the overall K largest (ties to the
+//      earlier bin); slots by increasing depth;
 //   4. b0 from the counts outside the kept windows, r0 from the window counts.
 #pragma once
 #include "rt3d_device.cuh"
 
 namespace rt3d {
 
-constexpr int kInitWarps = 4;                 // upper bound; fewer for long histograms
+constexpr int kInitWarps = 8;        // upper bound on warps per CTA
+constexpr int kInitChunk = 256;      // filter positions per chunk
+constexpr int kInitStage = 256;      // staged entries per warp
 constexpr int kInitSmemBudget = 200 * 1024;
 
-__host__ __device__ constexpr int init_warp_bytes(int tmax)
+__host__ __device__ constexpr int init_buf(int sep) { return kInitChunk + 2 * sep; }
+
+__host__ __device__ constexpr int init_warp_bytes(int sep)
 {
-    // int32 filter output + uint8 window counts, 16-byte aligned
-    return ((tmax * 4 + 15) & ~15) + ((tmax + 15) & ~15);
+    // staging list + int32 filter chunk, 16-byte aligned
+    return kInitStage * 4 + ((init_buf(sep) * 4 + 15) & ~15);
 }
 
 __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
@@ -38,13 +53,23 @@ __device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
     return v;
 }
 
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
+{
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t n = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += n;
+    }
+    return v;
+}
+
 template <bool kDumpY, bool kCompactOnly>
 __global__ void __launch_bounds__(kInitWarps * 32)
 k_init(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const Work W)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     int* sK = reinterpret_cast<int*>(smem);
-    const int L = P.irf_len, O = P.irf_origin;
+    const int L = P.irf_len, O = P.irf_origin, sep = P.peak_sep;
     const int k_bytes = (L * 4 + 15) & ~15;
     for (int i = threadIdx.x; i < L; i += blockDim.x) sK[i] = P.lmf[i];
     __syncthreads();
@@ -57,43 +82,75 @@ k_init(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const
     const int T = F.nt;
     const float g = F.gain ? F.gain[lp] : 1.0f;
 
+    unsigned char* wbase = smem + k_bytes + warp * init_warp_bytes(sep);
+    uint32_t* stage = reinterpret_cast<uint32_t*>(wbase);
+    int* Y = reinterpret_cast<int*>(wbase + kInitStage * 4);
+
     // ---- 1. sparse entries -------------------------------------------------
     uint32_t start = 0, nnz = 0;
     unsigned long long total = 0;
-    const uint32_t* ent;
+    const uint32_t* ent;                 // generic pointer: shared stage or global list
     if (F.csr_off) {
         start = F.csr_off[lp];
         nnz = F.csr_off[lp + 1] - start;
-        ent = F.ent;
-        for (uint32_t e = lane; e < nnz; e += 32) total += ent[start + e] & 0xffffu;
+        ent = F.ent + start;
     } else {
         const uint16_t* row = F.dense + (long long)lp * T;
-        const bool vec = (T & 7) == 0;
-        uint32_t my = 0;
-        if (vec) {
-            for (int v = lane; v < T / 8; v += 32) {
-                const uint4 q = reinterpret_cast<const uint4*>(row)[v];
-                const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+        uint32_t n_stage = 0;
+        bool overflow = false;
+        if ((T & 7) == 0) {
+            const uint4* row4 = reinterpret_cast<const uint4*>(row);
+            const int nv = T >> 3;
+            for (int v0 = 0; v0 < nv; v0 += 128) {
+                uint4 q[4];
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    my += ((w4[c] & 0xffffu) != 0) + ((w4[c] >> 16) != 0);
-                    total += (w4[c] & 0xffffu) + (w4[c] >> 16);
+                for (int u = 0; u < 4; ++u) {
+                    const int v = v0 + u * 32 + lane;
+                    q[u] = v < nv ? row4[v] : make_uint4(0, 0, 0, 0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    unsigned words = __ballot_sync(0xffffffffu, (q[u].x | q[u].y | q[u].z | q[u].w) != 0u);
+                    while (words) {
+                        // one nonzero 16-byte word (8 bins) of lane src: lanes 0..7 unpack a bin each
+                        const int src = __ffs(words) - 1;
+                        words &= words - 1;
+                        const uint32_t wx = __shfl_sync(0xffffffffu, q[u].x, src);
+                        const uint32_t wy = __shfl_sync(0xffffffffu, q[u].y, src);
+                        const uint32_t wz = __shfl_sync(0xffffffffu, q[u].z, src);
+                        const uint32_t ww = __shfl_sync(0xffffffffu, q[u].w, src);
+                        const int j = lane & 7;
+                        const uint32_t word = j < 2 ? wx : (j < 4 ? wy : (j < 6 ? wz : ww));
+                        const uint32_t val = (j & 1) ? (word >> 16) : (word & 0xffffu);
+                        const unsigned m = __ballot_sync(0xffffffffu, lane < 8 && val != 0u);
+                        const uint32_t bin = 8u * (uint32_t)(v0 + u * 32 + src) + (uint32_t)j;
+                        if (lane < 8 && val != 0u) {
+                            const uint32_t pos = n_stage + __popc(m & ((1u << lane) - 1u));
+                            if (pos < (uint32_t)kInitStage) stage[pos] = (bin << 16) | val;
+                        }
+                        n_stage += __popc(m);
+                    }
                 }
             }
+            overflow = n_stage > (uint32_t)kInitStage;
         } else {
-            for (int b = lane; b < T; b += 32) {
-                const uint32_t z = row[b];
-                my += z != 0;
-                total += z;
+            for (int b0 = 0; b0 < T; b0 += 32) {
+                const int b = b0 + lane;
+                const uint32_t val = b < T ? (uint32_t)row[b] : 0u;
+                const unsigned m = __ballot_sync(0xffffffffu, val != 0u);
+                if (val) {
+                    const uint32_t pos = n_stage + __popc(m & ((1u << lane) - 1u));
+                    if (pos < (uint32_t)kInitStage) stage[pos] = ((uint32_t)b << 16) | val;
+                }
+                n_stage += __popc(m);
             }
+            overflow = n_stage > (uint32_t)kInitStage;
         }
-        uint32_t tot_nnz = my;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) tot_nnz += __shfl_xor_sync(0xffffffffu, tot_nnz, o);
+        nnz = n_stage;
         unsigned long long base = 0;
         if (lane == 0) {
-            base = atomicAdd(W.ent_count, (unsigned long long)tot_nnz);
-            if (base + tot_nnz > (unsigned long long)W.ent_cap) {
+            base = atomicAdd(W.ent_count, (unsigned long long)nnz);
+            if (base + nnz > (unsigned long long)W.ent_cap) {
                 atomicOr(W.status, kStatusCapacity);
                 base = ~0ull;
             }
@@ -102,128 +159,149 @@ k_init(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const
         if (base == ~0ull) {
             nnz = 0;
             start = 0;
-        } else {
+            ent = stage;
+        } else if (!overflow) {
             start = (uint32_t)base;
-            nnz = tot_nnz;
+            for (uint32_t e = lane; e < nnz; e += 32) W.ent[start + e] = stage[e];
+            ent = stage;
+        } else {
+            // more nonzero bins than the stage holds: re-read and emit to global
+            start = (uint32_t)base;
             uint32_t cursor = start;
-            // re-read in the same order and emit bins in increasing order
-            if (vec) {
-                for (int v0 = 0; v0 < T / 8; v0 += 32) {
-                    const int v = v0 + lane;
-                    uint32_t w4[4] = {0, 0, 0, 0};
-                    if (v < T / 8) {
-                        const uint4 q = reinterpret_cast<const uint4*>(row)[v];
-                        w4[0] = q.x; w4[1] = q.y; w4[2] = q.z; w4[3] = q.w;
-                    }
-                    uint32_t c = 0;
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) c += ((w4[s] & 0xffffu) != 0) + ((w4[s] >> 16) != 0);
-                    uint32_t incl = c;
-#pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        const uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
-                        if (lane >= o) incl += n;
-                    }
-                    uint32_t pos = cursor + incl - c;
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) {
-                        const uint32_t zl = w4[s] & 0xffffu, zh = w4[s] >> 16;
-                        const uint32_t b = 8u * v + 2u * s;
-                        if (zl) W.ent[pos++] = (b << 16) | zl;
-                        if (zh) W.ent[pos++] = ((b + 1) << 16) | zh;
-                    }
-                    cursor += __shfl_sync(0xffffffffu, incl, 31);
-                }
-            } else {
-                for (int b0 = 0; b0 < T; b0 += 32) {
-                    const int b = b0 + lane;
-                    const uint32_t z = b < T ? row[b] : 0u;
-                    const unsigned m = __ballot_sync(0xffffffffu, z != 0);
-                    if (z) W.ent[cursor + __popc(m & ((1u << lane) - 1u))] = ((uint32_t)b << 16) | z;
-                    cursor += __popc(m);
-                }
+            for (int b0 = 0; b0 < T; b0 += 32) {
+                const int b = b0 + lane;
+                const uint32_t z = b < T ? row[b] : 0u;
+                const unsigned m = __ballot_sync(0xffffffffu, z != 0);
+                if (z) W.ent[cursor + __popc(m & ((1u << lane) - 1u))] = ((uint32_t)b << 16) | z;
+                cursor += __popc(m);
             }
+            ent = W.ent + start;
         }
-        ent = W.ent;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
     if (lane == 0) W.seg[pix] = make_uint2(start, nnz);
     if (kCompactOnly) return;
     __syncwarp();   // entries written by this warp are read back below
+
+    // photons of the pixel
+    for (uint32_t e = lane; e < nnz; e += 32) total += ent[e] & 0xffffu;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) total += __shfl_xor_sync(0xffffffffu, total, o);
 
     // exact-arithmetic guard: every filter value must fit in int32
     const bool in_range = total * (unsigned long long)P.lmf_kmax < (1ull << 31);
     if (!in_range && lane == 0) atomicOr(W.status, kStatusRange);
     const bool active = in_range && g > 0.0f;
 
-    // ---- 2. log-matched filter (scatter) -----------------------------------
-    unsigned char* wbase = smem + k_bytes + warp * init_warp_bytes(B.max_t);
-    int* Y = reinterpret_cast<int*>(wbase);
-    uint8_t* Wc = wbase + ((B.max_t * 4 + 15) & ~15);
-    {
-        int4* y4 = reinterpret_cast<int4*>(Y);
-        for (int i = lane; i < (T + 3) / 4; i += 32) y4[i] = make_int4(0, 0, 0, 0);
-        uint4* w4 = reinterpret_cast<uint4*>(Wc);
-        for (int i = lane; i < (T + 15) / 16; i += 32) w4[i] = make_uint4(0, 0, 0, 0);
-    }
-    __syncwarp();
-    if (active || kDumpY) {
-        for (uint32_t e0 = 0; e0 < nnz; e0 += 32) {
-            const uint32_t mine = (e0 + lane < nnz) ? ent[start + e0 + lane] : 0u;
-            const int cnt = (int)min(32u, nnz - e0);
-            for (int j = 0; j < cnt; ++j) {
-                const uint32_t v = __shfl_sync(0xffffffffu, mine, j);
-                const int bin = (int)(v >> 16), z = (int)(v & 0xffffu);
-                for (int s = lane; s < L; s += 32) {
-                    const int tau = bin + O - s;
-                    if (tau >= 0 && tau < T) {
-                        Y[tau] += z * sK[s];
-                        Wc[tau] = (uint8_t)min((int)Wc[tau] + z, 255);
-                    }
-                }
-                __syncwarp();
-            }
-        }
-    }
-    if (kDumpY) {
-        for (int i = lane; i < T; i += 32) W.y_out[(long long)lp * T + i] = Y[i];
-        return;
-    }
-
-    // ---- 3. peak picking ---------------------------------------------------
-    const int K = P.k, sep = P.peak_sep;
+    // ---- 2 + 3. chunked matched filter and peak candidates ------------------
+    const int K = P.k;
     int by[kMaxK], bt[kMaxK];
     int nb = 0;
 #pragma unroll
     for (int k = 0; k < kMaxK; ++k) { by[k] = 0; bt[k] = 0; }
-    if (active) {
-        for (int tau = lane; tau < T; tau += 32) {
-            const int y = Y[tau];
-            if (y <= 0 || (int)Wc[tau] < P.peak_min_photons) continue;
-            bool ok = true;
-            const int qlo = max(0, tau - sep), qhi = min(T - 1, tau + sep);
-            for (int q = tau - 1; q >= qlo; --q)
-                if (Y[q] >= y) { ok = false; break; }
-            if (ok)
-                for (int q = tau + 1; q <= qhi; ++q)
-                    if (Y[q] > y) { ok = false; break; }
-            if (!ok) continue;
-            // insert into this lane's list (y descending; equal y keeps the earlier bin first)
-            int pos = nb;
+    const int nbuf = init_buf(sep);
+    const int gap = L - 1 + 2 * sep;     // entries farther apart never interact
+    if (kDumpY)
+        for (int i = lane; i < T; i += 32) W.y_out[(long long)lp * T + i] = 0;
+    uint32_t c_lo = (active || kDumpY) ? 0u : nnz;
+    while (c_lo < nnz) {
+        // the cluster [c_lo, c_hi): consecutive entries at most `gap` bins apart
+        uint32_t c_hi = c_lo;
+        unsigned long long cl_tot = 0;
+        while (true) {
+            const uint32_t e = c_hi + lane;
+            const bool in = e < nnz;
+            const uint32_t v = in ? ent[e] : 0u;
+            const bool brk = in && e + 1 < nnz && (int)(ent[e + 1] >> 16) - (int)(v >> 16) > gap;
+            const unsigned mb = __ballot_sync(0xffffffffu, brk);
+            const unsigned mi = __ballot_sync(0xffffffffu, in);
+            // entries up to and including the first break belong to the cluster
+            const int take = mb ? (__ffs(mb)) : __popc(mi);
+            uint32_t cnt = (lane < take) ? (v & 0xffffu) : 0u;
 #pragma unroll
-            for (int k = kMaxK - 1; k >= 0; --k)
-                if (k < nb && by[k] < y) pos = k;
-            if (pos >= K) continue;
+            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+            cl_tot += cnt;
+            c_hi += take;
+            if (mb || take < 32) break;
+        }
+        const uint32_t e_first = c_lo, e_last = c_hi - 1;
+        c_lo = c_hi;
+        if (!kDumpY && cl_tot < (unsigned long long)P.peak_min_photons) continue;
+        const int lo = max(0, (int)(ent[e_first] >> 16) + O - L + 1);
+        const int hi = min(T - 1, (int)(ent[e_last] >> 16) + O);
+        uint32_t e_lo = e_first;
+        for (int cbase = lo; cbase <= hi; cbase += kInitChunk) {
+            // cluster entries reaching [cbase - sep, cbase + chunk + sep)
+            const int lo_b = cbase - sep - O;
+            const int hi_b = cbase + kInitChunk - 1 + sep - O + L - 1;
+            while (e_lo <= e_last) {
+                const uint32_t e = e_lo + lane;
+                const bool below = e <= e_last && (int)(ent[e] >> 16) < lo_b;
+                const unsigned m = __ballot_sync(0xffffffffu, below);
+                e_lo += __popc(m);
+                if (m != 0xffffffffu) break;
+            }
+            uint32_t e_hi = e_lo;
+            while (e_hi <= e_last) {
+                const uint32_t e = e_hi + lane;
+                const bool in = e <= e_last && (int)(ent[e] >> 16) <= hi_b;
+                const unsigned m = __ballot_sync(0xffffffffu, in);
+                e_hi += __popc(m);
+                if (m != 0xffffffffu) break;
+            }
+            const int cend = min(cbase + kInitChunk, hi + 1);
+            for (int i = lane; i < nbuf; i += 32) Y[i] = 0;
+            __syncwarp();
+            const int blo = max(0, cbase - sep), bhi = min(T, cbase + kInitChunk + sep);
+            for (uint32_t e = e_lo; e < e_hi; ++e) {
+                const uint32_t v = ent[e];
+                const int bin = (int)(v >> 16), z = (int)(v & 0xffffu);
+                for (int s = lane; s < L; s += 32) {
+                    const int tau = bin + O - s;
+                    if (tau >= blo && tau < bhi) Y[tau - cbase + sep] += z * sK[s];
+                }
+                __syncwarp();
+            }
+            if (kDumpY) {
+                for (int i = lane; cbase + i < cend; i += 32)
+                    W.y_out[(long long)lp * T + cbase + i] = Y[i + sep];
+                __syncwarp();
+                continue;
+            }
+            for (int i = lane; cbase + i < cend; i += 32) {
+                const int tau = cbase + i, yi = i + sep;
+                const int y = Y[yi];
+                if (y <= 0) continue;
+                if (sep > 0 && !(Y[yi - 1] < y && Y[yi + 1] <= y)) continue;   // immediate neighbours
+                bool ok = true;
+                for (int q = 2; q <= sep && ok; ++q) ok = Y[yi - q] < y && Y[yi + q] <= y;
+                if (!ok) continue;
+                // photons in the IRF window [tau - origin, tau - origin + L)
+                int wcount = 0;
+                for (uint32_t e = e_first; e <= e_last && wcount < P.peak_min_photons; ++e) {
+                    const uint32_t v = ent[e];
+                    const int bin = (int)(v >> 16);
+                    if (bin >= tau - O && bin <= tau - O + L - 1) wcount += (int)(v & 0xffffu);
+                }
+                if (wcount < P.peak_min_photons) continue;
+                // insert into this lane's list (y descending; equal y keeps the earlier bin first)
+                int pos = nb;
 #pragma unroll
-            for (int k = kMaxK - 1; k > 0; --k)
-                if (k > pos && k < K) { by[k] = by[k - 1]; bt[k] = bt[k - 1]; }
+                for (int k = kMaxK - 1; k >= 0; --k)
+                    if (k < nb && by[k] < y) pos = k;
+                if (pos >= K) continue;
 #pragma unroll
-            for (int k = 0; k < kMaxK; ++k)
-                if (k == pos) { by[k] = y; bt[k] = tau; }
-            if (nb < K) ++nb;
+                for (int k = kMaxK - 1; k > 0; --k)
+                    if (k > pos && k < K) { by[k] = by[k - 1]; bt[k] = bt[k - 1]; }
+#pragma unroll
+                for (int k = 0; k < kMaxK; ++k)
+                    if (k == pos) { by[k] = y; bt[k] = tau; }
+                if (nb < K) ++nb;
+            }
+            __syncwarp();
         }
     }
+    if (kDumpY) return;
+
     // K-round warp arg-max: key = (y << 32) | ~tau  (largest y, then smallest tau)
     int sel[kMaxK];
     int nsel = 0;
@@ -248,7 +326,7 @@ k_init(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const
     unsigned long long inside = 0;
     unsigned long long wsum[kMaxK] = {0, 0, 0, 0};
     for (uint32_t e = lane; e < nnz; e += 32) {
-        const uint32_t v = ent[start + e];
+        const uint32_t v = ent[e];
         const int bin = (int)(v >> 16);
         const unsigned z = v & 0xffffu;
         bool any = false;

@@ -191,48 +191,61 @@ k_phase_a(const __grid_constant__ KParams P, const __grid_constant__ Batch B, co
 }
 
 // ----------------------------------------------------------------------------
+constexpr int kHaloH = kTileH + 2 * kMaxWinR, kHaloW = kTileW + 2 * kMaxWinR;
+constexpr int kHalo = kHaloH * kHaloW;
+
 // APSS projection of one point (Results, "Depth update"; Guennebaud & Gross):
 // weighted algebraic-sphere fit s(x) = u0 + u1 x + u2 y + z + u4 |x|^2 over
 // the window (local coordinates scaled by 1/h), solved in centred form --
 // the 3x3 normal equations of (x, y, |x|^2) against z, then u0 from the
 // weighted means -- and projection along the line of sight onto s = 0.
-template <int HW>
-__device__ float apss_point(const float* st, const uint8_t* sa, int hstride, int R, int K,
-                            int ci, int cj, float tn, const KParams& P, int T)
+// The accumulation is branch-free: dead or absent slots hold a far sentinel
+// depth, so their weight is exactly zero; window offsets outside the lateral
+// radius are skipped uniformly across the warp.
+__device__ float apss_point(const float* st, int hstride, int R, int K, int ci, int cj, float tn,
+                            const KParams& P, int T)
 {
     const float inv_h = 1.0f / P.apss_h;
     const float px = P.pitch * inv_h;
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sz = 0.f, Sq = 0.f;
     float Sxx = 0.f, Sxy = 0.f, Syy = 0.f, Sxq = 0.f, Syq = 0.f, Sqq = 0.f;
     float Sxz = 0.f, Syz = 0.f, Sqz = 0.f;
-    int nw = 0, si = 0, sj = 0, sii = 0, sjj = 0, sij = 0;
+    // indicator sums of the pixel offsets of weighted neighbours (exact integers)
+    float nw = 0.f, si = 0.f, sj = 0.f, sii = 0.f, sjj = 0.f, sij = 0.f;
     for (int di = -R; di <= R; ++di) {
         const float y = (float)di * px;
         for (int dj = -R; dj <= R; ++dj) {
             const float x = (float)dj * px;
             const float r2 = x * x + y * y;
+            if (!(r2 < 1.0f)) continue;
             const int q = (ci + di) * hstride + (cj + dj);
             for (int m = 0; m < K; ++m) {
-                if (!sa[m * HW + q]) continue;
-                const float z = (st[m * HW + q] - tn) * inv_h;
+                const float z = (st[m * kHalo + q] - tn) * inv_h;
                 const float d2 = r2 + z * z;
-                if (!(d2 < 1.0f)) continue;
+                const bool in = d2 < 1.0f;
                 float w = 1.0f - d2;
                 w *= w;
-                w *= w;
+                w = in ? w * w : 0.0f;
+                const float ind = in ? 1.0f : 0.0f;
                 const float wx = w * x, wy = w * y, wq = w * d2;
                 S0 += w; Sx += wx; Sy += wy; Sz += w * z; Sq += wq;
                 Sxx += wx * x; Sxy += wx * y; Syy += wy * y;
                 Sxq += wx * d2; Syq += wy * d2; Sqq += wq * d2;
                 Sxz += wx * z; Syz += wy * z; Sqz += wq * z;
-                ++nw; si += di; sj += dj; sii += di * di; sjj += dj * dj; sij += di * dj;
+                nw += ind;
+                si += ind * (float)di;
+                sj += ind * (float)dj;
+                sii += ind * (float)(di * di);
+                sjj += ind * (float)(dj * dj);
+                sij += ind * (float)(di * dj);
             }
         }
     }
-    if (nw < P.apss_min_nb) return tn;
-    const long long vii = (long long)nw * sii - (long long)si * si;
-    const long long vjj = (long long)nw * sjj - (long long)sj * sj;
-    const long long vij = (long long)nw * sij - (long long)si * sj;
+    const long long n = (long long)nw;
+    if (n < P.apss_min_nb) return tn;
+    const long long vii = n * (long long)sii - (long long)si * (long long)si;
+    const long long vjj = n * (long long)sjj - (long long)sj * (long long)sj;
+    const long long vij = n * (long long)sij - (long long)si * (long long)sj;
     if (vii * vjj - vij * vij == 0) return tn;      // collinear pixel offsets
     const float iw = 1.0f / S0;
     const float mx = Sx * iw, my = Sy * iw, mz = Sz * iw, mq = Sq * iw;
@@ -263,33 +276,56 @@ __device__ float apss_point(const float* st, const uint8_t* sa, int hstride, int
     return clampf(tn + P.apss_h * zs, 0.0f, (float)(T - 1));
 }
 
-constexpr int kHaloH = kTileH + 2 * kMaxWinR, kHaloW = kTileW + 2 * kMaxWinR;
-constexpr int kHalo = kHaloH * kHaloW;
+constexpr float kDeadDepth = -1.0e12f;   // sentinel depth of dead or absent slots
 
-// Load a [k] plane set of float/alive values for the tile plus halo R.
-__device__ __forceinline__ void load_halo(const TileCtx& c, const FrameDesc& F, int R, int K,
-                                          const float* src, long long src_stride, int src_off,
-                                          const uint8_t* asrc, long long a_stride, int a_off,
-                                          float* st, uint8_t* sa)
+// Depths of the tile plus halo R; dead slots and pixels outside the frame get
+// the sentinel depth.
+__device__ __forceinline__ void load_halo_depth(const TileCtx& c, const FrameDesc& F, int R, int K,
+                                                const float* src, long long src_stride, int src_off,
+                                                const uint8_t* asrc, long long a_stride, float* st)
 {
     const int hh = kTileH + 2 * R, hw = kTileW + 2 * R;
     for (int idx = threadIdx.x; idx < hh * hw; idx += blockDim.x) {
         const int hi = idx / hw, hj = idx % hw;
         const int gi = c.i0 - R + hi, gj = c.j0 - R + hj;
-        const int q = hi * (kTileW + 2 * R) + hj;
         const bool in = gi >= 0 && gi < F.h && gj >= 0 && gj < F.w;
         const int lp = in ? gi * F.w + gj : 0;
         for (int m = 0; m < K; ++m) {
-            uint8_t a = 0;
-            float v = 0.0f;
-            if (in) {
-                a = asrc[(long long)m * a_stride + a_off + lp];
-                v = src[(long long)m * src_stride + src_off + lp];
-            }
-            sa[m * kHalo + q] = a;
-            st[m * kHalo + q] = v;
+            float v = kDeadDepth;
+            if (in && asrc[(long long)m * a_stride + lp]) v = src[(long long)m * src_stride + src_off + lp];
+            st[m * kHalo + idx] = v;
         }
     }
+}
+
+// Alive points of the tile's own pixels, as (local pixel << 2 | slot).
+__device__ __forceinline__ int compact_points(const float* st, int R, int K, bool inb, int li, int lj,
+                                              unsigned short* pts, int* s_warp)
+{
+    const int hstride = kTileW + 2 * R;
+    const int q0 = (li + R) * hstride + (lj + R);
+    int mine = 0;
+    if (inb)
+        for (int k = 0; k < K; ++k) mine += st[k * kHalo + q0] != kDeadDepth;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = mine;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += n;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    int before = 0, total = 0;
+    for (int w = 0; w < kTileThreads / 32; ++w) {
+        if (w < warp) before += s_warp[w];
+        total += s_warp[w];
+    }
+    int pos = before + incl - mine;
+    if (inb)
+        for (int k = 0; k < K; ++k)
+            if (st[k * kHalo + q0] != kDeadDepth) pts[pos++] = (unsigned short)((threadIdx.x << 2) | k);
+    return total;
 }
 
 // ----------------------------------------------------------------------------
@@ -299,28 +335,36 @@ k_phase_b(const __grid_constant__ KParams P, const __grid_constant__ Batch B, co
 {
     __shared__ float pad[kMaxIrf + 2 * kIrfPad];
     __shared__ float st[kMaxK * kHalo];
-    __shared__ uint8_t sa[kMaxK * kHalo];
     __shared__ float s_tn[kMaxK][kTileThreads];
+    __shared__ unsigned short s_pts[kMaxK * kTileThreads];
+    __shared__ int s_warp[kTileThreads / 32];
     load_irf(pad, P);
     const TileCtx c = tile_ctx(B);
     const FrameDesc& F = B.f[c.fi];
     const int np = F.npix, S = W.stride, R = P.win_r, K = P.k;
-    load_halo(c, F, R, K, W.t_half, S, F.pix_base, F.alive, np, 0, st, sa);
+    load_halo_depth(c, F, R, K, W.t_half, S, F.pix_base, F.alive, np, st);
     __syncthreads();
     const int hstride = kTileW + 2 * R;
-    if (c.inb) {
-        const int lp = c.gi * F.w + c.gj;
-        const int ci = c.li + R, cj = c.lj + R;
-        for (int k = 0; k < K; ++k) {
-            const int q = ci * hstride + cj;
-            float tn = st[k * kHalo + q];
-            if (sa[k * kHalo + q] && P.depth_den == RT3D_DEPTH_APSS)
-                tn = apss_point<kHalo>(st, sa, hstride, R, K, ci, cj, tn, P, F.nt);
-            s_tn[k][threadIdx.x] = tn;
-            F.t[(long long)k * np + lp] = tn;
+    const int q0 = (c.li + R) * hstride + (c.lj + R);
+    for (int k = 0; k < K; ++k) s_tn[k][threadIdx.x] = st[k * kHalo + q0];
+    const int n_pts = compact_points(st, R, K, c.inb, c.li, c.lj, s_pts, s_warp);
+    __syncthreads();
+    if (P.depth_den == RT3D_DEPTH_APSS) {
+        for (int i = threadIdx.x; i < n_pts; i += kTileThreads) {
+            const int px = s_pts[i] >> 2, k = s_pts[i] & 3;
+            const int ci = px / kTileW + R, cj = px % kTileW + R;
+            s_tn[k][px] = apss_point(st, hstride, R, K, ci, cj, st[k * kHalo + ci * hstride + cj], P, F.nt);
         }
     }
     __syncthreads();
+    if (c.inb) {
+        const int lp = c.gi * F.w + c.gj;
+        for (int k = 0; k < K; ++k) {
+            const float v = s_tn[k][threadIdx.x];
+            // dead slots keep the depth they had
+            F.t[(long long)k * np + lp] = v == kDeadDepth ? W.t_half[(long long)k * S + F.pix_base + lp] : v;
+        }
+    }
 
     const int grp = threadIdx.x / kG, gl = threadIdx.x % kG;
     const unsigned gmask = 0xffu << ((threadIdx.x & 31) & ~(kG - 1));
@@ -328,15 +372,15 @@ k_phase_b(const __grid_constant__ KParams P, const __grid_constant__ Batch B, co
         const int qi = c.i0 + q / kTileW, qj = c.j0 + q % kTileW;
         if (qi >= F.h || qj >= F.w) continue;
         const int qlp = qi * F.w + qj, qwp = F.pix_base + qlp;
-        const int hq = (q / kTileW + R) * hstride + (q % kTileW + R);
         float tk[kMaxK], rk[kMaxK];
         bool ak[kMaxK];
 #pragma unroll
         for (int k = 0; k < kMaxK; ++k) {
             const bool in = k < K;
-            tk[k] = in ? s_tn[k][q] : 0.0f;
+            const float v = in ? s_tn[k][q] : kDeadDepth;
+            ak[k] = v != kDeadDepth;
+            tk[k] = ak[k] ? v : 0.0f;
             rk[k] = in ? F.r[(long long)k * np + qlp] : 0.0f;
-            ak[k] = in && sa[k * kHalo + hq];
         }
         const float g = F.gain ? F.gain[qlp] : 1.0f;
         float sh[kMaxK], sdh[kMaxK], sz;
@@ -367,16 +411,16 @@ k_phase_c(const __grid_constant__ KParams P, const __grid_constant__ Batch B, co
     __shared__ float pad[kMaxIrf + 2 * kIrfPad];
     __shared__ float st[kMaxK * kHalo];
     __shared__ float sr[kMaxK * kHalo];
-    __shared__ uint8_t sa[kMaxK * kHalo];
     __shared__ float s_rn[kMaxK][kTileThreads];
     __shared__ uint8_t s_an[kMaxK][kTileThreads];
+    __shared__ unsigned short s_pts[kMaxK * kTileThreads];
+    __shared__ int s_warp[kTileThreads / 32];
     load_irf(pad, P);
     const TileCtx c = tile_ctx(B);
     const FrameDesc& F = B.f[c.fi];
     const int np = F.npix, S = W.stride, R = P.win_r, K = P.k;
-    load_halo(c, F, R, K, F.t, np, 0, F.alive, np, 0, st, sa);
+    load_halo_depth(c, F, R, K, F.t, np, 0, F.alive, np, st);
     {
-        // r_half for the same halo (alive already loaded)
         const int hh = kTileH + 2 * R, hw = kTileW + 2 * R;
         for (int idx = threadIdx.x; idx < hh * hw; idx += blockDim.x) {
             const int hi = idx / hw, hj = idx % hw;
@@ -389,44 +433,51 @@ k_phase_c(const __grid_constant__ KParams P, const __grid_constant__ Batch B, co
     }
     __syncthreads();
     const int hstride = kTileW + 2 * R;
-    if (c.inb) {
-        const int lp = c.gi * F.w + c.gj, wp = F.pix_base + lp;
-        const int ci = c.li + R, cj = c.lj + R, q0 = ci * hstride + cj;
+    const int q0 = (c.li + R) * hstride + (c.lj + R);
+    for (int k = 0; k < K; ++k) {
+        const bool al = st[k * kHalo + q0] != kDeadDepth;
+        s_an[k][threadIdx.x] = 0;
+        s_rn[k][threadIdx.x] = al ? sr[k * kHalo + q0] : (c.inb ? F.r[(long long)k * np + c.gi * F.w + c.gj] : 0.0f);
+    }
+    const int n_pts = compact_points(st, R, K, c.inb, c.li, c.lj, s_pts, s_warp);
+    __syncthreads();
+    {
         const float inv_h = 1.0f / P.int_h, px = P.pitch * inv_h;
-        for (int k = 0; k < K; ++k) {
-            uint8_t an = 0;
-            float rn = F.r[(long long)k * np + lp];
-            if (sa[k * kHalo + q0]) {
-                float rbar = sr[k * kHalo + q0];
-                if (P.int_den) {
-                    const float tn = st[k * kHalo + q0];
-                    float num = 0.0f, den = 0.0f;
-                    for (int di = -R; di <= R; ++di) {
-                        const float y = (float)di * px;
-                        for (int dj = -R; dj <= R; ++dj) {
-                            const float x = (float)dj * px;
-                            const int q = (ci + di) * hstride + (cj + dj);
-                            for (int m = 0; m < K; ++m) {
-                                if (!sa[m * kHalo + q]) continue;
-                                const float z = (st[m * kHalo + q] - tn) * inv_h;
-                                const float d2 = x * x + y * y + z * z;
-                                if (!(d2 < 1.0f)) continue;
-                                float w = 1.0f - d2;
-                                w *= w;
-                                w *= w;
-                                num += w * sr[m * kHalo + q];
-                                den += w;
-                            }
+        for (int i = threadIdx.x; i < n_pts; i += kTileThreads) {
+            const int pxl = s_pts[i] >> 2, k = s_pts[i] & 3;
+            const int ci = pxl / kTileW + R, cj = pxl % kTileW + R;
+            const int qc = ci * hstride + cj;
+            float rbar = sr[k * kHalo + qc];
+            if (P.int_den) {
+                const float tn = st[k * kHalo + qc];
+                float num = 0.0f, den = 0.0f;
+                for (int di = -R; di <= R; ++di) {
+                    const float y = (float)di * px;
+                    for (int dj = -R; dj <= R; ++dj) {
+                        const float x = (float)dj * px;
+                        const float r2 = x * x + y * y;
+                        if (!(r2 < 1.0f)) continue;
+                        const int q = (ci + di) * hstride + (cj + dj);
+                        for (int m = 0; m < K; ++m) {
+                            const float z = (st[m * kHalo + q] - tn) * inv_h;
+                            const float d2 = r2 + z * z;
+                            float w = 1.0f - d2;
+                            w *= w;
+                            w = d2 < 1.0f ? w * w : 0.0f;
+                            num += w * sr[m * kHalo + q];
+                            den += w;
                         }
                     }
-                    rbar = num / den;
                 }
-                rn = rbar;
-                an = rbar >= P.r_min ? 1 : 0;
+                rbar = num / den;
             }
-            s_rn[k][threadIdx.x] = rn;
-            s_an[k][threadIdx.x] = an;
+            s_rn[k][pxl] = rbar;
+            s_an[k][pxl] = rbar >= P.r_min ? 1 : 0;
         }
+    }
+    __syncthreads();
+    if (c.inb) {
+        const int lp = c.gi * F.w + c.gj, wp = F.pix_base + lp;
         // same-pixel points closer than merge_dist are one surface: the weaker
         // (the later slot on a tie) is removed and its intensity added to the other
         for (int a = 0; a < K; ++a)
@@ -440,7 +491,7 @@ k_phase_c(const __grid_constant__ KParams P, const __grid_constant__ Batch B, co
                 s_an[drop][threadIdx.x] = 0;
             }
         for (int k = 0; k < K; ++k) {
-            if (sa[k * kHalo + q0]) F.r[(long long)k * np + lp] = s_rn[k][threadIdx.x];
+            if (st[k * kHalo + q0] != kDeadDepth) F.r[(long long)k * np + lp] = s_rn[k][threadIdx.x];
             W.alive_b[(long long)k * S + wp] = s_an[k][threadIdx.x];
         }
     }
@@ -458,9 +509,9 @@ k_phase_c(const __grid_constant__ KParams P, const __grid_constant__ Batch B, co
 #pragma unroll
         for (int k = 0; k < kMaxK; ++k) {
             const bool in = k < K;
-            tk[k] = in ? st[k * kHalo + hq] : 0.0f;
-            rk[k] = in ? s_rn[k][q] : 0.0f;
             ak[k] = in && s_an[k][q];
+            tk[k] = ak[k] ? st[k * kHalo + hq] : 0.0f;
+            rk[k] = in ? s_rn[k][q] : 0.0f;
         }
         const float g = F.gain ? F.gain[qlp] : 1.0f;
         const float b = F.b[qlp];

@@ -147,7 +147,7 @@ bool params_ok(const rt3d_config* cfg, const rt3d_params* p)
     if (p->bkg_radius < 0 || p->bkg_radius > RT3D_MAX_BKG_R) return false;
     if (p->lmf_frac_bits < 0 || p->lmf_frac_bits > 12) return false;
     if (p->peak_min_photons < 0 || p->peak_min_photons > 255) return false;
-    if (p->peak_sep < 0 || p->peak_sep > RT3D_MAX_T) return false;
+    if (p->peak_sep < 0 || p->peak_sep > 4096) return false;
     if (p->lmf_precision < 0 || p->lmf_precision > 2) return false;
     if (p->warm_start < 0 || p->warm_start > 1) return false;
     return true;
@@ -267,22 +267,22 @@ rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3
     return RT3D_OK;
 }
 
-int init_warps(int max_t)
+int init_warps(int sep)
 {
-    int w = kInitSmemBudget / init_warp_bytes(max_t);
+    int w = kInitSmemBudget / init_warp_bytes(sep);
     return w < 1 ? 1 : (w > kInitWarps ? kInitWarps : w);
 }
 
-size_t init_smem(const KParams& K, int max_t)
+size_t init_smem(const KParams& K, int sep)
 {
-    return (size_t)((K.irf_len * 4 + 15) & ~15) + (size_t)init_warps(max_t) * init_warp_bytes(max_t);
+    return (size_t)((K.irf_len * 4 + 15) & ~15) + (size_t)init_warps(sep) * init_warp_bytes(sep);
 }
 
 rt3d_status launch_init(rt3d_ctx* c, const KParams& K, const Batch& B, Work W, cudaStream_t s,
                         bool dump, bool compact_only)
 {
-    const size_t smem = init_smem(K, B.max_t);
-    const int warps = init_warps(B.max_t);
+    const size_t smem = init_smem(K, K.peak_sep);
+    const int warps = init_warps(K.peak_sep);
     const int grid = (B.total_pix + warps - 1) / warps;
     if (grid == 0) return RT3D_OK;
     auto fn = dump ? k_init<true, false> : (compact_only ? k_init<false, true> : k_init<false, false>);
@@ -1015,8 +1015,8 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     RT3D_CUDA(cudaMemsetAsync(W.status, 0, sizeof(int), s));
     if (out->n_points) RT3D_CUDA(cudaMemsetAsync(out->n_points, 0, sizeof(int32_t), s));
 
-    const size_t smem = init_smem(K, B.max_t);
-    const int warps = init_warps(B.max_t);
+    const size_t smem = init_smem(K, K.peak_sep);
+    const int warps = init_warps(K.peak_sep);
     auto init_fn = p->warm_start ? k_init<false, true> : k_init<false, false>;
     RT3D_CUDA(cudaFuncSetAttribute(init_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     init_fn<<<(B.total_pix + warps - 1) / warps, warps * 32, smem, s>>>(K, B, W);
