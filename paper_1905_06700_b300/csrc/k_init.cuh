@@ -65,11 +65,14 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
 
 template <bool kDumpY, bool kCompactOnly>
 __global__ void __launch_bounds__(kInitWarps * 32)
-k_init(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const Work W)
+k_init(const CallRecord* __restrict__ rec, const Work W)
 {
+    const KParams& P = rec->P;
+    const Batch& B = rec->B;
     extern __shared__ __align__(16) unsigned char smem[];
     int* sK = reinterpret_cast<int*>(smem);
     const int L = P.irf_len, O = P.irf_origin, sep = P.peak_sep;
+    const int min_photons = P.peak_min_photons;
     const int k_bytes = (L * 4 + 15) & ~15;
     for (int i = threadIdx.x; i < L; i += blockDim.x) sK[i] = P.lmf[i];
     __syncthreads();
@@ -77,9 +80,10 @@ k_init(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pix = blockIdx.x * (int)(blockDim.x >> 5) + warp;
     if (pix >= B.total_pix) return;
-    const FrameDesc& F = B.f[frame_of_pixel(B, pix)];
+    const FrameDesc F = B.f[frame_of_pixel(B, pix)];   // register copy of the descriptor
     const int lp = pix - F.pix_base;
     const int T = F.nt;
+    if (lp == 0 && lane == 0 && F.n_points) *F.n_points = 0;   // counted by the finaliser
     const float g = F.gain ? F.gain[lp] : 1.0f;
 
     unsigned char* wbase = smem + k_bytes + warp * init_warp_bytes(sep);
@@ -225,7 +229,7 @@ k_init(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const
         }
         const uint32_t e_first = c_lo, e_last = c_hi - 1;
         c_lo = c_hi;
-        if (!kDumpY && cl_tot < (unsigned long long)P.peak_min_photons) continue;
+        if (!kDumpY && cl_tot < (unsigned long long)min_photons) continue;
         const int lo = max(0, (int)(ent[e_first] >> 16) + O - L + 1);
         const int hi = min(T - 1, (int)(ent[e_last] >> 16) + O);
         uint32_t e_lo = e_first;
@@ -261,12 +265,12 @@ k_init(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const
                 }
                 __syncwarp();
             }
-            if (kDumpY) {
+            if constexpr (kDumpY) {
                 for (int i = lane; cbase + i < cend; i += 32)
                     W.y_out[(long long)lp * T + cbase + i] = Y[i + sep];
                 __syncwarp();
                 continue;
-            }
+            } else {
             for (int i = lane; cbase + i < cend; i += 32) {
                 const int tau = cbase + i, yi = i + sep;
                 const int y = Y[yi];
@@ -277,12 +281,12 @@ k_init(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const
                 if (!ok) continue;
                 // photons in the IRF window [tau - origin, tau - origin + L)
                 int wcount = 0;
-                for (uint32_t e = e_first; e <= e_last && wcount < P.peak_min_photons; ++e) {
+                for (uint32_t e = e_first; e <= e_last && wcount < min_photons; ++e) {
                     const uint32_t v = ent[e];
                     const int bin = (int)(v >> 16);
                     if (bin >= tau - O && bin <= tau - O + L - 1) wcount += (int)(v & 0xffffu);
                 }
-                if (wcount < P.peak_min_photons) continue;
+                if (wcount < min_photons) continue;
                 // insert into this lane's list (y descending; equal y keeps the earlier bin first)
                 int pos = nb;
 #pragma unroll
@@ -298,6 +302,7 @@ k_init(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const
                 if (nb < K) ++nb;
             }
             __syncwarp();
+            }
         }
     }
     if (kDumpY) return;

@@ -8,16 +8,14 @@
 //   B: APSS(t_half)                                           + intensity step
 //   C: intensity low-pass + pruning                           + background step
 // A CTA owns an 8 x 16 pixel tile of one frame.  Neighbourhood work runs one
-// thread per pixel over a shared-memory copy of the tile and its halo; the
-// per-pixel gradient steps run one 8-lane group per pixel, lanes striding over
-// the pixel's nonzero bins (cost linear in active bins, Methods and Fig. 5).
+// thread per pixel (or per alive point) over a shared-memory copy of the tile
+// and its halo; the per-pixel gradient steps run one thread per pixel over the
+// pixel's nonzero bins (cost linear in active bins, Methods and Fig. 5).
 #pragma once
 #include "rt3d_device.cuh"
 
 namespace rt3d {
 
-constexpr int kG = 8;                             // lanes per pixel in gradient steps
-constexpr int kGroups = kTileThreads / kG;        // 16 groups per CTA
 
 struct TileCtx {
     int fi, i0, j0, li, lj, gi, gj;
@@ -48,33 +46,45 @@ __device__ __forceinline__ void load_irf(float* pad, const KParams& P)
     }
 }
 
-// Sums over the nonzero bins of one pixel, one 8-lane group:
+// Sums over the nonzero bins of one pixel, by one thread:
 //   sh[k] = sum z h(t - t_k)/lambda, sdh[k] = sum z h'(t - t_k)/lambda,
 //   sz = sum z/lambda, lambda = max(g (sum_alive r_k h(t - t_k) + b), lam_floor).
-__device__ __forceinline__ void pixel_sums(const uint32_t* ent, uint2 sg, int gl, unsigned gmask,
-                                           const float* pad, const KParams& P,
-                                           const float* tk, const float* rk, const bool* ak,
-                                           float b, float g, float* sh, float* sdh, float& sz)
+// Every slot is evaluated (a dead slot enters lambda with r = 0), so lanes of
+// a warp do not diverge on which slots are alive; the next entry is fetched
+// while the current one is computed.
+__device__ __forceinline__ void pixel_sums(const uint32_t* ent, uint2 sg, const float* pad,
+                                           const KParams& P, const float* tk, const float* rk,
+                                           const bool* ak, float b, float g, float* sh, float* sdh,
+                                           float& sz)
 {
+    const int K = P.k, L = P.irf_len, O = P.irf_origin;
+    float rr[kMaxK];
 #pragma unroll
-    for (int k = 0; k < kMaxK; ++k) { sh[k] = 0.0f; sdh[k] = 0.0f; }
+    for (int k = 0; k < kMaxK; ++k) {
+        sh[k] = 0.0f;
+        sdh[k] = 0.0f;
+        rr[k] = ak[k] ? rk[k] : 0.0f;
+    }
     sz = 0.0f;
-    for (uint32_t e = gl; e < sg.y; e += kG) {
-        const uint32_t v = ent[sg.x + e];
-        const float tb = (float)(v >> 16), z = (float)(v & 0xffffu);
+    const float lam_floor = P.lam_floor;
+    uint32_t v = sg.y ? ent[sg.x] : 0u;
+    for (uint32_t e = 0; e < sg.y; ++e) {
+        const uint32_t cur = v;
+        if (e + 1 < sg.y) v = ent[sg.x + e + 1];
+        const float tb = (float)(cur >> 16), z = (float)(cur & 0xffffu);
         float hv[kMaxK], dv[kMaxK];
         float acc = b;
 #pragma unroll
         for (int k = 0; k < kMaxK; ++k) {
             hv[k] = 0.0f;
             dv[k] = 0.0f;
-            if (k < P.k && ak[k]) {
-                irf_eval(pad, P.irf_len, P.irf_origin, tb - tk[k], hv[k], dv[k]);
-                acc += rk[k] * hv[k];
+            if (k < K) {
+                irf_eval(pad, L, O, tb - tk[k], hv[k], dv[k]);
+                acc += rr[k] * hv[k];
             }
         }
-        const float lam = fmaxf(g * acc, P.lam_floor);
-        const float inv = z / lam;
+        const float lam = fmaxf(g * acc, lam_floor);
+        const float inv = __fdividef(z, lam);
         sz += inv;
 #pragma unroll
         for (int k = 0; k < kMaxK; ++k) {
@@ -82,12 +92,6 @@ __device__ __forceinline__ void pixel_sums(const uint32_t* ent, uint2 sg, int gl
             sdh[k] += dv[k] * inv;
         }
     }
-#pragma unroll
-    for (int k = 0; k < kMaxK; ++k) {
-        sh[k] = group_sum<kG>(sh[k], gmask);
-        sdh[k] = group_sum<kG>(sdh[k], gmask);
-    }
-    sz = group_sum<kG>(sz, gmask);
 }
 
 // Background denoiser at pixel (i, j): periodic separable Gaussian over the
@@ -113,30 +117,37 @@ __device__ __forceinline__ float bkg_filter(const KParams& P, const float* bh, i
 }
 
 // ----------------------------------------------------------------------------
-// Phase A: background denoiser of the previous iteration + depth gradient step.
+// Phase A: background denoiser of the previous iteration + depth gradient step,
+// one thread per pixel.
 __global__ void __launch_bounds__(kTileThreads)
-k_phase_a(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const Work W, int first)
+k_phase_a(const CallRecord* __restrict__ rec, const Work W, int first)
 {
+    const KParams& P = rec->P;
+    const Batch& B = rec->B;
     __shared__ float pad[kMaxIrf + 2 * kIrfPad];
-    __shared__ float s_t[kMaxK][kTileThreads], s_r[kMaxK][kTileThreads];
-    __shared__ uint8_t s_a[kMaxK][kTileThreads];
-    __shared__ float s_b[kTileThreads], s_g[kTileThreads];
     load_irf(pad, P);
+    __syncthreads();
     const TileCtx c = tile_ctx(B);
     const FrameDesc& F = B.f[c.fi];
-    const int np = F.npix, S = W.stride;
+    if (!c.inb) return;
+    const int np = F.npix, S = W.stride, K = P.k;
     const int lp = c.gi * F.w + c.gj, wp = F.pix_base + lp;
-    if (c.inb) {
-        float b;
-        if (first) {
-            b = F.b[lp];
-        } else {
-            b = bkg_filter(P, W.b_half + F.pix_base, F.h, F.w, c.gi, c.gj);
-            F.b[lp] = b;
-        }
-        s_b[threadIdx.x] = b;
-        s_g[threadIdx.x] = F.gain ? F.gain[lp] : 1.0f;
-        for (int k = 0; k < P.k; ++k) {
+    float b;
+    if (first) {
+        b = F.b[lp];
+    } else {
+        b = bkg_filter(P, W.b_half + F.pix_base, F.h, F.w, c.gi, c.gj);
+        F.b[lp] = b;
+    }
+    const float g = F.gain ? F.gain[lp] : 1.0f;
+    float tk[kMaxK], rk[kMaxK];
+    bool ak[kMaxK];
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) {
+        tk[k] = 0.0f;
+        rk[k] = 0.0f;
+        ak[k] = false;
+        if (k < K) {
             uint8_t a;
             if (first) {
                 a = F.alive[(long long)k * np + lp];
@@ -144,49 +155,26 @@ k_phase_a(const __grid_constant__ KParams P, const __grid_constant__ Batch B, co
                 a = W.alive_b[(long long)k * S + wp];
                 F.alive[(long long)k * np + lp] = a;
             }
-            s_a[k][threadIdx.x] = a;
-            s_t[k][threadIdx.x] = F.t[(long long)k * np + lp];
-            s_r[k][threadIdx.x] = F.r[(long long)k * np + lp];
+            ak[k] = a != 0;
+            tk[k] = F.t[(long long)k * np + lp];
+            rk[k] = F.r[(long long)k * np + lp];
         }
     }
-    __syncthreads();
-
-    const int grp = threadIdx.x / kG, gl = threadIdx.x % kG;
-    const unsigned gmask = 0xffu << ((threadIdx.x & 31) & ~(kG - 1));
-    for (int q = grp; q < kTileThreads; q += kGroups) {
-        const int qi = c.i0 + q / kTileW, qj = c.j0 + q % kTileW;
-        if (qi >= F.h || qj >= F.w) continue;
-        const int qlp = qi * F.w + qj, qwp = F.pix_base + qlp;
-        float tk[kMaxK], rk[kMaxK];
-        bool ak[kMaxK];
+    float sh[kMaxK], sdh[kMaxK], sz;
+    pixel_sums(F.ent, W.seg[wp], pad, P, tk, rk, ak, b, g, sh, sdh, sz);
 #pragma unroll
-        for (int k = 0; k < kMaxK; ++k) {
-            const bool in = k < P.k;
-            tk[k] = in ? s_t[k][q] : 0.0f;
-            rk[k] = in ? s_r[k][q] : 0.0f;
-            ak[k] = in && s_a[k][q];
+    for (int k = 0; k < kMaxK; ++k) {
+        if (k >= K) continue;
+        float tn = tk[k];
+        if (ak[k] && g > 0.0f) {
+            float H, dH;
+            support_sums(pad, P, F.nt, tk[k], H, dH);
+            const float grad = g * rk[k] * (-dH + sdh[k]);
+            const float beta = P.t_step / (g * rk[k] + P.eps_r);
+            const float step = clampf(-beta * grad, -P.dt_max, P.dt_max);
+            tn = clampf(tk[k] + step, 0.0f, (float)(F.nt - 1));
         }
-        const float g = s_g[q];
-        float sh[kMaxK], sdh[kMaxK], sz;
-        pixel_sums(F.ent, W.seg[qwp], gl, gmask, pad, P, tk, rk, ak, s_b[q], g, sh, sdh, sz);
-        if (gl < P.k) {
-            const int k = gl;
-            float tn = 0.0f;
-#pragma unroll
-            for (int m = 0; m < kMaxK; ++m)
-                if (m == k) {
-                    tn = tk[m];
-                    if (ak[m] && g > 0.0f) {
-                        float H, dH;
-                        support_sums(pad, P, F.nt, tk[m], H, dH);
-                        const float grad = g * rk[m] * (-dH + sdh[m]);
-                        const float beta = P.t_step / (g * rk[m] + P.eps_r);
-                        const float step = clampf(-beta * grad, -P.dt_max, P.dt_max);
-                        tn = clampf(tk[m] + step, 0.0f, (float)(F.nt - 1));
-                    }
-                }
-            W.t_half[(long long)k * S + qwp] = tn;
-        }
+        W.t_half[(long long)k * S + wp] = tn;
     }
 }
 
@@ -219,6 +207,7 @@ __device__ float apss_point(const float* st, int hstride, int R, int K, int ci, 
             const float r2 = x * x + y * y;
             if (!(r2 < 1.0f)) continue;
             const int q = (ci + di) * hstride + (cj + dj);
+            float cnt = 0.0f;
             for (int m = 0; m < K; ++m) {
                 const float z = (st[m * kHalo + q] - tn) * inv_h;
                 const float d2 = r2 + z * z;
@@ -226,19 +215,19 @@ __device__ float apss_point(const float* st, int hstride, int R, int K, int ci, 
                 float w = 1.0f - d2;
                 w *= w;
                 w = in ? w * w : 0.0f;
-                const float ind = in ? 1.0f : 0.0f;
+                cnt += in ? 1.0f : 0.0f;
                 const float wx = w * x, wy = w * y, wq = w * d2;
                 S0 += w; Sx += wx; Sy += wy; Sz += w * z; Sq += wq;
                 Sxx += wx * x; Sxy += wx * y; Syy += wy * y;
                 Sxq += wx * d2; Syq += wy * d2; Sqq += wq * d2;
                 Sxz += wx * z; Syz += wy * z; Sqz += wq * z;
-                nw += ind;
-                si += ind * (float)di;
-                sj += ind * (float)dj;
-                sii += ind * (float)(di * di);
-                sjj += ind * (float)(dj * dj);
-                sij += ind * (float)(di * dj);
             }
+            nw += cnt;
+            si += cnt * (float)di;
+            sj += cnt * (float)dj;
+            sii += cnt * (float)(di * di);
+            sjj += cnt * (float)(dj * dj);
+            sij += cnt * (float)(di * dj);
         }
     }
     const long long n = (long long)nw;
@@ -331,8 +320,10 @@ __device__ __forceinline__ int compact_points(const float* st, int R, int K, boo
 // ----------------------------------------------------------------------------
 // Phase B: APSS depth denoiser + intensity gradient step.
 __global__ void __launch_bounds__(kTileThreads)
-k_phase_b(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const Work W)
+k_phase_b(const CallRecord* __restrict__ rec, const Work W)
 {
+    const KParams& P = rec->P;
+    const Batch& B = rec->B;
     __shared__ float pad[kMaxIrf + 2 * kIrfPad];
     __shared__ float st[kMaxK * kHalo];
     __shared__ float s_tn[kMaxK][kTileThreads];
@@ -366,39 +357,32 @@ k_phase_b(const __grid_constant__ KParams P, const __grid_constant__ Batch B, co
         }
     }
 
-    const int grp = threadIdx.x / kG, gl = threadIdx.x % kG;
-    const unsigned gmask = 0xffu << ((threadIdx.x & 31) & ~(kG - 1));
-    for (int q = grp; q < kTileThreads; q += kGroups) {
-        const int qi = c.i0 + q / kTileW, qj = c.j0 + q % kTileW;
-        if (qi >= F.h || qj >= F.w) continue;
-        const int qlp = qi * F.w + qj, qwp = F.pix_base + qlp;
+    if (!c.inb) return;
+    {
+        const int lp = c.gi * F.w + c.gj, wp = F.pix_base + lp;
         float tk[kMaxK], rk[kMaxK];
         bool ak[kMaxK];
 #pragma unroll
         for (int k = 0; k < kMaxK; ++k) {
             const bool in = k < K;
-            const float v = in ? s_tn[k][q] : kDeadDepth;
+            const float v = in ? s_tn[k][threadIdx.x] : kDeadDepth;
             ak[k] = v != kDeadDepth;
             tk[k] = ak[k] ? v : 0.0f;
-            rk[k] = in ? F.r[(long long)k * np + qlp] : 0.0f;
+            rk[k] = in ? F.r[(long long)k * np + lp] : 0.0f;
         }
-        const float g = F.gain ? F.gain[qlp] : 1.0f;
+        const float g = F.gain ? F.gain[lp] : 1.0f;
         float sh[kMaxK], sdh[kMaxK], sz;
-        pixel_sums(F.ent, W.seg[qwp], gl, gmask, pad, P, tk, rk, ak, F.b[qlp], g, sh, sdh, sz);
-        if (gl < K) {
-            const int k = gl;
-            float rn = 0.0f;
+        pixel_sums(F.ent, W.seg[wp], pad, P, tk, rk, ak, F.b[lp], g, sh, sdh, sz);
 #pragma unroll
-            for (int m = 0; m < kMaxK; ++m)
-                if (m == k) {
-                    rn = rk[m];
-                    if (ak[m] && g > 0.0f) {
-                        float H, dH;
-                        support_sums(pad, P, F.nt, tk[m], H, dH);
-                        rn = fmaxf(rk[m] - P.r_step * (rk[m] + P.eps_r) * (H - sh[m]), 0.0f);
-                    }
-                }
-            W.r_half[(long long)k * S + qwp] = rn;
+        for (int k = 0; k < kMaxK; ++k) {
+            if (k >= K) continue;
+            float rn = rk[k];
+            if (ak[k] && g > 0.0f) {
+                float H, dH;
+                support_sums(pad, P, F.nt, tk[k], H, dH);
+                rn = fmaxf(rk[k] - P.r_step * (rk[k] + P.eps_r) * (H - sh[k]), 0.0f);
+            }
+            W.r_half[(long long)k * S + wp] = rn;
         }
     }
 }
@@ -406,8 +390,10 @@ k_phase_b(const __grid_constant__ KParams P, const __grid_constant__ Batch B, co
 // ----------------------------------------------------------------------------
 // Phase C: intensity low-pass on the surface + pruning + background gradient step.
 __global__ void __launch_bounds__(kTileThreads)
-k_phase_c(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const Work W)
+k_phase_c(const CallRecord* __restrict__ rec, const Work W)
 {
+    const KParams& P = rec->P;
+    const Batch& B = rec->B;
     __shared__ float pad[kMaxIrf + 2 * kIrfPad];
     __shared__ float st[kMaxK * kHalo];
     __shared__ float sr[kMaxK * kHalo];
@@ -497,32 +483,25 @@ k_phase_c(const __grid_constant__ KParams P, const __grid_constant__ Batch B, co
     }
     __syncthreads();
 
-    const int grp = threadIdx.x / kG, gl = threadIdx.x % kG;
-    const unsigned gmask = 0xffu << ((threadIdx.x & 31) & ~(kG - 1));
-    for (int q = grp; q < kTileThreads; q += kGroups) {
-        const int qi = c.i0 + q / kTileW, qj = c.j0 + q % kTileW;
-        if (qi >= F.h || qj >= F.w) continue;
-        const int qlp = qi * F.w + qj, qwp = F.pix_base + qlp;
-        const int hq = (q / kTileW + R) * hstride + (q % kTileW + R);
+    if (!c.inb) return;
+    {
+        const int lp = c.gi * F.w + c.gj, wp = F.pix_base + lp;
         float tk[kMaxK], rk[kMaxK];
         bool ak[kMaxK];
 #pragma unroll
         for (int k = 0; k < kMaxK; ++k) {
             const bool in = k < K;
-            ak[k] = in && s_an[k][q];
-            tk[k] = ak[k] ? st[k * kHalo + hq] : 0.0f;
-            rk[k] = in ? s_rn[k][q] : 0.0f;
+            ak[k] = in && s_an[k][threadIdx.x];
+            tk[k] = ak[k] ? st[k * kHalo + q0] : 0.0f;
+            rk[k] = in ? s_rn[k][threadIdx.x] : 0.0f;
         }
-        const float g = F.gain ? F.gain[qlp] : 1.0f;
-        const float b = F.b[qlp];
+        const float g = F.gain ? F.gain[lp] : 1.0f;
+        const float b = F.b[lp];
         float sh[kMaxK], sdh[kMaxK], sz;
-        pixel_sums(F.ent, W.seg[qwp], gl, gmask, pad, P, tk, rk, ak, b, g, sh, sdh, sz);
-        if (gl == 0) {
-            float bn = b;
-            if (g > 0.0f)
-                bn = fmaxf(b - P.b_step * (b + P.eps_b) * (1.0f - sz / (float)F.nt), P.b_floor);
-            W.b_half[qwp] = bn;
-        }
+        pixel_sums(F.ent, W.seg[wp], pad, P, tk, rk, ak, b, g, sh, sdh, sz);
+        float bn = b;
+        if (g > 0.0f) bn = fmaxf(b - P.b_step * (b + P.eps_b) * (1.0f - sz / (float)F.nt), P.b_floor);
+        W.b_half[wp] = bn;
     }
 }
 
@@ -530,8 +509,10 @@ k_phase_c(const __grid_constant__ KParams P, const __grid_constant__ Batch B, co
 // Finaliser: the last iteration's pruning and background denoiser land in the
 // result buffers; alive points are counted per frame.
 __global__ void __launch_bounds__(kTileThreads)
-k_final(const __grid_constant__ KParams P, const __grid_constant__ Batch B, const Work W, int ran)
+k_final(const CallRecord* __restrict__ rec, const Work W, int ran)
 {
+    const KParams& P = rec->P;
+    const Batch& B = rec->B;
     __shared__ int s_cnt;
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();

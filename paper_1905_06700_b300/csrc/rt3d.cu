@@ -42,6 +42,8 @@ struct rt3d_ctx {
     long long stride = 0;           // workspace pixels = max_batch * max_h * max_w
     int* d_status = nullptr;
     unsigned long long* d_count = nullptr;
+    CallRecord* d_rec = nullptr;    // per-call tables and frame descriptors (device)
+    CallRecord h_rec;               // host copy, uploaded once per call
     uint32_t* d_tmp = nullptr;      // [stride + 1] scratch of rt3d_compact
     long long launches = 0;
     bool profiling = false;
@@ -278,6 +280,15 @@ size_t init_smem(const KParams& K, int sep)
     return (size_t)((K.irf_len * 4 + 15) & ~15) + (size_t)init_warps(sep) * init_warp_bytes(sep);
 }
 
+// One upload per call of the tables and frame descriptors the kernels read.
+// The host copy is pageable, so the runtime stages it before returning and
+// it may be rewritten by the next call at once.
+rt3d_status upload_record(rt3d_ctx* c, cudaStream_t s)
+{
+    RT3D_CUDA(cudaMemcpyAsync(c->d_rec, &c->h_rec, sizeof(CallRecord), cudaMemcpyHostToDevice, s));
+    return RT3D_OK;
+}
+
 rt3d_status launch_init(rt3d_ctx* c, const KParams& K, const Batch& B, Work W, cudaStream_t s,
                         bool dump, bool compact_only)
 {
@@ -289,39 +300,37 @@ rt3d_status launch_init(rt3d_ctx* c, const KParams& K, const Batch& B, Work W, c
     RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     {
         LaunchScope ls(c, s, kcInit);
-        fn<<<grid, warps * 32, smem, s>>>(K, B, W);
+        fn<<<grid, warps * 32, smem, s>>>(c->d_rec, W);
     }
     RT3D_CUDA(cudaGetLastError());
     return RT3D_OK;
 }
 
-rt3d_status launch_loop(rt3d_ctx* c, const KParams& K, const Batch& B, cudaStream_t s, int n_iter)
+rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
 {
     for (int it = 0; it < n_iter; ++it) {
         {
             LaunchScope ls(c, s, kcA);
-            k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W, it == 0 ? 1 : 0);
+            k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W, it == 0 ? 1 : 0);
         }
         {
             LaunchScope ls(c, s, kcB);
-            k_phase_b<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W);
+            k_phase_b<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W);
         }
         {
             LaunchScope ls(c, s, kcC);
-            k_phase_c<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W);
+            k_phase_c<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W);
         }
     }
     RT3D_CUDA(cudaGetLastError());
     return RT3D_OK;
 }
 
-rt3d_status launch_final(rt3d_ctx* c, const KParams& K, const Batch& B, cudaStream_t s, int ran)
+rt3d_status launch_final(rt3d_ctx* c, const Batch& B, cudaStream_t s, int ran)
 {
-    for (int i = 0; i < B.n; ++i)
-        if (B.f[i].n_points) RT3D_CUDA(cudaMemsetAsync(B.f[i].n_points, 0, sizeof(int32_t), s));
     {
         LaunchScope ls(c, s, kcFinal);
-        k_final<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W, ran);
+        k_final<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W, ran);
     }
     RT3D_CUDA(cudaGetLastError());
     return RT3D_OK;
@@ -346,18 +355,20 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
     rt3d_status st = check_common(c, n, f, p, out);
     if (st != RT3D_OK) return st;
     RT3D_CUDA(cudaSetDevice(c->cfg.device));
-    KParams K;
+    KParams& K = c->h_rec.P;
     st = build_kparams(c, p, &K);
     if (st != RT3D_OK) return st;
-    Batch B;
+    Batch& B = c->h_rec.B;
     st = build_batch(c, n, f, out, &B);
+    if (st != RT3D_OK) return st;
+    st = upload_record(c, s);
     if (st != RT3D_OK) return st;
     RT3D_CUDA(cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), s));
     st = launch_init(c, K, B, c->W, s, false, p->warm_start != 0);
     if (st != RT3D_OK) return st;
-    st = launch_loop(c, K, B, s, p->n_iter);
+    st = launch_loop(c, B, s, p->n_iter);
     if (st != RT3D_OK) return st;
-    return launch_final(c, K, B, s, p->n_iter > 0 ? 1 : 0);
+    return launch_final(c, B, s, p->n_iter > 0 ? 1 : 0);
 }
 
 }  // namespace
@@ -466,6 +477,7 @@ rt3d_status rt3d_create(const rt3d_config* cfg, const rt3d_irf* irf, rt3d_ctx_t*
     alloc((void**)&c->W.alive_b, (size_t)K * c->stride);
     alloc((void**)&c->d_status, sizeof(int));
     alloc((void**)&c->d_tmp, sizeof(uint32_t) * (c->stride + 1));
+    alloc((void**)&c->d_rec, sizeof(CallRecord));
     if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(c->W.alive_b, 0, (size_t)K * c->stride);
     if (e != cudaSuccess) {
@@ -486,7 +498,7 @@ void rt3d_destroy(rt3d_ctx_t* c)
     if (!c) return;
     cudaSetDevice(c->cfg.device);
     void* ptrs[] = {c->W.seg, c->W.ent, c->d_count, c->W.t_half, c->W.r_half, c->W.b_half,
-                    c->W.alive_b, c->d_status, c->d_tmp, c->s_dense, c->s_off, c->s_ent,
+                    c->W.alive_b, c->d_status, c->d_tmp, c->d_rec, c->s_dense, c->s_off, c->s_ent,
                     c->s_gain, c->s_t, c->s_r, c->s_b, c->s_alive, c->s_np};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -577,11 +589,13 @@ rt3d_status rt3d_lmf(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d_params* p, i
     if (st != RT3D_OK) return st;
     RT3D_CUDA(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
-    KParams K;
+    KParams& K = c->h_rec.P;
     st = build_kparams(c, p, &K);
     if (st != RT3D_OK) return st;
-    Batch B;
+    Batch& B = c->h_rec.B;
     st = build_batch(c, 1, f, nullptr, &B);
+    if (st != RT3D_OK) return st;
+    st = upload_record(c, s);
     if (st != RT3D_OK) return st;
     Work W = c->W;
     W.y_out = y;
@@ -597,16 +611,18 @@ rt3d_status rt3d_init(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d_params* p, 
     if (st != RT3D_OK) return st;
     RT3D_CUDA(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
-    KParams K;
+    KParams& K = c->h_rec.P;
     st = build_kparams(c, p, &K);
     if (st != RT3D_OK) return st;
-    Batch B;
+    Batch& B = c->h_rec.B;
     st = build_batch(c, 1, f, out, &B);
+    if (st != RT3D_OK) return st;
+    st = upload_record(c, s);
     if (st != RT3D_OK) return st;
     RT3D_CUDA(cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), s));
     st = launch_init(c, K, B, c->W, s, false, false);
     if (st != RT3D_OK) return st;
-    return launch_final(c, K, B, s, 0);
+    return launch_final(c, B, s, 0);
 }
 
 rt3d_status rt3d_reconstruct(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d_params* p,
@@ -700,11 +716,13 @@ rt3d_status rt3d_phase(rt3d_ctx_t* c, int phase, int first, const rt3d_frame* f,
     if (!f->csr_off) return RT3D_E_INVALID;
     RT3D_CUDA(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
-    KParams K;
+    KParams& K = c->h_rec.P;
     st = build_kparams(c, p, &K);
     if (st != RT3D_OK) return st;
-    Batch B;
+    Batch& B = c->h_rec.B;
     st = build_batch(c, 1, f, state, &B);
+    if (st != RT3D_OK) return st;
+    st = upload_record(c, s);
     if (st != RT3D_OK) return st;
     // sparse segments of the caller's list
     st = launch_init(c, K, B, c->W, s, false, true);
@@ -727,9 +745,9 @@ rt3d_status rt3d_phase(rt3d_ctx_t* c, int phase, int first, const rt3d_frame* f,
         RT3D_CUDA(cudaMemcpyAsync(c->W.b_half, state->b, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
     {
         LaunchScope ls(c, s, phase == 0 ? kcA : (phase == 1 ? kcB : kcC));
-        if (phase == 0) k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W, first);
-        if (phase == 1) k_phase_b<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W);
-        if (phase == 2) k_phase_c<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, c->W);
+        if (phase == 0) k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W, first);
+        if (phase == 1) k_phase_b<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W);
+        if (phase == 2) k_phase_c<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W);
     }
     RT3D_CUDA(cudaGetLastError());
     for (int k = 0; k < Kp; ++k) {
@@ -841,7 +859,8 @@ constexpr long long kStaticOffB = kStaticOffR + kStaticHalfBytes;
 constexpr long long kStaticOffA = kStaticOffB + kStaticBBytes;
 constexpr long long kStaticOffCount = (kStaticOffA + kStaticAliveBytes + 255) & ~255ll;
 constexpr long long kStaticOffStatus = kStaticOffCount + 256;
-constexpr long long kStaticBytes = kStaticOffStatus + 256;
+constexpr long long kStaticOffRec = kStaticOffStatus + 256;
+constexpr long long kStaticBytes = kStaticOffRec + (((long long)sizeof(CallRecord) + 255) & ~255ll);
 
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
 
@@ -967,7 +986,8 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     unsigned char* base = nullptr;
     rt3d_status st = static_scratch(device, &base);
     if (st != RT3D_OK) return st;
-    KParams K;
+    CallRecord rec;                      // host copy, uploaded into the static array
+    KParams& K = rec.P;
     st = static_kparams(irf, p, &K);
     if (st != RT3D_OK) return st;
 
@@ -984,7 +1004,7 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     W.status = reinterpret_cast<int*>(base + kStaticOffStatus);
     W.y_out = nullptr;
 
-    Batch B;
+    Batch& B = rec.B;
     std::memset(&B, 0, sizeof(Batch));
     B.n = 1;
     FrameDesc& d = B.f[0];
@@ -1010,22 +1030,24 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     B.max_t = f->t;
 
     cudaStream_t s = (cudaStream_t)stream;
+    const CallRecord* d_rec = reinterpret_cast<const CallRecord*>(base + kStaticOffRec);
+    // pageable source: staged by the runtime before the call returns
+    RT3D_CUDA(cudaMemcpyAsync((void*)d_rec, &rec, sizeof(CallRecord), cudaMemcpyHostToDevice, s));
     // the allocation cursor and the device status word start at zero every call
     RT3D_CUDA(cudaMemsetAsync(W.ent_count, 0, sizeof(unsigned long long), s));
     RT3D_CUDA(cudaMemsetAsync(W.status, 0, sizeof(int), s));
-    if (out->n_points) RT3D_CUDA(cudaMemsetAsync(out->n_points, 0, sizeof(int32_t), s));
 
     const size_t smem = init_smem(K, K.peak_sep);
     const int warps = init_warps(K.peak_sep);
     auto init_fn = p->warm_start ? k_init<false, true> : k_init<false, false>;
     RT3D_CUDA(cudaFuncSetAttribute(init_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    init_fn<<<(B.total_pix + warps - 1) / warps, warps * 32, smem, s>>>(K, B, W);
+    init_fn<<<(B.total_pix + warps - 1) / warps, warps * 32, smem, s>>>(d_rec, W);
     for (int it = 0; it < p->n_iter; ++it) {
-        k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, W, it == 0 ? 1 : 0);
-        k_phase_b<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, W);
-        k_phase_c<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, W);
+        k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W, it == 0 ? 1 : 0);
+        k_phase_b<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W);
+        k_phase_c<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W);
     }
-    k_final<<<B.total_tiles, kTileThreads, 0, s>>>(K, B, W, p->n_iter > 0 ? 1 : 0);
+    k_final<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W, p->n_iter > 0 ? 1 : 0);
     RT3D_CUDA(cudaGetLastError());
     return RT3D_OK;
 }

@@ -1,10 +1,11 @@
 // rt3d_device.cuh -- types and device helpers shared by the rt3d kernels.
 //
-// Everything a kernel needs travels by value in two __grid_constant__
-// parameters: KParams (the method's constants, the normalised IRF, the
-// quantised log-IRF and the background filter taps) and Batch (one descriptor
-// per frame).  No constant-memory tables, so every launch is self-contained
-// and capturable in a CUDA graph.
+// What a kernel needs about a call lives in one device-resident CallRecord:
+// KParams (the method's constants, the normalised IRF, the quantised log-IRF
+// and the background filter taps) and Batch (one descriptor per frame),
+// uploaded once per call.  Launches then carry only a pointer to it and the
+// small Work descriptor, so the launch sequence of a call shape is fixed and
+// can be replayed as a CUDA graph.
 #pragma once
 
 #include <cstdint>
@@ -59,6 +60,11 @@ struct FrameDesc {
 struct Batch {
     int n, total_tiles, total_pix, max_t;
     FrameDesc f[kMaxBatch];
+};
+
+struct CallRecord {
+    KParams P;
+    Batch B;
 };
 
 struct Work {
