@@ -82,6 +82,26 @@ def algorithmic_bytes(n_frames: int, nnz_total: int, k: int) -> dict:
     }
 
 
+def lateral_offsets(prm) -> int:
+    """Window offsets (di, dj) inside the APSS radius: the candidate pixels of a point."""
+    R, p, h = prm["win_r"], prm["pixel_pitch"], prm["apss_radius"]
+    return sum(1 for di in range(-R, R + 1) for dj in range(-R, R + 1)
+               if (p * di) ** 2 + (p * dj) ** 2 < h * h)
+
+
+def algorithmic_flops(n_frames: int, nnz_total: int, n_points: int, k: int, prm) -> dict:
+    """FP32 operations each loop kernel must execute per launch:
+      APSS         per alive point: (offsets in radius) x K candidates x 36 (distance,
+                   weight, 14 moment multiply-adds) + 60 (centred 3x3 solve, projection)
+      low-pass     per alive point: (offsets) x K x 12
+      gradient step per nonzero bin: K x 24 (cubic IRF value and slope, lambda, sums)."""
+    off = lateral_offsets(prm)
+    grad = nnz_total * k * 24
+    return {"phase_a": grad,
+            "phase_b": n_points * (off * k * 36 + 60) + grad,
+            "phase_c": n_points * off * k * 12 + grad}
+
+
 class Clocks:
     """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
 
@@ -93,7 +113,7 @@ class Clocks:
         self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
         try:
             self.p = subprocess.Popen(["nvidia-smi", f"--id={gpu_index}", f"--query-gpu={self.FIELDS}",
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "50"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except OSError:
             self.p = None
@@ -124,11 +144,13 @@ class Clocks:
 
 
 def measured_peaks() -> dict:
+    """HBM copy bandwidth (measured) and the FP32 FMA peak derived from the unit
+    counts: 148 SMs x 128 FP32 lanes x 2 FLOP x the maximum SM clock."""
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(path):
-        d = json.load(open(path))
-        return {"hbm_gbs": d.get("hbm_gbs", 6400.0), "source": "measured"}
-    return {"hbm_gbs": 6400.0, "source": "fallback"}
+    d = json.load(open(path)) if os.path.exists(path) else {}
+    mhz = d.get("sm_max_mhz", 2032.0)
+    return {"hbm_gbs": d.get("hbm_gbs", 6400.0), "source": "measured" if d else "fallback",
+            "fp32_tflops": 148 * 128 * 2 * mhz * 1e6 / 1e12}
 
 
 def traffic_record(kernel: str):
@@ -212,23 +234,36 @@ def run_ours(args, world, rank, local):
     frames_all = nb * args.steps * world
     value = frames_all / (t_max / 1000.0)
 
-    # ---------------- dominant kernel vs the HBM roofline
+    # ---------------- dominant kernel vs its roofline
+    n_points = int(sum(int(o["n_points"].item()) for o in outs))
     alg = algorithmic_bytes(nb, nnz_total, K)
+    flops = algorithmic_flops(nb, nnz_total, n_points, K, prm)
+    peaks = measured_peaks()
     per_kernel = {}
     for name in KERNEL_NAMES:
         ms, n = ktimes[name]
         if n:
-            per_kernel[name] = dict(ms_total=ms, launches=n, ms_per_launch=ms / n,
-                                    alg_bytes_per_launch=alg[name],
-                                    gbs=alg[name] / (ms / n / 1000.0) / 1e9)
+            sec = ms / n / 1000.0
+            d = dict(ms_total=ms, launches=n, ms_per_launch=ms / n,
+                     alg_bytes_per_launch=alg[name], gbs=alg[name] / sec / 1e9,
+                     hbm_frac=alg[name] / sec / 1e9 / peaks["hbm_gbs"])
+            if name in flops:
+                d.update(alg_flops_per_launch=flops[name], tflops=flops[name] / sec / 1e12,
+                         alu_frac=flops[name] / sec / 1e12 / peaks["fp32_tflops"])
+            per_kernel[name] = d
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_total"])
-    peaks = measured_peaks()
     d = per_kernel[dom]
-    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(d["gbs"], 1),
-                "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": round(d["gbs"] / peaks["hbm_gbs"], 4),
-                "peak_source": f"{peaks['source']} (burst copy)",
-                "traffic": traffic_record(dom)}
+    if dom == "init" or dom == "final":
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(d["gbs"], 1),
+                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(d["hbm_frac"], 4),
+                    "peak_source": f"{peaks['source']} copy bandwidth (burst)",
+                    "traffic": traffic_record(dom)}
+    else:
+        roofline = {"bound": "alu", "kernel": dom, "achieved": round(d["tflops"], 2),
+                    "peak": round(peaks["fp32_tflops"], 1), "unit": "TFLOP/s",
+                    "frac": round(d["alu_frac"], 4),
+                    "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 x max SM clock",
+                    "traffic": traffic_record(dom)}
 
     result = None
     if rank == 0:
@@ -274,6 +309,10 @@ def run_ours(args, world, rank, local):
                            "frame_samples": len(lat)},
             "e2e": e2e,
             "roofline": roofline,
+            "init_roofline": {"bound": "hbm", "achieved": round(per_kernel["init"]["gbs"], 1),
+                              "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                              "frac": round(per_kernel["init"]["hbm_frac"], 4),
+                              "traffic": traffic_record("init")} if "init" in per_kernel else None,
             "kernels": {k: {kk: round(vv, 4) if isinstance(vv, float) else vv for kk, vv in v.items()}
                         for k, v in per_kernel.items()},
             "gpu_launches": int(launches),

@@ -64,7 +64,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
 }
 
 template <bool kDumpY, bool kCompactOnly>
-__global__ void __launch_bounds__(kInitWarps * 32)
+__global__ void __launch_bounds__(kInitWarps * 32, 5)
 k_init(const CallRecord* __restrict__ rec, const Work W)
 {
     const KParams& P = rec->P;
@@ -80,7 +80,7 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int pix = blockIdx.x * (int)(blockDim.x >> 5) + warp;
     if (pix >= B.total_pix) return;
-    const FrameDesc F = B.f[frame_of_pixel(B, pix)];   // register copy of the descriptor
+    const FrameDesc& F = B.f[frame_of_pixel(B, pix)];
     const int lp = pix - F.pix_base;
     const int T = F.nt;
     if (lp == 0 && lane == 0 && F.n_points) *F.n_points = 0;   // counted by the finaliser
