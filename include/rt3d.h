@@ -216,7 +216,9 @@ rt3d_status rt3d_init(rt3d_ctx_t* ctx, const rt3d_frame* f, const rt3d_params* p
                       rt3d_result* out, void* stream);
 
 /* The whole method on one frame: initialisation (or warm start) then
- * params.n_iter PALM iterations.  Results land in `out`. */
+ * params.n_iter PALM iterations.  Results land in `out`.  The launch sequence
+ * of each call geometry (frame sizes, iteration count) is captured once as a
+ * CUDA graph on a private stream and replayed on `stream`. */
 rt3d_status rt3d_reconstruct(rt3d_ctx_t* ctx, const rt3d_frame* f, const rt3d_params* p,
                              rt3d_result* out, void* stream);
 
@@ -252,11 +254,14 @@ rt3d_status rt3d_device_status(rt3d_ctx_t* ctx, void* stream);
 /* Kernel launches made by this context since creation (all entry points). */
 int64_t rt3d_launch_count(rt3d_ctx_t* ctx);
 
-/* Per-kernel timing with CUDA events recorded on the launch stream around
- * each launch (off by default).  rt3d_kernel_times synchronises and returns,
- * for kernel class i (0 init, 1 phase A, 2 phase B, 3 phase C, 4 final,
- * 5 synthesize), the accumulated milliseconds and launch count since the last
- * reset. */
+/* Per-kernel timing with CUDA events recorded around each launch (off by
+ * default).  rt3d_kernel_times synchronises and returns, for kernel class i
+ * (0 init, 1 phase A, 2 phase B, 3 phase C, 4 final, 5 synthesize, 6 compact),
+ * the accumulated milliseconds and launch count since the last reset.  The
+ * reconstruction entry points replay a CUDA graph per call geometry (captured
+ * on first use); a graph re-records the same events, so its kernels count once,
+ * from its latest replay -- averages per launch are exact, totals are one
+ * replay's. */
 rt3d_status rt3d_set_profiling(rt3d_ctx_t* ctx, int on);
 rt3d_status rt3d_kernel_times(rt3d_ctx_t* ctx, double* ms, int64_t* launches, int n, int reset);
 

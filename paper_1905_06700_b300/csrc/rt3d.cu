@@ -9,8 +9,10 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
+#include <tuple>
 #include <vector>
 
 #include "rt3d.h"
@@ -32,6 +34,26 @@ struct PendingTiming {
     cudaEvent_t a, b;
 };
 
+// One captured launch sequence of a call geometry (same grids, same smem,
+// same iteration count) replayed as a CUDA graph; its kernels read the call
+// record, so replays differ only in what was uploaded into it.
+struct GraphKey {
+    int total_pix, total_tiles, n_iter, warm, init_warps, profiled;
+    size_t init_smem;
+    bool operator<(const GraphKey& o) const
+    {
+        return std::tie(total_pix, total_tiles, n_iter, warm, init_warps, profiled, init_smem) <
+               std::tie(o.total_pix, o.total_tiles, o.n_iter, o.warm, o.init_warps, o.profiled,
+                        o.init_smem);
+    }
+};
+
+struct GraphEntry {
+    cudaGraphExec_t exec = nullptr;
+    std::vector<PendingTiming> timing;   // event pairs recorded by the graph itself
+    int kernels = 0;
+};
+
 }  // namespace
 
 struct rt3d_ctx {
@@ -48,6 +70,10 @@ struct rt3d_ctx {
     long long launches = 0;
     bool profiling = false;
     std::vector<PendingTiming> pending;
+    std::map<GraphKey, GraphEntry> graphs;
+    GraphEntry* capturing = nullptr;        // set while a launch sequence is being captured
+    std::vector<GraphEntry*> pending_graphs;
+    cudaStream_t cap_stream = nullptr;
     std::vector<cudaEvent_t> event_pool;
     double ms[kNumKernelClasses] = {0};
     long long counts[kNumKernelClasses] = {0};
@@ -98,18 +124,27 @@ struct LaunchScope {
     cudaEvent_t a = nullptr, b = nullptr;
     LaunchScope(rt3d_ctx* c_, cudaStream_t s_, int cls_) : c(c_), s(s_), cls(cls_)
     {
-        ++c->launches;
+        if (c->capturing) ++c->capturing->kernels;
+        else ++c->launches;
         if (c->profiling) {
             a = take_event(c);
             b = take_event(c);
-            cudaEventRecord(a, s);
+            record(a);
         }
+    }
+    // inside a capture only an "external" record becomes a node that the
+    // replayed graph records
+    void record(cudaEvent_t e)
+    {
+        if (c->capturing) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+        else cudaEventRecord(e, s);
     }
     ~LaunchScope()
     {
         if (a) {
-            cudaEventRecord(b, s);
-            c->pending.push_back({cls, a, b});
+            record(b);
+            if (c->capturing) c->capturing->timing.push_back({cls, a, b});
+            else c->pending.push_back({cls, a, b});
         }
     }
 };
@@ -363,12 +398,46 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
     if (st != RT3D_OK) return st;
     st = upload_record(c, s);
     if (st != RT3D_OK) return st;
-    RT3D_CUDA(cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), s));
-    st = launch_init(c, K, B, c->W, s, false, p->warm_start != 0);
-    if (st != RT3D_OK) return st;
-    st = launch_loop(c, B, s, p->n_iter);
-    if (st != RT3D_OK) return st;
-    return launch_final(c, B, s, p->n_iter > 0 ? 1 : 0);
+    const GraphKey key{B.total_pix, B.total_tiles, p->n_iter, p->warm_start != 0,
+                       init_warps(K.peak_sep), c->profiling ? 1 : 0, init_smem(K, K.peak_sep)};
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+        // capture the launch sequence of this geometry once, on a private stream
+        if (!c->cap_stream) RT3D_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        GraphEntry entry;
+        c->capturing = &entry;
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+        rt3d_status cst = RT3D_OK;
+        if (e == cudaSuccess) {
+            e = cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->cap_stream);
+            if (e == cudaSuccess) cst = launch_init(c, K, B, c->W, c->cap_stream, false, p->warm_start != 0);
+            if (e == cudaSuccess && cst == RT3D_OK) cst = launch_loop(c, B, c->cap_stream, p->n_iter);
+            if (e == cudaSuccess && cst == RT3D_OK) cst = launch_final(c, B, c->cap_stream, p->n_iter > 0 ? 1 : 0);
+            const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        c->capturing = nullptr;
+        if (e == cudaSuccess && cst == RT3D_OK) e = cudaGraphInstantiate(&entry.exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess || cst != RT3D_OK) {
+            for (auto& pt : entry.timing) {
+                cudaEventDestroy(pt.a);
+                cudaEventDestroy(pt.b);
+            }
+            cudaGetLastError();
+            return cst != RT3D_OK ? cst : cuda_fail(e);
+        }
+        it = c->graphs.emplace(key, std::move(entry)).first;
+    }
+    RT3D_CUDA(cudaGraphLaunch(it->second.exec, s));
+    c->launches += it->second.kernels;
+    if (c->profiling) {
+        bool seen = false;
+        for (GraphEntry* g : c->pending_graphs) seen |= g == &it->second;
+        if (!seen) c->pending_graphs.push_back(&it->second);
+    }
+    return RT3D_OK;
 }
 
 }  // namespace
@@ -506,6 +575,14 @@ void rt3d_destroy(rt3d_ctx_t* c)
         cudaEventDestroy(pt.a);
         cudaEventDestroy(pt.b);
     }
+    for (auto& kv : c->graphs) {
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        for (auto& pt : kv.second.timing) {
+            cudaEventDestroy(pt.a);
+            cudaEventDestroy(pt.b);
+        }
+    }
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (auto ev : c->event_pool) cudaEventDestroy(ev);
     delete c;
 }
@@ -802,6 +879,17 @@ rt3d_status rt3d_kernel_times(rt3d_ctx_t* c, double* ms, int64_t* launches, int 
         c->event_pool.push_back(pt.b);
     }
     c->pending.clear();
+    // a replayed graph re-records the same events: its kernels are timed once,
+    // from its most recent launch
+    for (GraphEntry* g : c->pending_graphs)
+        for (auto& pt : g->timing) {
+            if (cudaEventSynchronize(pt.b) != cudaSuccess) return RT3D_E_CUDA;
+            float v = 0.0f;
+            cudaEventElapsedTime(&v, pt.a, pt.b);
+            c->ms[pt.cls] += v;
+            c->counts[pt.cls] += 1;
+        }
+    c->pending_graphs.clear();
     for (int i = 0; i < n && i < kNumKernelClasses; ++i) {
         if (ms) ms[i] = c->ms[i];
         if (launches) launches[i] = c->counts[i];
