@@ -81,6 +81,8 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
     const int pix = blockIdx.x * (int)(blockDim.x >> 5) + warp;
     if (pix >= B.total_pix) return;
     const FrameDesc& F = B.f[frame_of_pixel(B, pix)];
+    // frames whose cold start runs in the tensor-core init
+    if (!kCompactOnly && F.tc) return;
     const int lp = pix - F.pix_base;
     const int T = F.nt;
     if (lp == 0 && lane == 0 && F.n_points) *F.n_points = 0;   // counted by the finaliser
@@ -153,7 +155,7 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
         nnz = n_stage;
         unsigned long long base = 0;
         if (lane == 0) {
-            base = atomicAdd(W.ent_count, (unsigned long long)nnz);
+            base = (unsigned long long)B.ent_base_int + atomicAdd(W.ent_count, (unsigned long long)nnz);
             if (base + nnz > (unsigned long long)W.ent_cap) {
                 atomicOr(W.status, kStatusCapacity);
                 base = ~0ull;

@@ -15,10 +15,13 @@
 #include <tuple>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "rt3d.h"
 #include "rt3d_device.cuh"
 #include "k_synth.cuh"
 #include "k_init.cuh"
+#include "k_init_tc.cuh"
 #include "k_loop.cuh"
 #include "k_compact.cuh"
 
@@ -26,8 +29,11 @@ using namespace rt3d;
 
 namespace {
 
-constexpr int kNumKernelClasses = 8;
-enum KernelClass { kcInit = 0, kcA = 1, kcB = 2, kcC = 3, kcFinal = 4, kcSynth = 5, kcCompact = 6, kcOther = 7 };
+constexpr int kNumKernelClasses = 9;
+enum KernelClass {
+    kcInit = 0, kcA = 1, kcB = 2, kcC = 3, kcFinal = 4, kcSynth = 5, kcCompact = 6, kcOther = 7,
+    kcInitTc = 8
+};
 
 struct PendingTiming {
     int cls;
@@ -40,11 +46,13 @@ struct PendingTiming {
 struct GraphKey {
     int total_pix, total_tiles, n_iter, warm, init_warps, profiled;
     size_t init_smem;
+    int tc_tiles, tc_stages, tc_nd, any_int;
     bool operator<(const GraphKey& o) const
     {
-        return std::tie(total_pix, total_tiles, n_iter, warm, init_warps, profiled, init_smem) <
+        return std::tie(total_pix, total_tiles, n_iter, warm, init_warps, profiled, init_smem, tc_tiles,
+                        tc_stages, tc_nd, any_int) <
                std::tie(o.total_pix, o.total_tiles, o.n_iter, o.warm, o.init_warps, o.profiled,
-                        o.init_smem);
+                        o.init_smem, o.tc_tiles, o.tc_stages, o.tc_nd, o.any_int);
     }
 };
 
@@ -67,6 +75,10 @@ struct rt3d_ctx {
     CallRecord* d_rec = nullptr;    // per-call tables and frame descriptors (device)
     CallRecord h_rec;               // host copy, uploaded once per call
     uint32_t* d_tmp = nullptr;      // [stride + 1] scratch of rt3d_compact
+    // tensor-core matched filter: band operands (device) and the host image last uploaded
+    uint8_t* d_band = nullptr;
+    std::vector<uint8_t> band_img, band_last;
+    int n_sms = 0;
     long long launches = 0;
     bool profiling = false;
     std::vector<PendingTiming> pending;
@@ -202,6 +214,8 @@ bool config_ok(const rt3d_config* cfg)
     return cfg->device >= 0;
 }
 
+rt3d_status build_tc_params(const rt3d_params* p, KParams* K);
+
 // Per-call tables derived from the IRF and the parameters.
 rt3d_status build_kparams(const rt3d_ctx* c, const rt3d_params* p, KParams* K)
 {
@@ -262,16 +276,134 @@ rt3d_status build_kparams(const rt3d_ctx* c, const rt3d_params* p, KParams* K)
         }
         for (int d = 0; d <= 2 * p->bkg_radius; ++d) K->bkg_ker[d] = (float)(tap[d] / ks);
     }
+    return build_tc_params(p, K);
+}
+
+// ---- tensor-core matched filter: operand tables and TMA descriptors
+
+// FP16 bits of a non-negative integer below 2^11 and BF16 bits of v 2^100 for
+// v below 2^8: both exact (the float's low mantissa bits are zero).
+uint16_t fp16_bits_of_int(int v)
+{
+    if (v == 0) return 0;
+    uint32_t fb;
+    const float f = (float)v;
+    std::memcpy(&fb, &f, 4);
+    const int e = (int)((fb >> 23) & 0xff) - 127;
+    return (uint16_t)(((e + 15) << 10) | ((fb >> 13) & 0x3ff));
+}
+
+uint16_t bf16_bits_scaled(int v)
+{
+    if (v == 0) return 0;
+    uint32_t fb;
+    const float f = std::ldexp((float)v, 100);
+    std::memcpy(&fb, &f, 4);
+    return (uint16_t)(fb >> 16);
+}
+
+// Tensor-core parameters of the log-matched filter (precision modes BF16 and
+// FP16): the block offsets an output tile reads, the nonzero K-steps of each
+// band, the stage count that fits shared memory and the exactness limits.
+rt3d_status build_tc_params(const rt3d_params* p, KParams* K)
+{
+    K->tc_mode = 0;
+    if (p->lmf_precision == RT3D_LMF_INT) return RT3D_OK;
+    const int L = K->irf_len, O = K->irf_origin;
+    if (p->peak_sep < 1 || p->peak_sep > kTcMaxSep) return RT3D_E_INVALID;
+    const int dlo = -((O + kTcBlk - 1) / kTcBlk);
+    const int dhi = (kTcBlk - 1 - O + L - 1) / kTcBlk;
+    const int nd = dhi - dlo + 1;
+    if (nd > kTcMaxOff) return RT3D_E_INVALID;
+    const int avail = kTcSmemLimit - tc_smem_bytes(nd, 0);
+    const int stages = std::min(kTcMaxStages, avail / kTcStageBytes);
+    if (stages < nd + 1) return RT3D_E_INVALID;
+    K->tc_mode = p->lmf_precision == RT3D_LMF_BF16 ? 1 : 2;
+    K->tc_dlo = dlo;
+    K->tc_nd = nd;
+    K->tc_stages = stages;
+    for (int di = 0; di < kTcMaxOff; ++di) {
+        int mask = 0;
+        for (int ks = 0; ks < 4 && di < nd; ++ks) {
+            // taps s = 64 d + i - n + origin for i in the K-step, n in [0, 64)
+            const int smin = kTcBlk * (dlo + di) + 16 * ks - 63 + O;
+            const int smax = kTcBlk * (dlo + di) + 16 * ks + 15 + O;
+            if (smax >= 0 && smin <= L - 1) mask |= 1 << ks;
+        }
+        K->tc_ksmask[di] = mask;
+    }
+    const bool bf16 = K->tc_mode == 1;
+    K->tc_count_limit = bf16 ? 128 : 1024;
+    const int unit_exp = bf16 ? -33 : -24;
+    const float wmin = std::ldexp((float)p->peak_min_photons, unit_exp);
+    std::memcpy(&K->tc_wmin_bits, &wmin, 4);
+    K->tc_unit_inv = std::ldexp(1.0f, -unit_exp);
     return RT3D_OK;
+}
+
+// The nd band operands, 128 x 64 each, in the 128-byte-swizzled K-major
+// layout the MMA reads (row n at 128 n bytes, 16-byte chunk c at c ^ (n & 7)).
+void build_band_image(const KParams& K, std::vector<uint8_t>& img)
+{
+    img.assign((size_t)K.tc_nd * kTcBBytes, 0);
+    const bool bf16 = K.tc_mode == 1;
+    const uint16_t one = bf16 ? bf16_bits_scaled(1) : fp16_bits_of_int(1);
+    for (int di = 0; di < K.tc_nd; ++di) {
+        uint8_t* blk = img.data() + (size_t)di * kTcBBytes;
+        for (int n = 0; n < kTcN; ++n)
+            for (int i = 0; i < kTcBlk; ++i) {
+                const int col = n % kTcBlk;
+                const int sidx = kTcBlk * (K.tc_dlo + di) + i - col + K.irf_origin;
+                if (sidx < 0 || sidx >= K.irf_len) continue;
+                uint16_t v;
+                if (n < kTcBlk) v = bf16 ? bf16_bits_scaled(K.lmf[sidx]) : fp16_bits_of_int(K.lmf[sidx]);
+                else v = one;
+                const size_t off = (size_t)n * 128 + (size_t)((((i >> 3) ^ (n & 7)) << 4)) + (size_t)(i & 7) * 2;
+                std::memcpy(blk + off, &v, 2);
+            }
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+// TMA descriptor of a dense histogram [npix][T] uint16: boxes of 64 bins x
+// 128 pixels, 128-byte swizzle, zero fill outside the histogram.
+rt3d_status encode_histogram_map(const rt3d_frame* f, CUtensorMap* map)
+{
+    auto enc = tensor_map_encoder();
+    if (!enc) return RT3D_E_CUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)f->t, (cuuint64_t)f->h * (cuuint64_t)f->w};
+    cuuint64_t strides[1] = {(cuuint64_t)f->t * 2};
+    cuuint32_t box[2] = {(cuuint32_t)kTcBlk, (cuuint32_t)kTcRows};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, (void*)f->dense, dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? RT3D_OK : RT3D_E_INVALID;
 }
 
 // Batch descriptors for n frames whose results go to out[i].
 rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_result* out,
-                        Batch* B)
+                        Batch* B, CallRecord* rec = nullptr, bool tc_init = false)
 {
     std::memset(B, 0, sizeof(Batch));
     B->n = n;
     int tiles = 0, pix = 0, tmax = 0;
+    int tc_tiles = 0;
+    long long tc_ent = 0;
     for (int i = 0; i < n; ++i) {
         FrameDesc& d = B->f[i];
         d.h = f[i].h;
@@ -289,6 +421,24 @@ rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3
         d.use_csr = f[i].csr_off != nullptr;
         d.ent = d.use_csr ? f[i].csr_ent : c->W.ent;
         d.gain = f[i].gain;
+        d.tc_tile_base = tc_tiles;
+        // tensor-core init of a dense frame whose rows TMA can address (16-byte
+        // aligned start and row stride); other frames take the CUDA-core path,
+        // which computes the identical integer filter
+        if (tc_init && !d.use_csr && f[i].t % 8 == 0 && ((uintptr_t)f[i].dense & 15) == 0) {
+            // each pixel's entries at a fixed offset (pixel x bins) of the
+            // frame's region, so no allocation order is needed
+            const long long cells = (long long)d.npix * f[i].t;
+            if (cells > 0xffffffffll || tc_ent + cells > c->W.ent_cap) return RT3D_E_INVALID;
+            d.tc = 1;
+            d.ent = c->W.ent + tc_ent;
+            tc_ent += cells;
+            tc_tiles += (d.npix + kTcRows - 1) / kTcRows;
+            if (rec) {
+                const rt3d_status st = encode_histogram_map(&f[i], &rec->maps[i]);
+                if (st != RT3D_OK) return st;
+            }
+        }
         if (out) {
             d.t = out[i].t;
             d.r = out[i].r;
@@ -298,6 +448,9 @@ rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3
         }
     }
     if (pix > c->stride) return RT3D_E_INVALID;
+    B->tc_tiles = tc_tiles;
+    B->tc_entries = tc_ent;
+    B->ent_base_int = tc_ent;
     B->total_tiles = tiles;
     B->total_pix = pix;
     B->max_t = tmax;
@@ -320,24 +473,61 @@ size_t init_smem(const KParams& K, int sep)
 // it may be rewritten by the next call at once.
 rt3d_status upload_record(rt3d_ctx* c, cudaStream_t s)
 {
-    RT3D_CUDA(cudaMemcpyAsync(c->d_rec, &c->h_rec, sizeof(CallRecord), cudaMemcpyHostToDevice, s));
+    const size_t bytes = c->h_rec.B.tc_tiles > 0 ? offsetof(CallRecord, maps) + sizeof(CUtensorMap) * c->h_rec.B.n
+                                                 : offsetof(CallRecord, maps);
+    RT3D_CUDA(cudaMemcpyAsync(c->d_rec, &c->h_rec, bytes, cudaMemcpyHostToDevice, s));
+    // band operands of the tensor-core filter, re-uploaded only when they change
+    if (c->h_rec.P.tc_mode && c->h_rec.B.tc_tiles > 0) {
+        build_band_image(c->h_rec.P, c->band_img);
+        if (c->band_img != c->band_last) {
+            if (!c->d_band) RT3D_CUDA(cudaMalloc((void**)&c->d_band, (size_t)kTcMaxOff * kTcBBytes));
+            RT3D_CUDA(cudaMemcpyAsync(c->d_band, c->band_img.data(), c->band_img.size(), cudaMemcpyHostToDevice, s));
+            c->band_last = c->band_img;
+        }
+    }
     return RT3D_OK;
+}
+
+// some frame initialised by the CUDA-core kernel
+bool batch_has_int(const Batch& B)
+{
+    for (int i = 0; i < B.n; ++i)
+        if (!B.f[i].tc) return true;
+    return false;
 }
 
 rt3d_status launch_init(rt3d_ctx* c, const KParams& K, const Batch& B, Work W, cudaStream_t s,
                         bool dump, bool compact_only)
 {
-    const size_t smem = init_smem(K, K.peak_sep);
-    const int warps = init_warps(K.peak_sep);
-    const int grid = (B.total_pix + warps - 1) / warps;
-    if (grid == 0) return RT3D_OK;
-    auto fn = dump ? k_init<true, false> : (compact_only ? k_init<false, true> : k_init<false, false>);
-    RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    {
-        LaunchScope ls(c, s, kcInit);
-        fn<<<grid, warps * 32, smem, s>>>(c->d_rec, W);
+    // the tensor-core kernel takes the dense frames of a cold start; the
+    // CUDA-core kernel the rest (it skips those frames)
+    const bool tc = K.tc_mode != 0 && !compact_only && B.tc_tiles > 0;
+    if (!tc || compact_only || batch_has_int(B)) {
+        const size_t smem = init_smem(K, K.peak_sep);
+        const int warps = init_warps(K.peak_sep);
+        const int grid = (B.total_pix + warps - 1) / warps;
+        if (grid > 0) {
+            auto fn = dump ? k_init<true, false> : (compact_only ? k_init<false, true> : k_init<false, false>);
+            RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+            {
+                LaunchScope ls(c, s, kcInit);
+                fn<<<grid, warps * 32, smem, s>>>(c->d_rec, W);
+            }
+            RT3D_CUDA(cudaGetLastError());
+        }
     }
-    RT3D_CUDA(cudaGetLastError());
+    if (tc) {
+        if (!c->n_sms) RT3D_CUDA(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, c->cfg.device));
+        const int smem = tc_smem_bytes(K.tc_nd, K.tc_stages);
+        const int grid = std::min(c->n_sms, B.tc_tiles);
+        auto fn = dump ? k_init_tc<true> : k_init_tc<false>;
+        RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        {
+            LaunchScope ls(c, s, kcInitTc);
+            fn<<<grid, kTcThreads, smem, s>>>(c->d_rec, W, c->d_band);
+        }
+        RT3D_CUDA(cudaGetLastError());
+    }
     return RT3D_OK;
 }
 
@@ -394,12 +584,13 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
     st = build_kparams(c, p, &K);
     if (st != RT3D_OK) return st;
     Batch& B = c->h_rec.B;
-    st = build_batch(c, n, f, out, &B);
+    st = build_batch(c, n, f, out, &B, &c->h_rec, K.tc_mode != 0 && !p->warm_start);
     if (st != RT3D_OK) return st;
     st = upload_record(c, s);
     if (st != RT3D_OK) return st;
     const GraphKey key{B.total_pix, B.total_tiles, p->n_iter, p->warm_start != 0,
-                       init_warps(K.peak_sep), c->profiling ? 1 : 0, init_smem(K, K.peak_sep)};
+                       init_warps(K.peak_sep), c->profiling ? 1 : 0, init_smem(K, K.peak_sep),
+                       B.tc_tiles, K.tc_stages, K.tc_nd, batch_has_int(B) ? 1 : 0};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         // capture the launch sequence of this geometry once, on a private stream
@@ -568,7 +759,7 @@ void rt3d_destroy(rt3d_ctx_t* c)
     cudaSetDevice(c->cfg.device);
     void* ptrs[] = {c->W.seg, c->W.ent, c->d_count, c->W.t_half, c->W.r_half, c->W.b_half,
                     c->W.alive_b, c->d_status, c->d_tmp, c->d_rec, c->s_dense, c->s_off, c->s_ent,
-                    c->s_gain, c->s_t, c->s_r, c->s_b, c->s_alive, c->s_np};
+                    c->s_gain, c->s_t, c->s_r, c->s_b, c->s_alive, c->s_np, c->d_band};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& pt : c->pending) {
@@ -670,7 +861,7 @@ rt3d_status rt3d_lmf(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d_params* p, i
     st = build_kparams(c, p, &K);
     if (st != RT3D_OK) return st;
     Batch& B = c->h_rec.B;
-    st = build_batch(c, 1, f, nullptr, &B);
+    st = build_batch(c, 1, f, nullptr, &B, &c->h_rec, K.tc_mode != 0);
     if (st != RT3D_OK) return st;
     st = upload_record(c, s);
     if (st != RT3D_OK) return st;
@@ -692,7 +883,7 @@ rt3d_status rt3d_init(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d_params* p, 
     st = build_kparams(c, p, &K);
     if (st != RT3D_OK) return st;
     Batch& B = c->h_rec.B;
-    st = build_batch(c, 1, f, out, &B);
+    st = build_batch(c, 1, f, out, &B, &c->h_rec, K.tc_mode != 0);
     if (st != RT3D_OK) return st;
     st = upload_record(c, s);
     if (st != RT3D_OK) return st;
@@ -852,6 +1043,7 @@ rt3d_status rt3d_device_status(rt3d_ctx_t* c, void* stream)
     RT3D_CUDA(cudaMemcpyAsync(&h, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
     RT3D_CUDA(cudaMemsetAsync(c->d_status, 0, sizeof(int), s));
     RT3D_CUDA(cudaStreamSynchronize(s));
+    if (h & kStatusTimeout) return RT3D_E_TIMEOUT;
     if (h & kStatusCapacity) return RT3D_E_CAPACITY;
     if (h & kStatusRange) return RT3D_E_RANGE;
     return RT3D_OK;

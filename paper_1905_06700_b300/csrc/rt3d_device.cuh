@@ -9,6 +9,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "rt3d.h"
@@ -25,6 +26,11 @@ constexpr int kIrfPad = 3;          // zero samples on each side of the padded I
 // device status bits (or-ed into Work::status)
 constexpr int kStatusCapacity = 1;
 constexpr int kStatusRange = 2;
+constexpr int kStatusTimeout = 4;
+
+// tensor-core matched filter: the block offsets a 64-position output tile
+// reads (its window of bins spans at most this many 64-bin blocks)
+constexpr int kTcMaxOff = 5;
 
 struct KParams {
     int n_iter, k;
@@ -36,6 +42,14 @@ struct KParams {
     float irf_sum;                  // sum of the float IRF samples (H in the interior)
     int peak_sep, peak_min_photons;
     int lmf_kmax;                   // largest quantised log-IRF value
+    // tensor-core matched filter (dense frames, lmf_precision BF16 / FP16)
+    int tc_mode;                    // 0 off, 1 BF16 operands, 2 FP16 operands
+    int tc_dlo, tc_nd;              // bin blocks j + tc_dlo .. j + tc_dlo + tc_nd - 1 feed output tile j
+    int tc_ksmask[kTcMaxOff];       // per block offset: which 16-bin K-steps carry nonzero taps
+    int tc_stages;                  // shared-memory stages of histogram blocks
+    int tc_count_limit;             // counts >= this are not exact as raw operand bits
+    int tc_wmin_bits;               // float bits of peak_min_photons in accumulator units
+    float tc_unit_inv;              // accumulator value * tc_unit_inv = exact integer
     float irf[kMaxIrf];             // normalised IRF samples
     int lmf[kMaxIrf];               // quantised log-IRF K_s
     float bkg_ker[2 * kMaxBkgR + 1];
@@ -50,6 +64,8 @@ struct FrameDesc {
     const uint32_t* csr_off;
     const uint32_t* ent;            // entries the loop reads (caller's or workspace)
     const float* gain;
+    int tc;                         // cold start of this frame runs in the tensor-core init
+    int tc_tile_base;               // its first 128-pixel tile there
     float* t;                       // [k][h][w] primary state (the result buffers)
     float* r;
     uint8_t* alive;
@@ -59,12 +75,16 @@ struct FrameDesc {
 
 struct Batch {
     int n, total_tiles, total_pix, max_t;
+    int tc_tiles;                   // 128-pixel tiles of the tensor-core init
+    long long tc_entries;           // entries reserved for its frames (pixels x bins)
+    long long ent_base_int;         // the CUDA-core init allocates entries from here on
     FrameDesc f[kMaxBatch];
 };
 
 struct CallRecord {
     KParams P;
     Batch B;
+    CUtensorMap maps[kMaxBatch];    // TMA descriptors of the dense histograms (tensor-core init)
 };
 
 struct Work {
@@ -91,6 +111,16 @@ __device__ __forceinline__ int frame_of_tile(const Batch& B, int tile)
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (B.f[mid].tile_base <= tile) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int frame_of_tc_tile(const Batch& B, int tile)
+{
+    int lo = 0, hi = B.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.f[mid].tc_tile_base <= tile) lo = mid; else hi = mid - 1;
     }
     return lo;
 }

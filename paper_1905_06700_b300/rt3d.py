@@ -334,11 +334,11 @@ class Context:
         check(lib().rt3d_set_profiling(self.handle, int(on)), "rt3d_set_profiling")
 
     def kernel_times(self, reset=False):
-        ms = (C.c_double * 8)()
-        n = (C.c_int64 * 8)()
-        check(lib().rt3d_kernel_times(self.handle, ms, n, 8, int(reset)), "rt3d_kernel_times")
-        names = ["init", "phase_a", "phase_b", "phase_c", "final", "synth", "compact", "other"]
-        return {names[i]: (ms[i], n[i]) for i in range(8)}
+        ms = (C.c_double * 9)()
+        n = (C.c_int64 * 9)()
+        check(lib().rt3d_kernel_times(self.handle, ms, n, 9, int(reset)), "rt3d_kernel_times")
+        names = ["init", "phase_a", "phase_b", "phase_c", "final", "synth", "compact", "other", "init_tc"]
+        return {names[i]: (ms[i], n[i]) for i in range(9)}
 
     def get_sparse(self, n_pix: int, n_ent: int, stream=None):
         seg = np.zeros((n_pix, 2), np.uint32)
