@@ -351,6 +351,9 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
             const uint32_t idesc = tc_idesc(P.tc_mode == 1 ? 1 : 0);
+            int ksmask[kTcMaxOff];            // kept in registers: read once
+#pragma unroll
+            for (int di = 0; di < kTcMaxOff; ++di) ksmask[di] = P.tc_ksmask[di];
             uint32_t g0 = 0, acc_cnt = 0;
             bool stop = false;
             for (int tile = blockIdx.x; tile < B.tc_tiles && !stop; tile += gridDim.x) {
@@ -367,17 +370,20 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
                     tc_fence_after();
                     const uint32_t dt = tmem + a * kTcN;
                     uint32_t accumulate = 0;
-                    for (int di = 0; di < nd && !stop; ++di) {
+#pragma unroll
+                    for (int di = 0; di < kTcMaxOff; ++di) {
+                        if (di >= nd || stop) continue;
                         const int b = j + dlo + di;
                         if (b < 0 || b >= nbk) continue;
                         const uint32_t gb = g0 + (uint32_t)b;
                         const uint32_t s = gb % (uint32_t)S;
+                        // TMA completion is observed through the barrier; the MMA
+                        // reads the stage in the same (async) proxy
                         if (!mbar_wait(bar_full + 8 * s, (gb / S) & 1u, abort_flag)) {
                             stop = true;
                             break;
                         }
-                        tc_fence_after();
-                        const int mask = P.tc_ksmask[di];
+                        const int mask = ksmask[di];
                         for (int ks = 0; ks < 4; ++ks) {
                             // the block of offset 0 always issues its first step, so
                             // every accumulator is written even for an all-zero band
@@ -463,40 +469,32 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
                         break;
                     }
                     const unsigned char* srow = gbase + (size_t)(nd + s) * kTcStageBytes + row * 128;
-                    uint32_t zw[32];
+                    // 16-byte chunk c (bins 8c .. 8c + 7) sits at chunk c ^ (row & 7)
+                    uint32_t nzc = 0;
 #pragma unroll
                     for (int c = 0; c < 8; ++c) {
                         const uint4 q = *reinterpret_cast<const uint4*>(srow + ((c ^ (row & 7)) << 4));
-                        zw[4 * c] = q.x;
-                        zw[4 * c + 1] = q.y;
-                        zw[4 * c + 2] = q.z;
-                        zw[4 * c + 3] = q.w;
+                        nzc |= (uint32_t)((q.x | q.y | q.z | q.w) != 0u) << c;
+                    }
+                    if (valid) {
+                        // a lane's loop runs over its own nonzero chunks only
+                        const uint32_t bin0 = (uint32_t)c_next * kTcBlk;
+                        while (nzc) {
+                            const int c = __ffs(nzc) - 1;
+                            nzc &= nzc - 1;
+                            const uint4 q = *reinterpret_cast<const uint4*>(srow + ((c ^ (row & 7)) << 4));
+                            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+                            for (int h = 0; h < 8; ++h) {
+                                const uint32_t z = (w4[h >> 1] >> ((h & 1) * 16)) & 0xffffu;
+                                if (!kDumpY && z) eout[nnz++] = ((bin0 + 8 * c + h) << 16) | z;
+                                total += z;
+                                zmax = max(zmax, z);
+                            }
+                        }
                     }
                     __syncwarp();
                     if (lane == 0) mbar_arrive(bar_empty + 8 * s);
-                    if (valid && !kDumpY) {
-                        const uint32_t bin0 = (uint32_t)c_next * kTcBlk;
-#pragma unroll
-                        for (int c = 0; c < 8; ++c) {
-                            if ((zw[4 * c] | zw[4 * c + 1] | zw[4 * c + 2] | zw[4 * c + 3]) == 0u) continue;
-#pragma unroll
-                            for (int h = 0; h < 8; ++h) {
-                                const uint32_t z = (zw[4 * c + (h >> 1)] >> ((h & 1) * 16)) & 0xffffu;
-                                if (z) {
-                                    eout[nnz++] = ((bin0 + 8 * c + h) << 16) | z;
-                                    total += z;
-                                    zmax = z > zmax ? z : zmax;
-                                }
-                            }
-                        }
-                    } else if (valid) {
-#pragma unroll
-                        for (int c = 0; c < 32; ++c) {
-                            const uint32_t z0 = zw[c] & 0xffffu, z1 = zw[c] >> 16;
-                            zmax = max(zmax, max(z0, z1));
-                            total += z0 + z1;
-                        }
-                    }
                 }
                 if (stop) break;
 
@@ -532,15 +530,25 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
                     }
                     thr = nb == K ? by[K - 1] : 0;
                     // immediate local maxima of this tile (positions 0 .. 62)
-                    uint32_t clo = 0, chi2 = 0;
+                    // eight independent 8-bit accumulators keep the dependency chains short
+                    uint32_t cb[8];
 #pragma unroll
-                    for (int i = 0; i < 63; ++i) {
-                        const int yl = i == 0 ? cy63 : (int)yv[i - 1];
-                        const int yi = (int)yv[i];
-                        const bool c = (yi > max(thr, yl)) & (yi >= (int)yv[i + 1]) & ((int)wv[i] >= wmin);
-                        if (i < 32) clo |= (uint32_t)c << i;
-                        else chi2 |= (uint32_t)c << (i - 32);
+                    for (int g8 = 0; g8 < 8; ++g8) {
+                        uint32_t m = 0;
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const int i = 8 * g8 + k;
+                            if (i < 63) {
+                                const int yl = i == 0 ? cy63 : (int)yv[i - 1];
+                                const int yi = (int)yv[i];
+                                const bool c = (yi > max(thr, yl)) & (yi >= (int)yv[i + 1]) & ((int)wv[i] >= wmin);
+                                m |= (uint32_t)c << k;
+                            }
+                        }
+                        cb[g8] = m;
                     }
+                    const uint32_t clo = cb[0] | (cb[1] << 8) | (cb[2] << 16) | (cb[3] << 24);
+                    const uint32_t chi2 = cb[4] | (cb[5] << 8) | (cb[6] << 16) | (cb[7] << 24);
                     const uint64_t cand = ((uint64_t)chi2 << 32) | clo;
                     cy62 = (int)yv[62];
                     cy63 = (int)yv[63];
