@@ -17,7 +17,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "build", "liboracle.so")
-SOURCES = ["synth.c", "model.c", "init.c", "denoise.c", "palm.c"]
+SOURCES = ["synth.c", "model.c", "init.c", "denoise.c", "palm.c", "net.c"]
 
 _lib = None
 
@@ -65,7 +65,9 @@ class Params(C.Structure):
                 ("depth_denoiser", C.c_int), ("intensity_denoiser", C.c_int),
                 ("bkg_mode", C.c_int), ("bkg_sigma", C.c_double), ("bkg_radius", C.c_int),
                 ("lmf_delta_rel", C.c_double), ("lmf_frac_bits", C.c_int),
-                ("peak_min_photons", C.c_int), ("peak_sep", C.c_int)]
+                ("peak_min_photons", C.c_int), ("peak_sep", C.c_int),
+                ("net_theta", C.POINTER(C.c_double)), ("net_scale", C.c_double),
+                ("net_fallback", C.c_double)]
 
 
 def lib():
@@ -76,6 +78,13 @@ def lib():
         _lib.or_nll_dense.restype = C.c_double
         _lib.or_peaks.restype = C.c_int
         _lib.or_num_threads.restype = C.c_int
+        _lib.or_net_nparams.restype = C.c_long
+        _lib.or_net_offset.restype = C.c_long
+        _lib.or_net_cin.restype = C.c_int
+        _lib.or_net_cout.restype = C.c_int
+        _lib.or_bf16.restype = C.c_double
+        _lib.or_bf16.argtypes = [C.c_double]
+        _lib.or_net_loss.restype = C.c_double
     return _lib
 
 
@@ -89,9 +98,23 @@ def _f32(v):
 
 
 def make_params(d: dict) -> Params:
+    """Oracle parameters from a parameter dict; floats pass through float32 so
+    that both sides see the same constants.  The learned denoiser's parameter
+    vector, if any, is d["net_theta"] (float64 array, kept alive by the
+    returned object)."""
     p = Params()
     for name, ctype in Params._fields_:
-        v = d[name]
+        if name == "net_theta":
+            th = d.get("net_theta")
+            if th is not None:
+                th = np.ascontiguousarray(th, np.float64)
+                p._theta = th
+                p.net_theta = th.ctypes.data_as(C.POINTER(C.c_double))
+            continue
+        if name in ("net_scale", "net_fallback") and name not in d:
+            v = 1.0
+        else:
+            v = d[name]
         setattr(p, name, int(v) if ctype is C.c_int else _f32(v))
     return p
 
@@ -287,3 +310,87 @@ def reconstruct(dense, irf: OIrf, prm: dict, gain=None) -> OState:
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+# ---------------------------------------------------------------------------
+# learned depth denoiser (extension; net.c)
+
+NET_LAYERS = 4
+
+
+def net_nparams() -> int:
+    return int(lib().or_net_nparams())
+
+
+def net_offset(layer: int, bias: bool) -> int:
+    return int(lib().or_net_offset(int(layer), int(bool(bias))))
+
+
+def net_channels():
+    return [(int(lib().or_net_cin(l)), int(lib().or_net_cout(l))) for l in range(NET_LAYERS)]
+
+
+def bf16(x):
+    a = np.array(x, dtype=np.float64, copy=True)
+    lib().or_bf16_round(_ptr(a, C.c_double), C.c_long(a.size))
+    return a
+
+
+def net_features(st: OState, scale: float) -> np.ndarray:
+    k, h, w = st.t.shape
+    x = np.zeros((6, h, w), np.float64)
+    lib().or_net_features(int(h), int(w), C.byref(st.c()), C.c_double(scale), _ptr(x, C.c_double))
+    return x
+
+
+def _acts_size(n, h, w):
+    return sum(n * ci * h * w for ci, _ in net_channels())
+
+
+def net_forward(theta, x, bf16_round=True):
+    """x [n][6][h][w] -> (acts, y [n][2][h][w])."""
+    theta = np.ascontiguousarray(theta, np.float64)
+    x = np.ascontiguousarray(x, np.float64)
+    n, c, h, w = x.shape
+    acts = np.zeros(_acts_size(n, h, w), np.float64)
+    y = np.zeros((n, 2, h, w), np.float64)
+    lib().or_net_forward(int(n), int(h), int(w), _ptr(theta, C.c_double), _ptr(x, C.c_double),
+                         int(bool(bf16_round)), _ptr(acts, C.c_double), _ptr(y, C.c_double))
+    return acts, y
+
+
+def net_loss(y, target, mask):
+    y = np.ascontiguousarray(y, np.float64)
+    target = np.ascontiguousarray(target, np.float64)
+    mask = np.ascontiguousarray(mask, np.uint8)
+    n, _, h, w = y.shape
+    dy = np.zeros_like(y)
+    loss = lib().or_net_loss(int(n), int(h), int(w), _ptr(y, C.c_double), _ptr(target, C.c_double),
+                             _ptr(mask, C.c_uint8), _ptr(dy, C.c_double))
+    return float(loss), dy
+
+
+def net_backward(theta, acts, dy, bf16_round=True, want_dx=False):
+    theta = np.ascontiguousarray(theta, np.float64)
+    dy = np.ascontiguousarray(dy, np.float64)
+    n, _, h, w = dy.shape
+    dtheta = np.zeros_like(theta)
+    dx = np.zeros((n, 6, h, w), np.float64) if want_dx else None
+    lib().or_net_backward(int(n), int(h), int(w), _ptr(theta, C.c_double), _ptr(acts, C.c_double),
+                          _ptr(dy, C.c_double), int(bool(bf16_round)), _ptr(dtheta, C.c_double),
+                          _ptr(dx, C.c_double) if want_dx else None)
+    return dtheta, dx
+
+
+def adamw(theta, g, m, v, step, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0):
+    """One AdamW step, in place on theta, m, v (float64 arrays)."""
+    for a in (theta, m, v):
+        assert a.dtype == np.float64 and a.flags.c_contiguous
+    g = np.ascontiguousarray(g, np.float64)
+    lib().or_adamw(_ptr(theta, C.c_double), _ptr(g, C.c_double), _ptr(m, C.c_double), _ptr(v, C.c_double),
+                   int(step), C.c_double(lr), C.c_double(beta1), C.c_double(beta2), C.c_double(eps),
+                   C.c_double(wd))
+
+
+def learned_depth(h, w, t, prm: dict, st: OState):
+    lib().or_learned_depth(int(h), int(w), int(t), C.byref(make_params(prm)), C.byref(st.c()))

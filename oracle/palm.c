@@ -14,6 +14,7 @@ void or_palm(const or_frame* f, const or_irf* irf, const or_params* p, or_state*
     for (int it = 0; it < n_iter; ++it) {
         or_t_step(f, irf, p, s);                         /* depth: gradient step */
         if (p->depth_denoiser == 1) or_apss(f->h, f->w, f->t, p, s);   /* depth: APSS */
+        if (p->depth_denoiser == 2) or_learned_depth(f->h, f->w, f->t, p, s);   /* depth: learned */
         or_r_step(f, irf, p, s);                         /* intensity: gradient step */
         or_int_lowpass(f->h, f->w, p, s);                /* intensity: low-pass + pruning */
         or_b_step(f, irf, p, s);                         /* background: gradient step */

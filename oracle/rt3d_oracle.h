@@ -68,6 +68,10 @@ typedef struct {
     int bkg_radius;
     double lmf_delta_rel;
     int lmf_frac_bits, peak_min_photons, peak_sep;
+    /* learned depth denoiser (depth_denoiser == 2): flat parameters, feature
+     * and output depth scale (bins), per-point APSS fallback threshold (bins) */
+    const double* net_theta;
+    double net_scale, net_fallback;
 } or_params;
 
 /* ---- synthetic photons (input generation, not the method) ---- */
@@ -102,6 +106,25 @@ void or_r_step(const or_frame* f, const or_irf* irf, const or_params* p, or_stat
 void or_int_lowpass(int h, int w, const or_params* p, or_state* s);
 void or_b_step(const or_frame* f, const or_irf* irf, const or_params* p, or_state* s);
 void or_bkg_lowpass(int h, int w, const or_params* p, double* b);
+
+/* ---- learned depth denoiser (extension; net.c) ---- */
+#define OR_NET_LAYERS 4
+int or_net_cin(int layer);
+int or_net_cout(int layer);
+long or_net_offset(int layer, int bias);
+long or_net_nparams(void);
+double or_bf16(double x);
+void or_bf16_round(double* x, long n);
+void or_net_features(int h, int w, const or_state* s, double scale, double* x);
+void or_net_forward(int n, int h, int w, const double* theta, const double* x, int bf16, double* acts,
+                    double* y);
+double or_net_loss(int n, int h, int w, const double* y, const double* target, const uint8_t* mask,
+                   double* dy);
+void or_net_backward(int n, int h, int w, const double* theta, const double* acts, const double* dy,
+                     int bf16, double* dtheta, double* dx);
+void or_adamw(double* theta, const double* g, double* m, double* v, int step, double lr, double beta1,
+              double beta2, double eps, double wd);
+void or_learned_depth(int h, int w, int t, const or_params* p, or_state* s);
 
 /* ---- whole method ---- */
 void or_palm(const or_frame* f, const or_irf* irf, const or_params* p, or_state* s, int n_iter);
