@@ -140,6 +140,9 @@ typedef struct {
     int32_t peak_sep;              /* local-maximum half-width, bins, >= 0 */
     int32_t lmf_precision;         /* RT3D_LMF_* */
     int32_t warm_start;            /* 1: start from the points already in the result */
+    float net_scale;               /* learned depth denoiser: depth scale of its features and output (bins), > 0 */
+    float net_fallback;            /* learned depth denoiser: a point whose proposed move exceeds this (bins)
+                                      takes the APSS update instead */
 } rt3d_params;
 
 /* Output (and, with warm_start, input) point cloud: DEVICE buffers owned by
@@ -293,6 +296,66 @@ rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_frame* f,
 rt3d_status rt3d_get_sparse(rt3d_ctx_t* ctx, uint32_t* seg_host, int64_t n_pix,
                             uint32_t* ent_host, int64_t n_ent, int64_t* n_ent_used,
                             void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned depth denoiser.  Not in the paper: an extension that stands in for
+ * the APSS depth step (Results, "Depth update") with a small convolutional
+ * network trained on pairs the plain method generates; APSS stays as the
+ * per-point fallback (params.net_fallback) and as the judge of its error.
+ *
+ * Network: four 3x3 convolutions 6 -> 48 -> 48 -> 48 -> 2, zero padding,
+ * bias, ReLU after the first three; RT3D_NET_PARAMS FP32 parameters, for each
+ * layer W[co][ci][ky][kx] then b[co].  The convolutions use the bfloat16
+ * rounding of the weights and of every layer input, with FP32 sums.
+ * Features per pixel, first two slots k, from the n alive points of any slot
+ * in the 8 neighbouring pixels within 4 scale in depth of t_k (its surface):
+ * (t_k - their mean depth) / scale clamped to +-4 (0 if n = 0), log(1 + r_k),
+ * (1 + n) / 9 for alive points (0 for dead or absent ones), channels
+ * (t0, r0, a0, t1, r1, a1).  Output
+ * y = (dt_0, dt_1) / scale.  Loss: masked mean of (y - target)^2.  Optimiser:
+ * AdamW, decay on weights only.
+ * --------------------------------------------------------------------------- */
+#define RT3D_NET_PARAMS 45074
+
+typedef struct rt3d_net rt3d_net_t;
+
+typedef struct {
+    float lr, beta1, beta2, eps, weight_decay;
+} rt3d_adamw;
+
+/* A network with device parameters, AdamW state and a workspace for batches
+ * of up to max_images images of up to max_h x max_w pixels.  Parameters
+ * start at zero (set them with rt3d_net_set_params). */
+rt3d_status rt3d_net_create(int device, int max_images, int max_h, int max_w, rt3d_net_t** out);
+void rt3d_net_destroy(rt3d_net_t* net);
+
+/* HOST FP32 [RT3D_NET_PARAMS] in / out.  Setting resets the AdamW state. */
+rt3d_status rt3d_net_set_params(rt3d_net_t* net, const float* theta);
+rt3d_status rt3d_net_get_params(rt3d_net_t* net, float* theta);
+
+/* Features of n point clouds (DEVICE): t, r [n][k][h][w] float, alive
+ * [n][k][h][w] uint8 -> x [n][6][h][w] float holding bfloat16 values. */
+rt3d_status rt3d_net_features(rt3d_net_t* net, int n, int k, int h, int w, const float* t, const float* r,
+                              const uint8_t* alive, float scale, float* x, void* stream);
+
+/* Forward pass (DEVICE): x [n][6][h][w] -> y [n][2][h][w]. */
+rt3d_status rt3d_net_forward(rt3d_net_t* net, int n, int h, int w, const float* x, float* y, void* stream);
+
+/* Forward, loss and backward (DEVICE): target [n][2][h][w] float, mask
+ * [n][2][h][w] uint8 -> grad [RT3D_NET_PARAMS] (gradient of the masked mean
+ * loss), loss [1]. */
+rt3d_status rt3d_net_gradient(rt3d_net_t* net, int n, int h, int w, const float* x, const float* target,
+                              const uint8_t* mask, float* grad, float* loss, void* stream);
+
+/* One training step: gradient as above, then AdamW on the parameters.
+ * loss [1] (DEVICE) receives the step's loss; may be NULL. */
+rt3d_status rt3d_net_train_step(rt3d_net_t* net, int n, int h, int w, const float* x, const float* target,
+                                const uint8_t* mask, const rt3d_adamw* opt, float* loss, void* stream);
+
+/* The network a context's loop uses when params.depth_denoiser is
+ * RT3D_DEPTH_LEARNED (NULL detaches).  The network must outlive its use; the
+ * context allocates its inference buffers here. */
+rt3d_status rt3d_set_depth_net(rt3d_ctx_t* ctx, rt3d_net_t* net);
 
 #ifdef __cplusplus
 }

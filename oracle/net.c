@@ -6,9 +6,12 @@
  * pairs the plain method generates.  The reading implemented here:
  *
  *  - features, per pixel and for the first two slots k (absent slots give 0):
- *      f_t = clamp((t_k - m_k) / scale, -4, 4), m_k the mean depth of the alive
- *            slot-k points of the 8 neighbouring pixels (t_k itself if none),
- *      f_r = log(1 + r_k),  f_a = 1   (alive points only; dead points give 0);
+ *    the point's same-surface neighbours are the alive points of any slot in
+ *    the 8 neighbouring pixels whose depth is within 4 scale of t_k (the
+ *    decision in single precision, like the kernel); with n of them and m
+ *    their mean depth,
+ *      f_t = clamp((t_k - m) / scale, -4, 4)  (0 when n = 0),
+ *      f_r = log(1 + r_k),  f_a = (1 + n) / 9  (alive points only; dead give 0);
  *    channel order (f_t0, f_r0, f_a0, f_t1, f_r1, f_a1);
  *  - network: four 3x3 convolutions, 6 -> 48 -> 48 -> 48 -> 2 channels, zero
  *    padding, bias, ReLU after the first three; output y = (dt_0, dt_1) / scale;
@@ -74,6 +77,7 @@ void or_net_features(int h, int w, const or_state* s, double scale, double* x)
                 const long p = (long)i * w + j;
                 double ft = 0.0, fr = 0.0, fa = 0.0;
                 if (k < s->k && s->alive[k * npix + p]) {
+                    const double tk = s->t[k * npix + p];
                     double sum = 0.0;
                     int n = 0;
                     for (int di = -1; di <= 1; ++di)
@@ -81,19 +85,22 @@ void or_net_features(int h, int w, const or_state* s, double scale, double* x)
                             if (di == 0 && dj == 0) continue;
                             const int ii = i + di, jj = j + dj;
                             if (ii < 0 || ii >= h || jj < 0 || jj >= w) continue;
-                            const long q = k * npix + (long)ii * w + jj;
-                            if (!s->alive[q]) continue;
-                            sum += s->t[q];
-                            ++n;
+                            for (int kk = 0; kk < s->k; ++kk) {
+                                const long q = kk * npix + (long)ii * w + jj;
+                                if (!s->alive[q]) continue;
+                                if (!(fabsf((float)(s->t[q] - tk)) <= (float)(4.0 * scale))) continue;
+                                sum += s->t[q];
+                                ++n;
+                            }
                         }
-                    const double tk = s->t[k * npix + p];
-                    const double m = n > 0 ? sum / n : tk;
-                    ft = (tk - m) / scale;
-                    if (ft > 4.0) ft = 4.0;
-                    if (ft < -4.0) ft = -4.0;
+                    if (n > 0) {
+                        ft = (tk - sum / n) / scale;
+                        if (ft > 4.0) ft = 4.0;
+                        if (ft < -4.0) ft = -4.0;
+                    }
                     const double rk = s->r[k * npix + p];
                     fr = log1p(rk > 0.0 ? rk : 0.0);
-                    fa = 1.0;
+                    fa = (1.0 + n) / 9.0;
                 }
                 x[(3 * k + 0) * npix + p] = ft;
                 x[(3 * k + 1) * npix + p] = fr;

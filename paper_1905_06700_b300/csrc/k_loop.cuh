@@ -346,6 +346,22 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W)
             const int ci = px / kTileW + R, cj = px % kTileW + R;
             s_tn[k][px] = apss_point(st, hstride, R, K, ci, cj, st[k * kHalo + ci * hstride + cj], P, F.nt);
         }
+    } else if (P.depth_den == RT3D_DEPTH_LEARNED) {
+        // the network's move where it stays within the fallback bound, APSS elsewhere
+        for (int i = threadIdx.x; i < n_pts; i += kTileThreads) {
+            const int px = s_pts[i] >> 2, k = s_pts[i] & 3;
+            const int ci = px / kTileW + R, cj = px % kTileW + R;
+            const float t0 = st[k * kHalo + ci * hstride + cj];
+            if (k < 2) {
+                const int gi = c.i0 + px / kTileW, gj = c.j0 + px % kTileW;
+                const float d = W.net_y[((long long)F.pix_base + gi * F.w + gj) * 2 + k] * P.net_scale;
+                if (fabsf(d) <= P.net_fallback) {
+                    s_tn[k][px] = clampf(t0 + d, 0.0f, (float)(F.nt - 1));
+                    continue;
+                }
+            }
+            s_tn[k][px] = apss_point(st, hstride, R, K, ci, cj, t0, P, F.nt);
+        }
     }
     __syncthreads();
     if (c.inb) {

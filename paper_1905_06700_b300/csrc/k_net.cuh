@@ -1,0 +1,403 @@
+// k_net.cuh -- learned depth denoiser (an extension of the method: a small
+// convolutional network standing in for the APSS depth step of Results,
+// "Depth update"; APSS stays as the per-point fallback).
+//
+// Network: four 3x3 convolutions, 6 -> 48 -> 48 -> 48 -> 2 channels, zero
+// padding, bias, ReLU after the first three.  Input features per pixel, for
+// the first two point slots k (dead or absent points give 0): with n the
+// alive points of any slot in the 8 neighbouring pixels whose depth lies
+// within 4 scale of t_k (the point's surface) and m their mean depth,
+//   f_t = clamp((t_k - m) / scale, -4, 4) (0 when n = 0),
+//   f_r = log(1 + r_k), f_a = (1 + n) / 9;
+// channels (f_t0, f_r0, f_a0, f_t1, f_r1, f_a1).
+// Output: y = (dt_0, dt_1) / scale.
+//
+// Precision: the parameters are FP32 masters; the convolutions use their
+// bfloat16 rounding (nearest even), every layer input is stored in bfloat16
+// (activations NHWC), sums and the output are FP32.  Training (backward,
+// AdamW) is FP32 and treats the roundings as identity.
+//
+// Tiling: one CTA per 8 x 16 pixel tile of a frame (the loop kernels' tiles),
+// one thread per output pixel; the input tile with its one-pixel halo and the
+// layer's weights (all input channels, a block of output channels) sit in
+// shared memory as FP32; per-pixel rows are padded by one word so that
+// neighbouring threads hit different banks.
+#pragma once
+#include "rt3d_device.cuh"
+
+namespace rt3d {
+
+constexpr int kNetLayers = 4;
+__host__ __device__ constexpr int net_cin(int l) { return l == 0 ? 6 : 48; }
+__host__ __device__ constexpr int net_cout(int l) { return l == 3 ? 2 : 48; }
+__host__ __device__ constexpr long net_woff(int l)
+{
+    return l == 0 ? 0 : net_woff(l - 1) + (long)net_cout(l - 1) * net_cin(l - 1) * 9 + net_cout(l - 1);
+}
+__host__ __device__ constexpr long net_boff(int l) { return net_woff(l) + (long)net_cout(l) * net_cin(l) * 9; }
+constexpr long kNetParams = net_woff(kNetLayers);
+static_assert(kNetParams == 45074, "parameter count");
+// FP32 copies of the rounded weights, per layer: forward [ci][k][co] and
+// backward-data [co][8 - k][ci] (flipped taps, transposed channels)
+__host__ __device__ constexpr long net_wfoff(int l)
+{
+    return l == 0 ? 0 : net_wfoff(l - 1) + (long)net_cout(l - 1) * net_cin(l - 1) * 9;
+}
+constexpr long kNetWeights = net_wfoff(kNetLayers);
+constexpr int kNetCh = 48;                    // widest layer
+constexpr int kNetHaloH = kTileH + 2, kNetHaloW = kTileW + 2, kNetHalo = kNetHaloH * kNetHaloW;
+
+__device__ __forceinline__ float bf16_bits_to_f(uint16_t b) { return __uint_as_float((uint32_t)b << 16); }
+
+// round to bfloat16, nearest even (no NaN or infinity reaches here)
+__device__ __forceinline__ uint16_t f_to_bf16_bits(float f)
+{
+    const uint32_t u = __float_as_uint(f);
+    return (uint16_t)((u + 0x7fffu + ((u >> 16) & 1u)) >> 16);
+}
+
+__device__ __forceinline__ float bf16_round(float f) { return bf16_bits_to_f(f_to_bf16_bits(f)); }
+
+// Pixel of a tile of the batch (the loop kernels' 8 x 16 tiling).
+struct NetPix {
+    int fi, gi, gj, lp, pix;   // frame, row, column, pixel in frame, pixel in batch
+    bool in;
+};
+
+__device__ __forceinline__ NetPix net_pix(const Batch& B, int tile, int li, int lj)
+{
+    NetPix q;
+    q.fi = frame_of_tile(B, tile);
+    const FrameDesc& F = B.f[q.fi];
+    const int t = tile - F.tile_base;
+    q.gi = (t / F.tiles_w) * kTileH + li;
+    q.gj = (t % F.tiles_w) * kTileW + lj;
+    q.in = q.gi < F.h && q.gj < F.w;
+    q.lp = q.gi * F.w + q.gj;
+    q.pix = F.pix_base + q.lp;
+    return q;
+}
+
+// ---------------------------------------------------------------- features
+
+// Depth, intensity and liveness of slot k at pixel q of a frame: a view of
+// either the loop's state (half-step depths in the workspace) or a caller's
+// [k][h][w] arrays.
+struct NetStateView {
+    const float* t;     // slot k of pixel lp at t[k * t_slot + t_base + lp]
+    const float* r;
+    const uint8_t* alive;
+    long long t_slot, r_slot, a_slot;
+    long long t_base, r_base, a_base;
+};
+
+__device__ __forceinline__ void net_features_at(const NetStateView& v, int K, int h, int w, int gi, int gj,
+                                                float scale, float (&x)[6])
+{
+    const int lp = gi * w + gj;
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        float ft = 0.0f, fr = 0.0f, fa = 0.0f;
+        if (k < K && v.alive[k * v.a_slot + v.a_base + lp]) {
+            const float tk = v.t[k * v.t_slot + v.t_base + lp];
+            const float reach = 4.0f * scale;
+            float sum = 0.0f;
+            int n = 0;
+            for (int di = -1; di <= 1; ++di)
+                for (int dj = -1; dj <= 1; ++dj) {
+                    if (di == 0 && dj == 0) continue;
+                    const int ii = gi + di, jj = gj + dj;
+                    if (ii < 0 || ii >= h || jj < 0 || jj >= w) continue;
+                    const int q = ii * w + jj;
+                    for (int kk = 0; kk < K; ++kk) {
+                        if (!v.alive[kk * v.a_slot + v.a_base + q]) continue;
+                        const float tq = v.t[kk * v.t_slot + v.t_base + q];
+                        if (!(fabsf(tq - tk) <= reach)) continue;
+                        sum += tq;
+                        ++n;
+                    }
+                }
+            if (n > 0) ft = clampf((tk - sum / (float)n) / scale, -4.0f, 4.0f);
+            fr = log1pf(fmaxf(v.r[k * v.r_slot + v.r_base + lp], 0.0f));
+            fa = (float)(1 + n) / 9.0f;
+        }
+        x[3 * k] = ft;
+        x[3 * k + 1] = fr;
+        x[3 * k + 2] = fa;
+    }
+}
+
+// Features of the loop's half-step state (t_half, r, alive) -> x [pix][6] bf16.
+__global__ void __launch_bounds__(kTileThreads)
+k_net_features_loop(const CallRecord* __restrict__ rec, const Work W, uint16_t* __restrict__ x, float scale)
+{
+    const Batch& B = rec->B;
+    const NetPix q = net_pix(B, blockIdx.x, threadIdx.x / kTileW, threadIdx.x % kTileW);
+    if (!q.in) return;
+    const FrameDesc& F = B.f[q.fi];
+    NetStateView v{W.t_half, F.r, F.alive, W.stride, F.npix, F.npix, F.pix_base, 0, 0};
+    float f[6];
+    net_features_at(v, rec->P.k, F.h, F.w, q.gi, q.gj, scale, f);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) x[(long long)q.pix * 6 + c] = f_to_bf16_bits(f[c]);
+}
+
+// Features of n caller images, state [n][K][h][w] -> x [n][6][h][w] (FP32
+// holding the bf16-rounded values).
+__global__ void k_net_features_images(int n, int K, int h, int w, const float* __restrict__ t,
+                                      const float* __restrict__ r, const uint8_t* __restrict__ alive,
+                                      float scale, float* __restrict__ x)
+{
+    const long long npix = (long long)h * w;
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * npix) return;
+    const int im = (int)(idx / npix);
+    const int lp = (int)(idx % npix);
+    const long long base = (long long)im * K * npix;
+    NetStateView v{t, r, alive, npix, npix, npix, base, base, base};
+    float f[6];
+    net_features_at(v, K, h, w, lp / w, lp % w, scale, f);
+#pragma unroll
+    for (int c = 0; c < 6; ++c) x[((long long)im * 6 + c) * npix + lp] = bf16_round(f[c]);
+}
+
+// x [n][6][h][w] FP32 -> NHWC bf16
+__global__ void k_net_pack_input(long long npix, int n, const float* __restrict__ x, uint16_t* __restrict__ a0)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * npix) return;
+    const long long im = idx / npix, p = idx % npix;
+#pragma unroll
+    for (int c = 0; c < 6; ++c) a0[idx * 6 + c] = f_to_bf16_bits(x[(im * 6 + c) * npix + p]);
+}
+
+// ------------------------------------------------------------- convolution
+
+enum NetConvMode { kConvHidden = 0, kConvOut = 1, kConvBackData = 2 };
+
+__host__ __device__ constexpr int net_conv_smem(int ci, int co_blk)
+{
+    return (kNetHalo * (ci + 1) + ci * 9 * co_blk) * 4;
+}
+
+// One 3x3 convolution over the batch's tiles.  blockIdx.y selects a block of
+// CO_BLK output channels.
+//   kConvHidden:   in bf16 [pix][CI] -> relu(conv + b) as bf16 [pix][CO]
+//   kConvOut:      in bf16 [pix][CI] -> conv + b as FP32 [pix][CO]
+//   kConvBackData: in FP32 gradients [pix][CI] -> conv * (ref > 0) as FP32
+//                  [pix][CO] (ref: the stored activations of the layer input)
+// wt: FP32 [CI][9][CO] (flipped and transposed for kConvBackData).
+template <int CI, int CO, int CO_BLK, int MODE>
+__global__ void __launch_bounds__(kTileThreads)
+k_net_conv(const Batch* __restrict__ Bp, const void* __restrict__ in, const float* __restrict__ wt,
+           const float* __restrict__ bias, void* __restrict__ out, const uint16_t* __restrict__ ref)
+{
+    const Batch& B = *Bp;
+    extern __shared__ float net_smem[];
+    float* s_in = net_smem;                                  // [halo px][CI + 1]
+    float* s_w = net_smem + kNetHalo * (CI + 1);             // [CI][9][CO_BLK]
+    const int co0 = blockIdx.y * CO_BLK;
+    const int tile = blockIdx.x;
+    const int fi = frame_of_tile(B, tile);
+    const FrameDesc& F = B.f[fi];
+    const int t = tile - F.tile_base;
+    const int gi0 = (t / F.tiles_w) * kTileH - 1, gj0 = (t % F.tiles_w) * kTileW - 1;
+    // weights of this output block
+    for (int e = threadIdx.x; e < CI * 9 * CO_BLK; e += kTileThreads) {
+        const int c = e % CO_BLK, rest = e / CO_BLK;
+        s_w[e] = wt[(long long)rest * CO + co0 + c];
+    }
+    // input tile with halo (zero outside the frame)
+    for (int e = threadIdx.x; e < kNetHalo * CI; e += kTileThreads) {
+        const int hp = e / CI, c = e % CI;
+        const int gi = gi0 + hp / kNetHaloW, gj = gj0 + hp % kNetHaloW;
+        float v = 0.0f;
+        if (gi >= 0 && gi < F.h && gj >= 0 && gj < F.w) {
+            const long long p = (long long)F.pix_base + gi * F.w + gj;
+            if (MODE == kConvBackData) v = static_cast<const float*>(in)[p * CI + c];
+            else v = bf16_bits_to_f(static_cast<const uint16_t*>(in)[p * CI + c]);
+        }
+        s_in[hp * (CI + 1) + c] = v;
+    }
+    __syncthreads();
+    const int li = threadIdx.x / kTileW, lj = threadIdx.x % kTileW;
+    const int gi = gi0 + 1 + li, gj = gj0 + 1 + lj;
+    if (gi >= F.h || gj >= F.w) return;
+    float acc[CO_BLK];
+#pragma unroll
+    for (int c = 0; c < CO_BLK; ++c) acc[c] = (MODE == kConvBackData) ? 0.0f : bias[co0 + c];
+    for (int ci = 0; ci < CI; ++ci) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float v = s_in[((li + k / 3) * kNetHaloW + lj + k % 3) * (CI + 1) + ci];
+            const float* wk = s_w + (ci * 9 + k) * CO_BLK;
+#pragma unroll
+            for (int c = 0; c < CO_BLK; ++c) acc[c] = fmaf(v, wk[c], acc[c]);
+        }
+    }
+    const long long p = (long long)F.pix_base + gi * F.w + gj;
+    if (MODE == kConvHidden) {
+        uint16_t* o = static_cast<uint16_t*>(out) + p * CO + co0;
+#pragma unroll
+        for (int c = 0; c < CO_BLK; ++c) o[c] = f_to_bf16_bits(fmaxf(acc[c], 0.0f));
+    } else if (MODE == kConvOut) {
+        float* o = static_cast<float*>(out) + p * CO + co0;
+#pragma unroll
+        for (int c = 0; c < CO_BLK; ++c) o[c] = acc[c];
+    } else {
+        float* o = static_cast<float*>(out) + p * CO + co0;
+        const uint16_t* rr = ref + p * CO + co0;
+#pragma unroll
+        for (int c = 0; c < CO_BLK; ++c) o[c] = bf16_bits_to_f(rr[c]) > 0.0f ? acc[c] : 0.0f;
+    }
+}
+
+// Weight and bias gradients of one layer: dW[co][ci][k] += sum_p dz[p][co]
+// a[p + k][ci], db[co] += sum_p dz[p][co], over the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...  One thread per (ci, k); each CTA adds its sums
+// once (atomics into the FP32 gradient vector).
+template <int CI, int CO>
+__global__ void __launch_bounds__(((CI * 9 + 31) / 32) * 32)
+k_net_wgrad(const Batch* __restrict__ Bp, const uint16_t* __restrict__ a, const float* __restrict__ dz,
+            float* __restrict__ dW, float* __restrict__ db)
+{
+    const Batch& B = *Bp;
+    extern __shared__ float net_smem[];
+    float* s_a = net_smem;                                   // [halo px][CI + 1]
+    float* s_dz = net_smem + kNetHalo * (CI + 1);            // [128][CO]
+    const int item = threadIdx.x;                            // (ci, k)
+    const bool active = item < CI * 9;
+    const int ci = active ? item / 9 : 0, k = active ? item % 9 : 0;
+    float acc[CO];
+#pragma unroll
+    for (int c = 0; c < CO; ++c) acc[c] = 0.0f;
+    float bacc = 0.0f;
+    for (int tile = blockIdx.x; tile < B.total_tiles; tile += gridDim.x) {
+        const int fi = frame_of_tile(B, tile);
+        const FrameDesc& F = B.f[fi];
+        const int t = tile - F.tile_base;
+        const int gi0 = (t / F.tiles_w) * kTileH - 1, gj0 = (t % F.tiles_w) * kTileW - 1;
+        __syncthreads();
+        for (int e = threadIdx.x; e < kNetHalo * CI; e += blockDim.x) {
+            const int hp = e / CI, c = e % CI;
+            const int gi = gi0 + hp / kNetHaloW, gj = gj0 + hp % kNetHaloW;
+            float v = 0.0f;
+            if (gi >= 0 && gi < F.h && gj >= 0 && gj < F.w)
+                v = bf16_bits_to_f(a[((long long)F.pix_base + gi * F.w + gj) * CI + c]);
+            s_a[hp * (CI + 1) + c] = v;
+        }
+        for (int e = threadIdx.x; e < kTileThreads * CO; e += blockDim.x) {
+            const int px = e / CO, c = e % CO;
+            const int gi = gi0 + 1 + px / kTileW, gj = gj0 + 1 + px % kTileW;
+            float v = 0.0f;
+            if (gi < F.h && gj < F.w) v = dz[((long long)F.pix_base + gi * F.w + gj) * CO + c];
+            s_dz[px * CO + c] = v;
+        }
+        __syncthreads();
+        if (active) {
+            for (int px = 0; px < kTileThreads; ++px) {
+                const int li = px / kTileW, lj = px % kTileW;
+                const float av = s_a[((li + k / 3) * kNetHaloW + lj + k % 3) * (CI + 1) + ci];
+                const float* dzp = s_dz + px * CO;
+#pragma unroll
+                for (int c = 0; c < CO; ++c) acc[c] = fmaf(av, dzp[c], acc[c]);
+            }
+        }
+        if (threadIdx.x < CO)
+            for (int px = 0; px < kTileThreads; ++px) bacc += s_dz[px * CO + threadIdx.x];
+    }
+    if (active)
+#pragma unroll
+        for (int c = 0; c < CO; ++c) atomicAdd(&dW[((long long)c * CI + ci) * 9 + k], acc[c]);
+    if (threadIdx.x < CO) atomicAdd(&db[threadIdx.x], bacc);
+}
+
+// ------------------------------------------------------------------ loss
+
+// y, target [n][2][h][w] planes (FP32) and mask -> dy [pix][2] = 2 m (y - t)
+// (the 1 / sum m factor is applied in the optimiser step), acc[0] += sum m
+// (y - t)^2, acc[1] += sum m.
+__global__ void k_net_loss(long long npix, int n, const float* __restrict__ y, const float* __restrict__ target,
+                           const uint8_t* __restrict__ mask, float* __restrict__ dy, float* __restrict__ acc)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    float se = 0.0f, ms = 0.0f;
+    if (idx < (long long)n * npix) {
+        const long long im = idx / npix, p = idx % npix;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const long long q = (im * 2 + k) * npix + p;
+            const float e = mask[q] ? y[q] - target[q] : 0.0f;
+            dy[idx * 2 + k] = 2.0f * e;
+            se += e * e;
+            ms += mask[q] ? 1.0f : 0.0f;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        se += __shfl_xor_sync(0xffffffffu, se, o);
+        ms += __shfl_xor_sync(0xffffffffu, ms, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(&acc[0], se);
+        atomicAdd(&acc[1], ms);
+    }
+}
+
+// y [pix][2] (NHWC) -> planes [n][2][h][w]
+__global__ void k_net_unpack_output(long long npix, int n, const float* __restrict__ yh, float* __restrict__ y)
+{
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= (long long)n * npix) return;
+    const long long im = idx / npix, p = idx % npix;
+    y[(im * 2) * npix + p] = yh[idx * 2];
+    y[(im * 2 + 1) * npix + p] = yh[idx * 2 + 1];
+}
+
+// --------------------------------------------------------------- optimiser
+
+// Per layer: the forward weights [ci][k][co] and the backward-data weights
+// [co][8 - k][ci], both the bfloat16 rounding of the FP32 masters.
+__global__ void k_net_prep_weights(const float* __restrict__ theta, float* __restrict__ wf, float* __restrict__ wb)
+{
+    const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= kNetWeights) return;
+    int l = 0;
+    while (l + 1 < kNetLayers && e >= net_wfoff(l + 1)) ++l;
+    const int CI = net_cin(l), CO = net_cout(l);
+    const long long q = e - net_wfoff(l);          // index in W[co][ci][k]
+    const int co = (int)(q / (CI * 9)), ci = (int)((q / 9) % CI), k = (int)(q % 9);
+    const float v = bf16_round(theta[net_woff(l) + q]);
+    wf[net_wfoff(l) + ((long long)ci * 9 + k) * CO + co] = v;
+    wb[net_wfoff(l) + ((long long)co * 9 + (8 - k)) * CI + ci] = v;
+}
+
+// AdamW (decoupled weight decay on convolution weights only); g = grad /
+// max(1, acc[1]) (the masked mean's normaliser); clears the gradient.
+__global__ void k_net_adamw(float* __restrict__ theta, float* __restrict__ grad, float* __restrict__ m,
+                            float* __restrict__ v, const float* __restrict__ acc, float lr, float beta1,
+                            float beta2, float eps, float wd, float c1, float c2)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= kNetParams) return;
+    int l = 0;
+    while (l + 1 < kNetLayers && q >= net_woff(l + 1)) ++l;
+    const bool is_w = q < net_boff(l);
+    const float g = grad[q] / fmaxf(acc[1], 1.0f);
+    const float mq = beta1 * m[q] + (1.0f - beta1) * g;
+    const float vq = beta2 * v[q] + (1.0f - beta2) * g * g;
+    m[q] = mq;
+    v[q] = vq;
+    const float upd = (mq / c1) / (sqrtf(vq / c2) + eps);
+    theta[q] -= lr * (upd + (is_w ? wd * theta[q] : 0.0f));
+    grad[q] = 0.0f;
+}
+
+// gradient / max(1, acc[1]) (the masked mean's gradient) into out
+__global__ void k_net_scale_grad(const float* __restrict__ grad, const float* __restrict__ acc, float* __restrict__ out)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < kNetParams) out[q] = grad[q] / fmaxf(acc[1], 1.0f);
+}
+
+}  // namespace rt3d

@@ -22,6 +22,7 @@
 #include "k_synth.cuh"
 #include "k_init.cuh"
 #include "k_init_tc.cuh"
+#include "k_net.cuh"
 #include "k_loop.cuh"
 #include "k_compact.cuh"
 
@@ -31,7 +32,7 @@ namespace {
 
 constexpr int kNumKernelClasses = 9;
 enum KernelClass {
-    kcInit = 0, kcA = 1, kcB = 2, kcC = 3, kcFinal = 4, kcSynth = 5, kcCompact = 6, kcOther = 7,
+    kcInit = 0, kcA = 1, kcB = 2, kcC = 3, kcFinal = 4, kcSynth = 5, kcCompact = 6, kcNet = 7,
     kcInitTc = 8
 };
 
@@ -46,13 +47,13 @@ struct PendingTiming {
 struct GraphKey {
     int total_pix, total_tiles, n_iter, warm, init_warps, profiled;
     size_t init_smem;
-    int tc_tiles, tc_stages, tc_nd, any_int;
+    int tc_tiles, tc_stages, tc_nd, any_int, learned;
     bool operator<(const GraphKey& o) const
     {
         return std::tie(total_pix, total_tiles, n_iter, warm, init_warps, profiled, init_smem, tc_tiles,
-                        tc_stages, tc_nd, any_int) <
+                        tc_stages, tc_nd, any_int, learned) <
                std::tie(o.total_pix, o.total_tiles, o.n_iter, o.warm, o.init_warps, o.profiled,
-                        o.init_smem, o.tc_tiles, o.tc_stages, o.tc_nd, o.any_int);
+                        o.init_smem, o.tc_tiles, o.tc_stages, o.tc_nd, o.any_int, o.learned);
     }
 };
 
@@ -63,6 +64,27 @@ struct GraphEntry {
 };
 
 }  // namespace
+
+// The learned depth denoiser: FP32 master parameters with AdamW state, the
+// rounded weight layouts the convolutions read, and a training workspace.
+struct rt3d_net {
+    int device = 0, max_images = 0, max_h = 0, max_w = 0;
+    long long max_pix = 0;
+    float* theta = nullptr;         // [kNetParams]
+    float* grad = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    float* wf = nullptr;            // [kNetWeights] forward layout
+    float* wb = nullptr;            // [kNetWeights] backward-data layout
+    float* acc = nullptr;           // [2] loss sums
+    uint16_t* a[4] = {nullptr, nullptr, nullptr, nullptr};   // layer inputs, NHWC bf16
+    float* yh = nullptr;            // [pix][2]
+    float* g0 = nullptr;            // [pix][48] gradient ping-pong
+    float* g1 = nullptr;
+    Batch* d_batch = nullptr;
+    Batch h_batch{};
+    int step = 0;
+};
 
 struct rt3d_ctx {
     rt3d_config cfg{};
@@ -79,6 +101,12 @@ struct rt3d_ctx {
     uint8_t* d_band = nullptr;
     std::vector<uint8_t> band_img, band_last;
     int n_sms = 0;
+    // learned depth denoiser: the attached network and the loop's inference buffers
+    rt3d_net* net = nullptr;
+    uint16_t* net_a0 = nullptr;     // [stride][6]
+    uint16_t* net_a1 = nullptr;     // [stride][48]
+    uint16_t* net_a2 = nullptr;     // [stride][48]
+    float* net_y = nullptr;         // [stride][2]
     long long launches = 0;
     bool profiling = false;
     std::vector<PendingTiming> pending;
@@ -199,6 +227,7 @@ bool params_ok(const rt3d_config* cfg, const rt3d_params* p)
     if (p->peak_sep < 0 || p->peak_sep > 4096) return false;
     if (p->lmf_precision < 0 || p->lmf_precision > 2) return false;
     if (p->warm_start < 0 || p->warm_start > 1) return false;
+    if (!(p->net_scale > 0.0f) || !std::isfinite(p->net_scale) || !std::isfinite(p->net_fallback)) return false;
     return true;
 }
 
@@ -245,6 +274,8 @@ rt3d_status build_kparams(const rt3d_ctx* c, const rt3d_params* p, KParams* K)
     K->irf_origin = c->irf_origin;
     K->peak_sep = p->peak_sep;
     K->peak_min_photons = p->peak_min_photons;
+    K->net_scale = p->net_scale;
+    K->net_fallback = p->net_fallback;
     float fsum = 0.0f;
     double hmax = 0.0;
     for (int s = 0; s < c->irf_len; ++s) {
@@ -531,12 +562,53 @@ rt3d_status launch_init(rt3d_ctx* c, const KParams& K, const Batch& B, Work W, c
     return RT3D_OK;
 }
 
+template <int CI, int CO, int CO_BLK, int MODE>
+rt3d_status launch_conv(rt3d_ctx* c, int tiles, const Batch* B, const void* in, const float* wt,
+                        const float* bias, void* out, const uint16_t* ref, cudaStream_t s)
+{
+    auto fn = k_net_conv<CI, CO, CO_BLK, MODE>;
+    const int smem = net_conv_smem(CI, CO_BLK);
+    RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    LaunchScope ls(c, s, kcNet);
+    fn<<<dim3(tiles, CO / CO_BLK), kTileThreads, smem, s>>>(B, in, wt, bias, out, ref);
+    return RT3D_OK;
+}
+
+// Forward pass of the network over a batch's tiles: a0 -> a1 -> a2 -> a3 -> y.
+rt3d_status net_forward_tiles(rt3d_ctx* c, const rt3d_net* net, int tiles, const Batch* B, const uint16_t* a0,
+                              uint16_t* a1, uint16_t* a2, uint16_t* a3, float* y, cudaStream_t s)
+{
+    rt3d_status st = launch_conv<6, 48, 48, kConvHidden>(c, tiles, B, a0, net->wf + net_wfoff(0),
+                                                         net->theta + net_boff(0), a1, nullptr, s);
+    if (st == RT3D_OK)
+        st = launch_conv<48, 48, 24, kConvHidden>(c, tiles, B, a1, net->wf + net_wfoff(1),
+                                                  net->theta + net_boff(1), a2, nullptr, s);
+    if (st == RT3D_OK)
+        st = launch_conv<48, 48, 24, kConvHidden>(c, tiles, B, a2, net->wf + net_wfoff(2),
+                                                  net->theta + net_boff(2), a3, nullptr, s);
+    if (st == RT3D_OK)
+        st = launch_conv<48, 2, 2, kConvOut>(c, tiles, B, a3, net->wf + net_wfoff(3), net->theta + net_boff(3),
+                                             y, nullptr, s);
+    return st;
+}
+
 rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
 {
+    const bool learned = c->h_rec.P.depth_den == RT3D_DEPTH_LEARNED;
     for (int it = 0; it < n_iter; ++it) {
         {
             LaunchScope ls(c, s, kcA);
             k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W, it == 0 ? 1 : 0);
+        }
+        if (learned) {
+            {
+                LaunchScope ls(c, s, kcNet);
+                k_net_features_loop<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W, c->net_a0,
+                                                                           c->h_rec.P.net_scale);
+            }
+            const rt3d_status st = net_forward_tiles(c, c->net, B.total_tiles, &c->d_rec->B, c->net_a0, c->net_a1,
+                                                     c->net_a2, c->net_a1, c->net_y, s);
+            if (st != RT3D_OK) return st;
         }
         {
             LaunchScope ls(c, s, kcB);
@@ -570,7 +642,7 @@ rt3d_status check_common(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_par
         if (!frame_ok(&c->cfg, &f[i])) return RT3D_E_INVALID;
         if (out && (!out[i].t || !out[i].r || !out[i].alive || !out[i].b)) return RT3D_E_INVALID;
     }
-    if (p->depth_denoiser == RT3D_DEPTH_LEARNED) return RT3D_E_UNIMPL;
+    if (p->depth_denoiser == RT3D_DEPTH_LEARNED && !c->net) return RT3D_E_INVALID;
     return RT3D_OK;
 }
 
@@ -590,7 +662,8 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
     if (st != RT3D_OK) return st;
     const GraphKey key{B.total_pix, B.total_tiles, p->n_iter, p->warm_start != 0,
                        init_warps(K.peak_sep), c->profiling ? 1 : 0, init_smem(K, K.peak_sep),
-                       B.tc_tiles, K.tc_stages, K.tc_nd, batch_has_int(B) ? 1 : 0};
+                       B.tc_tiles, K.tc_stages, K.tc_nd, batch_has_int(B) ? 1 : 0,
+                       K.depth_den == RT3D_DEPTH_LEARNED ? 1 : 0};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         // capture the launch sequence of this geometry once, on a private stream
@@ -685,6 +758,8 @@ rt3d_status rt3d_default_params(rt3d_params* p)
     p->peak_sep = 8;
     p->lmf_precision = RT3D_LMF_INT;
     p->warm_start = 0;
+    p->net_scale = 3.0f;
+    p->net_fallback = 6.0f;
     return RT3D_OK;
 }
 
@@ -759,7 +834,8 @@ void rt3d_destroy(rt3d_ctx_t* c)
     cudaSetDevice(c->cfg.device);
     void* ptrs[] = {c->W.seg, c->W.ent, c->d_count, c->W.t_half, c->W.r_half, c->W.b_half,
                     c->W.alive_b, c->d_status, c->d_tmp, c->d_rec, c->s_dense, c->s_off, c->s_ent,
-                    c->s_gain, c->s_t, c->s_r, c->s_b, c->s_alive, c->s_np, c->d_band};
+                    c->s_gain, c->s_t, c->s_r, c->s_b, c->s_alive, c->s_np, c->d_band,
+                    c->net_a0, c->net_a1, c->net_a2, c->net_y};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto& pt : c->pending) {
@@ -1113,6 +1189,280 @@ rt3d_status rt3d_get_sparse(rt3d_ctx_t* c, uint32_t* seg_host, int64_t n_pix, ui
 
 }  // extern "C"
 
+// ---------------------------------------------------------------- learned depth denoiser
+
+namespace {
+
+// n images of h x w as a batch of the loop kernels' tiles
+rt3d_status net_batch(rt3d_net* net, int n, int h, int w, cudaStream_t s)
+{
+    if (n < 1 || n > net->max_images || h < 1 || w < 1 || h > net->max_h || w > net->max_w) return RT3D_E_INVALID;
+    Batch& B = net->h_batch;
+    std::memset(&B, 0, sizeof(Batch));
+    B.n = n;
+    const int tw = (w + kTileW - 1) / kTileW, th = (h + kTileH - 1) / kTileH;
+    for (int i = 0; i < n; ++i) {
+        FrameDesc& d = B.f[i];
+        d.h = h;
+        d.w = w;
+        d.npix = h * w;
+        d.tiles_w = tw;
+        d.tile_base = i * tw * th;
+        d.pix_base = i * h * w;
+    }
+    B.total_tiles = n * tw * th;
+    B.total_pix = n * h * w;
+    RT3D_CUDA(cudaMemcpyAsync(net->d_batch, &B, sizeof(Batch), cudaMemcpyHostToDevice, s));
+    return RT3D_OK;
+}
+
+template <int CI, int CO>
+rt3d_status launch_wgrad(const rt3d_net* net, int l, const uint16_t* a, const float* dz, cudaStream_t s)
+{
+    auto fn = k_net_wgrad<CI, CO>;
+    const int threads = ((CI * 9 + 31) / 32) * 32;
+    const int smem = (kNetHalo * (CI + 1) + kTileThreads * CO) * 4;
+    RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    const int grid = std::min(net->h_batch.total_tiles, 296);
+    fn<<<grid, threads, smem, s>>>(net->d_batch, a, dz, net->grad + net_woff(l), net->grad + net_boff(l));
+    RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}
+
+// forward, loss and backward of n images into net->grad (unnormalised) and net->acc
+rt3d_status net_fwd_bwd(rt3d_net* net, int n, int h, int w, const float* x, const float* target,
+                        const uint8_t* mask, cudaStream_t s)
+{
+    rt3d_status st = net_batch(net, n, h, w, s);
+    if (st != RT3D_OK) return st;
+    const long long npix = (long long)h * w;
+    const long long cnt = npix * n;
+    const int blocks = (int)((cnt + 255) / 256);
+    k_net_pack_input<<<blocks, 256, 0, s>>>(npix, n, x, net->a[0]);
+    // a throwaway context object carries only the launch bookkeeping
+    rt3d_ctx tmp;
+    st = net_forward_tiles(&tmp, net, net->h_batch.total_tiles, net->d_batch, net->a[0], net->a[1], net->a[2],
+                           net->a[3], net->yh, s);
+    if (st != RT3D_OK) return st;
+    float* yplanes = net->g1;   // [n][2][h][w] scratch before the backward pass needs g1
+    k_net_unpack_output<<<blocks, 256, 0, s>>>(npix, n, net->yh, yplanes);
+    RT3D_CUDA(cudaMemsetAsync(net->acc, 0, 2 * sizeof(float), s));
+    k_net_loss<<<blocks, 256, 0, s>>>(npix, n, yplanes, target, mask, net->g0, net->acc);
+    const int T = net->h_batch.total_tiles;
+    const Batch* Bd = net->d_batch;
+    // layer 3: dy (g0, 2 channels) -> dz2 (g1)
+    st = launch_wgrad<48, 2>(net, 3, net->a[3], net->g0, s);
+    if (st == RT3D_OK)
+        st = launch_conv<2, 48, 48, kConvBackData>(&tmp, T, Bd, net->g0, net->wb + net_wfoff(3), nullptr, net->g1,
+                                                   net->a[3], s);
+    // layer 2: dz2 (g1) -> dz1 (g0)
+    if (st == RT3D_OK) st = launch_wgrad<48, 48>(net, 2, net->a[2], net->g1, s);
+    if (st == RT3D_OK)
+        st = launch_conv<48, 48, 24, kConvBackData>(&tmp, T, Bd, net->g1, net->wb + net_wfoff(2), nullptr, net->g0,
+                                                    net->a[2], s);
+    // layer 1: dz1 (g0) -> dz0 (g1)
+    if (st == RT3D_OK) st = launch_wgrad<48, 48>(net, 1, net->a[1], net->g0, s);
+    if (st == RT3D_OK)
+        st = launch_conv<48, 48, 24, kConvBackData>(&tmp, T, Bd, net->g0, net->wb + net_wfoff(1), nullptr, net->g1,
+                                                    net->a[1], s);
+    // layer 0
+    if (st == RT3D_OK) st = launch_wgrad<6, 48>(net, 0, net->a[0], net->g1, s);
+    RT3D_CUDA(cudaGetLastError());
+    return st;
+}
+
+rt3d_status net_prep(rt3d_net* net, cudaStream_t s)
+{
+    k_net_prep_weights<<<(int)((kNetWeights + 255) / 256), 256, 0, s>>>(net->theta, net->wf, net->wb);
+    RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rt3d_status rt3d_net_create(int device, int max_images, int max_h, int max_w, rt3d_net_t** out)
+{
+    if (!out) return RT3D_E_INVALID;
+    *out = nullptr;
+    if (max_images < 1 || max_images > RT3D_MAX_BATCH || max_h < 1 || max_w < 1) return RT3D_E_INVALID;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return RT3D_E_CUDA;
+    RT3D_CUDA(cudaSetDevice(device));
+    rt3d_net* net = new (std::nothrow) rt3d_net();
+    if (!net) return RT3D_E_NOMEM;
+    net->device = device;
+    net->max_images = max_images;
+    net->max_h = max_h;
+    net->max_w = max_w;
+    net->max_pix = (long long)max_images * max_h * max_w;
+    cudaError_t e = cudaSuccess;
+    auto alloc = [&](void** ptr, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+    };
+    const size_t P = sizeof(float) * kNetParams;
+    alloc((void**)&net->theta, P);
+    alloc((void**)&net->grad, P);
+    alloc((void**)&net->m, P);
+    alloc((void**)&net->v, P);
+    alloc((void**)&net->wf, sizeof(float) * kNetWeights);
+    alloc((void**)&net->wb, sizeof(float) * kNetWeights);
+    alloc((void**)&net->acc, 2 * sizeof(float));
+    alloc((void**)&net->a[0], sizeof(uint16_t) * 6 * net->max_pix);
+    for (int l = 1; l < 4; ++l) alloc((void**)&net->a[l], sizeof(uint16_t) * kNetCh * net->max_pix);
+    alloc((void**)&net->yh, sizeof(float) * 2 * net->max_pix);
+    alloc((void**)&net->g0, sizeof(float) * kNetCh * net->max_pix);
+    alloc((void**)&net->g1, sizeof(float) * kNetCh * net->max_pix);
+    alloc((void**)&net->d_batch, sizeof(Batch));
+    if (e == cudaSuccess) e = cudaMemset(net->theta, 0, P);
+    if (e == cudaSuccess) e = cudaMemset(net->grad, 0, P);
+    if (e == cudaSuccess) e = cudaMemset(net->m, 0, P);
+    if (e == cudaSuccess) e = cudaMemset(net->v, 0, P);
+    if (e == cudaSuccess && net_prep(net, nullptr) != RT3D_OK) e = cudaErrorUnknown;
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        rt3d_net_destroy(net);
+        return cuda_fail(e);
+    }
+    *out = net;
+    return RT3D_OK;
+}
+
+void rt3d_net_destroy(rt3d_net_t* net)
+{
+    if (!net) return;
+    cudaSetDevice(net->device);
+    void* ptrs[] = {net->theta, net->grad, net->m, net->v, net->wf, net->wb, net->acc, net->a[0], net->a[1],
+                    net->a[2], net->a[3], net->yh, net->g0, net->g1, net->d_batch};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete net;
+}
+
+rt3d_status rt3d_net_set_params(rt3d_net_t* net, const float* theta)
+{
+    if (!net || !theta) return RT3D_E_INVALID;
+    RT3D_CUDA(cudaSetDevice(net->device));
+    const size_t P = sizeof(float) * kNetParams;
+    RT3D_CUDA(cudaMemcpy(net->theta, theta, P, cudaMemcpyHostToDevice));
+    RT3D_CUDA(cudaMemset(net->grad, 0, P));
+    RT3D_CUDA(cudaMemset(net->m, 0, P));
+    RT3D_CUDA(cudaMemset(net->v, 0, P));
+    net->step = 0;
+    rt3d_status st = net_prep(net, nullptr);
+    if (st != RT3D_OK) return st;
+    RT3D_CUDA(cudaDeviceSynchronize());
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_net_get_params(rt3d_net_t* net, float* theta)
+{
+    if (!net || !theta) return RT3D_E_INVALID;
+    RT3D_CUDA(cudaSetDevice(net->device));
+    RT3D_CUDA(cudaDeviceSynchronize());
+    RT3D_CUDA(cudaMemcpy(theta, net->theta, sizeof(float) * kNetParams, cudaMemcpyDeviceToHost));
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_net_features(rt3d_net_t* net, int n, int k, int h, int w, const float* t, const float* r,
+                              const uint8_t* alive, float scale, float* x, void* stream)
+{
+    if (!net || !t || !r || !alive || !x || n < 1 || k < 1 || k > RT3D_MAX_K || h < 1 || w < 1) return RT3D_E_INVALID;
+    if (!(scale > 0.0f)) return RT3D_E_INVALID;
+    RT3D_CUDA(cudaSetDevice(net->device));
+    const long long cnt = (long long)n * h * w;
+    k_net_features_images<<<(int)((cnt + 255) / 256), 256, 0, (cudaStream_t)stream>>>(n, k, h, w, t, r, alive,
+                                                                                      scale, x);
+    RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_net_forward(rt3d_net_t* net, int n, int h, int w, const float* x, float* y, void* stream)
+{
+    if (!net || !x || !y) return RT3D_E_INVALID;
+    RT3D_CUDA(cudaSetDevice(net->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    rt3d_status st = net_batch(net, n, h, w, s);
+    if (st != RT3D_OK) return st;
+    const long long npix = (long long)h * w;
+    const int blocks = (int)((npix * n + 255) / 256);
+    k_net_pack_input<<<blocks, 256, 0, s>>>(npix, n, x, net->a[0]);
+    rt3d_ctx tmp;
+    st = net_forward_tiles(&tmp, net, net->h_batch.total_tiles, net->d_batch, net->a[0], net->a[1], net->a[2],
+                           net->a[3], net->yh, s);
+    if (st != RT3D_OK) return st;
+    k_net_unpack_output<<<blocks, 256, 0, s>>>(npix, n, net->yh, y);
+    RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_net_gradient(rt3d_net_t* net, int n, int h, int w, const float* x, const float* target,
+                              const uint8_t* mask, float* grad, float* loss, void* stream)
+{
+    if (!net || !x || !target || !mask || !grad) return RT3D_E_INVALID;
+    RT3D_CUDA(cudaSetDevice(net->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    RT3D_CUDA(cudaMemsetAsync(net->grad, 0, sizeof(float) * kNetParams, s));
+    rt3d_status st = net_fwd_bwd(net, n, h, w, x, target, mask, s);
+    if (st != RT3D_OK) return st;
+    k_net_scale_grad<<<(int)((kNetParams + 255) / 256), 256, 0, s>>>(net->grad, net->acc, grad);
+    RT3D_CUDA(cudaGetLastError());
+    if (loss) k_net_scale_grad<<<1, 1, 0, s>>>(net->acc, net->acc, loss);   // acc[0] / max(1, acc[1])
+    RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_net_train_step(rt3d_net_t* net, int n, int h, int w, const float* x, const float* target,
+                                const uint8_t* mask, const rt3d_adamw* opt, float* loss, void* stream)
+{
+    if (!net || !x || !target || !mask || !opt) return RT3D_E_INVALID;
+    if (!(opt->lr >= 0.0f) || !(opt->beta1 >= 0.0f && opt->beta1 < 1.0f) || !(opt->beta2 >= 0.0f && opt->beta2 < 1.0f) ||
+        !(opt->eps > 0.0f) || !(opt->weight_decay >= 0.0f))
+        return RT3D_E_INVALID;
+    RT3D_CUDA(cudaSetDevice(net->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    rt3d_status st = net_fwd_bwd(net, n, h, w, x, target, mask, s);
+    if (st != RT3D_OK) return st;
+    if (loss) k_net_scale_grad<<<1, 1, 0, s>>>(net->acc, net->acc, loss);
+    net->step += 1;
+    const float c1 = 1.0f - (float)std::pow((double)opt->beta1, net->step);
+    const float c2 = 1.0f - (float)std::pow((double)opt->beta2, net->step);
+    k_net_adamw<<<(int)((kNetParams + 255) / 256), 256, 0, s>>>(net->theta, net->grad, net->m, net->v, net->acc,
+                                                               opt->lr, opt->beta1, opt->beta2, opt->eps,
+                                                               opt->weight_decay, c1, c2);
+    RT3D_CUDA(cudaGetLastError());
+    return net_prep(net, s);
+}
+
+rt3d_status rt3d_set_depth_net(rt3d_ctx_t* c, rt3d_net_t* net)
+{
+    if (!c) return RT3D_E_INVALID;
+    if (net && net->device != c->cfg.device) return RT3D_E_INVALID;
+    RT3D_CUDA(cudaSetDevice(c->cfg.device));
+    if (net && !c->net_a0) {
+        cudaError_t e = cudaSuccess;
+        auto alloc = [&](void** ptr, size_t bytes) {
+            if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
+        };
+        alloc((void**)&c->net_a0, sizeof(uint16_t) * 6 * c->stride);
+        alloc((void**)&c->net_a1, sizeof(uint16_t) * kNetCh * c->stride);
+        alloc((void**)&c->net_a2, sizeof(uint16_t) * kNetCh * c->stride);
+        alloc((void**)&c->net_y, sizeof(float) * 2 * c->stride);
+        if (e != cudaSuccess) return cuda_fail(e);
+        c->W.net_y = c->net_y;
+        // graphs captured before hold the old Work descriptor
+        for (auto& kv : c->graphs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        c->graphs.clear();
+        c->pending_graphs.clear();
+    }
+    c->net = net;
+    return RT3D_OK;
+}
+
+}  // extern "C"
+
 // ============================================================================
 // Reconstruction without any allocation (rt3d_reconstruct_noalloc).
 //
@@ -1202,6 +1552,8 @@ rt3d_status static_kparams(const rt3d_irf* irf, const rt3d_params* p, KParams* K
     K->irf_origin = irf->origin;
     K->peak_sep = p->peak_sep;
     K->peak_min_photons = p->peak_min_photons;
+    K->net_scale = p->net_scale;
+    K->net_fallback = p->net_fallback;
     float fsum = 0.0f;
     double hmax = 0.0;
     for (int s = 0; s < irf->len; ++s) {

@@ -50,6 +50,7 @@ struct KParams {
     int tc_count_limit;             // counts >= this are not exact as raw operand bits
     int tc_wmin_bits;               // float bits of peak_min_photons in accumulator units
     float tc_unit_inv;              // accumulator value * tc_unit_inv = exact integer
+    float net_scale, net_fallback;  // learned depth denoiser: feature/output scale, APSS fallback threshold
     float irf[kMaxIrf];             // normalised IRF samples
     int lmf[kMaxIrf];               // quantised log-IRF K_s
     float bkg_ker[2 * kMaxBkgR + 1];
@@ -97,6 +98,7 @@ struct Work {
     float* b_half;                  // [stride]
     uint8_t* alive_b;               // [K][stride] pruning output (ping-pong with alive)
     int32_t* y_out;                 // matched-filter dump (rt3d_lmf) or null
+    const float* net_y;             // learned depth denoiser output [pix][2] (dt / scale) or null
     int stride;
     int* status;
 };

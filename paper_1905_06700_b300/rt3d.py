@@ -64,7 +64,16 @@ class Params(C.Structure):
                 ("bkg_mode", C.c_int32), ("bkg_sigma", C.c_float), ("bkg_radius", C.c_int32),
                 ("lmf_delta_rel", C.c_float), ("lmf_frac_bits", C.c_int32),
                 ("peak_min_photons", C.c_int32), ("peak_sep", C.c_int32),
-                ("lmf_precision", C.c_int32), ("warm_start", C.c_int32)]
+                ("lmf_precision", C.c_int32), ("warm_start", C.c_int32),
+                ("net_scale", C.c_float), ("net_fallback", C.c_float)]
+
+
+class AdamW(C.Structure):
+    _fields_ = [("lr", C.c_float), ("beta1", C.c_float), ("beta2", C.c_float), ("eps", C.c_float),
+                ("weight_decay", C.c_float)]
+
+
+NET_PARAMS = 45074
 
 
 class Result(C.Structure):
@@ -98,6 +107,15 @@ def lib():
         "rt3d_default_params": (C.c_int, [C.POINTER(Params)]),
         "rt3d_validate": (C.c_int, [C.POINTER(Config), C.POINTER(Frame), C.POINTER(Params)]),
         "rt3d_create": (C.c_int, [C.POINTER(Config), C.POINTER(Irf), C.POINTER(_P)]),
+        "rt3d_net_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
+        "rt3d_net_destroy": (None, [_P]),
+        "rt3d_net_set_params": (C.c_int, [_P, _P]),
+        "rt3d_net_get_params": (C.c_int, [_P, _P]),
+        "rt3d_net_features": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.c_float, _P, _P]),
+        "rt3d_net_forward": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P]),
+        "rt3d_net_gradient": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, _P, _P, _P]),
+        "rt3d_net_train_step": (C.c_int, [_P, C.c_int, C.c_int, C.c_int, _P, _P, _P, C.POINTER(AdamW), _P, _P]),
+        "rt3d_set_depth_net": (C.c_int, [_P, _P]),
         "rt3d_destroy": (None, [_P]),
         "rt3d_synthesize": (C.c_int, [_P, C.POINTER(Scene), C.c_uint64, _P, _P]),
         "rt3d_compact": (C.c_int, [_P, C.POINTER(Frame), _P, _P, C.c_int64,
@@ -324,6 +342,12 @@ class Context:
                                C.byref(rs), _stream(stream)), "rt3d_phase")
         return state
 
+    def set_depth_net(self, net):
+        """Attach a Net as the loop's learned depth denoiser (None detaches)."""
+        check(lib().rt3d_set_depth_net(self.handle, net.handle if net is not None else None),
+              "rt3d_set_depth_net")
+        self._net = net
+
     def device_status(self, stream=None) -> int:
         return lib().rt3d_device_status(self.handle, _stream(stream))
 
@@ -337,7 +361,7 @@ class Context:
         ms = (C.c_double * 9)()
         n = (C.c_int64 * 9)()
         check(lib().rt3d_kernel_times(self.handle, ms, n, 9, int(reset)), "rt3d_kernel_times")
-        names = ["init", "phase_a", "phase_b", "phase_c", "final", "synth", "compact", "other", "init_tc"]
+        names = ["init", "phase_a", "phase_b", "phase_c", "final", "synth", "compact", "net", "init_tc"]
         return {names[i]: (ms[i], n[i]) for i in range(9)}
 
     def get_sparse(self, n_pix: int, n_ent: int, stream=None):
@@ -388,3 +412,68 @@ def rt3d_reconstruct_noalloc(irf_samples, irf_origin: int, frame: Frame, params,
     p = params_from(params)
     return lib().rt3d_reconstruct_noalloc(C.byref(irf), C.byref(frame), C.byref(p),
                                           C.byref(result), _stream(stream))
+
+
+class Net:
+    """The learned depth denoiser's network (device parameters, AdamW state and
+    a training workspace for up to max_images images of max_h x max_w)."""
+
+    def __init__(self, max_images: int, max_h: int, max_w: int, device: int = 0):
+        import torch
+        self.torch = torch
+        self.device = torch.device("cuda", device)
+        h = _P()
+        check(lib().rt3d_net_create(int(device), int(max_images), int(max_h), int(max_w), C.byref(h)),
+              "rt3d_net_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rt3d_net_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, theta):
+        a = np.ascontiguousarray(np.asarray(theta, np.float32))
+        assert a.size == NET_PARAMS
+        check(lib().rt3d_net_set_params(self.handle, a.ctypes.data_as(_P)), "rt3d_net_set_params")
+
+    def get_params(self) -> np.ndarray:
+        a = np.zeros(NET_PARAMS, np.float32)
+        check(lib().rt3d_net_get_params(self.handle, a.ctypes.data_as(_P)), "rt3d_net_get_params")
+        return a
+
+    def features(self, t, r, alive, scale: float, stream=None):
+        """t, r, alive [n][k][h][w] (device) -> x [n][6][h][w]."""
+        n, k, h, w = t.shape
+        x = self.torch.empty((n, 6, h, w), dtype=self.torch.float32, device=self.device)
+        check(lib().rt3d_net_features(self.handle, n, k, h, w, _ptr(t), _ptr(r), _ptr(alive), float(scale),
+                                      _ptr(x), _stream(stream)), "rt3d_net_features")
+        return x
+
+    def forward(self, x, stream=None):
+        n, _, h, w = x.shape
+        y = self.torch.empty((n, 2, h, w), dtype=self.torch.float32, device=self.device)
+        check(lib().rt3d_net_forward(self.handle, n, h, w, _ptr(x), _ptr(y), _stream(stream)),
+              "rt3d_net_forward")
+        return y
+
+    def gradient(self, x, target, mask, stream=None):
+        n, _, h, w = x.shape
+        g = self.torch.empty(NET_PARAMS, dtype=self.torch.float32, device=self.device)
+        loss = self.torch.empty(1, dtype=self.torch.float32, device=self.device)
+        check(lib().rt3d_net_gradient(self.handle, n, h, w, _ptr(x), _ptr(target), _ptr(mask), _ptr(g),
+                                      _ptr(loss), _stream(stream)), "rt3d_net_gradient")
+        return g, loss
+
+    def train_step(self, x, target, mask, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0,
+                   loss=None, stream=None):
+        n, _, h, w = x.shape
+        opt = AdamW(lr, beta1, beta2, eps, weight_decay)
+        check(lib().rt3d_net_train_step(self.handle, n, h, w, _ptr(x), _ptr(target), _ptr(mask), C.byref(opt),
+                                        _ptr(loss), _stream(stream)), "rt3d_net_train_step")

@@ -340,6 +340,7 @@ def make_params(scene: Scene, **over) -> dict:
         lmf_delta_rel=1e-3, lmf_frac_bits=5, peak_min_photons=2,
         peak_sep=max(2, int(math.ceil(2.0 * math.sqrt(var)))),
         lmf_precision=0, warm_start=0,
+        net_scale=math.sqrt(var), net_fallback=math.sqrt(var) / 3.0,
     )
     p.update(over)
     return p

@@ -1,0 +1,226 @@
+"""Learned depth denoiser on the GPU (the library's own forward, backward and
+AdamW kernels) against the FP64 oracle, its place in the PALM loop, and what
+training it gains over the method without a depth denoiser."""
+import numpy as np
+import pytest
+
+import scenes
+from gpu_util import make_ctx, np_of, oracle_irf, torch_mod, upload_u16, workload_params
+
+pytestmark = pytest.mark.gpu
+
+
+def _net(n=4, h=32, w=32):
+    from paper_1905_06700_b300 import rt3d as R
+    return R.Net(n, h, w)
+
+
+def _theta(seed=0):
+    from paper_1905_06700_b300 import learned
+    th = learned.init_params(seed).astype(np.float64)
+    rng = np.random.default_rng(seed + 7)
+    th += rng.normal(0, 0.02, th.size)          # nonzero biases too
+    return th.astype(np.float32)
+
+
+def _random_state(rng, n, k, h, w):
+    i, j = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    t = np.stack([np.stack([300 + 80 * kk + 1.5 * i - 0.7 * j + rng.normal(0, 2, (h, w)) for kk in range(k)])
+                  for _ in range(n)]).astype(np.float32)
+    r = rng.uniform(0, 8, (n, k, h, w)).astype(np.float32)
+    alive = (rng.random((n, k, h, w)) < 0.8).astype(np.uint8)
+    return t, r, alive
+
+
+def test_features_match_oracle(orc):
+    torch = torch_mod()
+    rng = np.random.default_rng(1)
+    n, k, h, w = 2, 3, 13, 21
+    t, r, a = _random_state(rng, n, k, h, w)
+    net = _net(n, h, w)
+    x = net.features(torch.from_numpy(t).cuda(), torch.from_numpy(r).cuda(), torch.from_numpy(a).cuda(),
+                     3.0).cpu().numpy()
+    exact = 0
+    for im in range(n):
+        st = orc.new_state(k, h, w)
+        st.t[:] = t[im]
+        st.r[:] = r[im]
+        st.alive[:] = a[im]
+        want = orc.bf16(orc.net_features(st, 3.0))
+        # FP32 vs FP64 sums may straddle a bfloat16 rounding boundary: one unit at most
+        assert np.all(np.abs(x[im] - want) <= 2.0 ** -7 * np.abs(want) + 1e-30)
+        exact += int((x[im] == want).sum())
+    assert exact >= 0.99 * x.size
+
+
+def test_forward_matches_oracle(orc):
+    torch = torch_mod()
+    rng = np.random.default_rng(2)
+    n, h, w = 2, 19, 35                               # ragged 8x16 tiles
+    th = _theta(2)
+    x = orc.bf16(rng.normal(0, 1, (n, 6, h, w)))
+    net = _net(n, h, w)
+    net.set_params(th)
+    y = net.forward(torch.from_numpy(x.astype(np.float32)).cuda()).cpu().numpy()
+    _, want = orc.net_forward(th.astype(np.float64), x, bf16_round=True)
+    scale = np.abs(want).max()
+    err = np.abs(y - want)
+    assert err.max() <= 5e-3 * scale, err.max() / scale
+    assert np.median(err) <= 1e-5 * scale
+    assert np.array_equal(net.get_params(), th)
+
+
+def test_gradient_matches_oracle(orc):
+    torch = torch_mod()
+    rng = np.random.default_rng(3)
+    n, h, w = 2, 17, 20
+    th = _theta(3)
+    x = orc.bf16(rng.normal(0, 1, (n, 6, h, w)))
+    tg = rng.normal(0, 0.5, (n, 2, h, w))
+    m = (rng.random((n, 2, h, w)) < 0.7).astype(np.uint8)
+    net = _net(n, h, w)
+    net.set_params(th)
+    g, loss = net.gradient(torch.from_numpy(x.astype(np.float32)).cuda(),
+                           torch.from_numpy(tg.astype(np.float32)).cuda(), torch.from_numpy(m).cuda())
+    g = g.cpu().numpy().astype(np.float64)
+    acts, y = orc.net_forward(th.astype(np.float64), x, bf16_round=True)
+    lo, dy = orc.net_loss(y, tg, m)
+    want, _ = orc.net_backward(th.astype(np.float64), acts, dy, bf16_round=True)
+    assert float(loss.cpu()[0]) == pytest.approx(lo, rel=1e-4)
+    for l in range(4):
+        for bias in (False, True):
+            a, b = orc.net_offset(l, bias), (orc.net_offset(l, True) if not bias else orc.net_offset(l + 1, False))
+            rel = np.linalg.norm(g[a:b] - want[a:b]) / max(np.linalg.norm(want[a:b]), 1e-30)
+            assert rel <= 2e-3, (l, bias, rel)
+
+
+def test_adamw_step_matches_oracle(orc):
+    torch = torch_mod()
+    rng = np.random.default_rng(4)
+    n, h, w = 1, 16, 16
+    th = _theta(4)
+    x = torch.from_numpy(orc.bf16(rng.normal(0, 1, (n, 6, h, w))).astype(np.float32)).cuda()
+    tg = torch.from_numpy(rng.normal(0, 0.5, (n, 2, h, w)).astype(np.float32)).cuda()
+    m = torch.from_numpy((rng.random((n, 2, h, w)) < 0.7).astype(np.uint8)).cuda()
+    net = _net(n, h, w)
+    net.set_params(th)
+    g, _ = net.gradient(x, tg, m)
+    g = g.cpu().numpy().astype(np.float64)
+    net.train_step(x, tg, m, lr=1e-3, weight_decay=0.01)
+    got = net.get_params().astype(np.float64)
+    want = th.astype(np.float64).copy()
+    mm = np.zeros_like(want)
+    vv = np.zeros_like(want)
+    orc.adamw(want, g, mm, vv, 1, 1e-3, 0.9, 0.999, 1e-8, 0.01)
+    # the step recomputes the gradient (atomic sums, another order): where |g|
+    # is near eps the normalised step g / (|g| + eps) is ill-conditioned, so
+    # equality is asked where |g| >> eps and the AdamW step bound everywhere
+    big = np.abs(g) > 1e-5
+    assert np.abs(got - want)[big].max() <= 1e-6
+    assert np.all(np.abs(got - th) <= 1e-3 * (1 + 0.01 * np.abs(th)) + 1e-7)
+
+
+def test_training_reduces_the_loss():
+    """A fixed random network as teacher: the student's loss falls."""
+    torch = torch_mod()
+    from paper_1905_06700_b300 import learned
+    rng = np.random.default_rng(5)
+    n, h, w = 4, 24, 24
+    teacher = _net(n, h, w)
+    teacher.set_params(_theta(11))
+    xs = [torch.from_numpy(rng.normal(0, 1, (1, 6, h, w)).astype(np.float32)).cuda() for _ in range(16)]
+    pairs = [(x, teacher.forward(x), torch.ones((1, 2, h, w), dtype=torch.uint8, device="cuda")) for x in xs]
+    net = _net(n, h, w)
+    net.set_params(learned.init_params(3))
+    losses = learned.train(net, pairs, steps=150, batch=4, lr=2e-3, weight_decay=0.0)
+    assert losses[-10:].mean() < 0.5 * losses[:10].mean(), (losses[:10].mean(), losses[-10:].mean())
+
+
+def _recon(ctx, prm, z):
+    return np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
+
+
+def test_loop_limits_are_exact(orc):
+    """In the loop: a zero network moves no point (= no depth denoiser), a
+    fallback below zero hands every point to APSS (= the plain method)."""
+    sc = scenes.small_random(21, 19, 256, n_comp=2, seed=11)
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    net = _net(1, sc.h, sc.w)
+    ctx.set_depth_net(net)
+    net.set_params(np.zeros(45074, np.float32))
+    a = _recon(ctx, dict(prm, depth_denoiser=2), z)
+    b = _recon(ctx, dict(prm, depth_denoiser=0), z)
+    for key in ("t", "r", "alive", "b"):
+        assert np.array_equal(a[key], b[key]), key
+    net.set_params(_theta(5))
+    c = _recon(ctx, dict(prm, depth_denoiser=2, net_fallback=-1.0), z)
+    d = _recon(ctx, dict(prm, depth_denoiser=1), z)
+    for key in ("t", "r", "alive", "b"):
+        assert np.array_equal(c[key], d[key]), key
+
+
+@pytest.mark.parametrize("n_iter", [1, 5])
+def test_loop_with_a_network_matches_oracle(orc, n_iter):
+    """The learned form against the FP64 oracle running the same network.
+    FP32 feature and layer sums may round a bfloat16 input differently from
+    FP64 ones; one iteration is held close, several state their error."""
+    sc = scenes.small_random(21, 19, 256, n_comp=2, seed=12)
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    th = _theta(6)
+    prm = workload_params(sc, n_iter=n_iter)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    net = _net(1, sc.h, sc.w)
+    net.set_params(th)
+    ctx.set_depth_net(net)
+    g = _recon(ctx, dict(prm, depth_denoiser=2), z)
+    o = orc.reconstruct(z, oracle_irf(orc, sc), dict(prm, depth_denoiser=2, net_theta=th.astype(np.float64)))
+    both = g["alive"].astype(bool) & o.alive.astype(bool)
+    flips = int((g["alive"].astype(bool) != o.alive.astype(bool)).sum())
+    dt = np.abs(g["t"].astype(np.float64) - o.t)[both]
+    print("learned form vs oracle, %d iteration(s): points" % n_iter, int(both.sum()), "flips", flips,
+          "dt median %.2e p99 %.2e max %.2e" % (np.median(dt), np.percentile(dt, 99), dt.max()))
+    assert flips <= 0.01 * max(1, int(o.alive.sum()))
+    if n_iter == 1:
+        assert np.median(dt) <= 1e-4 and np.percentile(dt, 99) <= 0.05
+    else:
+        assert np.median(dt) <= 2e-2 and np.percentile(dt, 99) <= 0.2
+
+
+def test_trained_network_gains_over_no_depth_denoiser():
+    """Train on pairs the plain method makes on random-shape scenes, then on
+    held-out scenes the learned form's depth error is below the method's
+    without a depth denoiser (APSS reported beside it)."""
+    torch = torch_mod()
+    from paper_1905_06700_b300 import learned
+    from paper_1905_06700_b300 import rt3d as R
+    H = W = 48
+    T = 1024
+    base = scenes.random_shapes(H, W, T, seed=0)
+    prm = dict(scenes.make_params(base), n_iter=12)
+    ctx = R.Context(H, W, T, prm["k_max"], base.irf.samples, base.irf.origin)
+    net = R.Net(8, H, W)
+    pairs = []
+    for s in range(24):
+        sc = scenes.random_shapes(H, W, T, seed=1000 + s)
+        d = ctx.synthesize(scenes.sampling_tables(sc))
+        pairs += learned.frame_pairs(ctx, net, d, prm)
+    net.set_params(learned.init_params(0))
+    losses = learned.train(net, pairs, steps=600, batch=8, lr=2e-3, weight_decay=1e-4)
+    ctx.set_depth_net(net)
+    inlier = 5.0 * float(np.sqrt(base.irf.variance()))
+    res = {0: [], 1: [], 2: []}
+    for s in range(6):
+        sc = scenes.random_shapes(H, W, T, seed=5000 + s)
+        d = ctx.synthesize(scenes.sampling_tables(sc))
+        for den in (0, 1, 2):
+            out = ctx.reconstruct(dict(prm, depth_denoiser=den), dense=d)
+            res[den].append(learned.depth_errors(out, sc.depth, inlier))
+    (none, fn), (apss, fa), (lrn, fl) = ((float(np.mean([r[0] for r in res[k]])),
+                                          float(np.mean([r[1] for r in res[k]]))) for k in (0, 1, 2))
+    print("training loss %.4f -> %.4f; inlier depth RMSE (bins) / inlier fraction: none %.3f / %.3f, "
+          "APSS %.3f / %.3f, learned %.3f / %.3f"
+          % (losses[:20].mean(), losses[-20:].mean(), none, fn, apss, fa, lrn, fl))
+    assert losses[-20:].mean() < 0.7 * losses[:20].mean()
+    assert lrn < 0.8 * none

@@ -175,17 +175,39 @@ def test_features_of_a_plane_and_of_a_spike():
     x = O.net_features(st, 3.0)
     # a linear surface equals its 8-neighbour mean in the interior
     assert np.allclose(x[0, 1:-1, 1:-1], 0.0, atol=1e-12)
-    assert np.allclose(x[1], np.log1p(3.0)) and np.all(x[2] == 1.0)
+    assert np.allclose(x[1], np.log1p(3.0))
+    assert np.all(x[2, 1:-1, 1:-1] == 1.0) and x[2, 0, 0] == pytest.approx(4 / 9)   # 8 / 3 neighbours
     assert np.all(x[3:] == 0.0)                     # empty second slot
     st.t[0, 3, 4] += 6.0
     x = O.net_features(st, 3.0)
     assert x[0, 3, 4] == pytest.approx(2.0)
     assert x[0, 3, 5] == pytest.approx(-6.0 / 8 / 3.0)
+    # beyond 4 scale in depth a point is on another surface: no neighbours
     st.t[0, 3, 4] += 100.0
-    assert O.net_features(st, 3.0)[0, 3, 4] == 4.0   # clamped
+    x = O.net_features(st, 3.0)
+    assert x[0, 3, 4] == 0.0 and x[2, 3, 4] == pytest.approx(1 / 9)
+    # its right-hand neighbour keeps 7 plane neighbours, whose mean offset is
+    # (0, +1/7) pixels: 1.5 / 7 bins below the plane value (slope -1.5 in j)
+    assert x[0, 3, 5] == pytest.approx(1.5 / 7 / 3.0) and x[2, 3, 5] == pytest.approx(8 / 9)
     st.alive[0, 2, 2] = 0
     x = O.net_features(st, 3.0)
     assert x[0, 2, 2] == x[1, 2, 2] == x[2, 2, 2] == 0.0
+
+
+def test_features_use_same_surface_points_of_any_slot():
+    """A second surface 300 bins behind does not enter a point's neighbours;
+    the same surface held in another slot of a neighbour does."""
+    st = _plane_state(5, 5)
+    st.t[1] = st.t[0] + 300.0
+    st.r[1] = 1.0
+    st.alive[1] = 1
+    x = O.net_features(st, 3.0)
+    assert x[0, 2, 2] == pytest.approx(0.0, abs=1e-12) and x[2, 2, 2] == 1.0
+    assert x[3, 2, 2] == pytest.approx(0.0, abs=1e-12) and x[5, 2, 2] == 1.0
+    # swap the slots of one neighbour: the same points, the same features
+    st.t[[0, 1], 2, 3] = st.t[[1, 0], 2, 3]
+    y = O.net_features(st, 3.0)
+    assert y[0, 2, 2] == pytest.approx(0.0, abs=1e-12) and y[2, 2, 2] == 1.0
 
 
 def test_learned_step_limits():
