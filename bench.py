@@ -38,6 +38,7 @@ METRIC = "frames/s (141x141 px x 4096 bins, multi-surface, full method)"
 UNIT = "frames/s"
 H, W, T, K = 141, 141, 4096, 3
 KERNEL_NAMES = ["init", "phase_a", "phase_b", "phase_c", "final"]
+WEIGHTS = os.path.join(ROOT, "paper_1905_06700_b300", "weights", "learned_depth.bin")
 
 
 def parse():
@@ -53,6 +54,9 @@ def parse():
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="duration of the continuous-batching serving run (0 = skip)")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the precision (tensor-core init) and learned forms")
+    ap.add_argument("--form-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -297,6 +301,13 @@ def run_ours(args, world, rank, local):
         # ---------------- continuous-batching serving of mixed streams
         serving = run_serving(args, local) if args.serve_seconds > 0 else None
 
+        # ---------------- the precision and learned forms
+        forms = None
+        if not args.no_forms:
+            forms = {"tensor_core_init_on_this_workload": run_tc_headline(args, ctx, prm, frames, outs, peaks),
+                     "precision": run_precision_form(args, local, peaks),
+                     "learned": run_learned_form(args, local)}
+
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4),
@@ -324,6 +335,7 @@ def run_ours(args, world, rank, local):
             "clocks": clk,
             "parity": parity,
             "serving": serving,
+            "forms": forms,
             "cpu_baseline": cpu,
         }
     if world > 1:
@@ -331,6 +343,153 @@ def run_ours(args, world, rank, local):
         torch.distributed.destroy_process_group()
     ctx.close()
     return result
+
+
+def time_steps(ctx, prm, frames, outs, steps, warmup=2):
+    """Mean ms per batched call and mean ms per launch of each kernel class."""
+    import torch
+    for _ in range(warmup):
+        ctx.reconstruct_batch(prm, frames, outs)
+    torch.cuda.synchronize()
+    ctx.set_profiling(True)
+    ctx.kernel_times(reset=True)
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        ctx.reconstruct_batch(prm, frames, outs)
+    b.record()
+    b.synchronize()
+    kt = ctx.kernel_times(reset=True)
+    ctx.set_profiling(False)
+    return a.elapsed_time(b) / steps, {k: v[0] / v[1] for k, v in kt.items() if v[1]}
+
+
+def init_bytes(n_px, t, k, nnz_total):
+    """Algorithmic bytes of the initialisation (see algorithmic_bytes)."""
+    return n_px * (2 * t + 8 + 9 * k + 4) + 4 * nnz_total
+
+
+def run_tc_headline(args, ctx, prm, frames, outs, peaks) -> dict:
+    """The tensor-core initialisation (FP16 and BF16 operands) on the benchmark
+    workload; results must equal the integer path's bit for bit."""
+    import torch
+    ref = [{k: v.clone() for k, v in o.items()} for o in outs]
+    nb = len(frames)
+    nnz = int(sum(int(torch.count_nonzero(f["dense"].view(torch.int16)).item()) for f in frames))
+    out = {}
+    for name, mode in (("fp16", 2), ("bf16", 1)):
+        ms, kt = time_steps(ctx, dict(prm, lmf_precision=mode), frames, outs, args.form_steps)
+        same = all(torch.equal(a[k], b[k]) for a, b in zip(ref, outs) for k in ("t", "r", "alive", "b"))
+        ib = init_bytes(nb * H * W, T, K, nnz)
+        gbs = ib / (kt["init_tc"] * 1e-3) / 1e9
+        out[name] = {"frames_per_s": round(nb / (ms / 1000), 2), "init_tc_ms": round(kt["init_tc"], 4),
+                     "init_gbs": round(gbs, 1), "init_hbm_frac": round(gbs / peaks["hbm_gbs"], 4),
+                     "bitwise_equal_to_integer_path": bool(same)}
+    for o, r in zip(outs, ref):
+        for k in o:
+            o[k].copy_(r[k])
+    return out
+
+
+def run_precision_form(args, device, peaks) -> dict:
+    """Precision form: 256 x 256 x 4096, two surfaces, SBR 0.1 (about 54
+    photons per pixel), 8 frames per step; the matched filter on CUDA cores
+    (integer) and on tensor cores (FP16 and BF16 operands, FP32 accumulation).
+    The filter output is an exact integer in every mode, so the results are
+    bitwise equal and the depth error against the FP64 oracle is that of the
+    FP32 loop (stated by the parity tests)."""
+    import torch
+    from paper_1905_06700_b300 import rt3d as R
+    h = w = 256
+    t = 4096
+    nb = 8
+    base = scenes.two_layer(h, w, t)
+    prm = scenes.make_params(base)
+    k = prm["k_max"]
+    ctx = R.Context(h, w, t, k, base.irf.samples, base.irf.origin, max_batch=nb, device=device)
+    dense = [ctx.synthesize(scenes.sampling_tables(scenes.two_layer(h, w, t, seed=1 + f))) for f in range(nb)]
+    torch.cuda.synchronize()
+    nnz = int(sum(int(torch.count_nonzero(d.view(torch.int16)).item()) for d in dense))
+    frames = [dict(dense=d) for d in dense]
+    outs = [ctx.new_result(h, w, k) for _ in range(nb)]
+    res = {"workload": "two_layer 256x256x4096, K=2, Gaussian IRF sigma 4, 5 signal photons/px, SBR 0.1, "
+                       "20 PALM iterations, 8 frames per step",
+           "nnz_per_pixel": round(nnz / (nb * h * w), 1)}
+    ref = None
+    for name, mode in (("integer", 0), ("fp16", 2), ("bf16", 1)):
+        ms, kt = time_steps(ctx, dict(prm, lmf_precision=mode), frames, outs, args.form_steps)
+        init_ms = kt.get("init", 0.0) + kt.get("init_tc", 0.0)
+        gbs = init_bytes(nb * h * w, t, k, nnz) / (init_ms * 1e-3) / 1e9
+        entry = {"frames_per_s": round(nb / (ms / 1000), 2), "init_ms": round(init_ms, 4),
+                 "init_gbs": round(gbs, 1), "init_hbm_frac": round(gbs / peaks["hbm_gbs"], 4)}
+        if ref is None:
+            ref = [{kk: v.clone() for kk, v in o.items()} for o in outs]
+        else:
+            entry["bitwise_equal_to_integer_path"] = bool(all(
+                torch.equal(a[kk], b[kk]) for a, b in zip(ref, outs) for kk in ("t", "r", "alive", "b")))
+        res[name] = entry
+    assert ctx.device_status() == R.RT3D_OK
+    ctx.close()
+    return res
+
+
+def run_learned_form(args, device) -> dict:
+    """Learned form: 256 x 256 x 2048 random planes, spheres and boxes (1-20
+    signal photons/px, SBR 0.05-2), the committed network in place of APSS;
+    throughput, single-frame latency and the inlier depth error against the
+    true surfaces (points within 5 IRF sigma) for no depth denoiser, APSS and
+    the learned form."""
+    import torch
+    from paper_1905_06700_b300 import learned
+    from paper_1905_06700_b300 import rt3d as R
+    if not os.path.exists(WEIGHTS):
+        return {"unavailable": "no trained checkpoint at paper_1905_06700_b300/weights/learned_depth.bin"}
+    theta, head = learned.load(WEIGHTS)
+    h = w = 256
+    t = 2048
+    nb = 8
+    base = scenes.random_shapes(h, w, t, seed=0)
+    prm = scenes.make_params(base)
+    k = prm["k_max"]
+    ctx = R.Context(h, w, t, k, base.irf.samples, base.irf.origin, max_batch=nb, device=device)
+    net = R.Net(1, h, w, device=device)
+    net.set_params(theta)
+    ctx.set_depth_net(net)
+    scs = [scenes.random_shapes(h, w, t, seed=200000 + f) for f in range(nb)]
+    dense = [ctx.synthesize(scenes.sampling_tables(sc)) for sc in scs]
+    torch.cuda.synchronize()
+    frames = [dict(dense=d) for d in dense]
+    outs = [ctx.new_result(h, w, k) for _ in range(nb)]
+    inlier = 5.0 * float(np.sqrt(base.irf.variance()))
+    res = {"workload": "random_shapes 256x256x2048 (seeds 200000-200007), K=2, Gaussian IRF sigma 3, "
+                       "20 PALM iterations, 8 frames per step",
+           "checkpoint": {kk: head[kk] for kk in ("trained_on", "training") if kk in head}}
+    for name, den in (("none", 0), ("apss", 1), ("learned", 2)):
+        p = dict(prm, depth_denoiser=den)
+        ms, kt = time_steps(ctx, p, frames, outs, args.form_steps)
+        errs = [learned.depth_errors(o, sc.depth, inlier) for o, sc in zip(outs, scs)]
+        lat = []
+        one = ctx.new_result(h, w, k)
+        for i in range(12):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.reconstruct(p, dense=dense[i % nb], out=one)
+            b.record()
+            b.synchronize()
+            if i >= 2:
+                lat.append(a.elapsed_time(b))
+        res[name] = {"frames_per_s": round(nb / (ms / 1000), 2),
+                     "frame_latency_ms_p50": round(float(np.percentile(lat, 50)), 3),
+                     "frame_latency_ms_p99": round(float(np.percentile(lat, 99)), 3),
+                     # phase B (APSS / fallback) + features and 4 convolutions of the network
+                     "depth_step_ms_per_iteration": round(kt.get("phase_b", 0.0) + 5 * kt.get("net", 0.0), 4),
+                     "inlier_depth_rmse_bins": round(float(np.mean([e[0] for e in errs])), 4),
+                     "inlier_fraction": round(float(np.mean([e[1] for e in errs])), 4)}
+    assert ctx.device_status() == R.RT3D_OK
+    ctx.close()
+    return res
 
 
 def run_e2e(args, ctx, prm, dense, R):

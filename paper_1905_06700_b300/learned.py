@@ -41,9 +41,11 @@ def init_params(seed: int = 0) -> np.ndarray:
     return theta
 
 
-def frame_pairs(ctx: "R.Context", net: "R.Net", dense, params: dict) -> List[Tuple]:
+def frame_pairs(ctx: "R.Context", net: "R.Net", dense, params: dict,
+                keep: Optional[Sequence[int]] = None) -> List[Tuple]:
     """(x [1][6][h][w], target [1][2][h][w], mask [1][2][h][w]) for every
-    iteration of the plain method (APSS depth denoiser) on one dense frame."""
+    iteration of the plain method (APSS depth denoiser) on one dense frame
+    (or the iterations listed in `keep`)."""
     torch = ctx.torch
     prm = dict(params, depth_denoiser=1, warm_start=0)   # the plain method: APSS
     h, w, t = dense.shape
@@ -64,7 +66,8 @@ def frame_pairs(ctx: "R.Context", net: "R.Net", dense, params: dict) -> List[Tup
             target[0, k] = (st["t"][k] - t_half[k]) / scale
             mask[0, k] = alive[k]
         target *= mask
-        pairs.append((x, target, mask))
+        if keep is None or it in keep:
+            pairs.append((x, target, mask))
         ctx.phase(2, 0, prm, csr, st, shape=(h, w, t))
     torch.cuda.current_stream().synchronize()
     return pairs
