@@ -24,6 +24,7 @@
 // neighbouring threads hit different banks.
 #pragma once
 #include "rt3d_device.cuh"
+#include "k_init_tc.cuh"   // tcgen05 / mbarrier helpers
 
 namespace rt3d {
 
@@ -398,6 +399,236 @@ __global__ void k_net_scale_grad(const float* __restrict__ grad, const float* __
 {
     const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (q < kNetParams) out[q] = grad[q] / fmaxf(acc[1], 1.0f);
+}
+
+
+// ======================================================================
+// Forward convolution on the tensor cores (tcgen05, BF16 operands, FP32
+// accumulation in tensor memory) as an implicit GEMM:
+//   D[128 pixels][CO] = sum over the 9 taps of A_tap[128][CI] B_tap[CI][CO],
+// one CTA per 128-pixel strip of an image row.  The strip's three input rows
+// with a one-pixel margin (3 x 130 pixels) sit in shared memory in the
+// no-swizzle K-major layout: 16-byte rows of 8 channels, chunk-major
+// ([chunk][pixel][8]), so the operand of tap (ky, kx) is the same buffer
+// started ky * 130 + kx pixels later (core matrices of 8 consecutive pixels
+// 128 bytes apart, chunks one plane apart).  B (the rounded weights) is a
+// prepared image [tap][k-step][chunk][out channel][8] in the same layout.
+// ======================================================================
+
+constexpr int kStrip = 128;
+constexpr int kStripHaloW = kStrip + 2;
+constexpr int kStripHalo = 3 * kStripHaloW;
+__host__ __device__ constexpr int net_pad16(int c) { return c < 16 ? 16 : (c + 15) / 16 * 16; }
+__host__ __device__ constexpr int net_tc_a_bytes(int ci) { return net_pad16(ci) / 8 * kStripHalo * 16; }
+__host__ __device__ constexpr int net_tc_b_bytes(int ci, int co) { return 9 * net_pad16(ci) * net_pad16(co) * 2; }
+__host__ __device__ constexpr long net_tcoff(int l)
+{
+    return l == 0 ? 0 : net_tcoff(l - 1) + net_tc_b_bytes(net_cin(l - 1), net_cout(l - 1)) / 2;
+}
+constexpr long kNetTcElems = net_tcoff(kNetLayers);   // bf16 elements of all B images
+
+// B images of all layers: element (t, s, c2, n, e) = W[n][16 s + 8 c2 + e][t]
+// rounded to bfloat16 (zero past the real channel counts).
+__global__ void k_net_prep_tc(const float* __restrict__ theta, uint16_t* __restrict__ img)
+{
+    const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= kNetTcElems) return;
+    int l = 0;
+    while (l + 1 < kNetLayers && q >= net_tcoff(l + 1)) ++l;
+    const int CI = net_cin(l), CO = net_cout(l), CIp = net_pad16(CI), COp = net_pad16(CO);
+    long long r = q - net_tcoff(l);
+    const int e = (int)(r % 8);
+    r /= 8;
+    const int n = (int)(r % COp);
+    r /= COp;
+    const int c2 = (int)(r % 2);
+    r /= 2;
+    const int s = (int)(r % (CIp / 16));
+    const int t = (int)(r / (CIp / 16));
+    const int ci = 16 * s + 8 * c2 + e;
+    float v = 0.0f;
+    if (n < CO && ci < CI) v = theta[net_woff(l) + ((long long)n * CI + ci) * 9 + t];
+    img[q] = f_to_bf16_bits(v);
+}
+
+__device__ __forceinline__ uint64_t tc_desc_plain(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    // no swizzle, K-major: LBO = byte distance of K-adjacent core matrices,
+    // SBO = byte distance of M/N-adjacent (8-row) core matrices; version 1
+    return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+           ((uint64_t)1 << 46);
+}
+
+template <int CI, int CO, int MODE>
+__global__ void __launch_bounds__(128)
+k_net_conv_tc(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, const uint16_t* __restrict__ bimg,
+              const float* __restrict__ bias, void* __restrict__ out, int* __restrict__ status)
+{
+    constexpr int CIp = net_pad16(CI), COp = net_pad16(CO), KS = CIp / 16;
+    static_assert(CI % 8 == 0 || CI == 6, "input rows are read as 16-byte chunks or three words");
+    constexpr int A_BYTES = net_tc_a_bytes(CI), B_BYTES = net_tc_b_bytes(CI, CO);
+    constexpr int TM_COLS = COp <= 32 ? 32 : 64;
+    constexpr uint32_t kChunkBytes = kStripHalo * 16;
+    const Batch& B = *Bp;
+    extern __shared__ __align__(128) unsigned char net_tc_smem[];
+    __shared__ uint32_t tslot;
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int s_abort;
+    unsigned char* sa = net_tc_smem;
+    unsigned char* sb = net_tc_smem + A_BYTES;
+    const uint32_t a_addr = smem_u32(sa), b_addr = smem_u32(sb);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < B_BYTES / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(sb)[i] = reinterpret_cast<const uint4*>(bimg)[i];
+    if (threadIdx.x == 0) {
+        mbar_init(smem_u32(&bar), 1);
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                     "r"(TM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COp >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+    uint32_t phase = 0;
+    for (int strip = blockIdx.x; strip < B.net_strips; strip += gridDim.x) {
+        // strip -> frame, row, first column
+        int lo = 0, hi = B.n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.f[mid].net_strip_base <= strip) lo = mid; else hi = mid - 1;
+        }
+        const FrameDesc& F = B.f[lo];
+        const int spr = (F.w + kStrip - 1) / kStrip;
+        const int local = strip - F.net_strip_base;
+        const int gi = local / spr, j0 = (local % spr) * kStrip;
+        // the three input rows with margins, zero outside the frame: thread q
+        // takes pixel q + 1 of each row (threads 0 and 1 also the two margin
+        // pixels), every 16-byte chunk; all loads are issued before the stores
+        {
+            const int q = threadIdx.x;
+#pragma unroll
+            for (int extra = 0; extra < 2; ++extra) {
+                // extra = 0: pixel q + 1 (q < 128); extra = 1: margin pixel 0 or 129 (q < 2)
+                if (extra == 1 && q >= 2) break;
+                const int p = extra == 0 ? q + 1 : (q == 0 ? 0 : kStripHaloW - 1);
+                const int jj = j0 - 1 + p;
+                const bool jin = jj >= 0 && jj < F.w;
+                uint4 v[3][CIp / 8];
+#pragma unroll
+                for (int r = 0; r < 3; ++r) {
+                    const int ii = gi - 1 + r;
+                    const bool in_f = jin && ii >= 0 && ii < F.h;
+                    const long long px = (long long)F.pix_base + (long long)ii * F.w + jj;
+#pragma unroll
+                    for (int c = 0; c < CIp / 8; ++c) {
+                        v[r][c] = make_uint4(0, 0, 0, 0);
+                        if (in_f && 8 * c < CI) {
+                            if constexpr (CI % 8 == 0) {
+                                v[r][c] = *reinterpret_cast<const uint4*>(in + px * CI + 8 * c);
+                            } else {
+                                // 6 channels = three 32-bit words per pixel
+                                const uint32_t* w32 = reinterpret_cast<const uint32_t*>(in + px * CI);
+                                v[r][c] = make_uint4(w32[0], w32[1], w32[2], 0u);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+#pragma unroll
+                    for (int c = 0; c < CIp / 8; ++c)
+                        *reinterpret_cast<uint4*>(sa + (size_t)c * kChunkBytes + (size_t)(r * kStripHaloW + p) * 16) =
+                            v[r][c];
+            }
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tc_fence_after();
+            uint32_t acc = 0;
+#pragma unroll 1
+            for (int t = 0; t < 9; ++t) {
+                const int ky = t / 3, kx = t % 3;
+#pragma unroll
+                for (int s = 0; s < KS; ++s) {
+                    const uint64_t da = tc_desc_plain(a_addr + (uint32_t)(2 * s) * kChunkBytes +
+                                                          (uint32_t)(ky * kStripHaloW + kx) * 16,
+                                                      kChunkBytes, 128);
+                    const uint64_t db = tc_desc_plain(b_addr + (uint32_t)((t * KS + s) * 2 * COp * 16),
+                                                      (uint32_t)(COp * 16), 128);
+                    tc_mma(tmem, da, db, idesc, acc);
+                    acc = 1;
+                }
+            }
+            tc_commit(smem_u32(&bar));
+        }
+        // wait for the accumulator (bounded)
+        {
+            bool ok = mbar_try_wait(smem_u32(&bar), phase);
+            if (!ok) {
+                const unsigned long long t0 = global_ns();
+                while (!(ok = mbar_try_wait_sleep(smem_u32(&bar), phase)))
+                    if (global_ns() - t0 > kTcWaitNs) break;
+            }
+            if (!ok) s_abort = 1;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        __syncthreads();
+        if (s_abort) break;
+        // epilogue: thread = pixel (its tensor-memory lane)
+        const int m = warp * 32 + lane;
+        float acc[COp];
+#pragma unroll
+        for (int c0 = 0; c0 < COp; c0 += 16) {
+            uint32_t v[16];
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                "%12, %13, %14, %15}, [%16];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                  "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                  "=r"(v[14]), "=r"(v[15])
+                : "r"(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0));
+            tc_wait_ld();
+#pragma unroll
+            for (int q = 0; q < 16; ++q) acc[c0 + q] = __uint_as_float(v[q]);
+        }
+        const int gj = j0 + m;
+        if (gj < F.w) {
+            const long long px = (long long)F.pix_base + gi * F.w + gj;
+            if (MODE == kConvHidden) {
+                uint32_t pk[CO / 2];
+#pragma unroll
+                for (int c = 0; c < CO / 2; ++c)
+                    pk[c] = (uint32_t)f_to_bf16_bits(fmaxf(acc[2 * c] + bias[2 * c], 0.0f)) |
+                            ((uint32_t)f_to_bf16_bits(fmaxf(acc[2 * c + 1] + bias[2 * c + 1], 0.0f)) << 16);
+                uint4* o = reinterpret_cast<uint4*>(static_cast<uint16_t*>(out) + px * CO);
+#pragma unroll
+                for (int c = 0; c < CO / 8; ++c) o[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+            } else {
+                float* o = static_cast<float*>(out) + px * CO;
+#pragma unroll
+                for (int c = 0; c < CO; ++c) o[c] = acc[c] + bias[c];
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    if (s_abort && threadIdx.x == 0 && status) atomicOr(status, kStatusTimeout);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_COLS) : "memory");
+    }
 }
 
 }  // namespace rt3d

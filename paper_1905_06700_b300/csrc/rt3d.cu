@@ -76,6 +76,8 @@ struct rt3d_net {
     float* v = nullptr;
     float* wf = nullptr;            // [kNetWeights] forward layout
     float* wb = nullptr;            // [kNetWeights] backward-data layout
+    uint16_t* wtc = nullptr;        // [kNetTcElems] tensor-core operand images of the rounded weights
+    int* status = nullptr;          // device status of the network's own calls
     float* acc = nullptr;           // [2] loss sums
     uint16_t* a[4] = {nullptr, nullptr, nullptr, nullptr};   // layer inputs, NHWC bf16
     float* yh = nullptr;            // [pix][2]
@@ -433,7 +435,7 @@ rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3
     std::memset(B, 0, sizeof(Batch));
     B->n = n;
     int tiles = 0, pix = 0, tmax = 0;
-    int tc_tiles = 0;
+    int tc_tiles = 0, strips = 0;
     long long tc_ent = 0;
     for (int i = 0; i < n; ++i) {
         FrameDesc& d = B->f[i];
@@ -453,6 +455,8 @@ rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3
         d.ent = d.use_csr ? f[i].csr_ent : c->W.ent;
         d.gain = f[i].gain;
         d.tc_tile_base = tc_tiles;
+        d.net_strip_base = strips;
+        strips += d.h * ((d.w + kStrip - 1) / kStrip);
         // tensor-core init of a dense frame whose rows TMA can address (16-byte
         // aligned start and row stride); other frames take the CUDA-core path,
         // which computes the identical integer filter
@@ -482,6 +486,7 @@ rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3
     B->tc_tiles = tc_tiles;
     B->tc_entries = tc_ent;
     B->ent_base_int = tc_ent;
+    B->net_strips = strips;
     B->total_tiles = tiles;
     B->total_pix = pix;
     B->max_t = tmax;
@@ -574,21 +579,39 @@ rt3d_status launch_conv(rt3d_ctx* c, int tiles, const Batch* B, const void* in, 
     return RT3D_OK;
 }
 
-// Forward pass of the network over a batch's tiles: a0 -> a1 -> a2 -> a3 -> y.
-rt3d_status net_forward_tiles(rt3d_ctx* c, const rt3d_net* net, int tiles, const Batch* B, const uint16_t* a0,
-                              uint16_t* a1, uint16_t* a2, uint16_t* a3, float* y, cudaStream_t s)
+template <int CI, int CO, int MODE>
+rt3d_status launch_conv_tc(rt3d_ctx* c, int strips, const Batch* B, const uint16_t* in, const uint16_t* img,
+                           const float* bias, void* out, int* status, cudaStream_t s)
 {
-    rt3d_status st = launch_conv<6, 48, 48, kConvHidden>(c, tiles, B, a0, net->wf + net_wfoff(0),
-                                                         net->theta + net_boff(0), a1, nullptr, s);
+    if (strips <= 0) return RT3D_OK;
+    auto fn = k_net_conv_tc<CI, CO, MODE>;
+    const int smem = net_tc_a_bytes(CI) + net_tc_b_bytes(CI, CO);
+    RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int dev = 0, sms = 148;
+    RT3D_CUDA(cudaGetDevice(&dev));
+    RT3D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int grid = std::min(strips, 2 * sms);
+    LaunchScope ls(c, s, kcNet);
+    fn<<<grid, 128, smem, s>>>(B, in, img, bias, out, status);
+    return RT3D_OK;
+}
+
+// Forward pass of the network over a batch's 128-pixel row strips on the
+// tensor cores: a0 -> a1 -> a2 -> a3 -> y.
+rt3d_status net_forward_tiles(rt3d_ctx* c, const rt3d_net* net, int strips, const Batch* B, const uint16_t* a0,
+                              uint16_t* a1, uint16_t* a2, uint16_t* a3, float* y, int* status, cudaStream_t s)
+{
+    rt3d_status st = launch_conv_tc<6, 48, kConvHidden>(c, strips, B, a0, net->wtc + net_tcoff(0),
+                                                        net->theta + net_boff(0), a1, status, s);
     if (st == RT3D_OK)
-        st = launch_conv<48, 48, 24, kConvHidden>(c, tiles, B, a1, net->wf + net_wfoff(1),
-                                                  net->theta + net_boff(1), a2, nullptr, s);
+        st = launch_conv_tc<48, 48, kConvHidden>(c, strips, B, a1, net->wtc + net_tcoff(1),
+                                                 net->theta + net_boff(1), a2, status, s);
     if (st == RT3D_OK)
-        st = launch_conv<48, 48, 24, kConvHidden>(c, tiles, B, a2, net->wf + net_wfoff(2),
-                                                  net->theta + net_boff(2), a3, nullptr, s);
+        st = launch_conv_tc<48, 48, kConvHidden>(c, strips, B, a2, net->wtc + net_tcoff(2),
+                                                 net->theta + net_boff(2), a3, status, s);
     if (st == RT3D_OK)
-        st = launch_conv<48, 2, 2, kConvOut>(c, tiles, B, a3, net->wf + net_wfoff(3), net->theta + net_boff(3),
-                                             y, nullptr, s);
+        st = launch_conv_tc<48, 2, kConvOut>(c, strips, B, a3, net->wtc + net_tcoff(3), net->theta + net_boff(3),
+                                             y, status, s);
     return st;
 }
 
@@ -606,8 +629,8 @@ rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
                 k_net_features_loop<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W, c->net_a0,
                                                                            c->h_rec.P.net_scale);
             }
-            const rt3d_status st = net_forward_tiles(c, c->net, B.total_tiles, &c->d_rec->B, c->net_a0, c->net_a1,
-                                                     c->net_a2, c->net_a1, c->net_y, s);
+            const rt3d_status st = net_forward_tiles(c, c->net, B.net_strips, &c->d_rec->B, c->net_a0, c->net_a1,
+                                                     c->net_a2, c->net_a1, c->net_y, c->W.status, s);
             if (st != RT3D_OK) return st;
         }
         {
@@ -1209,7 +1232,9 @@ rt3d_status net_batch(rt3d_net* net, int n, int h, int w, cudaStream_t s)
         d.tiles_w = tw;
         d.tile_base = i * tw * th;
         d.pix_base = i * h * w;
+        d.net_strip_base = i * h * ((w + kStrip - 1) / kStrip);
     }
+    B.net_strips = n * h * ((w + kStrip - 1) / kStrip);
     B.total_tiles = n * tw * th;
     B.total_pix = n * h * w;
     RT3D_CUDA(cudaMemcpyAsync(net->d_batch, &B, sizeof(Batch), cudaMemcpyHostToDevice, s));
@@ -1241,8 +1266,8 @@ rt3d_status net_fwd_bwd(rt3d_net* net, int n, int h, int w, const float* x, cons
     k_net_pack_input<<<blocks, 256, 0, s>>>(npix, n, x, net->a[0]);
     // a throwaway context object carries only the launch bookkeeping
     rt3d_ctx tmp;
-    st = net_forward_tiles(&tmp, net, net->h_batch.total_tiles, net->d_batch, net->a[0], net->a[1], net->a[2],
-                           net->a[3], net->yh, s);
+    st = net_forward_tiles(&tmp, net, net->h_batch.net_strips, net->d_batch, net->a[0], net->a[1], net->a[2],
+                           net->a[3], net->yh, net->status, s);
     if (st != RT3D_OK) return st;
     float* yplanes = net->g1;   // [n][2][h][w] scratch before the backward pass needs g1
     k_net_unpack_output<<<blocks, 256, 0, s>>>(npix, n, net->yh, yplanes);
@@ -1274,6 +1299,7 @@ rt3d_status net_fwd_bwd(rt3d_net* net, int n, int h, int w, const float* x, cons
 rt3d_status net_prep(rt3d_net* net, cudaStream_t s)
 {
     k_net_prep_weights<<<(int)((kNetWeights + 255) / 256), 256, 0, s>>>(net->theta, net->wf, net->wb);
+    k_net_prep_tc<<<(int)((kNetTcElems + 255) / 256), 256, 0, s>>>(net->theta, net->wtc);
     RT3D_CUDA(cudaGetLastError());
     return RT3D_OK;
 }
@@ -1308,6 +1334,8 @@ rt3d_status rt3d_net_create(int device, int max_images, int max_h, int max_w, rt
     alloc((void**)&net->v, P);
     alloc((void**)&net->wf, sizeof(float) * kNetWeights);
     alloc((void**)&net->wb, sizeof(float) * kNetWeights);
+    alloc((void**)&net->wtc, sizeof(uint16_t) * kNetTcElems);
+    alloc((void**)&net->status, sizeof(int));
     alloc((void**)&net->acc, 2 * sizeof(float));
     alloc((void**)&net->a[0], sizeof(uint16_t) * 6 * net->max_pix);
     for (int l = 1; l < 4; ++l) alloc((void**)&net->a[l], sizeof(uint16_t) * kNetCh * net->max_pix);
@@ -1315,6 +1343,7 @@ rt3d_status rt3d_net_create(int device, int max_images, int max_h, int max_w, rt
     alloc((void**)&net->g0, sizeof(float) * kNetCh * net->max_pix);
     alloc((void**)&net->g1, sizeof(float) * kNetCh * net->max_pix);
     alloc((void**)&net->d_batch, sizeof(Batch));
+    if (e == cudaSuccess) e = cudaMemset(net->status, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(net->theta, 0, P);
     if (e == cudaSuccess) e = cudaMemset(net->grad, 0, P);
     if (e == cudaSuccess) e = cudaMemset(net->m, 0, P);
@@ -1333,8 +1362,8 @@ void rt3d_net_destroy(rt3d_net_t* net)
 {
     if (!net) return;
     cudaSetDevice(net->device);
-    void* ptrs[] = {net->theta, net->grad, net->m, net->v, net->wf, net->wb, net->acc, net->a[0], net->a[1],
-                    net->a[2], net->a[3], net->yh, net->g0, net->g1, net->d_batch};
+    void* ptrs[] = {net->theta, net->grad, net->m, net->v, net->wf, net->wb, net->wtc, net->status, net->acc,
+                    net->a[0], net->a[1], net->a[2], net->a[3], net->yh, net->g0, net->g1, net->d_batch};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     delete net;
@@ -1389,8 +1418,8 @@ rt3d_status rt3d_net_forward(rt3d_net_t* net, int n, int h, int w, const float* 
     const int blocks = (int)((npix * n + 255) / 256);
     k_net_pack_input<<<blocks, 256, 0, s>>>(npix, n, x, net->a[0]);
     rt3d_ctx tmp;
-    st = net_forward_tiles(&tmp, net, net->h_batch.total_tiles, net->d_batch, net->a[0], net->a[1], net->a[2],
-                           net->a[3], net->yh, s);
+    st = net_forward_tiles(&tmp, net, net->h_batch.net_strips, net->d_batch, net->a[0], net->a[1], net->a[2],
+                           net->a[3], net->yh, net->status, s);
     if (st != RT3D_OK) return st;
     k_net_unpack_output<<<blocks, 256, 0, s>>>(npix, n, net->yh, y);
     RT3D_CUDA(cudaGetLastError());

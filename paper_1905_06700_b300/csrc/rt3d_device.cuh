@@ -67,6 +67,7 @@ struct FrameDesc {
     const float* gain;
     int tc;                         // cold start of this frame runs in the tensor-core init
     int tc_tile_base;               // its first 128-pixel tile there
+    int net_strip_base;             // first 128-pixel row strip of the frame (learned denoiser)
     float* t;                       // [k][h][w] primary state (the result buffers)
     float* r;
     uint8_t* alive;
@@ -79,6 +80,7 @@ struct Batch {
     int tc_tiles;                   // 128-pixel tiles of the tensor-core init
     long long tc_entries;           // entries reserved for its frames (pixels x bins)
     long long ent_base_int;         // the CUDA-core init allocates entries from here on
+    int net_strips;                 // 128-pixel row strips of all frames (learned denoiser)
     FrameDesc f[kMaxBatch];
 };
 
