@@ -69,6 +69,27 @@ def dist_env():
 
 # --------------------------------------------------------------------------- helpers
 
+def replica_seeds(rank: int, frames: int) -> list:
+    """Scene seeds of one replica: every rank reconstructs different frames."""
+    return [1 + rank * frames + f for f in range(frames)]
+
+
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """The slowest rank's time (the job's time); no collective on one GPU."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(frames_per_rank_step: int, steps: int, world: int, t_max_ms: float) -> float:
+    """Whole-job frames/s: all ranks' frames over the slowest rank's time."""
+    return frames_per_rank_step * steps * world / (t_max_ms / 1000.0)
+
+
 def algorithmic_bytes(n_frames: int, nnz_total: int, k: int) -> dict:
     """Bytes each kernel class must move per launch for n frames of H x W x T
     (every array read or written once; halos counted once).  Per pixel:
@@ -191,12 +212,11 @@ def run_ours(args, world, rank, local):
     prm = scenes.make_params(base)
     assert prm["k_max"] == K
     ctx = R.Context(H, W, T, K, base.irf.samples, base.irf.origin, max_batch=nb, device=local)
-    dense, seeds = [], []
-    for f in range(nb):
-        seed = 1 + rank * nb + f
+    dense = []
+    seeds = replica_seeds(rank, nb)
+    for seed in seeds:
         sc = scenes.net_object_wall(H, W, T, seed=seed)
         dense.append(ctx.synthesize(scenes.sampling_tables(sc)))
-        seeds.append(seed)
     torch.cuda.synchronize()
     nnz_total = int(sum(int(torch.count_nonzero(d.view(torch.int16)).item()) for d in dense))
     frames = [dict(dense=d) for d in dense]
@@ -232,13 +252,8 @@ def run_ours(args, world, rank, local):
     ktimes = ctx.kernel_times(reset=True)
     assert ctx.device_status() == R.RT3D_OK
 
-    t_max = ms_total
-    if world > 1:
-        tt = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    frames_all = nb * args.steps * world
-    value = frames_all / (t_max / 1000.0)
+    t_max = max_over_ranks(ms_total, world, dev)
+    value = job_throughput(nb, args.steps, world, t_max)
 
     # ---------------- dominant kernel vs its roofline
     n_points = int(sum(int(o["n_points"].item()) for o in outs))
