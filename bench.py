@@ -314,7 +314,11 @@ def run_ours(args, world, rank, local):
         cpu = None if (world > 1 or args.cpu_frames < 1) else cpu_baseline(args, prm)
 
         # ---------------- continuous-batching serving of mixed streams
-        serving = run_serving(args, local) if args.serve_seconds > 0 else None
+        serving = None
+        if args.serve_seconds > 0:
+            serving = {"plain": run_serving(args, local)}
+            if not args.no_forms:
+                serving["learned"] = run_serving(args, local, learned_form=True)
 
         # ---------------- the precision and learned forms
         forms = None
@@ -565,12 +569,13 @@ def cpu_baseline(args, prm) -> dict:
             "sample": f"{len(zs)} full 141x141x4096 frames (init + 20 iterations), FP64, OpenMP"}
 
 
-def run_serving(args, device: int) -> dict:
+def run_serving(args, device: int, learned_form: bool = False) -> dict:
     """Continuous batching of 16 scene streams of mixed frame size (32x32, 64x64,
     141x141, 256x256 pixels; 1024 or 4096 bins), moving 1 bin per frame, with
     Poisson arrivals at 500 frames/s in total; each frame warm-starts from its
     stream's device-resident point cloud.  Each stream cycles through 4
-    pre-synthesised frames (device-resident inputs)."""
+    pre-synthesised frames (device-resident inputs).  learned_form: the
+    committed network stands in for APSS (with its fallback)."""
     import torch
     from paper_1905_06700_b300 import rt3d as R
     from paper_1905_06700_b300.serve import GpuBackend, Request, Server, SlotLimits, poisson_arrivals, summarize
@@ -588,12 +593,22 @@ def run_serving(args, device: int) -> dict:
     torch.cuda.synchronize()
     synth.close()
     prm = scenes.make_params(scenes.net_object_wall(64, 64, 4096, irf=irf))
+    net = None
+    if learned_form:
+        from paper_1905_06700_b300 import learned
+        if not os.path.exists(WEIGHTS):
+            return {"unavailable": "no trained checkpoint"}
+        theta, _ = learned.load(WEIGHTS)
+        net = R.Net(1, 16, 16, device=device)
+        net.set_params(theta)
+        prm = dict(prm, depth_denoiser=2)
     lim = SlotLimits(max_frames=16, max_pixels=4 * 256 * 256, max_entries=2 * 256 * 256 * 4096,
                      max_h=256, max_w=256, max_t=4096)
     reqs = poisson_arrivals(16, 500.0, args.serve_seconds, sizes, seed=7)
     for r in reqs:
         r.payload = frames[(r.stream, r.index % ring)]
-    be = GpuBackend(2, lim, irf.samples, irf.origin, prm, k_max=3, frame_source=None, device=device)
+    be = GpuBackend(2, lim, irf.samples, irf.origin, prm, k_max=3, frame_source=None, device=device,
+                    depth_net=net)
     warm = [Request(s, 0, *sizes[s], 0.0) for s in range(16)]       # capture the graphs once
     for r in warm:
         r.payload = frames[(r.stream, 0)]
@@ -602,7 +617,8 @@ def run_serving(args, device: int) -> dict:
     srv = Server(be)
     done = srv.run(reqs, timeout_s=120)
     out = summarize(done)
-    out.update({"offered_frames_per_s": 500.0, "streams": 16, "slots": 2,
+    out.update({"form": "learned" if learned_form else "plain",
+                "offered_frames_per_s": 500.0, "streams": 16, "slots": 2,
                 "batches": len(srv.batches), "mean_batch": len(done) / max(1, len(srv.batches)),
                 "sizes": "32^2, 64^2, 141^2, 256^2 x T 1024/4096, K=3, 20 iterations, warm starts",
                 "clock": "host perf_counter, arrival to completion event observed"})

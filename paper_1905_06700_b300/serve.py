@@ -215,7 +215,7 @@ class GpuBackend(Backend):
     of the stream's next frame."""
 
     def __init__(self, n_slots: int, limits: SlotLimits, irf_samples, irf_origin, params: dict,
-                 k_max: int, frame_source: Callable[[Request], object], device: int = 0):
+                 k_max: int, frame_source: Callable[[Request], object], device: int = 0, depth_net=None):
         import torch
         from . import rt3d as R
         self.torch = torch
@@ -227,6 +227,10 @@ class GpuBackend(Backend):
         self.ctx = [R.Context(limits.max_h, limits.max_w, limits.max_t, k_max, irf_samples, irf_origin,
                               max_batch=limits.max_frames, max_entries=limits.max_entries, device=device)
                     for _ in range(n_slots)]
+        # the learned depth denoiser (read-only at inference) serves every slot
+        if depth_net is not None:
+            for c in self.ctx:
+                c.set_depth_net(depth_net)
         self.streams = [torch.cuda.Stream(device=device) for _ in range(n_slots)]
         self.events = [None] * n_slots
         self.slot_batch: Dict[int, List[Request]] = {}
