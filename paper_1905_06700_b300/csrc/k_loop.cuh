@@ -46,52 +46,236 @@ __device__ __forceinline__ void load_irf(float* pad, const KParams& P)
     }
 }
 
-// Sums over the nonzero bins of one pixel, by one thread:
-//   sh[k] = sum z h(t - t_k)/lambda, sdh[k] = sum z h'(t - t_k)/lambda,
-//   sz = sum z/lambda, lambda = max(g (sum_alive r_k h(t - t_k) + b), lam_floor).
-// Every slot is evaluated (a dead slot enters lambda with r = 0), so lanes of
-// a warp do not diverge on which slots are alive; the next entry is fetched
-// while the current one is computed.
-__device__ __forceinline__ void pixel_sums(const uint32_t* ent, uint2 sg, const float* pad,
-                                           const KParams& P, const float* tk, const float* rk,
-                                           const bool* ak, float b, float g, float* sh, float* sdh,
-                                           float& sz)
+// Catmull-Rom intervals of the IRF, for the bin sums.  Entry i holds the
+// interval that starts at sample k = i - 3,
+//   h(k + u) = c.x + u (c.y + u (c.z + u c.w)),   h'(k + u) = c.y + u (2 c.z + 3 c.w u),
+// the interpolant of irf_eval with its factor 1/2 folded into the coefficients
+// (an exact scaling).  Entries 0 and L + 4 (k = -3 and k = L + 1) are zero: an
+// argument outside the support (-2, L + 1) lands on them and gives h = h' = 0.
+constexpr int kCoefLen = kMaxIrf + 5;
+
+__device__ __forceinline__ void load_irf_coef(float* pad, float4* coef, const KParams& P)
 {
-    const int K = P.k, L = P.irf_len, O = P.irf_origin;
-    float rr[kMaxK];
-#pragma unroll
-    for (int k = 0; k < kMaxK; ++k) {
-        sh[k] = 0.0f;
-        sdh[k] = 0.0f;
-        rr[k] = ak[k] ? rk[k] : 0.0f;
+    load_irf(pad, P);
+    const int L = P.irf_len;
+    for (int i = threadIdx.x; i < L + 5; i += blockDim.x) {
+        const int k = i - 3;
+        float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        if (k >= -2 && k <= L) {
+            const float pm = k - 1 >= 0 && k - 1 < L ? P.irf[k - 1] : 0.0f;
+            const float p0 = k >= 0 && k < L ? P.irf[k] : 0.0f;
+            const float p1 = k + 1 >= 0 && k + 1 < L ? P.irf[k + 1] : 0.0f;
+            const float p2 = k + 2 >= 0 && k + 2 < L ? P.irf[k + 2] : 0.0f;
+            const float c1 = p1 - pm;
+            const float c2 = 2.0f * pm - 5.0f * p0 + 4.0f * p1 - p2;
+            const float c3 = -pm + 3.0f * p0 - 3.0f * p1 + p2;
+            c = make_float4(p0, 0.5f * c1, 0.5f * c2, 0.5f * c3);
+        }
+        coef[i] = c;
     }
-    sz = 0.0f;
-    const float lam_floor = P.lam_floor;
-    uint32_t v = sg.y ? ent[sg.x] : 0u;
-    for (uint32_t e = 0; e < sg.y; ++e) {
-        const uint32_t cur = v;
-        if (e + 1 < sg.y) v = ent[sg.x + e + 1];
-        const float tb = (float)(cur >> 16), z = (float)(cur & 0xffffu);
-        float hv[kMaxK], dv[kMaxK];
-        float acc = b;
+}
+
+// One (pixel, slot) of the bin sums: a bin tb lies in IRF interval
+// tb + base - 3 at fraction u, both fixed by the slot's depth (bins are
+// integers): y = tb - t + origin = tb + (origin - t).
+__device__ __forceinline__ void slot_frame(int origin, float t, int& base, float& u)
+{
+    const float y0 = (float)origin - t;
+    const float f = floorf(y0);
+    base = (int)f + 3;
+    u = y0 - f;
+}
+
+// Per-pixel record of the bin sums: u[K], base[K], rr[K], b, g, packed in
+// 16-byte words.
+template <int K>
+struct PixRec {
+    static constexpr int NW = (3 * K + 2 + 3) / 4;
+    float4 q[NW];
+};
+
+// Per-warp scratch of warp_pixel_sums: the 32 pixels' bin ranges and records,
+// and the partial sums of pixels whose bins are split between lanes.
+template <int K, int NS>
+struct WarpSums {
+    PixRec<K> rec[32];
+    float acc[NS][32], first[NS][32], last[NS][32];
+    uint32_t start[32];
+    int excl[32], incl[32], nextp[32];
+};
+
+// Sums over the nonzero bins of the warp's 32 pixels (one pixel per lane, `on`
+// false for lanes outside the frame):
+//   MODE 0: out[k] = sum z h'(t - t_k)/lambda          (depth step)
+//   MODE 1: out[k] = sum z h(t - t_k)/lambda           (intensity step)
+//   MODE 2: out[0] = sum z/lambda                      (background step)
+// with lambda = max(g (sum_k rr_k h(t - t_k) + b), lam_floor) and rr_k the
+// intensity of an alive slot, 0 for a dead one.
+// Work is balanced over lanes, not pixels: the warp's bins, concatenated in
+// pixel order, are cut into 32 contiguous runs of equal length (+-1) and lane
+// l sums run l.  A pixel whose bins fall in one run is summed in bin order by
+// one lane; a pixel split over lanes l1..l2 is the sum of its per-lane pieces
+// added in lane order.  The grouping depends only on the 32 pixels' bin counts,
+// so the result is deterministic and independent of the rest of the batch.
+template <int K, int MODE>
+__device__ __forceinline__ void warp_pixel_sums(const uint32_t* __restrict__ ent, uint2 sg, bool on,
+                                                const float4* coef, const KParams& P, const float* tk,
+                                                const float* rr, float b, float g,
+                                                WarpSums<K, (MODE == 2 ? 1 : K)>& S, float* out)
+{
+    constexpr int NS = MODE == 2 ? 1 : K;
+    constexpr int NW = PixRec<K>::NW;
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int cnt = on ? (int)sg.y : 0;
+    int incl = cnt;
 #pragma unroll
-        for (int k = 0; k < kMaxK; ++k) {
-            hv[k] = 0.0f;
-            dv[k] = 0.0f;
-            if (k < K) {
-                irf_eval(pad, L, O, tb - tk[k], hv[k], dv[k]);
-                acc += rr[k] * hv[k];
+    for (int o = 1; o < 32; o <<= 1) {
+        const int n = __shfl_up_sync(full, incl, o);
+        if (lane >= o) incl += n;
+    }
+    const int E = __shfl_sync(full, incl, 31);
+    const int excl = incl - cnt;
+    const unsigned nz = __ballot_sync(full, cnt > 0);
+    const unsigned above = lane == 31 ? 0u : nz & (full << (lane + 1));
+    {
+        float w[4 * NW];
+#pragma unroll
+        for (int i = 0; i < 4 * NW; ++i) w[i] = 0.0f;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            int base;
+            slot_frame(P.irf_origin, tk[k], base, w[k]);
+            w[K + k] = __int_as_float(base);
+            w[2 * K + k] = rr[k];
+        }
+        w[3 * K] = b;
+        w[3 * K + 1] = g;
+#pragma unroll
+        for (int i = 0; i < NW; ++i) S.rec[lane].q[i] = make_float4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
+    }
+    S.start[lane] = on ? sg.x : 0u;
+    S.excl[lane] = excl;
+    S.incl[lane] = incl;
+    S.nextp[lane] = above ? __ffs(above) - 1 : 32;
+    __syncwarp();
+
+    const unsigned cmax = (unsigned)(P.irf_len + 4);
+    const float lam_floor = P.lam_floor;
+    const int lo = (lane * E) >> 5, hi = ((lane + 1) * E) >> 5;
+    if (lo < hi) {
+        // the pixel holding bin lo: the first with incl > lo (it is nonempty)
+        int p = 0;
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1)
+            if (S.incl[p + s - 1] <= lo) p += s;
+        float up[K], rp[K], bp, gp;
+        int basep[K];
+        auto load_pixel = [&](int q) {
+            float w[4 * NW];
+#pragma unroll
+            for (int i = 0; i < NW; ++i) {
+                const float4 v = S.rec[q].q[i];
+                w[4 * i] = v.x;
+                w[4 * i + 1] = v.y;
+                w[4 * i + 2] = v.z;
+                w[4 * i + 3] = v.w;
+            }
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                up[k] = w[k];
+                basep[k] = __float_as_int(w[K + k]);
+                rp[k] = w[2 * K + k];
+            }
+            bp = w[3 * K];
+            gp = w[3 * K + 1];
+        };
+        float part[NS];
+        // a piece of pixel q ends: a lane's first piece of a pixel begun in an
+        // earlier run goes to first, a piece that continues into the next run
+        // to last, a whole pixel to acc
+        auto flush = [&](int q, bool starts_in, bool ends_in) {
+            float* dst = !starts_in ? &S.first[0][lane] : (!ends_in ? &S.last[0][lane] : &S.acc[0][q]);
+#pragma unroll
+            for (int j = 0; j < NS; ++j) {
+                dst[32 * j] = part[j];
+                part[j] = 0.0f;
+            }
+        };
+#pragma unroll
+        for (int j = 0; j < NS; ++j) part[j] = 0.0f;
+        load_pixel(p);
+        int p_incl = S.incl[p];
+        bool starts_in = S.excl[p] == lo;
+        bool open = true;
+        uint32_t addr = S.start[p] + (uint32_t)(lo - S.excl[p]);
+        uint32_t v = ent[addr];
+        for (int e = lo; e < hi; ++e) {
+            const uint32_t cur = v;
+            const bool cross = e + 1 == p_incl;
+            const bool more = e + 1 < hi;
+            int q = p;
+            uint32_t naddr = addr + 1;
+            if (cross && more) {
+                q = S.nextp[p];
+                naddr = S.start[q];
+            }
+            if (more) v = ent[naddr];
+            const int tb = (int)(cur >> 16);
+            const float z = (float)(cur & 0xffffu);
+            float hv[K], dv[K];
+            float acc = bp;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                const float4 c = coef[min((unsigned)(tb + basep[k]), cmax)];
+                const float u = up[k];
+                hv[k] = c.x + u * (c.y + u * (c.z + u * c.w));
+                dv[k] = c.y + u * (2.0f * c.z + 3.0f * c.w * u);
+                acc += rp[k] * hv[k];
+            }
+            const float lam = fmaxf(gp * acc, lam_floor);
+            const float inv = __fdividef(z, lam);
+            if (MODE == 2) {
+                part[0] += inv;
+            } else {
+#pragma unroll
+                for (int k = 0; k < NS; ++k) part[k] += (MODE == 0 ? dv[k] : hv[k]) * inv;
+            }
+            if (cross) {
+                flush(p, starts_in, true);
+                open = false;
+                if (more) {
+                    p = q;
+                    load_pixel(p);
+                    p_incl = S.incl[p];
+                    starts_in = true;
+                    open = true;
+                }
+            }
+            addr = naddr;
+        }
+        if (open) flush(p, starts_in, false);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < NS; ++j) out[j] = 0.0f;
+    if (cnt > 0) {
+        // lanes holding this pixel's first and last bin
+        const int l1 = (32 * excl + 31) / E, l2 = (32 * incl - 1) / E;
+        if (l1 == l2) {
+#pragma unroll
+            for (int j = 0; j < NS; ++j) out[j] = S.acc[j][lane];
+        } else {
+#pragma unroll
+            for (int j = 0; j < NS; ++j) out[j] = S.last[j][l1];
+            for (int l = l1 + 1; l <= l2; ++l) {
+                if (((l * E) >> 5) == (((l + 1) * E) >> 5)) continue;   // empty run
+#pragma unroll
+                for (int j = 0; j < NS; ++j) out[j] += S.first[j][l];
             }
         }
-        const float lam = fmaxf(g * acc, lam_floor);
-        const float inv = __fdividef(z, lam);
-        sz += inv;
-#pragma unroll
-        for (int k = 0; k < kMaxK; ++k) {
-            sh[k] += hv[k] * inv;
-            sdh[k] += dv[k] * inv;
-        }
     }
+    __syncwarp();
 }
 
 // Background denoiser at pixel (i, j): periodic separable Gaussian over the
@@ -118,53 +302,58 @@ __device__ __forceinline__ float bkg_filter(const KParams& P, const float* bh, i
 
 // ----------------------------------------------------------------------------
 // Phase A: background denoiser of the previous iteration + depth gradient step,
-// one thread per pixel.
+// one thread per pixel (the bin sums shared out over the warp).
+template <int K>
 __global__ void __launch_bounds__(kTileThreads)
 k_phase_a(const CallRecord* __restrict__ rec, const Work W, int first)
 {
     const KParams& P = rec->P;
     const Batch& B = rec->B;
     __shared__ float pad[kMaxIrf + 2 * kIrfPad];
-    load_irf(pad, P);
+    __shared__ float4 coef[kCoefLen];
+    __shared__ WarpSums<K, K> ws[kTileThreads / 32];
+    load_irf_coef(pad, coef, P);
     __syncthreads();
     const TileCtx c = tile_ctx(B);
     const FrameDesc& F = B.f[c.fi];
-    if (!c.inb) return;
-    const int np = F.npix, S = W.stride, K = P.k;
-    const int lp = c.gi * F.w + c.gj, wp = F.pix_base + lp;
-    float b;
-    if (first) {
-        b = F.b[lp];
-    } else {
-        b = bkg_filter(P, W.b_half + F.pix_base, F.h, F.w, c.gi, c.gj);
-        F.b[lp] = b;
-    }
-    const float g = F.gain ? F.gain[lp] : 1.0f;
-    float tk[kMaxK], rk[kMaxK];
-    bool ak[kMaxK];
+    const int np = F.npix, S = W.stride;
+    const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
+    const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
+    float b = 0.0f, g = 0.0f;
+    float tk[K], rk[K], rr[K];
+    bool ak[K];
 #pragma unroll
-    for (int k = 0; k < kMaxK; ++k) {
+    for (int k = 0; k < K; ++k) {
         tk[k] = 0.0f;
         rk[k] = 0.0f;
         ak[k] = false;
-        if (k < K) {
-            uint8_t a;
-            if (first) {
-                a = F.alive[(long long)k * np + lp];
-            } else {
-                a = W.alive_b[(long long)k * S + wp];
-                F.alive[(long long)k * np + lp] = a;
-            }
-            ak[k] = a != 0;
+    }
+    if (c.inb) {
+        // every load before the first store (one memory round trip)
+        uint8_t a[K];
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            a[k] = first ? F.alive[(long long)k * np + lp] : W.alive_b[(long long)k * S + wp];
             tk[k] = F.t[(long long)k * np + lp];
             rk[k] = F.r[(long long)k * np + lp];
         }
-    }
-    float sh[kMaxK], sdh[kMaxK], sz;
-    pixel_sums(F.ent, W.seg[wp], pad, P, tk, rk, ak, b, g, sh, sdh, sz);
+        g = F.gain ? F.gain[lp] : 1.0f;
+        b = first ? F.b[lp] : bkg_filter(P, W.b_half + F.pix_base, F.h, F.w, c.gi, c.gj);
+        if (!first) {
+            F.b[lp] = b;
 #pragma unroll
-    for (int k = 0; k < kMaxK; ++k) {
-        if (k >= K) continue;
+            for (int k = 0; k < K; ++k) F.alive[(long long)k * np + lp] = a[k];
+        }
+#pragma unroll
+        for (int k = 0; k < K; ++k) ak[k] = a[k] != 0;
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k) rr[k] = ak[k] ? rk[k] : 0.0f;
+    float sdh[K];
+    warp_pixel_sums<K, 0>(F.ent, sg, c.inb, coef, P, tk, rr, b, g, ws[threadIdx.x >> 5], sdh);
+    if (!c.inb) return;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
         float tn = tk[k];
         if (ak[k] && g > 0.0f) {
             float H, dH;
@@ -190,7 +379,8 @@ constexpr int kHalo = kHaloH * kHaloW;
 // The accumulation is branch-free: dead or absent slots hold a far sentinel
 // depth, so their weight is exactly zero; window offsets outside the lateral
 // radius are skipped uniformly across the warp.
-__device__ float apss_point(const float* st, int hstride, int R, int K, int ci, int cj, float tn,
+template <int K>
+__device__ float apss_point(const float* st, int hstride, int R, int ci, int cj, float tn,
                             const KParams& P, int T)
 {
     const float inv_h = 1.0f / P.apss_h;
@@ -208,6 +398,7 @@ __device__ float apss_point(const float* st, int hstride, int R, int K, int ci, 
             if (!(r2 < 1.0f)) continue;
             const int q = (ci + di) * hstride + (cj + dj);
             float cnt = 0.0f;
+#pragma unroll
             for (int m = 0; m < K; ++m) {
                 const float z = (st[m * kHalo + q] - tn) * inv_h;
                 const float d2 = r2 + z * z;
@@ -267,22 +458,50 @@ __device__ float apss_point(const float* st, int hstride, int R, int K, int ci, 
 
 constexpr float kDeadDepth = -1.0e12f;   // sentinel depth of dead or absent slots
 
-// Depths of the tile plus halo R; dead slots and pixels outside the frame get
-// the sentinel depth.
-__device__ __forceinline__ void load_halo_depth(const TileCtx& c, const FrameDesc& F, int R, int K,
-                                                const float* src, long long src_stride, int src_off,
-                                                const uint8_t* asrc, long long a_stride, float* st)
+constexpr int kHaloIters = (kHalo + kTileThreads - 1) / kTileThreads;
+
+// Depths of the tile plus halo R (dead slots and pixels outside the frame get
+// the sentinel depth) and, with kWithR, a second per-slot field (0 outside the
+// frame).  Every global load is issued before the first shared store, so the
+// halo costs one memory round trip.
+template <int K, bool kWithR>
+__device__ __forceinline__ void load_halo(const TileCtx& c, const FrameDesc& F, int R,
+                                          const float* src, long long src_stride, int src_off,
+                                          const uint8_t* asrc, long long a_stride, float* st,
+                                          const float* rsrc, long long r_stride, int r_off, float* sr)
 {
-    const int hh = kTileH + 2 * R, hw = kTileW + 2 * R;
-    for (int idx = threadIdx.x; idx < hh * hw; idx += blockDim.x) {
+    const int hh = kTileH + 2 * R, hw = kTileW + 2 * R, n = hh * hw;
+    float tv[kHaloIters][K], rv[kHaloIters][K];
+    uint8_t av[kHaloIters][K];
+    bool inn[kHaloIters];
+#pragma unroll
+    for (int it = 0; it < kHaloIters; ++it) {
+        const int idx = threadIdx.x + it * kTileThreads;
         const int hi = idx / hw, hj = idx % hw;
         const int gi = c.i0 - R + hi, gj = c.j0 - R + hj;
-        const bool in = gi >= 0 && gi < F.h && gj >= 0 && gj < F.w;
+        const bool in = idx < n && gi >= 0 && gi < F.h && gj >= 0 && gj < F.w;
         const int lp = in ? gi * F.w + gj : 0;
+        inn[it] = in;
+#pragma unroll
         for (int m = 0; m < K; ++m) {
-            float v = kDeadDepth;
-            if (in && asrc[(long long)m * a_stride + lp]) v = src[(long long)m * src_stride + src_off + lp];
-            st[m * kHalo + idx] = v;
+            av[it][m] = 0;
+            tv[it][m] = 0.0f;
+            rv[it][m] = 0.0f;
+            if (in) {
+                av[it][m] = asrc[(long long)m * a_stride + lp];
+                tv[it][m] = src[(long long)m * src_stride + src_off + lp];
+                if (kWithR) rv[it][m] = rsrc[(long long)m * r_stride + r_off + lp];
+            }
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < kHaloIters; ++it) {
+        const int idx = threadIdx.x + it * kTileThreads;
+        if (idx >= n) continue;
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+            st[m * kHalo + idx] = inn[it] && av[it][m] ? tv[it][m] : kDeadDepth;
+            if (kWithR) sr[m * kHalo + idx] = inn[it] ? rv[it][m] : 0.0f;
         }
     }
 }
@@ -319,21 +538,26 @@ __device__ __forceinline__ int compact_points(const float* st, int R, int K, boo
 
 // ----------------------------------------------------------------------------
 // Phase B: APSS depth denoiser + intensity gradient step.
-__global__ void __launch_bounds__(kTileThreads)
+template <int K>
+__global__ void __launch_bounds__(kTileThreads, 8)
 k_phase_b(const CallRecord* __restrict__ rec, const Work W)
 {
     const KParams& P = rec->P;
     const Batch& B = rec->B;
     __shared__ float pad[kMaxIrf + 2 * kIrfPad];
-    __shared__ float st[kMaxK * kHalo];
-    __shared__ float s_tn[kMaxK][kTileThreads];
-    __shared__ unsigned short s_pts[kMaxK * kTileThreads];
+    __shared__ float st[K * kHalo];
+    __shared__ float s_tn[K][kTileThreads];
+    __shared__ unsigned short s_pts[K * kTileThreads];
     __shared__ int s_warp[kTileThreads / 32];
-    load_irf(pad, P);
+    __shared__ float4 coef[kCoefLen];
+    __shared__ WarpSums<K, K> ws[kTileThreads / 32];
+    load_irf_coef(pad, coef, P);
     const TileCtx c = tile_ctx(B);
     const FrameDesc& F = B.f[c.fi];
-    const int np = F.npix, S = W.stride, R = P.win_r, K = P.k;
-    load_halo_depth(c, F, R, K, W.t_half, S, F.pix_base, F.alive, np, st);
+    const int np = F.npix, S = W.stride, R = P.win_r;
+    const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
+    const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
+    load_halo<K, false>(c, F, R, W.t_half, S, F.pix_base, F.alive, np, st, nullptr, 0, 0, nullptr);
     __syncthreads();
     const int hstride = kTileW + 2 * R;
     const int q0 = (c.li + R) * hstride + (c.lj + R);
@@ -344,7 +568,7 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W)
         for (int i = threadIdx.x; i < n_pts; i += kTileThreads) {
             const int px = s_pts[i] >> 2, k = s_pts[i] & 3;
             const int ci = px / kTileW + R, cj = px % kTileW + R;
-            s_tn[k][px] = apss_point(st, hstride, R, K, ci, cj, st[k * kHalo + ci * hstride + cj], P, F.nt);
+            s_tn[k][px] = apss_point<K>(st, hstride, R, ci, cj, st[k * kHalo + ci * hstride + cj], P, F.nt);
         }
     } else if (P.depth_den == RT3D_DEPTH_LEARNED) {
         // the network's move where it stays within the fallback bound, APSS elsewhere
@@ -360,79 +584,70 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W)
                     continue;
                 }
             }
-            s_tn[k][px] = apss_point(st, hstride, R, K, ci, cj, t0, P, F.nt);
+            s_tn[k][px] = apss_point<K>(st, hstride, R, ci, cj, t0, P, F.nt);
         }
     }
     __syncthreads();
-    if (c.inb) {
-        const int lp = c.gi * F.w + c.gj;
-        for (int k = 0; k < K; ++k) {
-            const float v = s_tn[k][threadIdx.x];
-            // dead slots keep the depth they had
-            F.t[(long long)k * np + lp] = v == kDeadDepth ? W.t_half[(long long)k * S + F.pix_base + lp] : v;
-        }
+    float tk[K], rk[K], rr[K], tn[K];
+    bool ak[K];
+    float g = 0.0f, b = 0.0f;
+    // every load before the first store (one memory round trip)
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float v = c.inb ? s_tn[k][threadIdx.x] : kDeadDepth;
+        ak[k] = v != kDeadDepth;
+        tk[k] = ak[k] ? v : 0.0f;
+        rk[k] = c.inb ? F.r[(long long)k * np + lp] : 0.0f;
+        rr[k] = ak[k] ? rk[k] : 0.0f;
+        // dead slots keep the depth they had
+        tn[k] = v;
+        if (c.inb && !ak[k]) tn[k] = W.t_half[(long long)k * S + wp];
     }
-
+    if (c.inb) {
+        g = F.gain ? F.gain[lp] : 1.0f;
+        b = F.b[lp];
+#pragma unroll
+        for (int k = 0; k < K; ++k) F.t[(long long)k * np + lp] = tn[k];
+    }
+    float sh[K];
+    warp_pixel_sums<K, 1>(F.ent, sg, c.inb, coef, P, tk, rr, b, g, ws[threadIdx.x >> 5], sh);
     if (!c.inb) return;
-    {
-        const int lp = c.gi * F.w + c.gj, wp = F.pix_base + lp;
-        float tk[kMaxK], rk[kMaxK];
-        bool ak[kMaxK];
 #pragma unroll
-        for (int k = 0; k < kMaxK; ++k) {
-            const bool in = k < K;
-            const float v = in ? s_tn[k][threadIdx.x] : kDeadDepth;
-            ak[k] = v != kDeadDepth;
-            tk[k] = ak[k] ? v : 0.0f;
-            rk[k] = in ? F.r[(long long)k * np + lp] : 0.0f;
+    for (int k = 0; k < K; ++k) {
+        float rn = rk[k];
+        if (ak[k] && g > 0.0f) {
+            float H, dH;
+            support_sums(pad, P, F.nt, tk[k], H, dH);
+            rn = fmaxf(rk[k] - P.r_step * (rk[k] + P.eps_r) * (H - sh[k]), 0.0f);
         }
-        const float g = F.gain ? F.gain[lp] : 1.0f;
-        float sh[kMaxK], sdh[kMaxK], sz;
-        pixel_sums(F.ent, W.seg[wp], pad, P, tk, rk, ak, F.b[lp], g, sh, sdh, sz);
-#pragma unroll
-        for (int k = 0; k < kMaxK; ++k) {
-            if (k >= K) continue;
-            float rn = rk[k];
-            if (ak[k] && g > 0.0f) {
-                float H, dH;
-                support_sums(pad, P, F.nt, tk[k], H, dH);
-                rn = fmaxf(rk[k] - P.r_step * (rk[k] + P.eps_r) * (H - sh[k]), 0.0f);
-            }
-            W.r_half[(long long)k * S + wp] = rn;
-        }
+        W.r_half[(long long)k * S + wp] = rn;
     }
 }
 
 // ----------------------------------------------------------------------------
 // Phase C: intensity low-pass on the surface + pruning + background gradient step.
+template <int K>
 __global__ void __launch_bounds__(kTileThreads)
 k_phase_c(const CallRecord* __restrict__ rec, const Work W)
 {
     const KParams& P = rec->P;
     const Batch& B = rec->B;
     __shared__ float pad[kMaxIrf + 2 * kIrfPad];
-    __shared__ float st[kMaxK * kHalo];
-    __shared__ float sr[kMaxK * kHalo];
-    __shared__ float s_rn[kMaxK][kTileThreads];
-    __shared__ uint8_t s_an[kMaxK][kTileThreads];
-    __shared__ unsigned short s_pts[kMaxK * kTileThreads];
+    __shared__ float st[K * kHalo];
+    __shared__ float sr[K * kHalo];
+    __shared__ float s_rn[K][kTileThreads];
+    __shared__ uint8_t s_an[K][kTileThreads];
+    __shared__ unsigned short s_pts[K * kTileThreads];
     __shared__ int s_warp[kTileThreads / 32];
-    load_irf(pad, P);
+    __shared__ float4 coef[kCoefLen];
+    __shared__ WarpSums<K, 1> ws[kTileThreads / 32];
+    load_irf_coef(pad, coef, P);
     const TileCtx c = tile_ctx(B);
     const FrameDesc& F = B.f[c.fi];
-    const int np = F.npix, S = W.stride, R = P.win_r, K = P.k;
-    load_halo_depth(c, F, R, K, F.t, np, 0, F.alive, np, st);
-    {
-        const int hh = kTileH + 2 * R, hw = kTileW + 2 * R;
-        for (int idx = threadIdx.x; idx < hh * hw; idx += blockDim.x) {
-            const int hi = idx / hw, hj = idx % hw;
-            const int gi = c.i0 - R + hi, gj = c.j0 - R + hj;
-            const bool in = gi >= 0 && gi < F.h && gj >= 0 && gj < F.w;
-            const int lp = in ? gi * F.w + gj : 0;
-            for (int m = 0; m < K; ++m)
-                sr[m * kHalo + idx] = in ? W.r_half[(long long)m * S + F.pix_base + lp] : 0.0f;
-        }
-    }
+    const int np = F.npix, S = W.stride, R = P.win_r;
+    const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
+    const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
+    load_halo<K, true>(c, F, R, F.t, np, 0, F.alive, np, st, W.r_half, S, F.pix_base, sr);
     __syncthreads();
     const int hstride = kTileW + 2 * R;
     const int q0 = (c.li + R) * hstride + (c.lj + R);
@@ -460,6 +675,7 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W)
                         const float r2 = x * x + y * y;
                         if (!(r2 < 1.0f)) continue;
                         const int q = (ci + di) * hstride + (cj + dj);
+#pragma unroll
                         for (int m = 0; m < K; ++m) {
                             const float z = (st[m * kHalo + q] - tn) * inv_h;
                             const float d2 = r2 + z * z;
@@ -479,7 +695,6 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W)
     }
     __syncthreads();
     if (c.inb) {
-        const int lp = c.gi * F.w + c.gj, wp = F.pix_base + lp;
         // same-pixel points closer than merge_dist are one surface: the weaker
         // (the later slot on a tie) is removed and its intensity added to the other
         for (int a = 0; a < K; ++a)
@@ -499,26 +714,24 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W)
     }
     __syncthreads();
 
-    if (!c.inb) return;
-    {
-        const int lp = c.gi * F.w + c.gj, wp = F.pix_base + lp;
-        float tk[kMaxK], rk[kMaxK];
-        bool ak[kMaxK];
+    float tk[K], rr[K];
 #pragma unroll
-        for (int k = 0; k < kMaxK; ++k) {
-            const bool in = k < K;
-            ak[k] = in && s_an[k][threadIdx.x];
-            tk[k] = ak[k] ? st[k * kHalo + q0] : 0.0f;
-            rk[k] = in ? s_rn[k][threadIdx.x] : 0.0f;
-        }
-        const float g = F.gain ? F.gain[lp] : 1.0f;
-        const float b = F.b[lp];
-        float sh[kMaxK], sdh[kMaxK], sz;
-        pixel_sums(F.ent, W.seg[wp], pad, P, tk, rk, ak, b, g, sh, sdh, sz);
-        float bn = b;
-        if (g > 0.0f) bn = fmaxf(b - P.b_step * (b + P.eps_b) * (1.0f - sz / (float)F.nt), P.b_floor);
-        W.b_half[wp] = bn;
+    for (int k = 0; k < K; ++k) {
+        const bool ak = c.inb && s_an[k][threadIdx.x];
+        tk[k] = ak ? st[k * kHalo + q0] : 0.0f;
+        rr[k] = ak ? s_rn[k][threadIdx.x] : 0.0f;
     }
+    float g = 0.0f, b = 0.0f;
+    if (c.inb) {
+        g = F.gain ? F.gain[lp] : 1.0f;
+        b = F.b[lp];
+    }
+    float sz;
+    warp_pixel_sums<K, 2>(F.ent, sg, c.inb, coef, P, tk, rr, b, g, ws[threadIdx.x >> 5], &sz);
+    if (!c.inb) return;
+    float bn = b;
+    if (g > 0.0f) bn = fmaxf(b - P.b_step * (b + P.eps_b) * (1.0f - sz / (float)F.nt), P.b_floor);
+    W.b_half[wp] = bn;
 }
 
 // ----------------------------------------------------------------------------

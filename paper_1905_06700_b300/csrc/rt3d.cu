@@ -615,13 +615,36 @@ rt3d_status net_forward_tiles(rt3d_ctx* c, const rt3d_net* net, int strips, cons
     return st;
 }
 
+// One PALM phase kernel (0: A, 1: B, 2: C), instantiated for the slot count.
+template <int K>
+void launch_phase_k(int phase, int first, int tiles, cudaStream_t s, const CallRecord* rec, const Work& W)
+{
+    if (phase == 0)
+        k_phase_a<K><<<tiles, kTileThreads, 0, s>>>(rec, W, first);
+    else if (phase == 1)
+        k_phase_b<K><<<tiles, kTileThreads, 0, s>>>(rec, W);
+    else
+        k_phase_c<K><<<tiles, kTileThreads, 0, s>>>(rec, W);
+}
+
+void launch_phase(int k, int phase, int first, int tiles, cudaStream_t s, const CallRecord* rec, const Work& W)
+{
+    static_assert(kMaxK == 4, "one instantiation per slot count");
+    switch (k) {
+    case 1: launch_phase_k<1>(phase, first, tiles, s, rec, W); break;
+    case 2: launch_phase_k<2>(phase, first, tiles, s, rec, W); break;
+    case 3: launch_phase_k<3>(phase, first, tiles, s, rec, W); break;
+    default: launch_phase_k<4>(phase, first, tiles, s, rec, W); break;
+    }
+}
+
 rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
 {
     const bool learned = c->h_rec.P.depth_den == RT3D_DEPTH_LEARNED;
     for (int it = 0; it < n_iter; ++it) {
         {
             LaunchScope ls(c, s, kcA);
-            k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W, it == 0 ? 1 : 0);
+            launch_phase(c->h_rec.P.k, 0, it == 0 ? 1 : 0, B.total_tiles, s, c->d_rec, c->W);
         }
         if (learned) {
             {
@@ -635,11 +658,11 @@ rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
         }
         {
             LaunchScope ls(c, s, kcB);
-            k_phase_b<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W);
+            launch_phase(c->h_rec.P.k, 1, 0, B.total_tiles, s, c->d_rec, c->W);
         }
         {
             LaunchScope ls(c, s, kcC);
-            k_phase_c<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W);
+            launch_phase(c->h_rec.P.k, 2, 0, B.total_tiles, s, c->d_rec, c->W);
         }
     }
     RT3D_CUDA(cudaGetLastError());
@@ -1112,9 +1135,7 @@ rt3d_status rt3d_phase(rt3d_ctx_t* c, int phase, int first, const rt3d_frame* f,
         RT3D_CUDA(cudaMemcpyAsync(c->W.b_half, state->b, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
     {
         LaunchScope ls(c, s, phase == 0 ? kcA : (phase == 1 ? kcB : kcC));
-        if (phase == 0) k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W, first);
-        if (phase == 1) k_phase_b<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W);
-        if (phase == 2) k_phase_c<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W);
+        launch_phase(K.k, phase, first, B.total_tiles, s, c->d_rec, c->W);
     }
     RT3D_CUDA(cudaGetLastError());
     for (int k = 0; k < Kp; ++k) {
@@ -1704,9 +1725,7 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     RT3D_CUDA(cudaFuncSetAttribute(init_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     init_fn<<<(B.total_pix + warps - 1) / warps, warps * 32, smem, s>>>(d_rec, W);
     for (int it = 0; it < p->n_iter; ++it) {
-        k_phase_a<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W, it == 0 ? 1 : 0);
-        k_phase_b<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W);
-        k_phase_c<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W);
+        for (int ph = 0; ph < 3; ++ph) launch_phase(K.k, ph, it == 0 ? 1 : 0, B.total_tiles, s, d_rec, W);
     }
     k_final<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W, p->n_iter > 0 ? 1 : 0);
     RT3D_CUDA(cudaGetLastError());
