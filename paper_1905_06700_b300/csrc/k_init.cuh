@@ -43,16 +43,6 @@ __host__ __device__ constexpr int init_warp_bytes(int sep)
     return kInitStage * 4 + ((init_buf(sep) * 4 + 15) & ~15);
 }
 
-__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        const unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
-        v = w > v ? w : v;
-    }
-    return v;
-}
-
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
 {
 #pragma unroll
@@ -255,9 +245,11 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
                 if (m != 0xffffffffu) break;
             }
             const int cend = min(cbase + kInitChunk, hi + 1);
-            for (int i = lane; i < nbuf; i += 32) Y[i] = 0;
+            // positions the scatter below can reach and the scan reads
+            const int nclr = min(nbuf, cend - cbase + 2 * sep);
+            for (int i = lane; i < nclr; i += 32) Y[i] = 0;
             __syncwarp();
-            const int blo = max(0, cbase - sep), bhi = min(T, cbase + kInitChunk + sep);
+            const int blo = max(0, cbase - sep), bhi = min(T, cend + sep);
             for (uint32_t e = e_lo; e < e_hi; ++e) {
                 const uint32_t v = ent[e];
                 const int bin = (int)(v >> 16), z = (int)(v & 0xffffu);
@@ -273,35 +265,50 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
                 __syncwarp();
                 continue;
             } else {
-            for (int i = lane; cbase + i < cend; i += 32) {
-                const int tau = cbase + i, yi = i + sep;
-                const int y = Y[yi];
-                if (y <= 0) continue;
-                if (sep > 0 && !(Y[yi - 1] < y && Y[yi + 1] <= y)) continue;   // immediate neighbours
-                bool ok = true;
-                for (int q = 2; q <= sep && ok; ++q) ok = Y[yi - q] < y && Y[yi + q] <= y;
-                if (!ok) continue;
-                // photons in the IRF window [tau - origin, tau - origin + L)
-                int wcount = 0;
-                for (uint32_t e = e_first; e <= e_last && wcount < min_photons; ++e) {
-                    const uint32_t v = ent[e];
-                    const int bin = (int)(v >> 16);
-                    if (bin >= tau - O && bin <= tau - O + L - 1) wcount += (int)(v & 0xffffu);
+            for (int i0 = 0; cbase + i0 < cend; i0 += 32) {
+                // local maxima against the immediate neighbours, 32 positions per vote
+                const int i = i0 + lane, yi = i + sep;
+                bool cand = false;
+                if (cbase + i < cend) {
+                    const int y = Y[yi];
+                    cand = y > 0 && (sep == 0 || (Y[yi - 1] < y && Y[yi + 1] <= y));
                 }
-                if (wcount < min_photons) continue;
-                // insert into this lane's list (y descending; equal y keeps the earlier bin first)
-                int pos = nb;
+                unsigned cm = __ballot_sync(0xffffffffu, cand);
+                while (cm) {
+                    // one candidate at a time, in bin order, tested by the whole warp
+                    const int ci = i0 + __ffs(cm) - 1;
+                    cm &= cm - 1;
+                    const int cyi = ci + sep, tau = cbase + ci;
+                    const int y = Y[cyi];
+                    // strict-left / non-strict-right maximum over +-sep: lanes over offsets
+                    bool ok = true;
+                    for (int q = 2 + lane; q <= sep; q += 32) ok = ok && Y[cyi - q] < y && Y[cyi + q] <= y;
+                    if (!__all_sync(0xffffffffu, ok)) continue;
+                    // photons in the IRF window [tau - origin, tau - origin + L): lanes over entries
+                    int wcount = 0;
+                    for (uint32_t e = e_first + lane; e <= e_last; e += 32) {
+                        const uint32_t v = ent[e];
+                        const int bin = (int)(v >> 16);
+                        if (bin >= tau - O && bin <= tau - O + L - 1) wcount += (int)(v & 0xffffu);
+                    }
 #pragma unroll
-                for (int k = kMaxK - 1; k >= 0; --k)
-                    if (k < nb && by[k] < y) pos = k;
-                if (pos >= K) continue;
+                    for (int o = 16; o > 0; o >>= 1) wcount += __shfl_xor_sync(0xffffffffu, wcount, o);
+                    if (wcount < min_photons) continue;
+                    // the warp's list of the K best (y descending; candidates arrive in
+                    // bin order, so equal y keeps the earlier bin first)
+                    int pos = nb;
 #pragma unroll
-                for (int k = kMaxK - 1; k > 0; --k)
-                    if (k > pos && k < K) { by[k] = by[k - 1]; bt[k] = bt[k - 1]; }
+                    for (int k = kMaxK - 1; k >= 0; --k)
+                        if (k < nb && by[k] < y) pos = k;
+                    if (pos >= K) continue;
 #pragma unroll
-                for (int k = 0; k < kMaxK; ++k)
-                    if (k == pos) { by[k] = y; bt[k] = tau; }
-                if (nb < K) ++nb;
+                    for (int k = kMaxK - 1; k > 0; --k)
+                        if (k > pos && k < K) { by[k] = by[k - 1]; bt[k] = bt[k - 1]; }
+#pragma unroll
+                    for (int k = 0; k < kMaxK; ++k)
+                        if (k == pos) { by[k] = y; bt[k] = tau; }
+                    if (nb < K) ++nb;
+                }
             }
             __syncwarp();
             }
@@ -309,25 +316,17 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
     }
     if (kDumpY) return;
 
-    // K-round warp arg-max: key = (y << 32) | ~tau  (largest y, then smallest tau)
+    // the K largest filter values (ties to the earlier bin), the same in every lane
     int sel[kMaxK];
-    int nsel = 0;
-    int head = 0;
-    for (int r = 0; r < K; ++r) {
-        unsigned long long key = 0;
+    int nsel = nb;
 #pragma unroll
-        for (int k = 0; k < kMaxK; ++k)
-            if (k == head && head < nb)
-                key = ((unsigned long long)(unsigned)by[k] << 32) | (0xffffffffu - (unsigned)bt[k]);
-        const unsigned long long best = warp_max_u64(key);
-        if (best == 0) break;
-        if (key == best) ++head;
-        sel[nsel++] = (int)(0xffffffffu - (unsigned)(best & 0xffffffffu));
-    }
+    for (int k = 0; k < kMaxK; ++k) sel[k] = bt[k];
     // slots by increasing depth
-    for (int a = 0; a < nsel; ++a)
-        for (int c = a + 1; c < nsel; ++c)
-            if (sel[c] < sel[a]) { const int tmp = sel[a]; sel[a] = sel[c]; sel[c] = tmp; }
+#pragma unroll
+    for (int a = 0; a < kMaxK; ++a)
+#pragma unroll
+        for (int c = a + 1; c < kMaxK; ++c)
+            if (c < nsel && sel[c] < sel[a]) { const int tmp = sel[a]; sel[a] = sel[c]; sel[c] = tmp; }
 
     // ---- 4. initial intensities and background ------------------------------
     unsigned long long inside = 0;
@@ -354,7 +353,10 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
     // bins covered by the union of the kept windows (windows sorted by start)
     int covered = 0, cur_lo = 0, cur_hi = -1;
     int winlen[kMaxK];
-    for (int k = 0; k < nsel; ++k) {
+#pragma unroll
+    for (int k = 0; k < kMaxK; ++k) {
+        winlen[k] = 0;
+        if (k >= nsel) continue;
         const int lo = max(sel[k] - O, 0), hi = min(sel[k] - O + L - 1, T - 1);
         winlen[k] = max(hi - lo + 1, 0);
         if (hi < lo) continue;

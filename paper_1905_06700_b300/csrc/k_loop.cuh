@@ -376,9 +376,10 @@ constexpr int kHalo = kHaloH * kHaloW;
 // the window (local coordinates scaled by 1/h), solved in centred form --
 // the 3x3 normal equations of (x, y, |x|^2) against z, then u0 from the
 // weighted means -- and projection along the line of sight onto s = 0.
-// The accumulation is branch-free: dead or absent slots hold a far sentinel
-// depth, so their weight is exactly zero; window offsets outside the lateral
-// radius are skipped uniformly across the warp.
+// Dead or absent slots hold a far sentinel depth, so their weight is exactly
+// zero; each thread accumulates only the slots inside the window (in slot
+// order), and window offsets outside the lateral radius are skipped uniformly
+// across the warp.
 template <int K>
 __device__ float apss_point(const float* st, int hstride, int R, int ci, int cj, float tn,
                             const KParams& P, int T)
@@ -397,16 +398,30 @@ __device__ float apss_point(const float* st, int hstride, int R, int ci, int cj,
             const float r2 = x * x + y * y;
             if (!(r2 < 1.0f)) continue;
             const int q = (ci + di) * hstride + (cj + dj);
-            float cnt = 0.0f;
+            float zk[K], d2k[K];
+            unsigned in = 0u;
 #pragma unroll
             for (int m = 0; m < K; ++m) {
-                const float z = (st[m * kHalo + q] - tn) * inv_h;
-                const float d2 = r2 + z * z;
-                const bool in = d2 < 1.0f;
+                zk[m] = (st[m * kHalo + q] - tn) * inv_h;
+                d2k[m] = r2 + zk[m] * zk[m];
+                if (d2k[m] < 1.0f) in |= 1u << m;
+            }
+            const float cnt = (float)__popc(in);
+            // only the slots inside the window: the others have weight exactly
+            // zero and would leave every sum unchanged
+            while (in) {
+                const int m = __ffs(in) - 1;
+                in &= in - 1u;
+                float z = zk[0], d2 = d2k[0];
+#pragma unroll
+                for (int j = 1; j < K; ++j)
+                    if (m == j) {
+                        z = zk[j];
+                        d2 = d2k[j];
+                    }
                 float w = 1.0f - d2;
                 w *= w;
-                w = in ? w * w : 0.0f;
-                cnt += in ? 1.0f : 0.0f;
+                w = w * w;
                 const float wx = w * x, wy = w * y, wq = w * d2;
                 S0 += w; Sx += wx; Sy += wy; Sz += w * z; Sq += wq;
                 Sxx += wx * x; Sxy += wx * y; Syy += wy * y;
@@ -539,7 +554,7 @@ __device__ __forceinline__ int compact_points(const float* st, int R, int K, boo
 // ----------------------------------------------------------------------------
 // Phase B: APSS depth denoiser + intensity gradient step.
 template <int K>
-__global__ void __launch_bounds__(kTileThreads, 8)
+__global__ void __launch_bounds__(kTileThreads, 7)
 k_phase_b(const CallRecord* __restrict__ rec, const Work W)
 {
     const KParams& P = rec->P;
