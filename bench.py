@@ -90,13 +90,15 @@ def job_throughput(frames_per_rank_step: int, steps: int, world: int, t_max_ms: 
     return frames_per_rank_step * steps * world / (t_max_ms / 1000.0)
 
 
-def algorithmic_bytes(n_frames: int, nnz_total: int, k: int) -> dict:
+def algorithmic_bytes(n_frames: int, nnz_total: int, k: int, fused_frac: float = 0.0) -> dict:
     """Bytes each kernel class must move per launch for n frames of H x W x T
     (every array read or written once; halos counted once).  Per pixel:
       init    2T dense read + 8 seg + 9K state + 4 b written, + 4 per nonzero entry written
       phase A 8 seg + 4 b_half + K (4 t + 4 r + 1 alive_b + 1 alive + 4 t_half) + 4 b, + 4/entry
       phase B 8 seg + K (4 t_half + 1 alive + 4 r + 4 t + 4 r_half) + 4 b, + 4/entry
-      phase C 8 seg + K (4 t + 4 r_half + 1 alive + 4 r + 1 alive_b) + 4 b + 4 b_half, + 4/entry
+      phase C 8 seg + K (4 t + 4 r_half + 1 alive + 4 r + 1 alive_b) + 4 b + 4 b_half, + 4/entry;
+              a launch that also runs the next iteration's depth step (fused_frac of
+              them) writes K x 4 t_half + 4 b more
       final   K (1 alive_b + 1 alive) + 4 b_half + 4 b."""
     px = n_frames * H * W
     e = 4 * nnz_total
@@ -104,7 +106,7 @@ def algorithmic_bytes(n_frames: int, nnz_total: int, k: int) -> dict:
         "init": px * (2 * T + 8 + 9 * k + 4) + e,
         "phase_a": px * (8 + 4 + k * 14 + 4) + e,
         "phase_b": px * (8 + k * 17 + 4) + e,
-        "phase_c": px * (8 + k * 14 + 8) + e,
+        "phase_c": px * (8 + k * 14 + 8) + e + fused_frac * px * (4 * k + 4),
         "final": px * (2 * k + 8),
     }
 
@@ -116,17 +118,29 @@ def lateral_offsets(prm) -> int:
                if (p * di) ** 2 + (p * dj) ** 2 < h * h)
 
 
-def algorithmic_flops(n_frames: int, nnz_total: int, n_points: int, k: int, prm) -> dict:
+def algorithmic_flops(n_frames: int, nnz_total: int, n_points: int, k: int, prm,
+                      fused_frac: float = 0.0) -> dict:
     """FP32 operations each loop kernel must execute per launch:
       APSS         per alive point: (offsets in radius) x K candidates x 36 (distance,
                    weight, 14 moment multiply-adds) + 60 (centred 3x3 solve, projection)
       low-pass     per alive point: (offsets) x K x 12
-      gradient step per nonzero bin: K x 24 (cubic IRF value and slope, lambda, sums)."""
+      gradient step per nonzero bin: K x 24 (cubic IRF value and slope, lambda, sums);
+      phase C launches that also run the next depth step (fused_frac) add its sums."""
     off = lateral_offsets(prm)
     grad = nnz_total * k * 24
     return {"phase_a": grad,
             "phase_b": n_points * (off * k * 36 + 60) + grad,
-            "phase_c": n_points * off * k * 12 + grad}
+            "phase_c": n_points * off * k * 12 + grad + fused_frac * grad}
+
+
+def fused_fraction(prm) -> float:
+    """Share of phase C launches that also run the next iteration's depth step
+    (the library fuses it when the background denoiser is the identity and the
+    depth denoiser is not the learned one): all but the last iteration's."""
+    n = int(prm["n_iter"])
+    if n <= 0 or prm.get("bkg_mode", 0) == 1 or prm.get("depth_denoiser", 1) == 2:
+        return 0.0
+    return (n - 1) / n
 
 
 class Clocks:
@@ -257,8 +271,9 @@ def run_ours(args, world, rank, local):
 
     # ---------------- dominant kernel vs its roofline
     n_points = int(sum(int(o["n_points"].item()) for o in outs))
-    alg = algorithmic_bytes(nb, nnz_total, K)
-    flops = algorithmic_flops(nb, nnz_total, n_points, K, prm)
+    ff = fused_fraction(prm)
+    alg = algorithmic_bytes(nb, nnz_total, K, ff)
+    flops = algorithmic_flops(nb, nnz_total, n_points, K, prm, ff)
     peaks = measured_peaks()
     per_kernel = {}
     for name in KERNEL_NAMES:

@@ -117,13 +117,14 @@ struct WarpSums {
 // one lane; a pixel split over lanes l1..l2 is the sum of its per-lane pieces
 // added in lane order.  The grouping depends only on the 32 pixels' bin counts,
 // so the result is deterministic and independent of the rest of the batch.
-template <int K, int MODE>
+template <int K, int MODE, int NSX>
 __device__ __forceinline__ void warp_pixel_sums(const uint32_t* __restrict__ ent, uint2 sg, bool on,
                                                 const float4* coef, const KParams& P, const float* tk,
                                                 const float* rr, float b, float g,
-                                                WarpSums<K, (MODE == 2 ? 1 : K)>& S, float* out)
+                                                WarpSums<K, NSX>& S, float* out)
 {
     constexpr int NS = MODE == 2 ? 1 : K;
+    static_assert(NSX >= NS, "scratch too small for the sums");
     constexpr int NW = PixRec<K>::NW;
     const unsigned full = 0xffffffffu;
     const int lane = threadIdx.x & 31;
@@ -300,6 +301,29 @@ __device__ __forceinline__ float bkg_filter(const KParams& P, const float* bh, i
     return acc;
 }
 
+// Depth gradient step of one pixel's slots (Results, "Depth update": a scaled
+// gradient step on the negative log-likelihood, clamped to dt_max and to the
+// histogram) from its bin sums sdh[k] = sum z h'(t - t_k)/lambda.
+template <int K>
+__device__ __forceinline__ void depth_step(const float* pad, const KParams& P, int T, const float* tk,
+                                           const float* rk, const bool* ak, float g, const float* sdh,
+                                           float* t_half, long long stride)
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        float tn = tk[k];
+        if (ak[k] && g > 0.0f) {
+            float H, dH;
+            support_sums(pad, P, T, tk[k], H, dH);
+            const float grad = g * rk[k] * (-dH + sdh[k]);
+            const float beta = P.t_step / (g * rk[k] + P.eps_r);
+            const float step = clampf(-beta * grad, -P.dt_max, P.dt_max);
+            tn = clampf(tk[k] + step, 0.0f, (float)(T - 1));
+        }
+        t_half[(long long)k * stride] = tn;
+    }
+}
+
 // ----------------------------------------------------------------------------
 // Phase A: background denoiser of the previous iteration + depth gradient step,
 // one thread per pixel (the bin sums shared out over the warp).
@@ -352,19 +376,7 @@ k_phase_a(const CallRecord* __restrict__ rec, const Work W, int first)
     float sdh[K];
     warp_pixel_sums<K, 0>(F.ent, sg, c.inb, coef, P, tk, rr, b, g, ws[threadIdx.x >> 5], sdh);
     if (!c.inb) return;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        float tn = tk[k];
-        if (ak[k] && g > 0.0f) {
-            float H, dH;
-            support_sums(pad, P, F.nt, tk[k], H, dH);
-            const float grad = g * rk[k] * (-dH + sdh[k]);
-            const float beta = P.t_step / (g * rk[k] + P.eps_r);
-            const float step = clampf(-beta * grad, -P.dt_max, P.dt_max);
-            tn = clampf(tk[k] + step, 0.0f, (float)(F.nt - 1));
-        }
-        W.t_half[(long long)k * S + wp] = tn;
-    }
+    depth_step<K>(pad, P, F.nt, tk, rk, ak, g, sdh, W.t_half + wp, S);
 }
 
 // ----------------------------------------------------------------------------
@@ -552,10 +564,12 @@ __device__ __forceinline__ int compact_points(const float* st, int R, int K, boo
 }
 
 // ----------------------------------------------------------------------------
-// Phase B: APSS depth denoiser + intensity gradient step.
+// Phase B: APSS depth denoiser + intensity gradient step.  alive_from_b: the
+// previous phase C ran this iteration's depth step, so the alive flags are
+// still in alive_b; they land in the frame here (phase C reads them there).
 template <int K>
 __global__ void __launch_bounds__(kTileThreads, 7)
-k_phase_b(const CallRecord* __restrict__ rec, const Work W)
+k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b)
 {
     const KParams& P = rec->P;
     const Batch& B = rec->B;
@@ -572,11 +586,17 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W)
     const int np = F.npix, S = W.stride, R = P.win_r;
     const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
     const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
-    load_halo<K, false>(c, F, R, W.t_half, S, F.pix_base, F.alive, np, st, nullptr, 0, 0, nullptr);
+    if (alive_from_b)
+        load_halo<K, false>(c, F, R, W.t_half, S, F.pix_base, W.alive_b + F.pix_base, S, st, nullptr, 0, 0,
+                            nullptr);
+    else
+        load_halo<K, false>(c, F, R, W.t_half, S, F.pix_base, F.alive, np, st, nullptr, 0, 0, nullptr);
     __syncthreads();
     const int hstride = kTileW + 2 * R;
     const int q0 = (c.li + R) * hstride + (c.lj + R);
     for (int k = 0; k < K; ++k) s_tn[k][threadIdx.x] = st[k * kHalo + q0];
+    if (alive_from_b && c.inb)
+        for (int k = 0; k < K; ++k) F.alive[(long long)k * np + lp] = st[k * kHalo + q0] != kDeadDepth ? 1 : 0;
     const int n_pts = compact_points(st, R, K, c.inb, c.li, c.lj, s_pts, s_warp);
     __syncthreads();
     if (P.depth_den == RT3D_DEPTH_APSS) {
@@ -641,9 +661,13 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W)
 
 // ----------------------------------------------------------------------------
 // Phase C: intensity low-pass on the surface + pruning + background gradient step.
+// fuse_next (background denoiser = identity): the next iteration's phase A
+// follows on the state each thread holds -- b <- b_half, alive <- alive_b (it
+// reaches the frame in the next phase B, since neighbours read the frame's
+// alive flags here), depth step into t_half.
 template <int K>
 __global__ void __launch_bounds__(kTileThreads)
-k_phase_c(const CallRecord* __restrict__ rec, const Work W)
+k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next)
 {
     const KParams& P = rec->P;
     const Batch& B = rec->B;
@@ -655,7 +679,7 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W)
     __shared__ unsigned short s_pts[K * kTileThreads];
     __shared__ int s_warp[kTileThreads / 32];
     __shared__ float4 coef[kCoefLen];
-    __shared__ WarpSums<K, 1> ws[kTileThreads / 32];
+    __shared__ WarpSums<K, K> ws[kTileThreads / 32];
     load_irf_coef(pad, coef, P);
     const TileCtx c = tile_ctx(B);
     const FrameDesc& F = B.f[c.fi];
@@ -743,10 +767,29 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W)
     }
     float sz;
     warp_pixel_sums<K, 2>(F.ent, sg, c.inb, coef, P, tk, rr, b, g, ws[threadIdx.x >> 5], &sz);
-    if (!c.inb) return;
     float bn = b;
-    if (g > 0.0f) bn = fmaxf(b - P.b_step * (b + P.eps_b) * (1.0f - sz / (float)F.nt), P.b_floor);
-    W.b_half[wp] = bn;
+    if (c.inb) {
+        if (g > 0.0f) bn = fmaxf(b - P.b_step * (b + P.eps_b) * (1.0f - sz / (float)F.nt), P.b_floor);
+        W.b_half[wp] = bn;
+    }
+    if (!fuse_next) return;
+
+    // next iteration: background denoiser (identity) and depth step
+    float tka[K], rka[K], rra[K];
+    bool aka[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        const float ts = st[k * kHalo + q0];
+        aka[k] = c.inb && s_an[k][threadIdx.x];
+        tka[k] = ts != kDeadDepth ? ts : (c.inb ? F.t[(long long)k * np + lp] : 0.0f);
+        rka[k] = c.inb ? s_rn[k][threadIdx.x] : 0.0f;
+        rra[k] = aka[k] ? rka[k] : 0.0f;
+    }
+    if (c.inb) F.b[lp] = bn;
+    float sdh[K];
+    warp_pixel_sums<K, 0>(F.ent, sg, c.inb, coef, P, tka, rra, bn, g, ws[threadIdx.x >> 5], sdh);
+    if (!c.inb) return;
+    depth_step<K>(pad, P, F.nt, tka, rka, aka, g, sdh, W.t_half + wp, S);
 }
 
 // ----------------------------------------------------------------------------

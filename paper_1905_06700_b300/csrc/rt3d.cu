@@ -47,13 +47,13 @@ struct PendingTiming {
 struct GraphKey {
     int total_pix, total_tiles, n_iter, warm, init_warps, profiled;
     size_t init_smem;
-    int tc_tiles, tc_stages, tc_nd, any_int, learned;
+    int tc_tiles, tc_stages, tc_nd, any_int, learned, fused;
     bool operator<(const GraphKey& o) const
     {
         return std::tie(total_pix, total_tiles, n_iter, warm, init_warps, profiled, init_smem, tc_tiles,
-                        tc_stages, tc_nd, any_int, learned) <
+                        tc_stages, tc_nd, any_int, learned, fused) <
                std::tie(o.total_pix, o.total_tiles, o.n_iter, o.warm, o.init_warps, o.profiled,
-                        o.init_smem, o.tc_tiles, o.tc_stages, o.tc_nd, o.any_int, o.learned);
+                        o.init_smem, o.tc_tiles, o.tc_stages, o.tc_nd, o.any_int, o.learned, o.fused);
     }
 };
 
@@ -616,33 +616,45 @@ rt3d_status net_forward_tiles(rt3d_ctx* c, const rt3d_net* net, int strips, cons
 }
 
 // One PALM phase kernel (0: A, 1: B, 2: C), instantiated for the slot count.
+// flag: phase A -- first iteration; phase B -- alive flags still in alive_b;
+// phase C -- run the next iteration's depth step too.
 template <int K>
-void launch_phase_k(int phase, int first, int tiles, cudaStream_t s, const CallRecord* rec, const Work& W)
+void launch_phase_k(int phase, int flag, int tiles, cudaStream_t s, const CallRecord* rec, const Work& W)
 {
     if (phase == 0)
-        k_phase_a<K><<<tiles, kTileThreads, 0, s>>>(rec, W, first);
+        k_phase_a<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag);
     else if (phase == 1)
-        k_phase_b<K><<<tiles, kTileThreads, 0, s>>>(rec, W);
+        k_phase_b<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag);
     else
-        k_phase_c<K><<<tiles, kTileThreads, 0, s>>>(rec, W);
+        k_phase_c<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag);
 }
 
-void launch_phase(int k, int phase, int first, int tiles, cudaStream_t s, const CallRecord* rec, const Work& W)
+void launch_phase(int k, int phase, int flag, int tiles, cudaStream_t s, const CallRecord* rec, const Work& W)
 {
     static_assert(kMaxK == 4, "one instantiation per slot count");
     switch (k) {
-    case 1: launch_phase_k<1>(phase, first, tiles, s, rec, W); break;
-    case 2: launch_phase_k<2>(phase, first, tiles, s, rec, W); break;
-    case 3: launch_phase_k<3>(phase, first, tiles, s, rec, W); break;
-    default: launch_phase_k<4>(phase, first, tiles, s, rec, W); break;
+    case 1: launch_phase_k<1>(phase, flag, tiles, s, rec, W); break;
+    case 2: launch_phase_k<2>(phase, flag, tiles, s, rec, W); break;
+    case 3: launch_phase_k<3>(phase, flag, tiles, s, rec, W); break;
+    default: launch_phase_k<4>(phase, flag, tiles, s, rec, W); break;
     }
+}
+
+// With the identity background denoiser the depth step needs only its own
+// pixel's state, so it rides on the previous iteration's phase C (two
+// launches per iteration instead of three).  The learned form keeps phase A
+// separate (its features run between phases A and B).
+bool fused_depth_step(const KParams& P)
+{
+    return P.bkg_mode != RT3D_BKG_LOWPASS && P.depth_den != RT3D_DEPTH_LEARNED;
 }
 
 rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
 {
     const bool learned = c->h_rec.P.depth_den == RT3D_DEPTH_LEARNED;
+    const bool fused = fused_depth_step(c->h_rec.P);
     for (int it = 0; it < n_iter; ++it) {
-        {
+        if (it == 0 || !fused) {
             LaunchScope ls(c, s, kcA);
             launch_phase(c->h_rec.P.k, 0, it == 0 ? 1 : 0, B.total_tiles, s, c->d_rec, c->W);
         }
@@ -658,11 +670,11 @@ rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
         }
         {
             LaunchScope ls(c, s, kcB);
-            launch_phase(c->h_rec.P.k, 1, 0, B.total_tiles, s, c->d_rec, c->W);
+            launch_phase(c->h_rec.P.k, 1, fused && it > 0 ? 1 : 0, B.total_tiles, s, c->d_rec, c->W);
         }
         {
             LaunchScope ls(c, s, kcC);
-            launch_phase(c->h_rec.P.k, 2, 0, B.total_tiles, s, c->d_rec, c->W);
+            launch_phase(c->h_rec.P.k, 2, fused && it + 1 < n_iter ? 1 : 0, B.total_tiles, s, c->d_rec, c->W);
         }
     }
     RT3D_CUDA(cudaGetLastError());
@@ -709,7 +721,7 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
     const GraphKey key{B.total_pix, B.total_tiles, p->n_iter, p->warm_start != 0,
                        init_warps(K.peak_sep), c->profiling ? 1 : 0, init_smem(K, K.peak_sep),
                        B.tc_tiles, K.tc_stages, K.tc_nd, batch_has_int(B) ? 1 : 0,
-                       K.depth_den == RT3D_DEPTH_LEARNED ? 1 : 0};
+                       K.depth_den == RT3D_DEPTH_LEARNED ? 1 : 0, fused_depth_step(K) ? 1 : 0};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         // capture the launch sequence of this geometry once, on a private stream
@@ -1135,7 +1147,7 @@ rt3d_status rt3d_phase(rt3d_ctx_t* c, int phase, int first, const rt3d_frame* f,
         RT3D_CUDA(cudaMemcpyAsync(c->W.b_half, state->b, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
     {
         LaunchScope ls(c, s, phase == 0 ? kcA : (phase == 1 ? kcB : kcC));
-        launch_phase(K.k, phase, first, B.total_tiles, s, c->d_rec, c->W);
+        launch_phase(K.k, phase, phase == 0 ? first : 0, B.total_tiles, s, c->d_rec, c->W);
     }
     RT3D_CUDA(cudaGetLastError());
     for (int k = 0; k < Kp; ++k) {
@@ -1725,7 +1737,10 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     RT3D_CUDA(cudaFuncSetAttribute(init_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     init_fn<<<(B.total_pix + warps - 1) / warps, warps * 32, smem, s>>>(d_rec, W);
     for (int it = 0; it < p->n_iter; ++it) {
-        for (int ph = 0; ph < 3; ++ph) launch_phase(K.k, ph, it == 0 ? 1 : 0, B.total_tiles, s, d_rec, W);
+        const bool fused = fused_depth_step(K);
+        if (it == 0 || !fused) launch_phase(K.k, 0, it == 0 ? 1 : 0, B.total_tiles, s, d_rec, W);
+        launch_phase(K.k, 1, fused && it > 0 ? 1 : 0, B.total_tiles, s, d_rec, W);
+        launch_phase(K.k, 2, fused && it + 1 < p->n_iter ? 1 : 0, B.total_tiles, s, d_rec, W);
     }
     k_final<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W, p->n_iter > 0 ? 1 : 0);
     RT3D_CUDA(cudaGetLastError());
