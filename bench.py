@@ -320,7 +320,9 @@ def run_ours(args, world, rank, local):
             lat = [float("nan")]
 
         # ---------------- end to end through the host entry point
-        e2e = run_e2e(args, ctx, prm, dense, R) if args.e2e_steps > 0 else None
+        e2e_forms = run_e2e(args, ctx, prm, dense, R) if args.e2e_steps > 0 else None
+        e2e = e2e_forms["dense"] if e2e_forms else None
+        e2e_sparse = e2e_forms["sparse"] if e2e_forms else None
 
         # ---------------- parity of the benchmark frame against the oracle
         parity = None if args.no_parity else bench_parity(prm, seeds[0], outs[0])
@@ -358,6 +360,7 @@ def run_ours(args, world, rank, local):
                            "frame_p99": round(float(np.percentile(lat, 99)), 4),
                            "frame_samples": len(lat)},
             "e2e": e2e,
+            "e2e_sparse": e2e_sparse,
             "roofline": roofline,
             "init_roofline": {"bound": "hbm", "achieved": round(per_kernel["init"]["gbs"], 1),
                               "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -526,27 +529,48 @@ def run_learned_form(args, device) -> dict:
     return res
 
 
+def _pinned(shape, dtype):
+    import torch
+    return torch.zeros(shape, dtype=dtype).pin_memory().numpy()
+
+
 def run_e2e(args, ctx, prm, dense, R):
-    """The same metric through rt3d_reconstruct_host: every step copies each
-    frame's histogram from pinned host memory and its results back."""
+    """The same metric through rt3d_reconstruct_batch_host: every step copies
+    the step's frames from page-locked host memory, reconstructs them as one
+    batch and copies the results back (also page-locked).  Two input forms of
+    the same photons (bitwise-identical results): the dense uint16 histograms
+    the benchmark synthesises, and their sparse (offsets, entries) list, the
+    form a photon-counting sensor's time tags arrive in."""
     import torch
     nb = len(dense)
-    host = [d.view(torch.int16).cpu().pin_memory() for d in dense]
-    host_np = [h.numpy().view(np.uint16) for h in host]
-    outs = [dict(t=np.zeros((K, H, W), np.float32), r=np.zeros((K, H, W), np.float32),
-                 alive=np.zeros((K, H, W), np.uint8), b=np.zeros((H, W), np.float32),
-                 n_points=np.zeros(1, np.int32)) for _ in range(nb)]
-    R.reconstruct_host(ctx, prm, host_np[0], out=outs[0])          # warm-up
-    t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        for i in range(nb):
-            R.reconstruct_host(ctx, prm, host_np[i], out=outs[i])
-    dt = time.perf_counter() - t0
-    h2d = nb * H * W * T * 2
+    outs = [dict(t=_pinned((K, H, W), torch.float32), r=_pinned((K, H, W), torch.float32),
+                 alive=_pinned((K, H, W), torch.uint8), b=_pinned((H, W), torch.float32),
+                 n_points=_pinned((1,), torch.int32)) for _ in range(nb)]
     d2h = nb * (K * H * W * 9 + H * W * 4 + 4)
-    return {"value": round(nb * args.e2e_steps / dt, 2), "unit": UNIT,
-            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-            "path": "rt3d_reconstruct_host, dense uint16 histograms in pinned host memory"}
+    res = {}
+    host_dense = [dict(dense=d.view(torch.int16).cpu().pin_memory().numpy().view(np.uint16)) for d in dense]
+    host_csr = []
+    for d in dense:
+        off, ent = ctx.compact(d)
+        o = torch.from_numpy(off.cpu().numpy().astype(np.uint32).view(np.int32)).pin_memory().numpy().view(np.uint32)
+        e = torch.from_numpy(ent.cpu().numpy().astype(np.uint32).view(np.int32)).pin_memory().numpy().view(np.uint32)
+        host_csr.append(dict(csr=(o, e, (H, W, T))))
+    for form, frames in (("dense", host_dense), ("sparse", host_csr)):
+        R.reconstruct_batch_host(ctx, prm, frames, outs)          # warm-up (staging, graph)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            R.reconstruct_batch_host(ctx, prm, frames, outs)
+        dt = time.perf_counter() - t0
+        if form == "dense":
+            h2d = nb * H * W * T * 2
+            path = "rt3d_reconstruct_batch_host, dense uint16 histograms in page-locked host memory"
+        else:
+            h2d = sum(f["csr"][0].nbytes + f["csr"][1].nbytes for f in frames)
+            path = ("rt3d_reconstruct_batch_host, sparse (offsets, bin<<16|count entries) lists of the same "
+                    "photons in page-locked host memory")
+        res[form] = {"value": round(nb * args.e2e_steps / dt, 2), "unit": UNIT,
+                     "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": d2h, "path": path}
+    return res
 
 
 def bench_parity(prm, seed, out):

@@ -238,6 +238,19 @@ rt3d_status rt3d_reconstruct_batch(rt3d_ctx_t* ctx, int n, const rt3d_frame* f,
 rt3d_status rt3d_reconstruct_host(rt3d_ctx_t* ctx, const rt3d_frame* f, const rt3d_params* p,
                                   rt3d_result* out, void* stream);
 
+/* Batched end-to-end form: n frames in HOST buffers (f[i]: HOST pointers;
+ * dense and/or csr_off/csr_ent, optional gain), results into HOST buffers
+ * out[i].  One copy per input array into a context staging area (grown to the
+ * call's size on first use, freed by rt3d_destroy), one batched
+ * reconstruction (as rt3d_reconstruct_batch), one copy back per result array;
+ * with params.warm_start, out[i] is also the starting state.  Synchronous:
+ * returns after the results are on the host.  Page-locked host buffers give
+ * full link bandwidth.  Errors: RT3D_E_INVALID for a NULL argument, n < 1 or
+ * anything rt3d_reconstruct_batch rejects; RT3D_E_NOMEM if the staging cannot
+ * be allocated. */
+rt3d_status rt3d_reconstruct_batch_host(rt3d_ctx_t* ctx, int n, const rt3d_frame* f,
+                                        const rt3d_params* p, rt3d_result* out, void* stream);
+
 /* One fused phase of iteration k, for testing the loop kernels in isolation.
  * state holds t, r, alive, b (device, as rt3d_result); the frame's sparse list
  * (csr_off/csr_ent) is required.  phase:

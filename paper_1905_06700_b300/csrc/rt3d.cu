@@ -130,6 +130,9 @@ struct rt3d_ctx {
     float* s_b = nullptr;
     uint8_t* s_alive = nullptr;
     int32_t* s_np = nullptr;
+    // staging of rt3d_reconstruct_batch_host (grown on demand)
+    unsigned char* s_batch = nullptr;
+    size_t s_batch_cap = 0;
 };
 
 namespace {
@@ -892,7 +895,7 @@ void rt3d_destroy(rt3d_ctx_t* c)
     cudaSetDevice(c->cfg.device);
     void* ptrs[] = {c->W.seg, c->W.ent, c->d_count, c->W.t_half, c->W.r_half, c->W.b_half,
                     c->W.alive_b, c->d_status, c->d_tmp, c->d_rec, c->s_dense, c->s_off, c->s_ent,
-                    c->s_gain, c->s_t, c->s_r, c->s_b, c->s_alive, c->s_np, c->d_band,
+                    c->s_gain, c->s_t, c->s_r, c->s_b, c->s_alive, c->s_np, c->s_batch, c->d_band,
                     c->net_a0, c->net_a1, c->net_a2, c->net_y};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1105,6 +1108,100 @@ rt3d_status rt3d_reconstruct_host(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d
     RT3D_CUDA(cudaMemcpyAsync(out->b, c->s_b, sizeof(float) * npix, cudaMemcpyDeviceToHost, s));
     if (out->n_points)
         RT3D_CUDA(cudaMemcpyAsync(out->n_points, c->s_np, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    RT3D_CUDA(cudaStreamSynchronize(s));
+    return RT3D_OK;
+}
+
+rt3d_status rt3d_reconstruct_batch_host(rt3d_ctx_t* c, int n, const rt3d_frame* f, const rt3d_params* p,
+                                        rt3d_result* out, void* stream)
+{
+    if (!c || !f || !p || !out || n < 1) return RT3D_E_INVALID;
+    rt3d_status st = check_common(c, n, f, p, out);
+    if (st != RT3D_OK) return st;
+    RT3D_CUDA(cudaSetDevice(c->cfg.device));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int Kp = p->k_max;
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    // one staging area: every frame's inputs, then every frame's results
+    struct Span { size_t dense, off, ent, gain, t, r, a, b, np; long long npix, nent; };
+    std::vector<Span> sp(n);
+    size_t bytes = 0;
+    for (int i = 0; i < n; ++i) {
+        Span& x = sp[i];
+        x.npix = (long long)f[i].h * f[i].w;
+        x.nent = f[i].csr_off ? (long long)f[i].csr_off[x.npix] : 0;
+        x.dense = bytes;
+        if (f[i].dense) bytes += al(sizeof(uint16_t) * x.npix * f[i].t);
+        x.off = bytes;
+        if (f[i].csr_off) bytes += al(sizeof(uint32_t) * (x.npix + 1));
+        x.ent = bytes;
+        if (f[i].csr_off) bytes += al(sizeof(uint32_t) * (x.nent > 0 ? x.nent : 1));
+        x.gain = bytes;
+        if (f[i].gain) bytes += al(sizeof(float) * x.npix);
+        x.t = bytes;
+        bytes += al(sizeof(float) * Kp * x.npix);
+        x.r = bytes;
+        bytes += al(sizeof(float) * Kp * x.npix);
+        x.a = bytes;
+        bytes += al((size_t)Kp * x.npix);
+        x.b = bytes;
+        bytes += al(sizeof(float) * x.npix);
+        x.np = bytes;
+        bytes += al(sizeof(int32_t));
+    }
+    if (bytes > c->s_batch_cap) {
+        // the previous staging may still be read by work queued on `s`
+        RT3D_CUDA(cudaStreamSynchronize(s));
+        if (c->s_batch) cudaFree(c->s_batch);
+        c->s_batch = nullptr;
+        c->s_batch_cap = 0;
+        RT3D_CUDA(cudaMalloc((void**)&c->s_batch, bytes));
+        c->s_batch_cap = bytes;
+    }
+    unsigned char* base = c->s_batch;
+    std::vector<rt3d_frame> df(f, f + n);
+    std::vector<rt3d_result> dr(n);
+    for (int i = 0; i < n; ++i) {
+        const Span& x = sp[i];
+        if (f[i].dense) {
+            df[i].dense = reinterpret_cast<const uint16_t*>(base + x.dense);
+            RT3D_CUDA(cudaMemcpyAsync(base + x.dense, f[i].dense, sizeof(uint16_t) * x.npix * f[i].t,
+                                      cudaMemcpyHostToDevice, s));
+        }
+        if (f[i].csr_off) {
+            df[i].csr_off = reinterpret_cast<const uint32_t*>(base + x.off);
+            df[i].csr_ent = reinterpret_cast<const uint32_t*>(base + x.ent);
+            RT3D_CUDA(cudaMemcpyAsync(base + x.off, f[i].csr_off, sizeof(uint32_t) * (x.npix + 1),
+                                      cudaMemcpyHostToDevice, s));
+            if (x.nent > 0)
+                RT3D_CUDA(cudaMemcpyAsync(base + x.ent, f[i].csr_ent, sizeof(uint32_t) * x.nent,
+                                          cudaMemcpyHostToDevice, s));
+        }
+        if (f[i].gain) {
+            df[i].gain = reinterpret_cast<const float*>(base + x.gain);
+            RT3D_CUDA(cudaMemcpyAsync(base + x.gain, f[i].gain, sizeof(float) * x.npix, cudaMemcpyHostToDevice, s));
+        }
+        dr[i] = rt3d_result{reinterpret_cast<float*>(base + x.t), reinterpret_cast<float*>(base + x.r),
+                            base + x.a, reinterpret_cast<float*>(base + x.b),
+                            reinterpret_cast<int32_t*>(base + x.np)};
+        if (p->warm_start) {
+            RT3D_CUDA(cudaMemcpyAsync(dr[i].t, out[i].t, sizeof(float) * Kp * x.npix, cudaMemcpyHostToDevice, s));
+            RT3D_CUDA(cudaMemcpyAsync(dr[i].r, out[i].r, sizeof(float) * Kp * x.npix, cudaMemcpyHostToDevice, s));
+            RT3D_CUDA(cudaMemcpyAsync(dr[i].alive, out[i].alive, (size_t)Kp * x.npix, cudaMemcpyHostToDevice, s));
+            RT3D_CUDA(cudaMemcpyAsync(dr[i].b, out[i].b, sizeof(float) * x.npix, cudaMemcpyHostToDevice, s));
+        }
+    }
+    st = run_batch(c, n, df.data(), p, dr.data(), s);
+    if (st != RT3D_OK) return st;
+    for (int i = 0; i < n; ++i) {
+        const long long npix = sp[i].npix;
+        RT3D_CUDA(cudaMemcpyAsync(out[i].t, dr[i].t, sizeof(float) * Kp * npix, cudaMemcpyDeviceToHost, s));
+        RT3D_CUDA(cudaMemcpyAsync(out[i].r, dr[i].r, sizeof(float) * Kp * npix, cudaMemcpyDeviceToHost, s));
+        RT3D_CUDA(cudaMemcpyAsync(out[i].alive, dr[i].alive, (size_t)Kp * npix, cudaMemcpyDeviceToHost, s));
+        RT3D_CUDA(cudaMemcpyAsync(out[i].b, dr[i].b, sizeof(float) * npix, cudaMemcpyDeviceToHost, s));
+        if (out[i].n_points)
+            RT3D_CUDA(cudaMemcpyAsync(out[i].n_points, dr[i].n_points, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    }
     RT3D_CUDA(cudaStreamSynchronize(s));
     return RT3D_OK;
 }

@@ -126,6 +126,8 @@ def lib():
                                        C.POINTER(Result), _P]),
         "rt3d_reconstruct_batch": (C.c_int, [_P, C.c_int, C.POINTER(Frame), C.POINTER(Params),
                                              C.POINTER(Result), _P]),
+        "rt3d_reconstruct_batch_host": (C.c_int, [_P, C.c_int, C.POINTER(Frame), C.POINTER(Params),
+                                                   C.POINTER(Result), _P]),
         "rt3d_reconstruct_host": (C.c_int, [_P, C.POINTER(Frame), C.POINTER(Params),
                                             C.POINTER(Result), _P]),
         "rt3d_phase": (C.c_int, [_P, C.c_int, C.c_int, C.POINTER(Frame), C.POINTER(Params),
@@ -400,6 +402,42 @@ def reconstruct_host(ctx: Context, params, dense: np.ndarray, gain: Optional[np.
     check(lib().rt3d_reconstruct_host(ctx.handle, C.byref(fr), C.byref(p), C.byref(rs),
                                       _stream(stream)), "rt3d_reconstruct_host")
     return out
+
+
+def reconstruct_batch_host(ctx: Context, params, frames: Sequence[dict], outs: Optional[Sequence[dict]] = None,
+                           stream=None) -> list:
+    """rt3d_reconstruct_batch_host: n frames of HOST numpy buffers in, HOST
+    results out, one batched reconstruction.  Each frame dict holds `dense`
+    ([h][w][t] uint16) and/or `csr` ((offsets, entries, (h, w, t))), and
+    optionally `gain`; page-locked arrays give full link bandwidth."""
+    p = params_from(params)
+    k = p.k_max
+    keep, frs, rss = [], [], []
+    outs = list(outs) if outs is not None else [None] * len(frames)
+    for i, f in enumerate(frames):
+        dense = f.get("dense")
+        csr = f.get("csr")
+        h, w, t = dense.shape if dense is not None else csr[2]
+        dense = None if dense is None else np.ascontiguousarray(dense, np.uint16)
+        gain = None if f.get("gain") is None else np.ascontiguousarray(f["gain"], np.float32)
+        off = ent = None
+        if csr is not None:
+            off = np.ascontiguousarray(csr[0], np.uint32)
+            ent = np.ascontiguousarray(csr[1], np.uint32)
+        keep += [dense, gain, off, ent]
+        frs.append(Frame(h, w, t, _host_ptr(dense), _host_ptr(off), _host_ptr(ent), _host_ptr(gain)))
+        if outs[i] is None:
+            outs[i] = dict(t=np.zeros((k, h, w), np.float32), r=np.zeros((k, h, w), np.float32),
+                           alive=np.zeros((k, h, w), np.uint8), b=np.zeros((h, w), np.float32),
+                           n_points=np.zeros(1, np.int32))
+        o = outs[i]
+        rss.append(Result(_host_ptr(o["t"]), _host_ptr(o["r"]), _host_ptr(o["alive"]), _host_ptr(o["b"]),
+                          _host_ptr(o.get("n_points"))))
+    fa = (Frame * len(frs))(*frs)
+    ra = (Result * len(rss))(*rss)
+    check(lib().rt3d_reconstruct_batch_host(ctx.handle, len(frs), fa, C.byref(p), ra, _stream(stream)),
+          "rt3d_reconstruct_batch_host")
+    return outs
 
 
 def rt3d_reconstruct_noalloc(irf_samples, irf_origin: int, frame: Frame, params, result: Result,

@@ -267,6 +267,29 @@ def test_host_entry_point_equals_device_path(orc):
     assert int(b["n_points"][0]) == a["n_points"]
 
 
+def test_batched_host_entry_point_equals_device_path(orc):
+    """Ragged frames in host buffers (dense, sparse, and with a gain map) through
+    rt3d_reconstruct_batch_host: bit for bit the device-resident batch."""
+    from paper_1905_06700_b300 import rt3d as R
+    torch = torch_mod()
+    scs = [scenes.small_random(13, 29, 300, n_comp=2, seed=4), scenes.small_random(17, 11, 300, n_comp=1, seed=5),
+           scenes.small_random(9, 21, 300, n_comp=2, seed=6)]
+    zs = [orc.synthesize(scenes.sampling_tables(sc)) for sc in scs]
+    prm = workload_params(scs[0])
+    ctx = make_ctx(scs[0], k=prm["k_max"], max_h=17, max_w=29, max_batch=3)
+    gain = np.random.default_rng(7).uniform(0.5, 1.5, (9, 21)).astype(np.float32)
+    dev = ctx.reconstruct_batch(prm, [dict(dense=upload_u16(zs[0])), dict(dense=upload_u16(zs[1])),
+                                      dict(dense=upload_u16(zs[2]), gain=torch.from_numpy(gain).cuda())])
+    off, ent = ctx.compact(upload_u16(zs[1]))
+    csr = (off.cpu().numpy().astype(np.uint32), ent.cpu().numpy().astype(np.uint32), zs[1].shape)
+    host = R.reconstruct_batch_host(ctx, prm, [dict(dense=zs[0]), dict(csr=csr), dict(dense=zs[2], gain=gain)])
+    for i in range(3):
+        a = np_of(dev[i])
+        for k in ("t", "r", "alive", "b"):
+            assert np.array_equal(a[k], host[i][k]), (i, k)
+        assert int(host[i]["n_points"][0]) == a["n_points"]
+
+
 def test_capacity_overflow_is_reported_not_faulted(orc):
     from paper_1905_06700_b300 import rt3d as R
     sc = scenes.small_random(16, 16, 256, n_comp=2, seed=3)
