@@ -199,25 +199,39 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
     if (kDumpY)
         for (int i = lane; i < T; i += 32) W.y_out[(long long)lp * T + i] = 0;
     uint32_t c_lo = (active || kDumpY) ? 0u : nnz;
+    // up to 32 entries: one lane per entry, the breaks between clusters in one vote
+    const bool small = nnz <= 32u;
+    uint32_t v_small = 0u;
+    unsigned brk_small = 0u;
+    if (small) {
+        v_small = (uint32_t)lane < nnz ? ent[lane] : 0u;
+        const uint32_t nxt = __shfl_down_sync(0xffffffffu, v_small, 1);
+        brk_small = __ballot_sync(0xffffffffu, (uint32_t)lane + 1u < nnz &&
+                                                   (int)(nxt >> 16) - (int)(v_small >> 16) > gap);
+    }
     while (c_lo < nnz) {
         // the cluster [c_lo, c_hi): consecutive entries at most `gap` bins apart
         uint32_t c_hi = c_lo;
         unsigned long long cl_tot = 0;
-        while (true) {
-            const uint32_t e = c_hi + lane;
-            const bool in = e < nnz;
-            const uint32_t v = in ? ent[e] : 0u;
-            const bool brk = in && e + 1 < nnz && (int)(ent[e + 1] >> 16) - (int)(v >> 16) > gap;
-            const unsigned mb = __ballot_sync(0xffffffffu, brk);
-            const unsigned mi = __ballot_sync(0xffffffffu, in);
-            // entries up to and including the first break belong to the cluster
-            const int take = mb ? (__ffs(mb)) : __popc(mi);
-            uint32_t cnt = (lane < take) ? (v & 0xffffu) : 0u;
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-            cl_tot += cnt;
-            c_hi += take;
-            if (mb || take < 32) break;
+        if (small) {
+            const unsigned after = brk_small >> c_lo;   // breaks at or after entry c_lo
+            c_hi = after ? c_lo + (uint32_t)__ffs(after) : nnz;
+            const bool mine = (uint32_t)lane >= c_lo && (uint32_t)lane < c_hi;
+            cl_tot = __reduce_add_sync(0xffffffffu, mine ? (v_small & 0xffffu) : 0u);
+        } else {
+            while (true) {
+                const uint32_t e = c_hi + lane;
+                const bool in = e < nnz;
+                const uint32_t v = in ? ent[e] : 0u;
+                const bool brk = in && e + 1 < nnz && (int)(ent[e + 1] >> 16) - (int)(v >> 16) > gap;
+                const unsigned mb = __ballot_sync(0xffffffffu, brk);
+                const unsigned mi = __ballot_sync(0xffffffffu, in);
+                // entries up to and including the first break belong to the cluster
+                const int take = mb ? (__ffs(mb)) : __popc(mi);
+                cl_tot += __reduce_add_sync(0xffffffffu, (lane < take) ? (v & 0xffffu) : 0u);
+                c_hi += take;
+                if (mb || take < 32) break;
+            }
         }
         const uint32_t e_first = c_lo, e_last = c_hi - 1;
         c_lo = c_hi;
@@ -225,18 +239,20 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
         const int lo = max(0, (int)(ent[e_first] >> 16) + O - L + 1);
         const int hi = min(T - 1, (int)(ent[e_last] >> 16) + O);
         uint32_t e_lo = e_first;
+        const bool one_chunk = hi - lo < kInitChunk;
         for (int cbase = lo; cbase <= hi; cbase += kInitChunk) {
-            // cluster entries reaching [cbase - sep, cbase + chunk + sep)
+            // cluster entries reaching [cbase - sep, cbase + chunk + sep): all of
+            // them when the cluster's positions fit one chunk
             const int lo_b = cbase - sep - O;
             const int hi_b = cbase + kInitChunk - 1 + sep - O + L - 1;
-            while (e_lo <= e_last) {
+            while (!one_chunk && e_lo <= e_last) {
                 const uint32_t e = e_lo + lane;
                 const bool below = e <= e_last && (int)(ent[e] >> 16) < lo_b;
                 const unsigned m = __ballot_sync(0xffffffffu, below);
                 e_lo += __popc(m);
                 if (m != 0xffffffffu) break;
             }
-            uint32_t e_hi = e_lo;
+            uint32_t e_hi = one_chunk ? e_last + 1 : e_lo;
             while (e_hi <= e_last) {
                 const uint32_t e = e_hi + lane;
                 const bool in = e <= e_last && (int)(ent[e] >> 16) <= hi_b;
@@ -285,15 +301,15 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
                     for (int q = 2 + lane; q <= sep; q += 32) ok = ok && Y[cyi - q] < y && Y[cyi + q] <= y;
                     if (!__all_sync(0xffffffffu, ok)) continue;
                     // photons in the IRF window [tau - origin, tau - origin + L): lanes over entries
-                    int wcount = 0;
+                    // (photon counts of an active pixel are below 2^31: 32-bit sums are exact)
+                    uint32_t wcount = 0;
                     for (uint32_t e = e_first + lane; e <= e_last; e += 32) {
                         const uint32_t v = ent[e];
                         const int bin = (int)(v >> 16);
-                        if (bin >= tau - O && bin <= tau - O + L - 1) wcount += (int)(v & 0xffffu);
+                        if (bin >= tau - O && bin <= tau - O + L - 1) wcount += v & 0xffffu;
                     }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) wcount += __shfl_xor_sync(0xffffffffu, wcount, o);
-                    if (wcount < min_photons) continue;
+                    wcount = __reduce_add_sync(0xffffffffu, wcount);
+                    if ((long long)wcount < (long long)min_photons) continue;
                     // the warp's list of the K best (y descending; candidates arrive in
                     // bin order, so equal y keeps the earlier bin first)
                     int pos = nb;
@@ -329,8 +345,9 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
             if (c < nsel && sel[c] < sel[a]) { const int tmp = sel[a]; sel[a] = sel[c]; sel[c] = tmp; }
 
     // ---- 4. initial intensities and background ------------------------------
-    unsigned long long inside = 0;
-    unsigned long long wsum[kMaxK] = {0, 0, 0, 0};
+    // window sums of an active pixel are below 2^31 (an inactive one keeps none)
+    uint32_t inside = 0;
+    uint32_t wsum[kMaxK] = {0, 0, 0, 0};
     for (uint32_t e = lane; e < nnz; e += 32) {
         const uint32_t v = ent[e];
         const int bin = (int)(v >> 16);
@@ -344,12 +361,9 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
             }
         if (any) inside += z;
     }
+    inside = __reduce_add_sync(0xffffffffu, inside);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        inside += __shfl_xor_sync(0xffffffffu, inside, o);
-#pragma unroll
-        for (int k = 0; k < kMaxK; ++k) wsum[k] += __shfl_xor_sync(0xffffffffu, wsum[k], o);
-    }
+    for (int k = 0; k < kMaxK; ++k) wsum[k] = __reduce_add_sync(0xffffffffu, wsum[k]);
     // bins covered by the union of the kept windows (windows sorted by start)
     int covered = 0, cur_lo = 0, cur_hi = -1;
     int winlen[kMaxK];
