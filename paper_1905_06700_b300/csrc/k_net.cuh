@@ -459,7 +459,18 @@ __device__ __forceinline__ uint64_t tc_desc_plain(uint32_t saddr, uint32_t lbo, 
            ((uint64_t)1 << 46);
 }
 
-template <int CI, int CO, int MODE>
+// Hidden activations for the pipelined layers are stored chunk-planar per
+// frame: element (row i, channel 8c + e, column j) at
+//   (i * C/8 + c) * w + j) * 8 + e   from the frame's first element,
+// so a halo box of one channel chunk is 130 contiguous 16-byte rows.
+template <int CO>
+__device__ __forceinline__ uint4* planar_chunk(uint16_t* out, const FrameDesc& F, int gi, int gj, int c)
+{
+    return reinterpret_cast<uint4*>(out + (long long)F.pix_base * CO +
+                                    (((long long)gi * (CO / 8) + c) * F.w + gj) * 8);
+}
+
+template <int CI, int CO, int MODE, bool kPlanarOut = false>
 __global__ void __launch_bounds__(128)
 k_net_conv_tc(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, const uint16_t* __restrict__ bimg,
               const float* __restrict__ bias, void* __restrict__ out, int* __restrict__ status)
@@ -610,9 +621,17 @@ k_net_conv_tc(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, con
                 for (int c = 0; c < CO / 2; ++c)
                     pk[c] = (uint32_t)f_to_bf16_bits(fmaxf(acc[2 * c] + bias[2 * c], 0.0f)) |
                             ((uint32_t)f_to_bf16_bits(fmaxf(acc[2 * c + 1] + bias[2 * c + 1], 0.0f)) << 16);
-                uint4* o = reinterpret_cast<uint4*>(static_cast<uint16_t*>(out) + px * CO);
+                if constexpr (kPlanarOut) {
 #pragma unroll
-                for (int c = 0; c < CO / 8; ++c) o[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+                    for (int c = 0; c < CO / 8; ++c)
+                        *planar_chunk<CO>(static_cast<uint16_t*>(out), F, gi, gj, c) =
+                            make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+                } else {
+                    uint4* o = reinterpret_cast<uint4*>(static_cast<uint16_t*>(out) + px * CO);
+#pragma unroll
+                    for (int c = 0; c < CO / 8; ++c)
+                        o[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+                }
             } else {
                 float* o = static_cast<float*>(out) + px * CO;
 #pragma unroll
@@ -628,6 +647,314 @@ k_net_conv_tc(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, con
     if (warp == 0) {
         __syncwarp();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TM_COLS) : "memory");
+    }
+}
+
+// ======================================================================
+// The same convolution as k_net_conv_tc for chunk-planar inputs (CI a
+// multiple of 8, see planar_chunk), pipelined.  A work item is a block of
+// kPipeRows output rows of one 128-pixel column strip; consecutive strips of
+// an item share two of their three input rows, so each input row is loaded
+// once per item into a ring of kPipeRing row buffers ([chunk][pixel][8], 130
+// pixels with the one-pixel margins) instead of three times.  Persistent CTAs
+// (one per SM) walk the items with
+//   warp 4      producer: each input row as 16-byte asynchronous copies
+//               (CI/8 contiguous runs of 130 x 16 bytes spread over the
+//               lanes; zero-size copies fill margin columns outside the
+//               frame with zeros), completion counted on the row's barrier;
+//   warp 5      MMA issuer (one thread), owns the tensor memory: per output
+//               row the 9 x CI/16 MMAs into one of two accumulators, then
+//               releases the input row it used for the last time;
+//   warps 0..3  epilogue, one thread per pixel (its tensor-memory lane).
+// The copies write through the generic proxy, so the MMA thread orders them
+// before its MMAs with a proxy fence after its wait.  Rows outside the frame
+// are a resident row of zeros.  The operand of tap
+// (ky, kx) starts kx pixels into the ring slot of input row ky, with
+// K-adjacent core matrices one chunk plane (130 x 16 bytes) apart.  The MMAs
+// run in the order k_net_conv_tc issues them, so both kernels give the same
+// sums.  Hidden outputs are written chunk-planar.  Every wait is bounded; on
+// expiry the CTA raises the timeout status and the roles drain.
+// ======================================================================
+
+constexpr int kPipeThreads = 6 * 32;
+constexpr int kPipeRows = 8;          // output rows per work item
+constexpr int kPipeRing = 6;          // input rows held in shared memory
+
+// 16-byte asynchronous copy; src_bytes = 0 writes 16 zero bytes
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"((unsigned long long)src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+
+// The barrier's pending count drops by one when this thread's earlier
+// asynchronous copies have completed.
+__device__ __forceinline__ void cp_async_arrive(uint32_t bar)
+{
+    asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// one input row in shared memory: CI/8 chunk planes of 130 x 16 bytes
+__host__ __device__ constexpr int net_pipe_row_bytes(int ci) { return (net_pad16(ci) / 8 * kStripHaloW * 16 + 127) / 128 * 128; }
+
+__host__ __device__ constexpr int net_pipe_smem(int ci, int co)
+{
+    return (kPipeRing + 1) * net_pipe_row_bytes(ci) + net_tc_b_bytes(ci, co);
+}
+
+// Wait for a phase regardless of the abort flag (bounded): used at teardown
+// for copies and MMAs still in flight.
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait_sleep(bar, parity))
+        if (global_ns() - t0 > kTcWaitNs) return false;
+    return true;
+}
+
+// Work items of the batch: per frame, ceil(w / 128) column strips x
+// ceil(h / kPipeRows) row blocks.  Item -> frame, first column, rows [g0, g1).
+__device__ __forceinline__ int net_pipe_items(const Batch& B)
+{
+    int n = 0;
+    for (int i = 0; i < B.n; ++i)
+        n += ((B.f[i].w + kStrip - 1) / kStrip) * ((B.f[i].h + kPipeRows - 1) / kPipeRows);
+    return n;
+}
+
+__device__ __forceinline__ void net_pipe_item(const Batch& B, int item, int& fi, int& j0, int& g0, int& g1)
+{
+    int base = 0;
+    fi = B.n - 1;
+    for (int i = 0; i < B.n; ++i) {
+        const int spr = (B.f[i].w + kStrip - 1) / kStrip;
+        const int cnt = spr * ((B.f[i].h + kPipeRows - 1) / kPipeRows);
+        if (item < base + cnt) {
+            fi = i;
+            break;
+        }
+        base += cnt;
+    }
+    const FrameDesc& F = B.f[fi];
+    const int spr = (F.w + kStrip - 1) / kStrip, local = item - base;
+    j0 = (local % spr) * kStrip;
+    g0 = (local / spr) * kPipeRows;
+    g1 = min(g0 + kPipeRows, F.h);
+}
+
+template <int CI, int CO, int MODE>
+__global__ void __launch_bounds__(kPipeThreads, 1)
+k_net_conv_pipe(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, const uint16_t* __restrict__ bimg,
+                const float* __restrict__ bias, void* __restrict__ out, int* __restrict__ status)
+{
+    static_assert(CI % 8 == 0, "16-byte input rows");
+    constexpr int CIp = net_pad16(CI), COp = net_pad16(CO), KS = CIp / 16, NC = CIp / 8;
+    constexpr int ROW = net_pipe_row_bytes(CI), B_BYTES = net_tc_b_bytes(CI, CO);
+    constexpr int R = kPipeRing;
+    constexpr int TM_COLS = COp <= 32 ? 32 : 64;            // one accumulator
+    constexpr uint32_t kPlane = kStripHaloW * 16;            // one chunk plane of one row
+    const Batch& B = *Bp;
+    extern __shared__ __align__(1024) unsigned char net_pipe_smem_buf[];
+    __shared__ uint32_t tslot;
+    __shared__ __align__(8) uint64_t bars[2 * R + 4];
+    __shared__ int s_abort;
+    __shared__ float s_bias[COp];
+    unsigned char* srow = net_pipe_smem_buf;                 // ring of R input rows
+    unsigned char* zrow = net_pipe_smem_buf + R * ROW;       // zeros: rows outside the frame
+    unsigned char* sb = zrow + ROW;                          // weights
+    const uint32_t row_addr = smem_u32(srow), zrow_addr = smem_u32(zrow), b_addr = smem_u32(sb);
+    const uint32_t bar_full = smem_u32(&bars[0]), bar_empty = smem_u32(&bars[R]);
+    const uint32_t bar_accf = smem_u32(&bars[2 * R]), bar_acce = smem_u32(&bars[2 * R + 2]);
+    volatile int* abort_flag = &s_abort;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = threadIdx.x; i < B_BYTES / 16; i += blockDim.x)
+        reinterpret_cast<uint4*>(sb)[i] = reinterpret_cast<const uint4*>(bimg)[i];
+    for (int i = threadIdx.x; i < ROW / 16; i += blockDim.x) reinterpret_cast<uint4*>(zrow)[i] = make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < COp; i += blockDim.x) s_bias[i] = i < CO ? bias[i] : 0.0f;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < R; ++i) {
+            mbar_init(bar_full + 8 * i, 32);
+            mbar_init(bar_empty + 8 * i, 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(bar_accf + 8 * i, 1);
+            mbar_init(bar_acce + 8 * i, 4);
+        }
+        s_abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 5) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                     "r"(2 * TM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    // weights and zeros were written by the generic proxy and are read by the MMAs
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tslot;
+    constexpr uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(COp >> 3) << 17) |
+                               ((uint32_t)(128 >> 4) << 24);
+    const int n_items = net_pipe_items(B);
+
+    if (warp == 4) {
+        // ------------------------------------------------ producer (whole warp)
+        uint32_t q = 0;                                      // rows loaded: ring position
+        bool stop = false;
+        for (int item = blockIdx.x; item < n_items && !stop; item += gridDim.x) {
+            int fi, j0, g0, g1;
+            net_pipe_item(B, item, fi, j0, g0, g1);
+            const FrameDesc& F = B.f[fi];
+            // in-frame columns [c_lo, c_hi) of the row's j0 - 1 .. j0 + 128
+            const int c_lo = max(j0 - 1, 0), c_hi = min(j0 + kStripHaloW - 1, F.w);
+            const int p_lo = c_lo - (j0 - 1), npx = c_hi - c_lo;
+            const uint16_t* fbase = in + (long long)F.pix_base * CIp;
+            for (int r = max(g0 - 1, 0); r <= min(g1, F.h - 1); ++r, ++q) {
+                const uint32_t slot = q % R;
+                if (!__all_sync(0xffffffffu, mbar_wait(bar_empty + 8 * slot, ((q / R) & 1u) ^ 1u, abort_flag))) {
+                    stop = true;
+                    break;
+                }
+                // (chunk, pixel slot) pairs spread over the lanes; slots outside
+                // the frame's columns are filled with zeros
+                const uint32_t dst0 = row_addr + slot * ROW;
+                for (int idx = lane; idx < NC * kStripHaloW; idx += 32) {
+                    const int c = idx / kStripHaloW, p = idx - c * kStripHaloW;
+                    const bool in_f = p >= p_lo && p < p_lo + npx;
+                    const uint16_t* src = fbase + (((long long)r * NC + c) * F.w + (in_f ? c_lo + p - p_lo : 0)) * 8;
+                    cp_async16(dst0 + (uint32_t)(c * kPlane + p * 16), src, in_f ? 16u : 0u);
+                }
+                cp_async_arrive(bar_full + 8 * slot);
+            }
+        }
+        // every copy has landed before the CTA leaves (matters after an abort)
+        if (lane == 0)
+            for (uint32_t x = q > (uint32_t)R ? q - R : 0u; x < q; ++x) mbar_drain(bar_full + 8 * (x % R), (x / R) & 1u);
+    } else if (warp == 5) {
+        // ------------------------------------------------ MMA issuer
+        if (lane == 0) {
+            uint32_t q = 0, k = 0;
+            bool stop = false;
+            for (int item = blockIdx.x; item < n_items && !stop; item += gridDim.x) {
+                int fi, j0, g0, g1;
+                net_pipe_item(B, item, fi, j0, g0, g1);
+                const int H = B.f[fi].h;
+                const int r_first = max(g0 - 1, 0), r_last = min(g1, H - 1);
+                for (int g = g0; g < g1; ++g, ++k) {
+                    const uint32_t a = k & 1u;
+                    uint32_t rows3[3];
+#pragma unroll
+                    for (int ky = 0; ky < 3; ++ky) {
+                        const int r = g - 1 + ky;
+                        rows3[ky] = zrow_addr;
+                        if (r < 0 || r >= H) continue;
+                        const uint32_t pos = q + (uint32_t)(r - r_first);
+                        if (!mbar_wait(bar_full + 8 * (pos % R), (pos / R) & 1u, abort_flag)) stop = true;
+                        rows3[ky] = row_addr + (pos % R) * ROW;
+                    }
+                    if (stop || !mbar_wait(bar_acce + 8 * a, ((k >> 1) & 1u) ^ 1u, abort_flag)) {
+                        stop = true;
+                        break;
+                    }
+                    // the rows were written by generic-proxy copies
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    tc_fence_after();
+                    uint32_t acc = 0;
+#pragma unroll
+                    for (int t = 0; t < 9; ++t) {
+                        const int ky = t / 3, kx = t % 3;
+#pragma unroll
+                        for (int s2 = 0; s2 < KS; ++s2) {
+                            const uint64_t da = tc_desc_plain(rows3[ky] + (uint32_t)(2 * s2) * kPlane + (uint32_t)kx * 16,
+                                                              kPlane, 128);
+                            const uint64_t db = tc_desc_plain(b_addr + (uint32_t)((t * KS + s2) * 2 * COp * 16),
+                                                              (uint32_t)(COp * 16), 128);
+                            tc_mma(tmem + a * TM_COLS, da, db, idesc, acc);
+                            acc = 1;
+                        }
+                    }
+                    tc_commit(bar_accf + 8 * a);
+                    // input row g - 1 is not read again
+                    if (g - 1 >= 0) tc_commit(bar_empty + 8 * ((q + (uint32_t)(g - 1 - r_first)) % R));
+                }
+                if (stop) break;
+                // nor are the item's last two input rows
+                for (int r = g1 - 1; r <= g1; ++r)
+                    if (r >= r_first && r <= r_last) tc_commit(bar_empty + 8 * ((q + (uint32_t)(r - r_first)) % R));
+                q += (uint32_t)(r_last - r_first + 1);
+            }
+            // every MMA has finished before the tensor memory is freed (matters after an abort)
+            if (k > 0) mbar_drain(bar_accf + 8 * ((k - 1) & 1u), ((k - 1) >> 1) & 1u);
+        }
+    } else {
+        // ------------------------------------------------ epilogue: thread = pixel
+        const int m = warp * 32 + lane;
+        uint32_t k = 0;
+        bool stop = false;
+        for (int item = blockIdx.x; item < n_items && !stop; item += gridDim.x) {
+            int fi, j0, g0, g1;
+            net_pipe_item(B, item, fi, j0, g0, g1);
+            const FrameDesc& F = B.f[fi];
+            for (int gi = g0; gi < g1; ++gi, ++k) {
+                const uint32_t a = k & 1u;
+                if (!__all_sync(0xffffffffu, mbar_wait(bar_accf + 8 * a, (k >> 1) & 1u, abort_flag))) {
+                    stop = true;
+                    break;
+                }
+                tc_fence_after();
+                float acc[COp];
+#pragma unroll
+                for (int c0 = 0; c0 < COp; c0 += 16) {
+                    uint32_t v[16];
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, "
+                        "%12, %13, %14, %15}, [%16];"
+                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                          "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]),
+                          "=r"(v[14]), "=r"(v[15])
+                        : "r"(tmem + ((uint32_t)(warp * 32) << 16) + a * TM_COLS + (uint32_t)c0));
+#pragma unroll
+                    for (int q2 = 0; q2 < 16; ++q2) acc[c0 + q2] = __uint_as_float(v[q2]);
+                }
+                tc_wait_ld();
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_acce + 8 * a);
+                const int gj = j0 + m;
+                if (gj < F.w) {
+                    if (MODE == kConvHidden) {
+                        uint32_t pk[CO / 2];
+#pragma unroll
+                        for (int c = 0; c < CO / 2; ++c)
+                            pk[c] = (uint32_t)f_to_bf16_bits(fmaxf(acc[2 * c] + s_bias[2 * c], 0.0f)) |
+                                    ((uint32_t)f_to_bf16_bits(fmaxf(acc[2 * c + 1] + s_bias[2 * c + 1], 0.0f)) << 16);
+#pragma unroll
+                        for (int c = 0; c < CO / 8; ++c)
+                            *planar_chunk<CO>(static_cast<uint16_t*>(out), F, gi, gj, c) =
+                                make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+                    } else {
+                        float* o = static_cast<float*>(out) + ((long long)F.pix_base + gi * F.w + gj) * CO;
+#pragma unroll
+                        for (int c = 0; c < CO; ++c) o[c] = acc[c] + s_bias[c];
+                    }
+                }
+            }
+        }
+    }
+
+    // ---- teardown: every role has left its loop (all waits are bounded)
+    if (*abort_flag && threadIdx.x == 0 && status) atomicOr(status, kStatusTimeout);
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 5) {
+        __syncwarp();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TM_COLS)
+                     : "memory");
     }
 }
 

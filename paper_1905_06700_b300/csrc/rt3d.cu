@@ -512,8 +512,9 @@ size_t init_smem(const KParams& K, int sep)
 // it may be rewritten by the next call at once.
 rt3d_status upload_record(rt3d_ctx* c, cudaStream_t s)
 {
-    const size_t bytes = c->h_rec.B.tc_tiles > 0 ? offsetof(CallRecord, maps) + sizeof(CUtensorMap) * c->h_rec.B.n
-                                                 : offsetof(CallRecord, maps);
+    size_t bytes = c->h_rec.B.tc_tiles > 0 ? offsetof(CallRecord, maps) + sizeof(CUtensorMap) * c->h_rec.B.n
+                                           : offsetof(CallRecord, maps);
+
     RT3D_CUDA(cudaMemcpyAsync(c->d_rec, &c->h_rec, bytes, cudaMemcpyHostToDevice, s));
     // band operands of the tensor-core filter, re-uploaded only when they change
     if (c->h_rec.P.tc_mode && c->h_rec.B.tc_tiles > 0) {
@@ -582,12 +583,12 @@ rt3d_status launch_conv(rt3d_ctx* c, int tiles, const Batch* B, const void* in, 
     return RT3D_OK;
 }
 
-template <int CI, int CO, int MODE>
+template <int CI, int CO, int MODE, bool kPlanarOut = false>
 rt3d_status launch_conv_tc(rt3d_ctx* c, int strips, const Batch* B, const uint16_t* in, const uint16_t* img,
                            const float* bias, void* out, int* status, cudaStream_t s)
 {
     if (strips <= 0) return RT3D_OK;
-    auto fn = k_net_conv_tc<CI, CO, MODE>;
+    auto fn = k_net_conv_tc<CI, CO, MODE, kPlanarOut>;
     const int smem = net_tc_a_bytes(CI) + net_tc_b_bytes(CI, CO);
     RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int dev = 0, sms = 148;
@@ -599,11 +600,45 @@ rt3d_status launch_conv_tc(rt3d_ctx* c, int strips, const Batch* B, const uint16
     return RT3D_OK;
 }
 
-// Forward pass of the network over a batch's 128-pixel row strips on the
-// tensor cores: a0 -> a1 -> a2 -> a3 -> y.
-rt3d_status net_forward_tiles(rt3d_ctx* c, const rt3d_net* net, int strips, const Batch* B, const uint16_t* a0,
-                              uint16_t* a1, uint16_t* a2, uint16_t* a3, float* y, int* status, cudaStream_t s)
+template <int CI, int CO, int MODE>
+rt3d_status launch_conv_pipe(rt3d_ctx* c, int strips, const Batch* B, const uint16_t* in, const uint16_t* img,
+                             const float* bias, void* out, int* status, cudaStream_t s)
 {
+    if (strips <= 0) return RT3D_OK;
+    auto fn = k_net_conv_pipe<CI, CO, MODE>;
+    const int smem = net_pipe_smem(CI, CO);
+    RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    int dev = 0, sms = 148;
+    RT3D_CUDA(cudaGetDevice(&dev));
+    RT3D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    LaunchScope ls(c, s, kcNet);
+    fn<<<sms, kPipeThreads, smem, s>>>(B, in, img, bias, out, status);
+    return RT3D_OK;
+}
+
+// Forward pass of the network over a batch's 128-pixel row strips on the
+// tensor cores: a0 -> a1 -> a2 -> a3 -> y.  pipelined: the 48-channel layers
+// run on the pipelined kernel with chunk-planar hidden activations (the
+// reconstruction loop); otherwise every layer uses the register-staged
+// kernel with NHWC activations (the network's own training calls).
+rt3d_status net_forward_tiles(rt3d_ctx* c, const rt3d_net* net, int strips, const Batch* B, const uint16_t* a0,
+                              uint16_t* a1, uint16_t* a2, uint16_t* a3, float* y, int* status, cudaStream_t s,
+                              bool pipelined = false)
+{
+    if (pipelined) {
+        rt3d_status st = launch_conv_tc<6, 48, kConvHidden, true>(c, strips, B, a0, net->wtc + net_tcoff(0),
+                                                                  net->theta + net_boff(0), a1, status, s);
+        if (st == RT3D_OK)
+            st = launch_conv_pipe<48, 48, kConvHidden>(c, strips, B, a1, net->wtc + net_tcoff(1),
+                                                       net->theta + net_boff(1), a2, status, s);
+        if (st == RT3D_OK)
+            st = launch_conv_pipe<48, 48, kConvHidden>(c, strips, B, a2, net->wtc + net_tcoff(2),
+                                                       net->theta + net_boff(2), a3, status, s);
+        if (st == RT3D_OK)
+            st = launch_conv_pipe<48, 2, kConvOut>(c, strips, B, a3, net->wtc + net_tcoff(3),
+                                                   net->theta + net_boff(3), y, status, s);
+        return st;
+    }
     rt3d_status st = launch_conv_tc<6, 48, kConvHidden>(c, strips, B, a0, net->wtc + net_tcoff(0),
                                                         net->theta + net_boff(0), a1, status, s);
     if (st == RT3D_OK)
@@ -667,8 +702,9 @@ rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
                 k_net_features_loop<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W, c->net_a0,
                                                                            c->h_rec.P.net_scale);
             }
-            const rt3d_status st = net_forward_tiles(c, c->net, B.net_strips, &c->d_rec->B, c->net_a0, c->net_a1,
-                                                     c->net_a2, c->net_a1, c->net_y, c->W.status, s);
+            const rt3d_status st = net_forward_tiles(
+                c, c->net, B.net_strips, &c->d_rec->B, c->net_a0, c->net_a1, c->net_a2, c->net_a1, c->net_y,
+                c->W.status, s, true);
             if (st != RT3D_OK) return st;
         }
         {
