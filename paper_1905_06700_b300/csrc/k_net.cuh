@@ -128,7 +128,8 @@ __device__ __forceinline__ void net_features_at(const NetStateView& v, int K, in
     }
 }
 
-// Features of the loop's half-step state (t_half, r, alive) -> x [pix][6] bf16.
+// Features of the loop's half-step state (t_half, r, alive) -> x [pix][8] bf16
+// (channels 6 and 7 zero: the chunk-planar input of the pipelined convolution).
 __global__ void __launch_bounds__(kTileThreads)
 k_net_features_loop(const CallRecord* __restrict__ rec, const Work W, uint16_t* __restrict__ x, float scale)
 {
@@ -139,8 +140,11 @@ k_net_features_loop(const CallRecord* __restrict__ rec, const Work W, uint16_t* 
     NetStateView v{W.t_half, F.r, F.alive, W.stride, F.npix, F.npix, F.pix_base, 0, 0};
     float f[6];
     net_features_at(v, rec->P.k, F.h, F.w, q.gi, q.gj, scale, f);
-#pragma unroll
-    for (int c = 0; c < 6; ++c) x[(long long)q.pix * 6 + c] = f_to_bf16_bits(f[c]);
+    // chunk-planar with 8 channels (the last two zero): one 16-byte row per pixel
+    const uint32_t w0 = (uint32_t)f_to_bf16_bits(f[0]) | ((uint32_t)f_to_bf16_bits(f[1]) << 16);
+    const uint32_t w1 = (uint32_t)f_to_bf16_bits(f[2]) | ((uint32_t)f_to_bf16_bits(f[3]) << 16);
+    const uint32_t w2 = (uint32_t)f_to_bf16_bits(f[4]) | ((uint32_t)f_to_bf16_bits(f[5]) << 16);
+    *reinterpret_cast<uint4*>(x + (long long)q.pix * 8) = make_uint4(w0, w1, w2, 0u);
 }
 
 // Features of n caller images, state [n][K][h][w] -> x [n][6][h][w] (FP32
@@ -470,7 +474,7 @@ __device__ __forceinline__ uint4* planar_chunk(uint16_t* out, const FrameDesc& F
                                     (((long long)gi * (CO / 8) + c) * F.w + gj) * 8);
 }
 
-template <int CI, int CO, int MODE, bool kPlanarOut = false>
+template <int CI, int CO, int MODE>
 __global__ void __launch_bounds__(128)
 k_net_conv_tc(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, const uint16_t* __restrict__ bimg,
               const float* __restrict__ bias, void* __restrict__ out, int* __restrict__ status)
@@ -564,17 +568,18 @@ k_net_conv_tc(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, con
         __syncthreads();
         if (threadIdx.x == 0) {
             tc_fence_after();
+            // descriptors differ from the first one only in the start-address field
+            const uint64_t da0 = tc_desc_plain(a_addr, kChunkBytes, 128);
+            const uint64_t db0 = tc_desc_plain(b_addr, (uint32_t)(COp * 16), 128);
             uint32_t acc = 0;
-#pragma unroll 1
+#pragma unroll
             for (int t = 0; t < 9; ++t) {
                 const int ky = t / 3, kx = t % 3;
 #pragma unroll
                 for (int s = 0; s < KS; ++s) {
-                    const uint64_t da = tc_desc_plain(a_addr + (uint32_t)(2 * s) * kChunkBytes +
-                                                          (uint32_t)(ky * kStripHaloW + kx) * 16,
-                                                      kChunkBytes, 128);
-                    const uint64_t db = tc_desc_plain(b_addr + (uint32_t)((t * KS + s) * 2 * COp * 16),
-                                                      (uint32_t)(COp * 16), 128);
+                    const uint64_t da = da0 + (uint64_t)(((uint32_t)(2 * s) * kChunkBytes +
+                                                          (uint32_t)(ky * kStripHaloW + kx) * 16) >> 4);
+                    const uint64_t db = db0 + (uint64_t)((uint32_t)((t * KS + s) * 2 * COp * 16) >> 4);
                     tc_mma(tmem, da, db, idesc, acc);
                     acc = 1;
                 }
@@ -621,17 +626,9 @@ k_net_conv_tc(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, con
                 for (int c = 0; c < CO / 2; ++c)
                     pk[c] = (uint32_t)f_to_bf16_bits(fmaxf(acc[2 * c] + bias[2 * c], 0.0f)) |
                             ((uint32_t)f_to_bf16_bits(fmaxf(acc[2 * c + 1] + bias[2 * c + 1], 0.0f)) << 16);
-                if constexpr (kPlanarOut) {
+                uint4* o = reinterpret_cast<uint4*>(static_cast<uint16_t*>(out) + px * CO);
 #pragma unroll
-                    for (int c = 0; c < CO / 8; ++c)
-                        *planar_chunk<CO>(static_cast<uint16_t*>(out), F, gi, gj, c) =
-                            make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
-                } else {
-                    uint4* o = reinterpret_cast<uint4*>(static_cast<uint16_t*>(out) + px * CO);
-#pragma unroll
-                    for (int c = 0; c < CO / 8; ++c)
-                        o[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
-                }
+                for (int c = 0; c < CO / 8; ++c) o[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
             } else {
                 float* o = static_cast<float*>(out) + px * CO;
 #pragma unroll
@@ -750,7 +747,9 @@ k_net_conv_pipe(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, c
                 const float* __restrict__ bias, void* __restrict__ out, int* __restrict__ status)
 {
     static_assert(CI % 8 == 0, "16-byte input rows");
-    constexpr int CIp = net_pad16(CI), COp = net_pad16(CO), KS = CIp / 16, NC = CIp / 8;
+    // NCS chunk planes per input row are stored, NC are read by the MMAs
+    // (planes NCS..NC-1 stay zero: CI below 16)
+    constexpr int CIp = net_pad16(CI), COp = net_pad16(CO), KS = CIp / 16, NC = CIp / 8, NCS = CI / 8;
     constexpr int ROW = net_pipe_row_bytes(CI), B_BYTES = net_tc_b_bytes(CI, CO);
     constexpr int R = kPipeRing;
     constexpr int TM_COLS = COp <= 32 ? 32 : 64;            // one accumulator
@@ -772,6 +771,11 @@ k_net_conv_pipe(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, c
     for (int i = threadIdx.x; i < B_BYTES / 16; i += blockDim.x)
         reinterpret_cast<uint4*>(sb)[i] = reinterpret_cast<const uint4*>(bimg)[i];
     for (int i = threadIdx.x; i < ROW / 16; i += blockDim.x) reinterpret_cast<uint4*>(zrow)[i] = make_uint4(0, 0, 0, 0);
+    if constexpr (NCS < NC)
+        for (int i = threadIdx.x; i < R * (NC - NCS) * (int)kPlane / 16; i += blockDim.x) {
+            const int slot = i / ((NC - NCS) * (int)kPlane / 16), rem = i % ((NC - NCS) * (int)kPlane / 16);
+            reinterpret_cast<uint4*>(srow + slot * ROW + NCS * kPlane)[rem] = make_uint4(0, 0, 0, 0);
+        }
     for (int i = threadIdx.x; i < COp; i += blockDim.x) s_bias[i] = i < CO ? bias[i] : 0.0f;
     if (threadIdx.x == 0) {
         for (int i = 0; i < R; ++i) {
@@ -812,7 +816,7 @@ k_net_conv_pipe(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, c
             // in-frame columns [c_lo, c_hi) of the row's j0 - 1 .. j0 + 128
             const int c_lo = max(j0 - 1, 0), c_hi = min(j0 + kStripHaloW - 1, F.w);
             const int p_lo = c_lo - (j0 - 1), npx = c_hi - c_lo;
-            const uint16_t* fbase = in + (long long)F.pix_base * CIp;
+            const uint16_t* fbase = in + (long long)F.pix_base * CI;
             for (int r = max(g0 - 1, 0); r <= min(g1, F.h - 1); ++r, ++q) {
                 const uint32_t slot = q % R;
                 if (!__all_sync(0xffffffffu, mbar_wait(bar_empty + 8 * slot, ((q / R) & 1u) ^ 1u, abort_flag))) {
@@ -822,10 +826,10 @@ k_net_conv_pipe(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, c
                 // (chunk, pixel slot) pairs spread over the lanes; slots outside
                 // the frame's columns are filled with zeros
                 const uint32_t dst0 = row_addr + slot * ROW;
-                for (int idx = lane; idx < NC * kStripHaloW; idx += 32) {
+                for (int idx = lane; idx < NCS * kStripHaloW; idx += 32) {
                     const int c = idx / kStripHaloW, p = idx - c * kStripHaloW;
                     const bool in_f = p >= p_lo && p < p_lo + npx;
-                    const uint16_t* src = fbase + (((long long)r * NC + c) * F.w + (in_f ? c_lo + p - p_lo : 0)) * 8;
+                    const uint16_t* src = fbase + (((long long)r * NCS + c) * F.w + (in_f ? c_lo + p - p_lo : 0)) * 8;
                     cp_async16(dst0 + (uint32_t)(c * kPlane + p * 16), src, in_f ? 16u : 0u);
                 }
                 cp_async_arrive(bar_full + 8 * slot);
@@ -837,6 +841,7 @@ k_net_conv_pipe(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, c
     } else if (warp == 5) {
         // ------------------------------------------------ MMA issuer
         if (lane == 0) {
+            const uint64_t db0 = tc_desc_plain(b_addr, (uint32_t)(COp * 16), 128);
             uint32_t q = 0, k = 0;
             bool stop = false;
             for (int item = blockIdx.x; item < n_items && !stop; item += gridDim.x) {
@@ -863,16 +868,18 @@ k_net_conv_pipe(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, c
                     // the rows were written by generic-proxy copies
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                     tc_fence_after();
+                    // descriptors differ from the row's or the weights' first one only
+                    // in the 16-byte start-address field (shared addresses stay below 2^18)
+                    const uint64_t da0[3] = {tc_desc_plain(rows3[0], kPlane, 128), tc_desc_plain(rows3[1], kPlane, 128),
+                                             tc_desc_plain(rows3[2], kPlane, 128)};
                     uint32_t acc = 0;
 #pragma unroll
                     for (int t = 0; t < 9; ++t) {
                         const int ky = t / 3, kx = t % 3;
 #pragma unroll
                         for (int s2 = 0; s2 < KS; ++s2) {
-                            const uint64_t da = tc_desc_plain(rows3[ky] + (uint32_t)(2 * s2) * kPlane + (uint32_t)kx * 16,
-                                                              kPlane, 128);
-                            const uint64_t db = tc_desc_plain(b_addr + (uint32_t)((t * KS + s2) * 2 * COp * 16),
-                                                              (uint32_t)(COp * 16), 128);
+                            const uint64_t da = da0[ky] + (uint64_t)(((uint32_t)(2 * s2) * kPlane + (uint32_t)kx * 16) >> 4);
+                            const uint64_t db = db0 + (uint64_t)((uint32_t)((t * KS + s2) * 2 * COp * 16) >> 4);
                             tc_mma(tmem + a * TM_COLS, da, db, idesc, acc);
                             acc = 1;
                         }

@@ -105,7 +105,7 @@ struct rt3d_ctx {
     int n_sms = 0;
     // learned depth denoiser: the attached network and the loop's inference buffers
     rt3d_net* net = nullptr;
-    uint16_t* net_a0 = nullptr;     // [stride][6]
+    uint16_t* net_a0 = nullptr;     // [stride][8] (6 features, 2 zero)
     uint16_t* net_a1 = nullptr;     // [stride][48]
     uint16_t* net_a2 = nullptr;     // [stride][48]
     float* net_y = nullptr;         // [stride][2]
@@ -583,12 +583,12 @@ rt3d_status launch_conv(rt3d_ctx* c, int tiles, const Batch* B, const void* in, 
     return RT3D_OK;
 }
 
-template <int CI, int CO, int MODE, bool kPlanarOut = false>
+template <int CI, int CO, int MODE>
 rt3d_status launch_conv_tc(rt3d_ctx* c, int strips, const Batch* B, const uint16_t* in, const uint16_t* img,
                            const float* bias, void* out, int* status, cudaStream_t s)
 {
     if (strips <= 0) return RT3D_OK;
-    auto fn = k_net_conv_tc<CI, CO, MODE, kPlanarOut>;
+    auto fn = k_net_conv_tc<CI, CO, MODE>;
     const int smem = net_tc_a_bytes(CI) + net_tc_b_bytes(CI, CO);
     RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     int dev = 0, sms = 148;
@@ -626,8 +626,10 @@ rt3d_status net_forward_tiles(rt3d_ctx* c, const rt3d_net* net, int strips, cons
                               bool pipelined = false)
 {
     if (pipelined) {
-        rt3d_status st = launch_conv_tc<6, 48, kConvHidden, true>(c, strips, B, a0, net->wtc + net_tcoff(0),
-                                                                  net->theta + net_boff(0), a1, status, s);
+        // a0 holds 8 channels per pixel (the last two zero); the weights of
+        // channels 6 and 7 are zero in the operand image
+        rt3d_status st = launch_conv_pipe<8, 48, kConvHidden>(c, strips, B, a0, net->wtc + net_tcoff(0),
+                                                              net->theta + net_boff(0), a1, status, s);
         if (st == RT3D_OK)
             st = launch_conv_pipe<48, 48, kConvHidden>(c, strips, B, a1, net->wtc + net_tcoff(1),
                                                        net->theta + net_boff(1), a2, status, s);
@@ -1640,7 +1642,7 @@ rt3d_status rt3d_set_depth_net(rt3d_ctx_t* c, rt3d_net_t* net)
         auto alloc = [&](void** ptr, size_t bytes) {
             if (e == cudaSuccess) e = cudaMalloc(ptr, bytes);
         };
-        alloc((void**)&c->net_a0, sizeof(uint16_t) * 6 * c->stride);
+        alloc((void**)&c->net_a0, sizeof(uint16_t) * 8 * c->stride);
         alloc((void**)&c->net_a1, sizeof(uint16_t) * kNetCh * c->stride);
         alloc((void**)&c->net_a2, sizeof(uint16_t) * kNetCh * c->stride);
         alloc((void**)&c->net_y, sizeof(float) * 2 * c->stride);
