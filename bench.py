@@ -135,10 +135,10 @@ def algorithmic_flops(n_frames: int, nnz_total: int, n_points: int, k: int, prm,
 
 def fused_fraction(prm) -> float:
     """Share of phase C launches that also run the next iteration's depth step
-    (the library fuses it when the background denoiser is the identity and the
-    depth denoiser is not the learned one): all but the last iteration's."""
+    (the library fuses it when the background denoiser is the identity): all
+    but the last iteration's."""
     n = int(prm["n_iter"])
-    if n <= 0 or prm.get("bkg_mode", 0) == 1 or prm.get("depth_denoiser", 1) == 2:
+    if n <= 0 or prm.get("bkg_mode", 0) == 1:
         return 0.0
     return (n - 1) / n
 

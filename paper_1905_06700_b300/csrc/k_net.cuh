@@ -131,13 +131,17 @@ __device__ __forceinline__ void net_features_at(const NetStateView& v, int K, in
 // Features of the loop's half-step state (t_half, r, alive) -> x [pix][8] bf16
 // (channels 6 and 7 zero: the chunk-planar input of the pipelined convolution).
 __global__ void __launch_bounds__(kTileThreads)
-k_net_features_loop(const CallRecord* __restrict__ rec, const Work W, uint16_t* __restrict__ x, float scale)
+k_net_features_loop(const CallRecord* __restrict__ rec, const Work W, uint16_t* __restrict__ x, float scale,
+                    int alive_from_b)
 {
     const Batch& B = rec->B;
     const NetPix q = net_pix(B, blockIdx.x, threadIdx.x / kTileW, threadIdx.x % kTileW);
     if (!q.in) return;
     const FrameDesc& F = B.f[q.fi];
-    NetStateView v{W.t_half, F.r, F.alive, W.stride, F.npix, F.npix, F.pix_base, 0, 0};
+    // after a phase C that ran the depth step the alive flags are still in alive_b
+    NetStateView v = alive_from_b
+                         ? NetStateView{W.t_half, F.r, W.alive_b, W.stride, F.npix, W.stride, F.pix_base, 0, F.pix_base}
+                         : NetStateView{W.t_half, F.r, F.alive, W.stride, F.npix, F.npix, F.pix_base, 0, 0};
     float f[6];
     net_features_at(v, rec->P.k, F.h, F.w, q.gi, q.gj, scale, f);
     // chunk-planar with 8 channels (the last two zero): one 16-byte row per pixel

@@ -682,11 +682,11 @@ void launch_phase(int k, int phase, int flag, int tiles, cudaStream_t s, const C
 
 // With the identity background denoiser the depth step needs only its own
 // pixel's state, so it rides on the previous iteration's phase C (two
-// launches per iteration instead of three).  The learned form keeps phase A
-// separate (its features run between phases A and B).
+// launches per iteration instead of three; the learned form's features and
+// network then run between that phase C and phase B).
 bool fused_depth_step(const KParams& P)
 {
-    return P.bkg_mode != RT3D_BKG_LOWPASS && P.depth_den != RT3D_DEPTH_LEARNED;
+    return P.bkg_mode != RT3D_BKG_LOWPASS;
 }
 
 rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
@@ -702,7 +702,8 @@ rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
             {
                 LaunchScope ls(c, s, kcNet);
                 k_net_features_loop<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W, c->net_a0,
-                                                                           c->h_rec.P.net_scale);
+                                                                           c->h_rec.P.net_scale,
+                                                                           fused && it > 0 ? 1 : 0);
             }
             const rt3d_status st = net_forward_tiles(
                 c, c->net, B.net_strips, &c->d_rec->B, c->net_a0, c->net_a1, c->net_a2, c->net_a1, c->net_y,
