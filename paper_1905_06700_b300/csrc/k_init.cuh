@@ -55,7 +55,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
 
 template <bool kDumpY, bool kCompactOnly>
 __global__ void __launch_bounds__(kInitWarps * 32, 5)
-k_init(const CallRecord* __restrict__ rec, const Work W)
+k_init(const CallRecord* __restrict__ rec, const Work W, int pix0, int pix_end)
 {
     const KParams& P = rec->P;
     const Batch& B = rec->B;
@@ -68,8 +68,9 @@ k_init(const CallRecord* __restrict__ rec, const Work W)
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int pix = blockIdx.x * (int)(blockDim.x >> 5) + warp;
-    if (pix >= B.total_pix) return;
+    // this launch covers the batch's pixels [pix0, pix_end)
+    const int pix = pix0 + (int)blockIdx.x * (int)(blockDim.x >> 5) + warp;
+    if (pix >= pix_end) return;
     const FrameDesc& F = B.f[frame_of_pixel(B, pix)];
     // frames whose cold start runs in the tensor-core init
     if (!kCompactOnly && F.tc) return;

@@ -22,12 +22,15 @@ struct TileCtx {
     bool inb;
 };
 
-__device__ __forceinline__ TileCtx tile_ctx(const Batch& B)
+// Tile of this CTA: tile0 + blockIdx.x of the batch (a launch may cover a
+// contiguous range of the batch's tiles).
+__device__ __forceinline__ TileCtx tile_ctx(const Batch& B, int tile0)
 {
     TileCtx c;
-    c.fi = frame_of_tile(B, blockIdx.x);
+    const int tile = tile0 + (int)blockIdx.x;
+    c.fi = frame_of_tile(B, tile);
     const FrameDesc& F = B.f[c.fi];
-    const int lt = blockIdx.x - F.tile_base;
+    const int lt = tile - F.tile_base;
     c.i0 = (lt / F.tiles_w) * kTileH;
     c.j0 = (lt % F.tiles_w) * kTileW;
     c.li = threadIdx.x / kTileW;
@@ -329,7 +332,7 @@ __device__ __forceinline__ void depth_step(const float* pad, const KParams& P, i
 // one thread per pixel (the bin sums shared out over the warp).
 template <int K>
 __global__ void __launch_bounds__(kTileThreads)
-k_phase_a(const CallRecord* __restrict__ rec, const Work W, int first)
+k_phase_a(const CallRecord* __restrict__ rec, const Work W, int first, int tile0)
 {
     const KParams& P = rec->P;
     const Batch& B = rec->B;
@@ -338,7 +341,7 @@ k_phase_a(const CallRecord* __restrict__ rec, const Work W, int first)
     __shared__ WarpSums<K, K> ws[kTileThreads / 32];
     load_irf_coef(pad, coef, P);
     __syncthreads();
-    const TileCtx c = tile_ctx(B);
+    const TileCtx c = tile_ctx(B, tile0);
     const FrameDesc& F = B.f[c.fi];
     const int np = F.npix, S = W.stride;
     const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
@@ -569,7 +572,7 @@ __device__ __forceinline__ int compact_points(const float* st, int R, int K, boo
 // still in alive_b; they land in the frame here (phase C reads them there).
 template <int K>
 __global__ void __launch_bounds__(kTileThreads, 7)
-k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b)
+k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, int tile0)
 {
     const KParams& P = rec->P;
     const Batch& B = rec->B;
@@ -581,7 +584,7 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b)
     __shared__ float4 coef[kCoefLen];
     __shared__ WarpSums<K, K> ws[kTileThreads / 32];
     load_irf_coef(pad, coef, P);
-    const TileCtx c = tile_ctx(B);
+    const TileCtx c = tile_ctx(B, tile0);
     const FrameDesc& F = B.f[c.fi];
     const int np = F.npix, S = W.stride, R = P.win_r;
     const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
@@ -667,7 +670,7 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b)
 // alive flags here), depth step into t_half.
 template <int K>
 __global__ void __launch_bounds__(kTileThreads)
-k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next)
+k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next, int tile0)
 {
     const KParams& P = rec->P;
     const Batch& B = rec->B;
@@ -681,7 +684,7 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next)
     __shared__ float4 coef[kCoefLen];
     __shared__ WarpSums<K, K> ws[kTileThreads / 32];
     load_irf_coef(pad, coef, P);
-    const TileCtx c = tile_ctx(B);
+    const TileCtx c = tile_ctx(B, tile0);
     const FrameDesc& F = B.f[c.fi];
     const int np = F.npix, S = W.stride, R = P.win_r;
     const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
@@ -796,14 +799,14 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next)
 // Finaliser: the last iteration's pruning and background denoiser land in the
 // result buffers; alive points are counted per frame.
 __global__ void __launch_bounds__(kTileThreads)
-k_final(const CallRecord* __restrict__ rec, const Work W, int ran)
+k_final(const CallRecord* __restrict__ rec, const Work W, int ran, int tile0)
 {
     const KParams& P = rec->P;
     const Batch& B = rec->B;
     __shared__ int s_cnt;
     if (threadIdx.x == 0) s_cnt = 0;
     __syncthreads();
-    const TileCtx c = tile_ctx(B);
+    const TileCtx c = tile_ctx(B, tile0);
     const FrameDesc& F = B.f[c.fi];
     int mine = 0;
     if (c.inb) {

@@ -47,13 +47,14 @@ struct PendingTiming {
 struct GraphKey {
     int total_pix, total_tiles, n_iter, warm, init_warps, profiled;
     size_t init_smem;
-    int tc_tiles, tc_stages, tc_nd, any_int, learned, fused;
+    int tc_tiles, tc_stages, tc_nd, any_int, learned, fused, split_tiles;
     bool operator<(const GraphKey& o) const
     {
         return std::tie(total_pix, total_tiles, n_iter, warm, init_warps, profiled, init_smem, tc_tiles,
-                        tc_stages, tc_nd, any_int, learned, fused) <
+                        tc_stages, tc_nd, any_int, learned, fused, split_tiles) <
                std::tie(o.total_pix, o.total_tiles, o.n_iter, o.warm, o.init_warps, o.profiled,
-                        o.init_smem, o.tc_tiles, o.tc_stages, o.tc_nd, o.any_int, o.learned, o.fused);
+                        o.init_smem, o.tc_tiles, o.tc_stages, o.tc_nd, o.any_int, o.learned, o.fused,
+                        o.split_tiles);
     }
 };
 
@@ -116,6 +117,8 @@ struct rt3d_ctx {
     GraphEntry* capturing = nullptr;        // set while a launch sequence is being captured
     std::vector<GraphEntry*> pending_graphs;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream2 = nullptr;    // second branch of a split capture
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     std::vector<cudaEvent_t> event_pool;
     double ms[kNumKernelClasses] = {0};
     long long counts[kNumKernelClasses] = {0};
@@ -536,22 +539,24 @@ bool batch_has_int(const Batch& B)
     return false;
 }
 
+// pix0 / pix_end: the batch pixels this launch covers (pix_end < 0: all)
 rt3d_status launch_init(rt3d_ctx* c, const KParams& K, const Batch& B, Work W, cudaStream_t s,
-                        bool dump, bool compact_only)
+                        bool dump, bool compact_only, int pix0 = 0, int pix_end = -1)
 {
+    if (pix_end < 0) pix_end = B.total_pix;
     // the tensor-core kernel takes the dense frames of a cold start; the
     // CUDA-core kernel the rest (it skips those frames)
     const bool tc = K.tc_mode != 0 && !compact_only && B.tc_tiles > 0;
     if (!tc || compact_only || batch_has_int(B)) {
         const size_t smem = init_smem(K, K.peak_sep);
         const int warps = init_warps(K.peak_sep);
-        const int grid = (B.total_pix + warps - 1) / warps;
+        const int grid = (pix_end - pix0 + warps - 1) / warps;
         if (grid > 0) {
             auto fn = dump ? k_init<true, false> : (compact_only ? k_init<false, true> : k_init<false, false>);
             RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             {
                 LaunchScope ls(c, s, kcInit);
-                fn<<<grid, warps * 32, smem, s>>>(c->d_rec, W);
+                fn<<<grid, warps * 32, smem, s>>>(c->d_rec, W, pix0, pix_end);
             }
             RT3D_CUDA(cudaGetLastError());
         }
@@ -658,25 +663,29 @@ rt3d_status net_forward_tiles(rt3d_ctx* c, const rt3d_net* net, int strips, cons
 // One PALM phase kernel (0: A, 1: B, 2: C), instantiated for the slot count.
 // flag: phase A -- first iteration; phase B -- alive flags still in alive_b;
 // phase C -- run the next iteration's depth step too.
+// (tiles [tile0, tile0 + tiles) of the batch)
 template <int K>
-void launch_phase_k(int phase, int flag, int tiles, cudaStream_t s, const CallRecord* rec, const Work& W)
+void launch_phase_k(int phase, int flag, int tiles, cudaStream_t s, const CallRecord* rec, const Work& W,
+                    int tile0)
 {
     if (phase == 0)
-        k_phase_a<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag);
+        k_phase_a<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag, tile0);
     else if (phase == 1)
-        k_phase_b<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag);
+        k_phase_b<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag, tile0);
     else
-        k_phase_c<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag);
+        k_phase_c<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag, tile0);
 }
 
-void launch_phase(int k, int phase, int flag, int tiles, cudaStream_t s, const CallRecord* rec, const Work& W)
+void launch_phase(int k, int phase, int flag, int tiles, cudaStream_t s, const CallRecord* rec, const Work& W,
+                  int tile0 = 0)
 {
     static_assert(kMaxK == 4, "one instantiation per slot count");
+    if (tiles <= 0) return;
     switch (k) {
-    case 1: launch_phase_k<1>(phase, flag, tiles, s, rec, W); break;
-    case 2: launch_phase_k<2>(phase, flag, tiles, s, rec, W); break;
-    case 3: launch_phase_k<3>(phase, flag, tiles, s, rec, W); break;
-    default: launch_phase_k<4>(phase, flag, tiles, s, rec, W); break;
+    case 1: launch_phase_k<1>(phase, flag, tiles, s, rec, W, tile0); break;
+    case 2: launch_phase_k<2>(phase, flag, tiles, s, rec, W, tile0); break;
+    case 3: launch_phase_k<3>(phase, flag, tiles, s, rec, W, tile0); break;
+    default: launch_phase_k<4>(phase, flag, tiles, s, rec, W, tile0); break;
     }
 }
 
@@ -689,14 +698,15 @@ bool fused_depth_step(const KParams& P)
     return P.bkg_mode != RT3D_BKG_LOWPASS;
 }
 
-rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
+rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter, int tile0 = 0, int tiles = -1)
 {
+    if (tiles < 0) tiles = B.total_tiles;
     const bool learned = c->h_rec.P.depth_den == RT3D_DEPTH_LEARNED;
     const bool fused = fused_depth_step(c->h_rec.P);
     for (int it = 0; it < n_iter; ++it) {
         if (it == 0 || !fused) {
             LaunchScope ls(c, s, kcA);
-            launch_phase(c->h_rec.P.k, 0, it == 0 ? 1 : 0, B.total_tiles, s, c->d_rec, c->W);
+            launch_phase(c->h_rec.P.k, 0, it == 0 ? 1 : 0, tiles, s, c->d_rec, c->W, tile0);
         }
         if (learned) {
             {
@@ -712,22 +722,24 @@ rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
         }
         {
             LaunchScope ls(c, s, kcB);
-            launch_phase(c->h_rec.P.k, 1, fused && it > 0 ? 1 : 0, B.total_tiles, s, c->d_rec, c->W);
+            launch_phase(c->h_rec.P.k, 1, fused && it > 0 ? 1 : 0, tiles, s, c->d_rec, c->W, tile0);
         }
         {
             LaunchScope ls(c, s, kcC);
-            launch_phase(c->h_rec.P.k, 2, fused && it + 1 < n_iter ? 1 : 0, B.total_tiles, s, c->d_rec, c->W);
+            launch_phase(c->h_rec.P.k, 2, fused && it + 1 < n_iter ? 1 : 0, tiles, s, c->d_rec, c->W, tile0);
         }
     }
     RT3D_CUDA(cudaGetLastError());
     return RT3D_OK;
 }
 
-rt3d_status launch_final(rt3d_ctx* c, const Batch& B, cudaStream_t s, int ran)
+rt3d_status launch_final(rt3d_ctx* c, const Batch& B, cudaStream_t s, int ran, int tile0 = 0, int tiles = -1)
 {
+    if (tiles < 0) tiles = B.total_tiles;
+    if (tiles <= 0) return RT3D_OK;
     {
         LaunchScope ls(c, s, kcFinal);
-        k_final<<<B.total_tiles, kTileThreads, 0, s>>>(c->d_rec, c->W, ran);
+        k_final<<<tiles, kTileThreads, 0, s>>>(c->d_rec, c->W, ran, tile0);
     }
     RT3D_CUDA(cudaGetLastError());
     return RT3D_OK;
@@ -760,14 +772,34 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
     if (st != RT3D_OK) return st;
     st = upload_record(c, s);
     if (st != RT3D_OK) return st;
+    // Two chains of frames (init, loop, finaliser each) captured as parallel
+    // branches: each chain's launches fill the other's partly empty last wave.
+    // Frames are independent, so the results are those of one chain.  Kept as
+    // one chain for the learned form and the tensor-core init (their kernels
+    // cover the whole batch) and while kernel times are recorded (so each
+    // kernel's duration is its own).
+    int n0 = 0, split_tiles = 0, split_pix = 0;
+    if (n >= 2 && B.tc_tiles == 0 && K.depth_den != RT3D_DEPTH_LEARNED && !c->profiling) {
+        // first chain: the frames whose tiles end by half the batch's tiles (at least one)
+        auto tiles_end = [&](int i) { return i + 1 < n ? B.f[i + 1].tile_base : B.total_tiles; };
+        while (n0 < n - 1 && 2 * tiles_end(n0) <= B.total_tiles) ++n0;
+        if (n0 == 0) n0 = 1;
+        split_tiles = B.f[n0].tile_base;
+        split_pix = B.f[n0].pix_base;
+    }
     const GraphKey key{B.total_pix, B.total_tiles, p->n_iter, p->warm_start != 0,
                        init_warps(K.peak_sep), c->profiling ? 1 : 0, init_smem(K, K.peak_sep),
                        B.tc_tiles, K.tc_stages, K.tc_nd, batch_has_int(B) ? 1 : 0,
-                       K.depth_den == RT3D_DEPTH_LEARNED ? 1 : 0, fused_depth_step(K) ? 1 : 0};
+                       K.depth_den == RT3D_DEPTH_LEARNED ? 1 : 0, fused_depth_step(K) ? 1 : 0, split_tiles};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         // capture the launch sequence of this geometry once, on a private stream
         if (!c->cap_stream) RT3D_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        if (split_tiles && !c->cap_stream2) {
+            RT3D_CUDA(cudaStreamCreateWithFlags(&c->cap_stream2, cudaStreamNonBlocking));
+            RT3D_CUDA(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+            RT3D_CUDA(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
+        }
         GraphEntry entry;
         c->capturing = &entry;
         cudaGraph_t graph = nullptr;
@@ -775,9 +807,29 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
         rt3d_status cst = RT3D_OK;
         if (e == cudaSuccess) {
             e = cudaMemsetAsync(c->d_count, 0, sizeof(unsigned long long), c->cap_stream);
-            if (e == cudaSuccess) cst = launch_init(c, K, B, c->W, c->cap_stream, false, p->warm_start != 0);
-            if (e == cudaSuccess && cst == RT3D_OK) cst = launch_loop(c, B, c->cap_stream, p->n_iter);
-            if (e == cudaSuccess && cst == RT3D_OK) cst = launch_final(c, B, c->cap_stream, p->n_iter > 0 ? 1 : 0);
+            const int ran = p->n_iter > 0 ? 1 : 0;
+            const bool warm = p->warm_start != 0;
+            if (split_tiles == 0) {
+                if (e == cudaSuccess) cst = launch_init(c, K, B, c->W, c->cap_stream, false, warm);
+                if (e == cudaSuccess && cst == RT3D_OK) cst = launch_loop(c, B, c->cap_stream, p->n_iter);
+                if (e == cudaSuccess && cst == RT3D_OK) cst = launch_final(c, B, c->cap_stream, ran);
+            } else {
+                // fork: frames [n0, n) on the second capture stream
+                if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, c->cap_stream);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cap_stream2, c->ev_fork, 0);
+                const int t1 = B.total_tiles - split_tiles;
+                if (e == cudaSuccess) cst = launch_init(c, K, B, c->W, c->cap_stream, false, warm, 0, split_pix);
+                if (e == cudaSuccess && cst == RT3D_OK)
+                    cst = launch_init(c, K, B, c->W, c->cap_stream2, false, warm, split_pix, B.total_pix);
+                if (e == cudaSuccess && cst == RT3D_OK) cst = launch_loop(c, B, c->cap_stream, p->n_iter, 0, split_tiles);
+                if (e == cudaSuccess && cst == RT3D_OK)
+                    cst = launch_loop(c, B, c->cap_stream2, p->n_iter, split_tiles, t1);
+                if (e == cudaSuccess && cst == RT3D_OK) cst = launch_final(c, B, c->cap_stream, ran, 0, split_tiles);
+                if (e == cudaSuccess && cst == RT3D_OK) cst = launch_final(c, B, c->cap_stream2, ran, split_tiles, t1);
+                // join
+                if (e == cudaSuccess) e = cudaEventRecord(c->ev_join, c->cap_stream2);
+                if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cap_stream, c->ev_join, 0);
+            }
             const cudaError_t e2 = cudaStreamEndCapture(c->cap_stream, &graph);
             if (e == cudaSuccess) e = e2;
         }
@@ -950,6 +1002,9 @@ void rt3d_destroy(rt3d_ctx_t* c)
         }
     }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     for (auto ev : c->event_pool) cudaEventDestroy(ev);
     delete c;
 }
@@ -1871,14 +1926,14 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     const int warps = init_warps(K.peak_sep);
     auto init_fn = p->warm_start ? k_init<false, true> : k_init<false, false>;
     RT3D_CUDA(cudaFuncSetAttribute(init_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    init_fn<<<(B.total_pix + warps - 1) / warps, warps * 32, smem, s>>>(d_rec, W);
+    init_fn<<<(B.total_pix + warps - 1) / warps, warps * 32, smem, s>>>(d_rec, W, 0, B.total_pix);
     for (int it = 0; it < p->n_iter; ++it) {
         const bool fused = fused_depth_step(K);
         if (it == 0 || !fused) launch_phase(K.k, 0, it == 0 ? 1 : 0, B.total_tiles, s, d_rec, W);
         launch_phase(K.k, 1, fused && it > 0 ? 1 : 0, B.total_tiles, s, d_rec, W);
         launch_phase(K.k, 2, fused && it + 1 < p->n_iter ? 1 : 0, B.total_tiles, s, d_rec, W);
     }
-    k_final<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W, p->n_iter > 0 ? 1 : 0);
+    k_final<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W, p->n_iter > 0 ? 1 : 0, 0);
     RT3D_CUDA(cudaGetLastError());
     return RT3D_OK;
 }
