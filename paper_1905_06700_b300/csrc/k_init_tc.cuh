@@ -261,7 +261,7 @@ __device__ __forceinline__ void tc_insert(int (&by)[kMaxK], int (&bt)[kMaxK], in
 
 template <bool kDumpY>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __restrict__ bimg)
+k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __restrict__ bimg, int tc0, int tc1)
 {
     const KParams& P = rec->P;
     const Batch& B = rec->B;
@@ -320,7 +320,7 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
         if (lane == 0) {
             uint32_t g = 0;
             bool stop = false;
-            for (int tile = blockIdx.x; tile < B.tc_tiles && !stop; tile += gridDim.x) {
+            for (int tile = tc0 + (int)blockIdx.x; tile < tc1 && !stop; tile += gridDim.x) {
                 const int f = frame_of_tc_tile(B, tile);
                 const FrameDesc& F = B.f[f];
                 const int pt = tile - F.tc_tile_base;
@@ -356,7 +356,7 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
             for (int di = 0; di < kTcMaxOff; ++di) ksmask[di] = P.tc_ksmask[di];
             uint32_t g0 = 0, acc_cnt = 0;
             bool stop = false;
-            for (int tile = blockIdx.x; tile < B.tc_tiles && !stop; tile += gridDim.x) {
+            for (int tile = tc0 + (int)blockIdx.x; tile < tc1 && !stop; tile += gridDim.x) {
                 const FrameDesc& F = B.f[frame_of_tc_tile(B, tile)];
                 const int nbk = (F.nt + kTcBlk - 1) / kTcBlk;
                 int rel = 0;   // next block whose stage is still held by the MMA
@@ -412,7 +412,7 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
         const uint32_t lane_base = tmem + ((uint32_t)(warp * 32) << 16);
         uint32_t g0 = 0, acc_cnt = 0;
         bool stop = false;
-        for (int tile = blockIdx.x; tile < B.tc_tiles && !stop; tile += gridDim.x) {
+        for (int tile = tc0 + (int)blockIdx.x; tile < tc1 && !stop; tile += gridDim.x) {
             const FrameDesc& F = B.f[frame_of_tc_tile(B, tile)];
             const int pt = tile - F.tc_tile_base;
             const int T = F.nt;

@@ -539,15 +539,17 @@ bool batch_has_int(const Batch& B)
     return false;
 }
 
-// pix0 / pix_end: the batch pixels this launch covers (pix_end < 0: all)
+// pix0 / pix_end: the batch pixels this launch covers, tc0 / tc1 the
+// tensor-core init's 128-pixel tiles of the same frames (negative: all)
 rt3d_status launch_init(rt3d_ctx* c, const KParams& K, const Batch& B, Work W, cudaStream_t s,
-                        bool dump, bool compact_only, int pix0 = 0, int pix_end = -1)
+                        bool dump, bool compact_only, int pix0 = 0, int pix_end = -1, int tc0 = 0, int tc1 = -1)
 {
     if (pix_end < 0) pix_end = B.total_pix;
+    if (tc1 < 0) tc1 = B.tc_tiles;
     // the tensor-core kernel takes the dense frames of a cold start; the
     // CUDA-core kernel the rest (it skips those frames)
-    const bool tc = K.tc_mode != 0 && !compact_only && B.tc_tiles > 0;
-    if (!tc || compact_only || batch_has_int(B)) {
+    const bool tc = K.tc_mode != 0 && !compact_only && tc1 > tc0;
+    if (!tc || compact_only || batch_has_int(B) || B.tc_tiles == 0) {
         const size_t smem = init_smem(K, K.peak_sep);
         const int warps = init_warps(K.peak_sep);
         const int grid = (pix_end - pix0 + warps - 1) / warps;
@@ -564,12 +566,12 @@ rt3d_status launch_init(rt3d_ctx* c, const KParams& K, const Batch& B, Work W, c
     if (tc) {
         if (!c->n_sms) RT3D_CUDA(cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, c->cfg.device));
         const int smem = tc_smem_bytes(K.tc_nd, K.tc_stages);
-        const int grid = std::min(c->n_sms, B.tc_tiles);
+        const int grid = std::min(c->n_sms, tc1 - tc0);
         auto fn = dump ? k_init_tc<true> : k_init_tc<false>;
         RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         {
             LaunchScope ls(c, s, kcInitTc);
-            fn<<<grid, kTcThreads, smem, s>>>(c->d_rec, W, c->d_band);
+            fn<<<grid, kTcThreads, smem, s>>>(c->d_rec, W, c->d_band, tc0, tc1);
         }
         RT3D_CUDA(cudaGetLastError());
     }
@@ -775,17 +777,18 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
     // Two chains of frames (init, loop, finaliser each) captured as parallel
     // branches: each chain's launches fill the other's partly empty last wave.
     // Frames are independent, so the results are those of one chain.  Kept as
-    // one chain for the learned form and the tensor-core init (their kernels
-    // cover the whole batch) and while kernel times are recorded (so each
-    // kernel's duration is its own).
-    int n0 = 0, split_tiles = 0, split_pix = 0;
-    if (n >= 2 && B.tc_tiles == 0 && K.depth_den != RT3D_DEPTH_LEARNED && !c->profiling) {
+    // one chain for the learned form (its network kernels cover the whole
+    // batch) and while kernel times are recorded (so each kernel's duration is
+    // its own).
+    int n0 = 0, split_tiles = 0, split_pix = 0, split_tc = 0;
+    if (n >= 2 && K.depth_den != RT3D_DEPTH_LEARNED && !c->profiling) {
         // first chain: the frames whose tiles end by half the batch's tiles (at least one)
         auto tiles_end = [&](int i) { return i + 1 < n ? B.f[i + 1].tile_base : B.total_tiles; };
         while (n0 < n - 1 && 2 * tiles_end(n0) <= B.total_tiles) ++n0;
         if (n0 == 0) n0 = 1;
         split_tiles = B.f[n0].tile_base;
         split_pix = B.f[n0].pix_base;
+        split_tc = B.f[n0].tc_tile_base;
     }
     const GraphKey key{B.total_pix, B.total_tiles, p->n_iter, p->warm_start != 0,
                        init_warps(K.peak_sep), c->profiling ? 1 : 0, init_smem(K, K.peak_sep),
@@ -814,13 +817,20 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
                 if (e == cudaSuccess && cst == RT3D_OK) cst = launch_loop(c, B, c->cap_stream, p->n_iter);
                 if (e == cudaSuccess && cst == RT3D_OK) cst = launch_final(c, B, c->cap_stream, ran);
             } else {
+                // the tensor-core init holds most of an SM's shared memory, so it
+                // runs once over the batch before the fork (a split one would
+                // lock the other chain's loop kernels out of the SMs)
+                const bool tc_init = B.tc_tiles > 0;
+                if (e == cudaSuccess && tc_init) cst = launch_init(c, K, B, c->W, c->cap_stream, false, warm);
                 // fork: frames [n0, n) on the second capture stream
                 if (e == cudaSuccess) e = cudaEventRecord(c->ev_fork, c->cap_stream);
                 if (e == cudaSuccess) e = cudaStreamWaitEvent(c->cap_stream2, c->ev_fork, 0);
                 const int t1 = B.total_tiles - split_tiles;
-                if (e == cudaSuccess) cst = launch_init(c, K, B, c->W, c->cap_stream, false, warm, 0, split_pix);
-                if (e == cudaSuccess && cst == RT3D_OK)
-                    cst = launch_init(c, K, B, c->W, c->cap_stream2, false, warm, split_pix, B.total_pix);
+                if (e == cudaSuccess && cst == RT3D_OK && !tc_init)
+                    cst = launch_init(c, K, B, c->W, c->cap_stream, false, warm, 0, split_pix, 0, split_tc);
+                if (e == cudaSuccess && cst == RT3D_OK && !tc_init)
+                    cst = launch_init(c, K, B, c->W, c->cap_stream2, false, warm, split_pix, B.total_pix, split_tc,
+                                      B.tc_tiles);
                 if (e == cudaSuccess && cst == RT3D_OK) cst = launch_loop(c, B, c->cap_stream, p->n_iter, 0, split_tiles);
                 if (e == cudaSuccess && cst == RT3D_OK)
                     cst = launch_loop(c, B, c->cap_stream2, p->n_iter, split_tiles, t1);
