@@ -386,6 +386,76 @@ k_phase_a(const CallRecord* __restrict__ rec, const Work W, int first, int tile0
 constexpr int kHaloH = kTileH + 2 * kMaxWinR, kHaloW = kTileW + 2 * kMaxWinR;
 constexpr int kHalo = kHaloH * kHaloW;
 
+// Window cells inside the lateral radius.  A neighbourhood sum (APSS moments,
+// intensity low-pass) runs over the cells (di, dj) of the (2R+1)^2 window whose
+// lateral distance, in units of the kernel radius h, is below one: the unit
+// disk.  The cells are listed once per tile, row-major (the order the sums run
+// in), with what the sums need of them, so the per-point loops carry no window
+// index arithmetic and no radius test.  The first three warps build the list:
+// win_vote (one vote per warp, before the tile's first barrier) and win_fill
+// (entries at their ranks, after it; readable after the next barrier).
+constexpr int kMaxWinCells = (2 * kMaxWinR + 1) * (2 * kMaxWinR + 1);
+static_assert(kMaxWinCells <= 96 && kTileThreads >= 96, "three warps vote over the window cells");
+
+__device__ __forceinline__ void win_cell(int t, int R, float px, int& di, int& dj, float& x, float& y,
+                                         float& r2)
+{
+    const int n = 2 * R + 1;
+    di = t / n - R;
+    dj = t % n - R;
+    y = (float)di * px;
+    x = (float)dj * px;
+    r2 = x * x + y * y;
+}
+
+__device__ __forceinline__ void win_vote(unsigned* vote, int R, float px)
+{
+    if (threadIdx.x >= 96) return;
+    const int t = threadIdx.x;
+    bool in = false;
+    if (t < (2 * R + 1) * (2 * R + 1)) {
+        int di, dj;
+        float x, y, r2;
+        win_cell(t, R, px, di, dj, x, y, r2);
+        in = r2 < 1.0f;
+    }
+    const unsigned m = __ballot_sync(0xffffffffu, in);
+    if ((t & 31) == 0) vote[t >> 5] = m;
+}
+
+// Cell list entries.  APSS (kApss): {x, y, r2, halo offset} and the cell's
+// packed indicator words -- (di+4) | (dj+4) << 12, di^2 | dj^2 << 13 and
+// 1 | (di dj + 16) << 9 -- whose multiples by a slot count sum, field by field
+// and without carries (at most 4 slots x 81 cells), to the exact pixel-offset
+// moments of the weighted neighbours.  Low-pass: {r2, halo offset}.
+template <bool kApss>
+__device__ __forceinline__ int win_fill(const unsigned* vote, int R, float px, int hstride, float4* g4,
+                                        uint4* ind, float2* g2)
+{
+    const unsigned v0 = vote[0], v1 = vote[1], v2 = vote[2];
+    const int t = threadIdx.x;
+    if (t < 96) {
+        const int w = t >> 5, l = t & 31;
+        const unsigned mw = w == 0 ? v0 : (w == 1 ? v1 : v2);
+        if ((mw >> l) & 1u) {
+            const int rank = (w > 0 ? __popc(v0) : 0) + (w > 1 ? __popc(v1) : 0) + __popc(mw & ((1u << l) - 1u));
+            int di, dj;
+            float x, y, r2;
+            win_cell(t, R, px, di, dj, x, y, r2);
+            const int q = di * hstride + dj;
+            if constexpr (kApss) {
+                g4[rank] = make_float4(x, y, r2, __int_as_float(q));
+                ind[rank] = make_uint4((unsigned)(di + 4) | ((unsigned)(dj + 4) << 12),
+                                       (unsigned)(di * di) | ((unsigned)(dj * dj) << 13),
+                                       1u | ((unsigned)(di * dj + 16) << 9), 0u);
+            } else {
+                g2[rank] = make_float2(r2, __int_as_float(q));
+            }
+        }
+    }
+    return __popc(v0) + __popc(v1) + __popc(v2);
+}
+
 // APSS projection of one point (Results, "Depth update"; Guennebaud & Gross):
 // weighted algebraic-sphere fit s(x) = u0 + u1 x + u2 y + z + u4 |x|^2 over
 // the window (local coordinates scaled by 1/h), solved in centred form --
@@ -393,69 +463,65 @@ constexpr int kHalo = kHaloH * kHaloW;
 // weighted means -- and projection along the line of sight onto s = 0.
 // Dead or absent slots hold a far sentinel depth, so their weight is exactly
 // zero; each thread accumulates only the slots inside the window (in slot
-// order), and window offsets outside the lateral radius are skipped uniformly
-// across the warp.
+// order) over the cells of the unit disk (win_fill's list; qc is the point's
+// halo index).
 template <int K>
-__device__ float apss_point(const float* st, int hstride, int R, int ci, int cj, float tn,
+__device__ float apss_point(const float* st, const float4* wg, const uint4* wi, int n_off, int qc, float tn,
                             const KParams& P, int T)
 {
     const float inv_h = 1.0f / P.apss_h;
-    const float px = P.pitch * inv_h;
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sz = 0.f, Sq = 0.f;
     float Sxx = 0.f, Sxy = 0.f, Syy = 0.f, Sxq = 0.f, Syq = 0.f, Sqq = 0.f;
     float Sxz = 0.f, Syz = 0.f, Sqz = 0.f;
-    // indicator sums of the pixel offsets of weighted neighbours (exact integers)
-    float nw = 0.f, si = 0.f, sj = 0.f, sii = 0.f, sjj = 0.f, sij = 0.f;
-    for (int di = -R; di <= R; ++di) {
-        const float y = (float)di * px;
-        for (int dj = -R; dj <= R; ++dj) {
-            const float x = (float)dj * px;
-            const float r2 = x * x + y * y;
-            if (!(r2 < 1.0f)) continue;
-            const int q = (ci + di) * hstride + (cj + dj);
-            float zk[K], d2k[K];
-            unsigned in = 0u;
+    // packed indicator sums of the pixel offsets of weighted neighbours (exact)
+    unsigned ia = 0u, ib = 0u, ic = 0u;
+    for (int o = 0; o < n_off; ++o) {
+        const float4 gc = wg[o];
+        const float x = gc.x, y = gc.y, r2 = gc.z;
+        const int q = qc + __float_as_int(gc.w);
+        float zk[K], d2k[K];
+        unsigned in = 0u;
 #pragma unroll
-            for (int m = 0; m < K; ++m) {
-                zk[m] = (st[m * kHalo + q] - tn) * inv_h;
-                d2k[m] = r2 + zk[m] * zk[m];
-                if (d2k[m] < 1.0f) in |= 1u << m;
-            }
-            const float cnt = (float)__popc(in);
-            // only the slots inside the window: the others have weight exactly
-            // zero and would leave every sum unchanged
-            while (in) {
-                const int m = __ffs(in) - 1;
-                in &= in - 1u;
-                float z = zk[0], d2 = d2k[0];
-#pragma unroll
-                for (int j = 1; j < K; ++j)
-                    if (m == j) {
-                        z = zk[j];
-                        d2 = d2k[j];
-                    }
-                float w = 1.0f - d2;
-                w *= w;
-                w = w * w;
-                const float wx = w * x, wy = w * y, wq = w * d2;
-                S0 += w; Sx += wx; Sy += wy; Sz += w * z; Sq += wq;
-                Sxx += wx * x; Sxy += wx * y; Syy += wy * y;
-                Sxq += wx * d2; Syq += wy * d2; Sqq += wq * d2;
-                Sxz += wx * z; Syz += wy * z; Sqz += wq * z;
-            }
-            nw += cnt;
-            si += cnt * (float)di;
-            sj += cnt * (float)dj;
-            sii += cnt * (float)(di * di);
-            sjj += cnt * (float)(dj * dj);
-            sij += cnt * (float)(di * dj);
+        for (int m = 0; m < K; ++m) {
+            zk[m] = (st[m * kHalo + q] - tn) * inv_h;
+            d2k[m] = r2 + zk[m] * zk[m];
+            if (d2k[m] < 1.0f) in |= 1u << m;
         }
+        const unsigned cnt = __popc(in);
+        // only the slots inside the window: the others have weight exactly
+        // zero and would leave every sum unchanged
+        while (in) {
+            const int m = __ffs(in) - 1;
+            in &= in - 1u;
+            float z = zk[0], d2 = d2k[0];
+#pragma unroll
+            for (int j = 1; j < K; ++j)
+                if (m == j) {
+                    z = zk[j];
+                    d2 = d2k[j];
+                }
+            float w = 1.0f - d2;
+            w *= w;
+            w = w * w;
+            const float wx = w * x, wy = w * y, wq = w * d2;
+            S0 += w; Sx += wx; Sy += wy; Sz += w * z; Sq += wq;
+            Sxx += wx * x; Sxy += wx * y; Syy += wy * y;
+            Sxq += wx * d2; Syq += wy * d2; Sqq += wq * d2;
+            Sxz += wx * z; Syz += wy * z; Sqz += wq * z;
+        }
+        const uint4 pk = wi[o];
+        ia += cnt * pk.x;
+        ib += cnt * pk.y;
+        ic += cnt * pk.z;
     }
-    const long long n = (long long)nw;
+    const long long n = (long long)(ic & 511u);
     if (n < P.apss_min_nb) return tn;
-    const long long vii = n * (long long)sii - (long long)si * (long long)si;
-    const long long vjj = n * (long long)sjj - (long long)sj * (long long)sj;
-    const long long vij = n * (long long)sij - (long long)si * (long long)sj;
+    const long long si = (long long)(ia & 4095u) - 4 * n, sj = (long long)(ia >> 12) - 4 * n;
+    const long long sii = (long long)(ib & 8191u), sjj = (long long)(ib >> 13);
+    const long long sij = (long long)(ic >> 9) - 16 * n;
+    const long long vii = n * sii - si * si;
+    const long long vjj = n * sjj - sj * sj;
+    const long long vij = n * sij - si * sj;
     if (vii * vjj - vij * vij == 0) return tn;      // collinear pixel offsets
     const float iw = 1.0f / S0;
     const float mx = Sx * iw, my = Sy * iw, mz = Sz * iw, mq = Sq * iw;
@@ -583,12 +649,18 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, in
     __shared__ int s_warp[kTileThreads / 32];
     __shared__ float4 coef[kCoefLen];
     __shared__ WarpSums<K, K> ws[kTileThreads / 32];
+    __shared__ float4 s_wg[kMaxWinCells];
+    __shared__ uint4 s_wi[kMaxWinCells];
+    __shared__ unsigned s_vote[3];
     load_irf_coef(pad, coef, P);
     const TileCtx c = tile_ctx(B, tile0);
     const FrameDesc& F = B.f[c.fi];
     const int np = F.npix, S = W.stride, R = P.win_r;
     const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
     const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
+    const bool apss = P.depth_den == RT3D_DEPTH_APSS || P.depth_den == RT3D_DEPTH_LEARNED;
+    const float apss_px = P.pitch * (1.0f / P.apss_h);
+    if (apss) win_vote(s_vote, R, apss_px);
     if (alive_from_b)
         load_halo<K, false>(c, F, R, W.t_half, S, F.pix_base, W.alive_b + F.pix_base, S, st, nullptr, 0, 0,
                             nullptr);
@@ -597,6 +669,7 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, in
     __syncthreads();
     const int hstride = kTileW + 2 * R;
     const int q0 = (c.li + R) * hstride + (c.lj + R);
+    const int n_off = apss ? win_fill<true>(s_vote, R, apss_px, hstride, s_wg, s_wi, nullptr) : 0;
     for (int k = 0; k < K; ++k) s_tn[k][threadIdx.x] = st[k * kHalo + q0];
     if (alive_from_b && c.inb)
         for (int k = 0; k < K; ++k) F.alive[(long long)k * np + lp] = st[k * kHalo + q0] != kDeadDepth ? 1 : 0;
@@ -606,7 +679,8 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, in
         for (int i = threadIdx.x; i < n_pts; i += kTileThreads) {
             const int px = s_pts[i] >> 2, k = s_pts[i] & 3;
             const int ci = px / kTileW + R, cj = px % kTileW + R;
-            s_tn[k][px] = apss_point<K>(st, hstride, R, ci, cj, st[k * kHalo + ci * hstride + cj], P, F.nt);
+            const int qc = ci * hstride + cj;
+            s_tn[k][px] = apss_point<K>(st, s_wg, s_wi, n_off, qc, st[k * kHalo + qc], P, F.nt);
         }
     } else if (P.depth_den == RT3D_DEPTH_LEARNED) {
         // the network's move where it stays within the fallback bound, APSS elsewhere
@@ -622,7 +696,7 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, in
                     continue;
                 }
             }
-            s_tn[k][px] = apss_point<K>(st, hstride, R, ci, cj, t0, P, F.nt);
+            s_tn[k][px] = apss_point<K>(st, s_wg, s_wi, n_off, ci * hstride + cj, t0, P, F.nt);
         }
     }
     __syncthreads();
@@ -683,16 +757,21 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next, int t
     __shared__ int s_warp[kTileThreads / 32];
     __shared__ float4 coef[kCoefLen];
     __shared__ WarpSums<K, K> ws[kTileThreads / 32];
+    __shared__ float2 s_wg[kMaxWinCells];
+    __shared__ unsigned s_vote[3];
     load_irf_coef(pad, coef, P);
     const TileCtx c = tile_ctx(B, tile0);
     const FrameDesc& F = B.f[c.fi];
     const int np = F.npix, S = W.stride, R = P.win_r;
     const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
     const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
+    const float int_px = P.pitch * (1.0f / P.int_h);
+    if (P.int_den) win_vote(s_vote, R, int_px);
     load_halo<K, true>(c, F, R, F.t, np, 0, F.alive, np, st, W.r_half, S, F.pix_base, sr);
     __syncthreads();
     const int hstride = kTileW + 2 * R;
     const int q0 = (c.li + R) * hstride + (c.lj + R);
+    const int n_off = P.int_den ? win_fill<false>(s_vote, R, int_px, hstride, nullptr, nullptr, s_wg) : 0;
     for (int k = 0; k < K; ++k) {
         const bool al = st[k * kHalo + q0] != kDeadDepth;
         s_an[k][threadIdx.x] = 0;
@@ -701,7 +780,7 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next, int t
     const int n_pts = compact_points(st, R, K, c.inb, c.li, c.lj, s_pts, s_warp);
     __syncthreads();
     {
-        const float inv_h = 1.0f / P.int_h, px = P.pitch * inv_h;
+        const float inv_h = 1.0f / P.int_h;
         for (int i = threadIdx.x; i < n_pts; i += kTileThreads) {
             const int pxl = s_pts[i] >> 2, k = s_pts[i] & 3;
             const int ci = pxl / kTileW + R, cj = pxl % kTileW + R;
@@ -710,23 +789,20 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next, int t
             if (P.int_den) {
                 const float tn = st[k * kHalo + qc];
                 float num = 0.0f, den = 0.0f;
-                for (int di = -R; di <= R; ++di) {
-                    const float y = (float)di * px;
-                    for (int dj = -R; dj <= R; ++dj) {
-                        const float x = (float)dj * px;
-                        const float r2 = x * x + y * y;
-                        if (!(r2 < 1.0f)) continue;
-                        const int q = (ci + di) * hstride + (cj + dj);
+                // the cells of the unit disk (win_fill's list)
+                for (int o = 0; o < n_off; ++o) {
+                    const float2 gc = s_wg[o];
+                    const float r2 = gc.x;
+                    const int q = qc + __float_as_int(gc.y);
 #pragma unroll
-                        for (int m = 0; m < K; ++m) {
-                            const float z = (st[m * kHalo + q] - tn) * inv_h;
-                            const float d2 = r2 + z * z;
-                            float w = 1.0f - d2;
-                            w *= w;
-                            w = d2 < 1.0f ? w * w : 0.0f;
-                            num += w * sr[m * kHalo + q];
-                            den += w;
-                        }
+                    for (int m = 0; m < K; ++m) {
+                        const float z = (st[m * kHalo + q] - tn) * inv_h;
+                        const float d2 = r2 + z * z;
+                        float w = 1.0f - d2;
+                        w *= w;
+                        w = d2 < 1.0f ? w * w : 0.0f;
+                        num += w * sr[m * kHalo + q];
+                        den += w;
                     }
                 }
                 rbar = num / den;
