@@ -10,6 +10,8 @@ steady-state launch.  Cases:
   learned       8 frames of 256x256x2048 random shapes, two PALM iterations
                 with the learned depth denoiser (the committed checkpoint)
   loop          4 frames of 141x141x4096 (the benchmark scene), 20 iterations
+  loop16        16 frames of the benchmark scene (the benchmark's batch; two
+                chains of 8 frames each), 20 iterations
 
 Usage: python paper_1905_06700_b300/profile_cases.py CASE
 """
@@ -40,10 +42,10 @@ def case(name: str):
         base = scenes.random_shapes(256, 256, 2048, seed=0)
         prm = dict(scenes.make_params(base), n_iter=2, depth_denoiser=2)
         nb, mk = 8, (lambda f: scenes.random_shapes(256, 256, 2048, seed=200000 + f))
-    elif name == "loop":
+    elif name in ("loop", "loop16"):
         base = scenes.net_object_wall()
         prm = scenes.make_params(base)
-        nb, mk = 4, (lambda f: scenes.net_object_wall(seed=1 + f))
+        nb, mk = (4 if name == "loop" else 16), (lambda f: scenes.net_object_wall(seed=1 + f))
     else:
         raise SystemExit(f"unknown case {name!r}")
     B.build()
