@@ -19,9 +19,14 @@
  * the reading used here is stated at the function; every such reading is
  * listed in the design notes of the repository.
  *
- * Parity status: every function below is pinned by a CPU test except the full
- * multi-iteration loop, whose combined output has no worked example in the
- * paper ("parity unpinned" for or_reconstruct as a whole; its steps are pinned).
+ * Parity status: every function below is pinned by a CPU test.  The paper has
+ * no worked example of the full multi-iteration loop; or_palm and
+ * or_reconstruct as a whole are pinned by properties the method has: noise-free
+ * counts of two slanted planes are a fixed point of the whole iteration with
+ * both denoisers and are recovered from a perturbed start, and the whole
+ * reconstruction is equivariant under a shift of the time axis and under
+ * transposing or mirroring the pixel grid.  The order of the steps within an
+ * iteration is the paper's (Fig. 2) as written; no property separates it.
  */
 #ifndef RT3D_ORACLE_H
 #define RT3D_ORACLE_H
