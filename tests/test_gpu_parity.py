@@ -304,6 +304,35 @@ def test_capacity_overflow_is_reported_not_faulted(orc):
     assert ctx2.device_status() == R.RT3D_OK
 
 
+def test_dense_pixels_init_and_reconstruct_match_oracle(orc):
+    """Pixels with ~400 nonzero bins of 1024 (background 0.5 photons per bin):
+    more entries than the init's per-warp stage holds (re-read and emitted to
+    global memory), one cluster spanning the whole histogram (several filter
+    chunks), the multi-round cluster search, and long bin runs per lane in the
+    loop's sums."""
+    sc = scenes.small_random(12, 10, 1024, n_comp=2, seed=31, mean_signal=50.0, bkg=0.5)
+    z, prm, ctx, g, o = _init_pair(orc, sc)
+    nnz = np.count_nonzero(z, axis=2)
+    assert nnz.min() > 256
+    assert np.array_equal(g["alive"], o.alive)
+    assert np.array_equal(g["t"].astype(np.float64), o.t)
+    np.testing.assert_allclose(g["r"], o.r, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(g["b"], o.b, rtol=1e-5, atol=1e-12)
+    seg, ent, used = ctx.get_sparse(sc.h * sc.w, int(nnz.sum()))
+    assert used == int(nnz.sum())
+    fr = orc.OFrame(z)
+    for p in range(sc.h * sc.w):
+        s, n = seg[p]
+        e = ent[s:s + n]
+        assert np.array_equal(e >> 16, fr.bin[fr.off[p]:fr.off[p + 1]])
+        assert np.array_equal(e & 0xFFFF, fr.cnt[fr.off[p]:fr.off[p + 1]])
+    g = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
+    o, probe = oracle_with_probe(orc, sc, z, prm)
+    ill = ill_conditioned(o, probe, TOL_T, TOL_R)
+    stats = compare_clouds(g, o, sc.t, TOL_T, TOL_R, ill=ill, max_ill_frac=0.02, label="dense pixels")
+    print("dense pixels", stats)
+
+
 def test_empty_histograms_give_no_points(orc):
     sc = scenes.small_random(7, 9, 128, n_comp=1, seed=1)
     z = np.zeros((sc.h, sc.w, sc.t), np.uint16)
