@@ -333,6 +333,48 @@ def test_dense_pixels_init_and_reconstruct_match_oracle(orc):
     print("dense pixels", stats)
 
 
+def test_longest_histogram_and_irf_match_oracle(orc):
+    """The largest histogram and IRF the library accepts (16384 bins, a
+    256-sample gamma IRF): eight filter taps per lane, 16-bit bin indices at
+    their top, the loop's interval table at its longest."""
+    irf = scenes.gamma_irf(6.0, 12.0, 256)
+    sc = scenes.small_random(3, 5, 16384, n_comp=2, seed=41, mean_signal=40.0, bkg=0.002, irf=irf)
+    z, prm, ctx, g, o = _init_pair(orc, sc)
+    assert np.array_equal(g["alive"], o.alive)
+    assert np.array_equal(g["t"].astype(np.float64), o.t)
+    np.testing.assert_allclose(g["r"], o.r, rtol=1e-5, atol=1e-6)
+    g = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
+    o, probe = oracle_with_probe(orc, sc, z, prm)
+    # depths near 16384 bins are FP32 numbers 2^-9 apart: the depth tolerance
+    # is four of those spacings (1e-3 bins is below the format's resolution)
+    tol_t = max(TOL_T, 4.0 * float(np.spacing(np.float32(sc.t))))
+    ill = ill_conditioned(o, probe, tol_t, TOL_R)
+    stats = compare_clouds(g, o, sc.t, tol_t, TOL_R, ill=ill, max_ill_frac=0.02, label="T=16384, L=256")
+    print("T=16384, L=256", stats)
+
+
+def test_filter_range_guard_is_reported_and_spares_other_pixels(orc):
+    """A pixel whose photons times the largest tap reach 2^31 cannot have an
+    exact int32 filter: the call reports RT3D_E_RANGE and that pixel keeps no
+    points, while every other pixel equals the oracle's."""
+    from paper_1905_06700_b300 import rt3d as R
+    sc = scenes.small_random(6, 7, 512, n_comp=2, seed=43)
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc)
+    kern = orc.lmf_kernel(oracle_irf(orc, sc), prm["lmf_delta_rel"], prm["lmf_frac_bits"])
+    z[2, 3, :] = 65535
+    assert int(z[2, 3].sum()) * int(np.abs(kern).max()) >= 2 ** 31
+    ctx = make_ctx(sc, k=prm["k_max"])
+    g = np_of(ctx.init(prm, dense=upload_u16(z)))
+    assert ctx.device_status() == R.RT3D_E_RANGE
+    assert not g["alive"][:, 2, 3].any()
+    o = orc.init(z, None, oracle_irf(orc, sc), prm)
+    keep = np.ones((sc.h, sc.w), bool)
+    keep[2, 3] = False
+    assert np.array_equal(g["alive"][:, keep], o.alive[:, keep])
+    assert np.array_equal(g["t"][:, keep].astype(np.float64), o.t[:, keep])
+
+
 def test_empty_histograms_give_no_points(orc):
     sc = scenes.small_random(7, 9, 128, n_comp=1, seed=1)
     z = np.zeros((sc.h, sc.w, sc.t), np.uint16)
