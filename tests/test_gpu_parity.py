@@ -254,6 +254,28 @@ def test_batch_results_equal_single_frame_results(orc):
             assert np.array_equal(np.asarray(s[k]), np.asarray(b[k])), k
 
 
+def test_largest_batch_equals_single_frames(orc):
+    """The largest batch (64 frames) of ragged sizes in one call (two chains of frames
+    in the captured graph) give bitwise the single-frame results."""
+    from paper_1905_06700_b300 import rt3d as R
+    irf = scenes.gaussian_irf(3.0, 12)
+    scs = []
+    for i in range(R.MAX_BATCH):
+        s = scenes.small_random(3 + i % 7, 5 + (i * 3) % 11, 128, n_comp=2, seed=100 + i)
+        s.irf = irf
+        scs.append(s)
+    zs = [orc.synthesize(scenes.sampling_tables(s)) for s in scs]
+    prm = workload_params(scs[0])
+    ctx = R.Context(9, 15, 128, 2, irf.samples, irf.origin, max_batch=len(scs))
+    frames = [dict(dense=upload_u16(z)) for z in zs]
+    batch = [np_of(o) for o in ctx.reconstruct_batch(prm, frames)]
+    assert ctx.device_status() == R.RT3D_OK
+    for z, b in zip(zs, batch):
+        s = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
+        for k in ("t", "r", "alive", "b", "n_points"):
+            assert np.array_equal(np.asarray(s[k]), np.asarray(b[k])), k
+
+
 def test_host_entry_point_equals_device_path(orc):
     from paper_1905_06700_b300 import rt3d as R
     sc = scenes.small_random(13, 29, 300, n_comp=2, seed=4)
