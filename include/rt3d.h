@@ -243,7 +243,12 @@ rt3d_status rt3d_reconstruct_host(rt3d_ctx_t* ctx, const rt3d_frame* f, const rt
  * out[i].  One copy per input array into a context staging area (grown to the
  * call's size on first use, freed by rt3d_destroy), one batched
  * reconstruction (as rt3d_reconstruct_batch), one copy back per result array;
- * with params.warm_start, out[i] is also the starting state.  Synchronous:
+ * with params.warm_start, out[i] is also the starting state.  When every
+ * frame is dense and holds at least 64 MiB of histogram, the frames run in up
+ * to four groups: their copies go on a stream of the context (after the work
+ * already queued on `stream`) and each group's reconstruction starts as soon
+ * as its own frames have arrived, overlapping the next groups' copies (the
+ * results are per frame, so they equal the single batch's).  Synchronous:
  * returns after the results are on the host.  Page-locked host buffers give
  * full link bandwidth.  Errors: RT3D_E_INVALID for a NULL argument, n < 1 or
  * anything rt3d_reconstruct_batch rejects; RT3D_E_NOMEM if the staging cannot

@@ -136,6 +136,10 @@ struct rt3d_ctx {
     // staging of rt3d_reconstruct_batch_host (grown on demand)
     unsigned char* s_batch = nullptr;
     size_t s_batch_cap = 0;
+    // its copy stream and group events (large dense frames: copies of the next
+    // group overlap the reconstruction of the current one)
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_copy[5] = {};
 };
 
 namespace {
@@ -1015,6 +1019,9 @@ void rt3d_destroy(rt3d_ctx_t* c)
     if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    for (auto ev : c->ev_copy)
+        if (ev) cudaEventDestroy(ev);
     for (auto ev : c->event_pool) cudaEventDestroy(ev);
     delete c;
 }
@@ -1216,6 +1223,12 @@ rt3d_status rt3d_reconstruct_host(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d
     return RT3D_OK;
 }
 
+// host batches: frames of at least this many dense bytes are copied in groups
+// that overlap the reconstruction (a 64 MB copy takes ~1.2 ms on the host link,
+// more than one frame's reconstruction)
+constexpr size_t kHostGroupMinBytes = 64ull << 20;
+constexpr int kHostMaxGroups = 4;
+
 rt3d_status rt3d_reconstruct_batch_host(rt3d_ctx_t* c, int n, const rt3d_frame* f, const rt3d_params* p,
                                         rt3d_result* out, void* stream)
 {
@@ -1265,46 +1278,78 @@ rt3d_status rt3d_reconstruct_batch_host(rt3d_ctx_t* c, int n, const rt3d_frame* 
     unsigned char* base = c->s_batch;
     std::vector<rt3d_frame> df(f, f + n);
     std::vector<rt3d_result> dr(n);
-    for (int i = 0; i < n; ++i) {
+    // Large dense frames are link-bound: the batch runs in up to four groups
+    // of frames whose copies, on a copy stream, run ahead of the groups'
+    // reconstructions (each group one batched call; results are per frame, so
+    // they equal the single call's).  Otherwise one group on `s`.
+    bool big_dense = n >= 2;
+    for (int i = 0; i < n && big_dense; ++i)
+        big_dense = f[i].dense && sizeof(uint16_t) * (size_t)sp[i].npix * f[i].t >= kHostGroupMinBytes;
+    const int G = big_dense ? std::min(n, kHostMaxGroups) : 1;
+    cudaStream_t cs = s;
+    if (G > 1) {
+        if (!c->copy_stream) RT3D_CUDA(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking));
+        for (int g = 0; g <= G; ++g)
+            if (!c->ev_copy[g]) RT3D_CUDA(cudaEventCreateWithFlags(&c->ev_copy[g], cudaEventDisableTiming));
+        cs = c->copy_stream;
+        // the copies follow the work already queued on `s`
+        RT3D_CUDA(cudaEventRecord(c->ev_copy[G], s));
+        RT3D_CUDA(cudaStreamWaitEvent(cs, c->ev_copy[G], 0));
+    }
+    auto copy_in = [&](int i) -> rt3d_status {
         const Span& x = sp[i];
         if (f[i].dense) {
             df[i].dense = reinterpret_cast<const uint16_t*>(base + x.dense);
             RT3D_CUDA(cudaMemcpyAsync(base + x.dense, f[i].dense, sizeof(uint16_t) * x.npix * f[i].t,
-                                      cudaMemcpyHostToDevice, s));
+                                      cudaMemcpyHostToDevice, cs));
         }
         if (f[i].csr_off) {
             df[i].csr_off = reinterpret_cast<const uint32_t*>(base + x.off);
             df[i].csr_ent = reinterpret_cast<const uint32_t*>(base + x.ent);
             RT3D_CUDA(cudaMemcpyAsync(base + x.off, f[i].csr_off, sizeof(uint32_t) * (x.npix + 1),
-                                      cudaMemcpyHostToDevice, s));
+                                      cudaMemcpyHostToDevice, cs));
             if (x.nent > 0)
                 RT3D_CUDA(cudaMemcpyAsync(base + x.ent, f[i].csr_ent, sizeof(uint32_t) * x.nent,
-                                          cudaMemcpyHostToDevice, s));
+                                          cudaMemcpyHostToDevice, cs));
         }
         if (f[i].gain) {
             df[i].gain = reinterpret_cast<const float*>(base + x.gain);
-            RT3D_CUDA(cudaMemcpyAsync(base + x.gain, f[i].gain, sizeof(float) * x.npix, cudaMemcpyHostToDevice, s));
+            RT3D_CUDA(cudaMemcpyAsync(base + x.gain, f[i].gain, sizeof(float) * x.npix, cudaMemcpyHostToDevice, cs));
         }
         dr[i] = rt3d_result{reinterpret_cast<float*>(base + x.t), reinterpret_cast<float*>(base + x.r),
                             base + x.a, reinterpret_cast<float*>(base + x.b),
                             reinterpret_cast<int32_t*>(base + x.np)};
         if (p->warm_start) {
-            RT3D_CUDA(cudaMemcpyAsync(dr[i].t, out[i].t, sizeof(float) * Kp * x.npix, cudaMemcpyHostToDevice, s));
-            RT3D_CUDA(cudaMemcpyAsync(dr[i].r, out[i].r, sizeof(float) * Kp * x.npix, cudaMemcpyHostToDevice, s));
-            RT3D_CUDA(cudaMemcpyAsync(dr[i].alive, out[i].alive, (size_t)Kp * x.npix, cudaMemcpyHostToDevice, s));
-            RT3D_CUDA(cudaMemcpyAsync(dr[i].b, out[i].b, sizeof(float) * x.npix, cudaMemcpyHostToDevice, s));
+            RT3D_CUDA(cudaMemcpyAsync(dr[i].t, out[i].t, sizeof(float) * Kp * x.npix, cudaMemcpyHostToDevice, cs));
+            RT3D_CUDA(cudaMemcpyAsync(dr[i].r, out[i].r, sizeof(float) * Kp * x.npix, cudaMemcpyHostToDevice, cs));
+            RT3D_CUDA(cudaMemcpyAsync(dr[i].alive, out[i].alive, (size_t)Kp * x.npix, cudaMemcpyHostToDevice, cs));
+            RT3D_CUDA(cudaMemcpyAsync(dr[i].b, out[i].b, sizeof(float) * x.npix, cudaMemcpyHostToDevice, cs));
         }
+        return RT3D_OK;
+    };
+    // every group's copies are queued first (the copy stream runs ahead)
+    for (int g = 0; g < G; ++g) {
+        for (int i = g * n / G; i < (g + 1) * n / G; ++i) {
+            st = copy_in(i);
+            if (st != RT3D_OK) return st;
+        }
+        if (G > 1) RT3D_CUDA(cudaEventRecord(c->ev_copy[g], cs));
     }
-    st = run_batch(c, n, df.data(), p, dr.data(), s);
-    if (st != RT3D_OK) return st;
-    for (int i = 0; i < n; ++i) {
-        const long long npix = sp[i].npix;
-        RT3D_CUDA(cudaMemcpyAsync(out[i].t, dr[i].t, sizeof(float) * Kp * npix, cudaMemcpyDeviceToHost, s));
-        RT3D_CUDA(cudaMemcpyAsync(out[i].r, dr[i].r, sizeof(float) * Kp * npix, cudaMemcpyDeviceToHost, s));
-        RT3D_CUDA(cudaMemcpyAsync(out[i].alive, dr[i].alive, (size_t)Kp * npix, cudaMemcpyDeviceToHost, s));
-        RT3D_CUDA(cudaMemcpyAsync(out[i].b, dr[i].b, sizeof(float) * npix, cudaMemcpyDeviceToHost, s));
-        if (out[i].n_points)
-            RT3D_CUDA(cudaMemcpyAsync(out[i].n_points, dr[i].n_points, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    for (int g = 0; g < G; ++g) {
+        const int i0 = g * n / G, i1 = (g + 1) * n / G;
+        if (G > 1) RT3D_CUDA(cudaStreamWaitEvent(s, c->ev_copy[g], 0));
+        st = run_batch(c, i1 - i0, df.data() + i0, p, dr.data() + i0, s);
+        if (st != RT3D_OK) return st;
+        for (int i = i0; i < i1; ++i) {
+            const long long npix = sp[i].npix;
+            RT3D_CUDA(cudaMemcpyAsync(out[i].t, dr[i].t, sizeof(float) * Kp * npix, cudaMemcpyDeviceToHost, s));
+            RT3D_CUDA(cudaMemcpyAsync(out[i].r, dr[i].r, sizeof(float) * Kp * npix, cudaMemcpyDeviceToHost, s));
+            RT3D_CUDA(cudaMemcpyAsync(out[i].alive, dr[i].alive, (size_t)Kp * npix, cudaMemcpyDeviceToHost, s));
+            RT3D_CUDA(cudaMemcpyAsync(out[i].b, dr[i].b, sizeof(float) * npix, cudaMemcpyDeviceToHost, s));
+            if (out[i].n_points)
+                RT3D_CUDA(cudaMemcpyAsync(out[i].n_points, dr[i].n_points, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                          s));
+        }
     }
     RT3D_CUDA(cudaStreamSynchronize(s));
     return RT3D_OK;

@@ -312,6 +312,38 @@ def test_batched_host_entry_point_equals_device_path(orc):
         assert int(host[i]["n_points"][0]) == a["n_points"]
 
 
+def test_batched_host_entry_point_in_copy_groups_equals_device_path(orc):
+    """Dense frames of 64 MiB and more: rt3d_reconstruct_batch_host copies them
+    in groups on its own stream while earlier groups are reconstructed (five
+    frames: four groups of 1, 1, 1 and 2); cold start, then a warm start from
+    those results, bit for bit the device-resident batch."""
+    from paper_1905_06700_b300 import rt3d as R
+    torch = torch_mod()
+    scs = [scenes.small_random(128, 128, 2048, n_comp=2, seed=60 + i) for i in range(5)]
+    for sc in scs[1:]:
+        sc.irf = scs[0].irf
+    prm = workload_params(scs[0], n_iter=4)
+    ctx = make_ctx(scs[0], k=prm["k_max"], max_batch=5)
+    dense = [ctx.synthesize(scenes.sampling_tables(sc)) for sc in scs]
+    host_z = [u16_np(d) for d in dense]
+    assert host_z[0].nbytes >= 64 << 20
+    dev = ctx.reconstruct_batch(prm, [dict(dense=d) for d in dense])
+    host = R.reconstruct_batch_host(ctx, prm, [dict(dense=z) for z in host_z])
+    for i in range(5):
+        a = np_of(dev[i])
+        for k in ("t", "r", "alive", "b"):
+            assert np.array_equal(a[k], host[i][k]), (i, k)
+        assert int(host[i]["n_points"][0]) == a["n_points"]
+    warm = dict(prm, warm_start=1)
+    dev = ctx.reconstruct_batch(warm, [dict(dense=d) for d in dense], outs=dev)
+    host = R.reconstruct_batch_host(ctx, warm, [dict(dense=z) for z in host_z], outs=host)
+    torch.cuda.synchronize()
+    for i in range(5):
+        a = np_of(dev[i])
+        for k in ("t", "r", "alive", "b"):
+            assert np.array_equal(a[k], host[i][k]), (i, k)
+
+
 def test_capacity_overflow_is_reported_not_faulted(orc):
     from paper_1905_06700_b300 import rt3d as R
     sc = scenes.small_random(16, 16, 256, n_comp=2, seed=3)
