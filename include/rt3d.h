@@ -319,7 +319,7 @@ rt3d_status rt3d_get_sparse(rt3d_ctx_t* ctx, uint32_t* seg_host, int64_t n_pix,
  * Learned depth denoiser.  Not in the paper: an extension that stands in for
  * the APSS depth step (Results, "Depth update") with a small convolutional
  * network trained on pairs the plain method generates; APSS stays as the
- * per-point fallback (params.net_fallback) and as the judge of its error.
+ * per-point fallback (params.net_fallback) and as the reference for its error.
  *
  * Network: four 3x3 convolutions 6 -> 48 -> 48 -> 48 -> 2, zero padding,
  * bias, ReLU after the first three; RT3D_NET_PARAMS FP32 parameters, for each
