@@ -1267,8 +1267,10 @@ rt3d_status rt3d_reconstruct_batch_host(rt3d_ctx_t* c, int n, const rt3d_frame* 
         bytes += al(sizeof(int32_t));
     }
     if (bytes > c->s_batch_cap) {
-        // the previous staging may still be read by work queued on `s`
+        // the previous staging may still be read by work queued on `s` (or
+        // written by a copy group of a call that stopped on an error)
         RT3D_CUDA(cudaStreamSynchronize(s));
+        if (c->copy_stream) RT3D_CUDA(cudaStreamSynchronize(c->copy_stream));
         if (c->s_batch) cudaFree(c->s_batch);
         c->s_batch = nullptr;
         c->s_batch_cap = 0;
@@ -1339,7 +1341,10 @@ rt3d_status rt3d_reconstruct_batch_host(rt3d_ctx_t* c, int n, const rt3d_frame* 
         const int i0 = g * n / G, i1 = (g + 1) * n / G;
         if (G > 1) RT3D_CUDA(cudaStreamWaitEvent(s, c->ev_copy[g], 0));
         st = run_batch(c, i1 - i0, df.data() + i0, p, dr.data() + i0, s);
-        if (st != RT3D_OK) return st;
+        if (st != RT3D_OK) {
+            if (G > 1) cudaStreamSynchronize(cs);   // no copy still writes the staging on return
+            return st;
+        }
         for (int i = i0; i < i1; ++i) {
             const long long npix = sp[i].npix;
             RT3D_CUDA(cudaMemcpyAsync(out[i].t, dr[i].t, sizeof(float) * Kp * npix, cudaMemcpyDeviceToHost, s));
