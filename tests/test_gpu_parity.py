@@ -429,6 +429,48 @@ def test_filter_range_guard_is_reported_and_spares_other_pixels(orc):
     assert np.array_equal(g["t"][:, keep].astype(np.float64), o.t[:, keep])
 
 
+def test_warm_start_on_a_moving_scene_matches_oracle(orc):
+    """A stream's next frame (the scene moved by one bin) started from the
+    previous frame's cloud: the GPU's warm start against the oracle's loop run
+    from the same state (every value rounded through float32, as the GPU
+    holds it), with the same perturbation probe for ill-conditioned points."""
+    from gpu_util import _round_bits
+    base = scenes.small_random(14, 23, 300, n_comp=2, seed=71)
+    sc1, sc2 = scenes.moving_frame(base, 0), scenes.moving_frame(base, 1)
+    z1 = orc.synthesize(scenes.sampling_tables(sc1))
+    z2 = orc.synthesize(scenes.sampling_tables(sc2))
+    prm = workload_params(base)
+    ctx = make_ctx(base, k=prm["k_max"])
+    g1 = ctx.reconstruct(prm, dense=upload_u16(z1))
+    a = np_of(g1)
+    start = orc.new_state(prm["k_max"], base.h, base.w)
+    start.t[:] = a["t"]
+    start.r[:] = a["r"]
+    start.alive[:] = a["alive"]
+    start.b[:] = a["b"]
+    g2 = np_of(ctx.reconstruct(dict(prm, warm_start=1), dense=upload_u16(z2), out=g1))
+    irf = oracle_irf(orc, base)
+    fr = orc.OFrame(z2)
+    o = start.copy()
+    orc.palm(fr, irf, prm, o, prm["n_iter"])
+    q = start.copy()
+
+    def rnd(st):
+        st.t[:] = st.t.astype(np.float32)
+        st.r[:] = _round_bits(st.r, 20)
+        st.b[:] = _round_bits(st.b, 20)
+    for _ in range(prm["n_iter"]):
+        orc.t_step(fr, irf, prm, q); rnd(q)
+        orc.apss(base.h, base.w, base.t, prm, q); rnd(q)
+        orc.r_step(fr, irf, prm, q); rnd(q)
+        orc.int_lowpass(base.h, base.w, prm, q); rnd(q)
+        orc.b_step(fr, irf, prm, q); rnd(q)
+        orc.bkg_lowpass(base.h, base.w, prm, q.b); rnd(q)
+    ill = ill_conditioned(o, q, TOL_T, TOL_R)
+    stats = compare_clouds(g2, o, base.t, TOL_T, TOL_R, ill=ill, max_ill_frac=0.02, label="warm start")
+    print("warm start", stats)
+
+
 def test_empty_histograms_give_no_points(orc):
     sc = scenes.small_random(7, 9, 128, n_comp=1, seed=1)
     z = np.zeros((sc.h, sc.w, sc.t), np.uint16)
