@@ -97,6 +97,26 @@ def test_tc_reconstruct_equals_integer_path(orc, mode):
     _same(w0, w1)
 
 
+@pytest.mark.parametrize("mode", sorted(MODES))
+def test_tc_reconstruct_with_gain_and_dead_pixels_equals_integer_path(orc, mode):
+    """A per-pixel gain map with dead pixels (gain 0): the tensor-core init's
+    b0 and r0 and the loop that follows equal the integer path's bit for bit."""
+    torch = torch_mod()
+    sc = scenes.small_random(17, 26, 320, n_comp=2, seed=13)
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc)
+    rng = np.random.default_rng(17)
+    gain = rng.uniform(0.4, 1.6, (sc.h, sc.w)).astype(np.float32)
+    gain[rng.random((sc.h, sc.w)) < 0.05] = 0.0
+    ctx = make_ctx(sc, k=prm["k_max"])
+    zd = upload_u16(z)
+    gd = torch.from_numpy(gain).cuda()
+    a = np_of(ctx.reconstruct(prm, dense=zd, gain=gd))
+    b = np_of(ctx.reconstruct(dict(prm, lmf_precision=MODES[mode]), dense=zd, gain=gd))
+    _same(a, b)
+    assert not a["alive"][:, gain == 0].any()
+
+
 def test_tc_full_size_two_layer_equals_integer_path(orc):
     """The precision-form workload (256 x 256 x 4096, two surfaces, SBR 0.1):
     initialisation and reconstruction bitwise equal to the integer path, and
