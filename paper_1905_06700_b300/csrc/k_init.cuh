@@ -30,7 +30,7 @@
 
 namespace rt3d {
 
-constexpr int kInitWarps = 8;        // upper bound on warps per CTA
+constexpr int kInitWarps = 2;        // warps (pixels) per CTA: small CTAs, 20 per SM
 constexpr int kInitChunk = 256;      // filter positions per chunk
 constexpr int kInitStage = 256;      // staged entries per warp
 constexpr int kInitSmemBudget = 200 * 1024;
@@ -54,7 +54,7 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
 }
 
 template <bool kDumpY, bool kCompactOnly>
-__global__ void __launch_bounds__(kInitWarps * 32, 5)
+__global__ void __launch_bounds__(kInitWarps * 32, 20)
 k_init(const CallRecord* __restrict__ rec, const Work W, int pix0, int pix_end)
 {
     const KParams& P = rec->P;
