@@ -12,6 +12,9 @@ steady-state launch.  Cases:
   loop          4 frames of 141x141x4096 (the benchmark scene), 20 iterations
   loop16        16 frames of the benchmark scene (the benchmark's batch; two
                 chains of 8 frames each), 20 iterations
+  net-forward   three forward passes of the committed network over 8 images
+                of 256x256 random features (the register-staged convolution
+                of the network's own training calls)
 
 Usage: python paper_1905_06700_b300/profile_cases.py CASE
 """
@@ -34,6 +37,17 @@ WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "l
 
 def case(name: str):
     import torch
+    if name == "net-forward":
+        B.build()
+        theta, _ = learned.load(WEIGHTS)
+        net = R.Net(8, 256, 256)
+        net.set_params(theta)
+        x = torch.randn((8, 6, 256, 256), generator=torch.Generator().manual_seed(0)).cuda()
+        for _ in range(3):
+            net.forward(x)
+        torch.cuda.synchronize()
+        print(name, "done")
+        return 0
     if name in ("init-tc", "init-int"):
         base = scenes.two_layer()
         prm = dict(scenes.make_params(base), n_iter=0, lmf_precision=2 if name == "init-tc" else 0)
