@@ -767,6 +767,12 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next, int t
     const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
     const float int_px = P.pitch * (1.0f / P.int_h);
     if (P.int_den) win_vote(s_vote, R, int_px);
+    // own pixel state read with the halo (one memory round trip)
+    float r_own[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) r_own[k] = c.inb ? F.r[(long long)k * np + lp] : 0.0f;
+    const float g_own = c.inb ? (F.gain ? F.gain[lp] : 1.0f) : 0.0f;
+    const float b_own = c.inb ? F.b[lp] : 0.0f;
     load_halo<K, true>(c, F, R, F.t, np, 0, F.alive, np, st, W.r_half, S, F.pix_base, sr);
     __syncthreads();
     const int hstride = kTileW + 2 * R;
@@ -775,7 +781,7 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next, int t
     for (int k = 0; k < K; ++k) {
         const bool al = st[k * kHalo + q0] != kDeadDepth;
         s_an[k][threadIdx.x] = 0;
-        s_rn[k][threadIdx.x] = al ? sr[k * kHalo + q0] : (c.inb ? F.r[(long long)k * np + c.gi * F.w + c.gj] : 0.0f);
+        s_rn[k][threadIdx.x] = al ? sr[k * kHalo + q0] : r_own[k];
     }
     const int n_pts = compact_points(st, R, K, c.inb, c.li, c.lj, s_pts, s_warp);
     __syncthreads();
@@ -839,11 +845,7 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next, int t
         tk[k] = ak ? st[k * kHalo + q0] : 0.0f;
         rr[k] = ak ? s_rn[k][threadIdx.x] : 0.0f;
     }
-    float g = 0.0f, b = 0.0f;
-    if (c.inb) {
-        g = F.gain ? F.gain[lp] : 1.0f;
-        b = F.b[lp];
-    }
+    const float g = g_own, b = b_own;
     float sz;
     warp_pixel_sums<K, 2>(F.ent, sg, c.inb, coef, P, tk, rr, b, g, ws[threadIdx.x >> 5], &sz);
     float bn = b;
