@@ -135,20 +135,90 @@ k_net_features_loop(const CallRecord* __restrict__ rec, const Work W, uint16_t* 
                     int alive_from_b)
 {
     const Batch& B = rec->B;
-    const NetPix q = net_pix(B, blockIdx.x, threadIdx.x / kTileW, threadIdx.x % kTileW);
-    if (!q.in) return;
-    const FrameDesc& F = B.f[q.fi];
+    const int K = rec->P.k;
+    // the tile's depths and alive flags with a one-pixel margin, read once
+    // (every load issued before the first shared store); a neighbour outside
+    // the frame is not alive
+    __shared__ float s_t[kMaxK][kNetHalo];
+    __shared__ uint8_t s_a[kMaxK][kNetHalo];
+    const int tile = (int)blockIdx.x;
+    const int fi = frame_of_tile(B, tile);
+    const FrameDesc& F = B.f[fi];
+    const int tl = tile - F.tile_base;
+    const int i0 = (tl / F.tiles_w) * kTileH - 1, j0 = (tl % F.tiles_w) * kTileW - 1;
     // after a phase C that ran the depth step the alive flags are still in alive_b
-    NetStateView v = alive_from_b
-                         ? NetStateView{W.t_half, F.r, W.alive_b, W.stride, F.npix, W.stride, F.pix_base, 0, F.pix_base}
-                         : NetStateView{W.t_half, F.r, F.alive, W.stride, F.npix, F.npix, F.pix_base, 0, 0};
+    const uint8_t* alive = alive_from_b ? W.alive_b + F.pix_base : F.alive;
+    const long long a_slot = alive_from_b ? (long long)W.stride : (long long)F.npix;
+    constexpr int kIters = (kNetHalo + kTileThreads - 1) / kTileThreads;
+    float tv[kIters][kMaxK];
+    uint8_t av[kIters][kMaxK];
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+        const int e = (int)threadIdx.x + it * kTileThreads;
+        const int gi = i0 + e / kNetHaloW, gj = j0 + e % kNetHaloW;
+        const bool in = e < kNetHalo && gi >= 0 && gi < F.h && gj >= 0 && gj < F.w;
+        const int lp = in ? gi * F.w + gj : 0;
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k) {
+            av[it][k] = 0;
+            tv[it][k] = 0.0f;
+            if (in && k < K) {
+                av[it][k] = alive[k * a_slot + lp];
+                tv[it][k] = W.t_half[(long long)k * W.stride + F.pix_base + lp];
+            }
+        }
+    }
+#pragma unroll
+    for (int it = 0; it < kIters; ++it) {
+        const int e = (int)threadIdx.x + it * kTileThreads;
+        if (e >= kNetHalo) continue;
+#pragma unroll
+        for (int k = 0; k < kMaxK; ++k) {
+            s_a[k][e] = av[it][k];
+            s_t[k][e] = tv[it][k];
+        }
+    }
+    __syncthreads();
+    const int li = (int)threadIdx.x / kTileW, lj = (int)threadIdx.x % kTileW;
+    const int gi = i0 + 1 + li, gj = j0 + 1 + lj;
+    if (gi >= F.h || gj >= F.w) return;
+    const int lp = gi * F.w + gj;
+    const int c0 = (li + 1) * kNetHaloW + (lj + 1);
+    // the features of net_features_at, in the same order of operations
     float f[6];
-    net_features_at(v, rec->P.k, F.h, F.w, q.gi, q.gj, scale, f);
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        float ft = 0.0f, fr = 0.0f, fa = 0.0f;
+        if (k < K && s_a[k][c0]) {
+            const float tk = s_t[k][c0];
+            const float reach = 4.0f * scale;
+            float sum = 0.0f;
+            int n = 0;
+            for (int di = -1; di <= 1; ++di)
+                for (int dj = -1; dj <= 1; ++dj) {
+                    if (di == 0 && dj == 0) continue;
+                    const int q = c0 + di * kNetHaloW + dj;
+                    for (int kk = 0; kk < K; ++kk) {
+                        if (!s_a[kk][q]) continue;
+                        const float tq = s_t[kk][q];
+                        if (!(fabsf(tq - tk) <= reach)) continue;
+                        sum += tq;
+                        ++n;
+                    }
+                }
+            if (n > 0) ft = clampf((tk - sum / (float)n) / scale, -4.0f, 4.0f);
+            fr = log1pf(fmaxf(F.r[(long long)k * F.npix + lp], 0.0f));
+            fa = (float)(1 + n) / 9.0f;
+        }
+        f[3 * k] = ft;
+        f[3 * k + 1] = fr;
+        f[3 * k + 2] = fa;
+    }
     // chunk-planar with 8 channels (the last two zero): one 16-byte row per pixel
     const uint32_t w0 = (uint32_t)f_to_bf16_bits(f[0]) | ((uint32_t)f_to_bf16_bits(f[1]) << 16);
     const uint32_t w1 = (uint32_t)f_to_bf16_bits(f[2]) | ((uint32_t)f_to_bf16_bits(f[3]) << 16);
     const uint32_t w2 = (uint32_t)f_to_bf16_bits(f[4]) | ((uint32_t)f_to_bf16_bits(f[5]) << 16);
-    *reinterpret_cast<uint4*>(x + (long long)q.pix * 8) = make_uint4(w0, w1, w2, 0u);
+    *reinterpret_cast<uint4*>(x + (long long)(F.pix_base + lp) * 8) = make_uint4(w0, w1, w2, 0u);
 }
 
 // Features of n caller images, state [n][K][h][w] -> x [n][6][h][w] (FP32
