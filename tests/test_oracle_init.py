@@ -120,3 +120,27 @@ def test_init_empty_and_dead_pixels(orc):
     st = orc.init(z, gain, irf, prm)
     assert st.alive.sum() == 0
     np.testing.assert_allclose(st.b, np.float32(prm["b_floor"]))
+
+
+def test_peaks_match_brute_force_on_random_tiny_inputs(orc):
+    """The peak picker against its definition evaluated by brute force: the
+    admissible positions (positive filter value, enough photons in the IRF
+    window, strictly above every value up to sep bins earlier and at least every
+    value up to sep bins later, the histogram ends cutting the neighbourhood),
+    the K best of them under (value descending, bin ascending) by a full sort,
+    reported by increasing bin.  Small integer values give many plateaus and
+    ties."""
+    rng = np.random.default_rng(11)
+    for _ in range(400):
+        t = int(rng.integers(1, 41))
+        y = rng.integers(-2, 7, t).astype(np.int64)
+        wc = rng.integers(0, 6, t).astype(np.int64)
+        sep = int(rng.integers(0, 5))
+        thr = int(rng.integers(0, 5))
+        kmax = int(rng.integers(1, 5))
+        adm = [tau for tau in range(t)
+               if y[tau] > 0 and wc[tau] >= thr
+               and all(y[tau] > y[q] for q in range(max(0, tau - sep), tau))
+               and all(y[tau] >= y[q] for q in range(tau + 1, min(t, tau + sep + 1)))]
+        want = sorted(sorted(adm, key=lambda tau: (-y[tau], tau))[:kmax])
+        assert list(orc.peaks(y, wc, sep, thr, kmax)) == want, (t, sep, thr, kmax, y.tolist(), wc.tolist())
