@@ -130,3 +130,65 @@ def test_background_lowpass_equals_fft_filter(orc, h, w, sigma, rad):
     ident = b.copy()
     orc.bkg_lowpass(h, w, _params(bkg_mode=0), ident)
     assert np.array_equal(ident, b)
+
+
+def test_apss_matches_weighted_least_squares_sphere_by_lstsq(orc):
+    """APSS on a generic cloud (a curved, noisy surface with dead points, plus a
+    second slot's partial layer inside the radius) against its definition solved
+    another way: for each point, the weighted least-squares algebraic sphere
+    s = u0 + u1 x + u2 y + z + u4 (x^2 + y^2 + z^2) over the alive points of every
+    slot in the window (local coordinates over h, weight (1 - d^2)^4 inside the
+    unit ball) by numpy's lstsq on the square-root-weighted design, and the
+    point moved along the line of sight to the root of s(0, 0, z) nearest to it
+    (numpy's polynomial roots), within one radius and the histogram."""
+    rng = np.random.default_rng(21)
+    h, w, t = 13, 15, 2000
+    prm = _params(k_max=2)
+    pitch, hh, R = prm["pixel_pitch"], prm["apss_radius"], prm["win_r"]
+    i, j = np.meshgrid(np.arange(h, dtype=np.float64), np.arange(w, dtype=np.float64), indexing="ij")
+    front = 700 + 4.0 * j - 2.5 * i + 0.35 * (i - 6) ** 2 - 0.2 * (j - 7) * (i - 6) + rng.normal(0, 2.5, (h, w))
+    front[rng.random((h, w)) < 0.15] = np.inf                       # dead points
+    layer = front + 25.0 + rng.normal(0, 2.0, (h, w))
+    layer[rng.random((h, w)) < 0.7] = np.inf
+    st = _cloud(orc, np.stack([front, layer]))
+    src_t, src_a = st.t.copy(), st.alive.copy()
+    orc.apss(h, w, t, prm, st)
+    checked = skipped = 0
+    for k in range(2):
+        for a in range(h):
+            for b in range(w):
+                if not src_a[k, a, b]:
+                    continue
+                t0 = src_t[k, a, b]
+                rows, wts, offs = [], [], []
+                for m in range(2):
+                    for di in range(-R, R + 1):
+                        for dj in range(-R, R + 1):
+                            ii, jj = a + di, b + dj
+                            if not (0 <= ii < h and 0 <= jj < w) or not src_a[m, ii, jj]:
+                                continue
+                            x, y, z = pitch * dj / hh, pitch * di / hh, (src_t[m, ii, jj] - t0) / hh
+                            d2 = x * x + y * y + z * z
+                            if d2 < 1.0:
+                                rows.append((x, y, z, d2))
+                                wts.append((1.0 - d2) ** 4)
+                                offs.append((di, dj))
+                got = st.t[k, a, b]
+                o = np.array(offs, np.float64).reshape(-1, 2)
+                if len(rows) < prm["apss_min_nb"] or np.linalg.matrix_rank(np.c_[np.ones(len(o)), o]) < 3:
+                    assert got == t0
+                    continue
+                r = np.array(rows)
+                sw = np.sqrt(np.array(wts))
+                A = np.c_[np.ones(len(r)), r[:, 0], r[:, 1], r[:, 3]] * sw[:, None]
+                u0, _, _, u4 = np.linalg.lstsq(A, -r[:, 2] * sw, rcond=None)[0]
+                roots = np.roots([u4, 1.0, u0]) if abs(u4) > 1e-12 else np.array([-u0])
+                real = roots[np.abs(roots.imag) < 1e-12].real
+                if len(real) == 0:
+                    skipped += 1
+                    continue
+                zs = float(np.clip(real[np.argmin(np.abs(real))], -1.0, 1.0))
+                want = float(np.clip(t0 + hh * zs, 0.0, t - 1.0))
+                assert abs(got - want) < 1e-7, (k, a, b, got, want)
+                checked += 1
+    assert checked > 150 and skipped <= 0.02 * checked
