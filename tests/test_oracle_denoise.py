@@ -192,3 +192,64 @@ def test_apss_matches_weighted_least_squares_sphere_by_lstsq(orc):
                 assert abs(got - want) < 1e-7, (k, a, b, got, want)
                 checked += 1
     assert checked > 150 and skipped <= 0.02 * checked
+
+
+def test_intensity_lowpass_pruning_and_merge_on_a_generic_cloud(orc):
+    """The intensity denoiser on a generic cloud (curved noisy front surface with
+    dead points, a second slot's partial layer inside the radius, random
+    intensities) against its definition evaluated by brute force: each alive
+    point's intensity becomes the (1 - d^2/h^2)^4-weighted mean of the
+    intensities of the alive points of every slot in its window within the 3-D
+    radius (itself included), points below r_min are removed, and two alive
+    points of one pixel closer in depth than merge_dist become one: the weaker
+    (the later slot on a tie) is removed and its intensity added to the other."""
+    rng = np.random.default_rng(33)
+    h, w = 11, 14
+    prm = _params(k_max=2, r_min=2.2, merge_dist=12.0)
+    pitch, hr, R = prm["pixel_pitch"], prm["int_radius"], prm["win_r"]
+    i, j = np.meshgrid(np.arange(h, dtype=np.float64), np.arange(w, dtype=np.float64), indexing="ij")
+    front = 600 + 3.0 * j - 2.0 * i + 0.3 * (i - 5) ** 2 + rng.normal(0, 2.5, (h, w))
+    front[rng.random((h, w)) < 0.15] = np.inf
+    layer = front + rng.uniform(5.0, 30.0, (h, w))
+    layer[rng.random((h, w)) < 0.6] = np.inf
+    st = _cloud(orc, np.stack([front, layer]))
+    st.r[:] = rng.uniform(0.5, 5.0, st.r.shape)
+    t0, r0, a0 = st.t.copy(), st.r.copy(), st.alive.copy()
+    orc.int_lowpass(h, w, prm, st)
+    rbar = r0.copy()
+    for k in range(2):
+        for a in range(h):
+            for b in range(w):
+                if not a0[k, a, b]:
+                    continue
+                num = den = 0.0
+                for m in range(2):
+                    for ii in range(max(0, a - R), min(h, a + R + 1)):
+                        for jj in range(max(0, b - R), min(w, b + R + 1)):
+                            if not a0[m, ii, jj]:
+                                continue
+                            d2 = ((pitch * (jj - b)) ** 2 + (pitch * (ii - a)) ** 2
+                                  + (t0[m, ii, jj] - t0[k, a, b]) ** 2) / hr ** 2
+                            if d2 < 1.0:
+                                num += (1.0 - d2) ** 4 * r0[m, ii, jj]
+                                den += (1.0 - d2) ** 4
+                rbar[k, a, b] = num / den
+    alive = a0.astype(bool) & (rbar.astype(np.float32) >= np.float32(prm["r_min"]))
+    want = rbar.copy()
+    merged = 0
+    for a in range(h):
+        for b in range(w):
+            if alive[0, a, b] and alive[1, a, b] and abs(t0[0, a, b] - t0[1, a, b]) < prm["merge_dist"]:
+                keep, drop = (1, 0) if want[1, a, b] > want[0, a, b] else (0, 1)
+                want[keep, a, b] += want[drop, a, b]
+                alive[drop, a, b] = False
+                merged += 1
+    assert merged > 3 and (a0.astype(bool) & ~alive).sum() > merged      # both rules were exercised
+    assert np.array_equal(st.alive.astype(bool), alive)
+    on = alive
+    np.testing.assert_allclose(st.r[on], want[on], rtol=1e-12)
+    # an exact tie (no low-pass): the later slot is the one removed
+    tie = _cloud(orc, np.array([[[100.0]], [[105.0]]]))
+    tie.r[:] = 3.0
+    orc.int_lowpass(1, 1, _params(k_max=2, r_min=0.5, merge_dist=12.0, intensity_denoiser=0), tie)
+    assert tie.alive[:, 0, 0].tolist() == [1, 0] and tie.r[0, 0, 0] == 6.0
