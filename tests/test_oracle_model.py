@@ -215,3 +215,46 @@ def test_step_projections(orc):
     z2 = np.zeros_like(z)
     orc.b_step(orc.OFrame(z2), irf, prm, st)
     assert st.b.min() >= np.float32(prm["b_floor"])
+
+
+def test_unit_steps_are_em_updates_and_never_raise_the_nll(orc):
+    """With step 1 and no regulariser offsets, the intensity and background steps
+    are the EM (Richardson-Lucy) updates of the Poisson mixture: each slot's
+    intensity is multiplied by its share of the photons, sum z h_k/lambda over
+    sum h_k, and the background by sum z/lambda over T, all slots of a pixel
+    from the same lambda.  EM never raises the negative log-likelihood, so
+    alternating the two steps gives a non-increasing NLL."""
+    rng = np.random.default_rng(8)
+    irf = _irf(orc)
+    t = 120
+    st = orc.new_state(2, 1, 2)
+    st.t[:, 0, :] = [[30.4, 47.9], [82.25, 71.6]]
+    st.r[:] = rng.uniform(2.0, 9.0, st.r.shape)
+    st.alive[:] = 1
+    st.b[:] = [[0.15, 0.4]]
+    z = rng.poisson(2.0, size=(1, 2, t)).astype(np.float64)
+    prm = _params(k_max=2, r_step=1.0, eps_r=0.0, b_step=1.0, eps_b=0.0)
+    fr = orc.OFrame(z)
+
+    def em(s):
+        r, b = s.r.copy(), s.b.copy()
+        for p in range(2):
+            hk = np.array([[orc.irf_eval(irf, tb - s.t[k, 0, p])[0] for tb in range(t)] for k in range(2)])
+            lam = b[0, p] + r[:, 0, p] @ hk
+            r[:, 0, p] = s.r[:, 0, p] * (hk @ (z[0, p] / lam)) / hk.sum(axis=1)
+            b[0, p] = s.b[0, p] * np.sum(z[0, p] / lam) / t
+        return r, b
+
+    want_r, _ = em(st)
+    orc.r_step(fr, irf, prm, st)
+    np.testing.assert_allclose(st.r, want_r, rtol=1e-12)
+    _, want_b = em(st)
+    orc.b_step(fr, irf, prm, st)
+    np.testing.assert_allclose(st.b, want_b, rtol=1e-12)
+    nll = [orc.nll_dense(z, None, st, irf, prm["lam_floor"])]
+    for _ in range(60):
+        orc.r_step(fr, irf, prm, st)
+        orc.b_step(fr, irf, prm, st)
+        nll.append(orc.nll_dense(z, None, st, irf, prm["lam_floor"]))
+    assert all(b <= a + 1e-9 * abs(a) for a, b in zip(nll, nll[1:]))
+    assert nll[-1] < nll[0]
