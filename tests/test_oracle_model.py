@@ -258,3 +258,27 @@ def test_unit_steps_are_em_updates_and_never_raise_the_nll(orc):
         nll.append(orc.nll_dense(z, None, st, irf, prm["lam_floor"]))
     assert all(b <= a + 1e-9 * abs(a) for a, b in zip(nll, nll[1:]))
     assert nll[-1] < nll[0]
+
+
+@pytest.mark.parametrize("tstar,delta", [(50.3, 0.02), (50.3, -0.03), (3.4, 0.02), (96.1, -0.02)])
+def test_depth_step_is_a_half_fisher_scoring_step(orc, tstar, delta):
+    """With noise-free counts and t_step = (g r / F) / 2, F = sum (g r h')^2 / lambda
+    the Fisher information of the depth at the truth, the depth step is half a
+    Fisher-scoring step: a small error delta becomes delta / 2 to first order,
+    from either side, also where the histogram's ends cut the IRF's support
+    (there the derivative of the IRF mass inside the histogram enters the
+    gradient)."""
+    irf = _irf(orc)
+    t, r, b = 100, 500.0, 0.05
+    hv = np.array([orc.irf_eval(irf, tb - tstar) for tb in range(t)])
+    lam = b + r * hv[:, 0]
+    fisher = np.sum((r * hv[:, 1]) ** 2 / lam)
+    st = orc.new_state(1, 1, 1)
+    st.t[:] = tstar + delta
+    st.r[:] = r
+    st.b[:] = b
+    st.alive[:] = 1
+    prm = _params(k_max=1, t_step=0.5 * r / fisher, eps_r=0.0, lam_floor=1e-12)
+    orc.t_step(orc.OFrame(lam.reshape(1, 1, t)), irf, prm, st)
+    ratio = (st.t[0, 0, 0] - tstar) / delta
+    assert abs(ratio - 0.5) < 0.03, ratio
