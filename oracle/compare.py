@@ -1,0 +1,155 @@
+"""Comparison of a reconstruction with FP64 oracle runs (test infrastructure only).
+
+Only the tests, the smoke check and the benchmark's CPU-baseline leg may
+import this module.  It holds no arithmetic of the method: it runs the
+oracle's own steps (oracle.py) and compares point clouds.
+
+The method takes discontinuous decisions (pruning at r_min, the merge
+distance, the denoisers' neighbour cut-offs) and has steep regions (photons
+on the onset of a gamma IRF), so a perturbation of the size of single
+precision rounding can move some points by far more than the rounding.  A
+*probe* is the oracle's loop with its state rounded after every step the way
+single-precision kernels round theirs: depths to float32, intensities and
+backgrounds to `bits` significant bits (about the rounding of a float32 sum
+of ~100 terms).  Points where the oracle and its probe disagree beyond half
+the tolerance are ill-conditioned; the GPU is held there to a bound set by
+the probes' own deviation (cloud_stats).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import oracle as O
+
+PROBE_BITS = (20, 18, 22)     # the probe ensemble: perturbations of 2^-20, 2^-18, 2^-22
+
+
+def round_bits(a, bits):
+    """Round every value to `bits` significant bits."""
+    m, e = np.frexp(a)
+    return np.ldexp(np.round(m * 2.0 ** bits) / 2.0 ** bits, e)
+
+
+def _rnd(st, bits):
+    st.t[:] = st.t.astype(np.float32)
+    st.r[:] = round_bits(st.r, bits)
+    st.b[:] = round_bits(st.b, bits)
+
+
+def probe_palm(fr, irf, prm, start, n_iter, bits):
+    """The oracle's PALM loop from `start` (copied), rounded after every step."""
+    st = start.copy()
+    _rnd(st, bits)
+    h, w, t = fr.hh, fr.ww, fr.tt
+    for _ in range(n_iter):
+        O.t_step(fr, irf, prm, st); _rnd(st, bits)
+        O.depth_denoise(h, w, t, prm, st); _rnd(st, bits)
+        O.r_step(fr, irf, prm, st); _rnd(st, bits)
+        O.int_lowpass(h, w, prm, st); _rnd(st, bits)
+        O.b_step(fr, irf, prm, st); _rnd(st, bits)
+        O.bkg_lowpass(h, w, prm, st.b); _rnd(st, bits)
+    return st
+
+
+def reconstruct_with_probes(dense, irf, prm, gain=None, bits_list=PROBE_BITS):
+    """(oracle reconstruction, [probe reconstructions]) of one frame."""
+    o = O.reconstruct(dense, irf, prm, gain=gain)
+    fr = O.OFrame(dense, gain)
+    s0 = O.init(dense, gain, irf, prm)
+    probes = [probe_palm(fr, irf, prm, s0, prm["n_iter"], b) for b in bits_list]
+    return o, probes
+
+
+def palm_with_probes(fr, irf, prm, start, n_iter, bits_list=PROBE_BITS):
+    """(oracle loop, [probe loops]) from a given start state (warm starts)."""
+    o = start.copy()
+    O.palm(fr, irf, prm, o, n_iter)
+    return o, [probe_palm(fr, irf, prm, start, n_iter, b) for b in bits_list]
+
+
+def ill_mask(o, probe, tol_t, tol_r):
+    """Points whose alive flag, depth (> tol_t/2) or intensity (> tol_r/2
+    relative, floor 0.1 photon) differ between the oracle and one probe."""
+    both = o.alive.astype(bool) & probe.alive.astype(bool)
+    ill = o.alive != probe.alive
+    ill |= both & (np.abs(o.t - probe.t) > 0.5 * tol_t)
+    ill |= both & (np.abs(o.r - probe.r) > 0.5 * tol_r * np.maximum(np.abs(o.r), 0.1))
+    return ill
+
+
+def cloud_stats(gpu, o, probes, T, tol_t, tol_r, r_min=None, ratio=2.0):
+    """Statistics of a reconstruction `gpu` (dict of numpy arrays t, r, alive,
+    b) against the oracle state `o`, with the ill-conditioned points taken
+    from the first probe.
+
+    Well-conditioned points: flips (alive differs), depth error (bins),
+    relative intensity error (floor 0.1 photon), background error relative to
+    the pixel's mean count rate b + sum r / T (pixels without ill points).
+
+    Ill-conditioned points: each must satisfy, against the probe ensemble's
+    envelope env = max over probes of |probe - oracle| (infinite where a probe
+    flips the point):
+      - a flip only where some probe flips the point too;
+      - |t_gpu - t_o| <= max(tol_t, ratio * env_t) and the same for the
+        relative intensity.
+    `ill_ratio_max` is the largest |gpu - oracle| / env over the ill points
+    whose error exceeds the tolerance (0 if none does).
+
+    Near-threshold points (the parity definition's exemption): oracle points
+    whose final intensity lies within 1e-5 r_min of r_min (counted only)."""
+    ga = gpu["alive"].astype(bool)
+    oa = o.alive.astype(bool)
+    ill = ill_mask(o, probes[0], tol_t, tol_r) if probes else np.zeros_like(oa)
+    ok = ~ill
+    both = ga & oa
+    dt_all = np.abs(gpu["t"].astype(np.float64) - o.t)
+    rfl = np.maximum(np.abs(o.r), 0.1)
+    dr_all = np.abs(gpu["r"].astype(np.float64) - o.r) / rfl
+    well = both & ok
+    ill_px = ill.any(0)
+    rate = o.b + (o.r * oa).sum(0) / T
+    db = (np.abs(gpu["b"].astype(np.float64) - o.b) / np.maximum(rate, 1e-12))[~ill_px]
+
+    # envelope of the probes' own deviations
+    env_t = np.zeros_like(o.t)
+    env_r = np.zeros_like(o.r)
+    probe_flip = np.zeros_like(oa)
+    for p in probes:
+        pa = p.alive.astype(bool)
+        probe_flip |= pa != oa
+        env_t = np.maximum(env_t, np.where(pa & oa, np.abs(p.t - o.t), 0.0))
+        env_r = np.maximum(env_r, np.where(pa & oa, np.abs(p.r - o.r) / rfl, 0.0))
+    env_t = np.where(probe_flip, np.inf, env_t)
+    env_r = np.where(probe_flip, np.inf, env_r)
+    ill_flips = ill & (ga != oa)
+    ill_flip_unexplained = ill_flips & ~probe_flip
+    ib = ill & both
+    bound_t = np.maximum(tol_t, ratio * env_t)
+    bound_r = np.maximum(tol_r, ratio * env_r)
+    ill_over = ib & ((dt_all > bound_t) | (dr_all > bound_r))
+    with np.errstate(divide="ignore", invalid="ignore"):
+        rt = np.where(ib & (dt_all > tol_t), dt_all / env_t, 0.0)
+        rr = np.where(ib & (dr_all > tol_r), dr_all / env_r, 0.0)
+    rt = np.nan_to_num(rt, nan=np.inf, posinf=np.inf)
+    rr = np.nan_to_num(rr, nan=np.inf, posinf=np.inf)
+    dtw = dt_all[well]
+    dta = dt_all[both]
+    st = dict(points=int(oa.sum()), ill=int(ill.sum()),
+              flips=int(((ga != oa) & ok).sum()),
+              dt_max=float(dtw.max()) if dtw.size else 0.0,
+              dt_p999=float(np.percentile(dtw, 99.9)) if dtw.size else 0.0,
+              dr_max=float(dr_all[well].max()) if well.any() else 0.0,
+              db_max=float(db.max()) if db.size else 0.0,
+              ill_flips=int(ill_flips.sum()),
+              ill_flips_unexplained=int(ill_flip_unexplained.sum()),
+              ill_over_bound=int(ill_over.sum()),
+              ill_ratio_max=float(max(rt.max(initial=0.0), rr.max(initial=0.0))),
+              ill_dt_max=float(dt_all[ib].max()) if ib.any() else 0.0,
+              all_dt_max=float(dta.max()) if dta.size else 0.0,
+              all_dt_p999=float(np.percentile(dta, 99.9)) if dta.size else 0.0,
+              all_frac_within_tol=float((dta <= tol_t).mean()) if dta.size else 1.0,
+              all_alive_mismatch=int((ga != oa).sum()))
+    if r_min is not None:
+        near = oa & (np.abs(o.r - r_min) <= 1e-5 * r_min)
+        st["near_threshold"] = int(near.sum())
+    return st

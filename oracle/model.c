@@ -229,6 +229,17 @@ void or_b_step(const or_frame* f, const or_irf* irf, const or_params* prm, or_st
     }
 }
 
+/* Threads of the OpenMP parallel loops (n >= 1); no effect without OpenMP. */
+void or_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 int or_num_threads(void)
 {
 #ifdef _OPENMP

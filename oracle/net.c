@@ -114,6 +114,9 @@ static void conv3x3(int h, int w, int ci_n, int co_n, const double* W, const dou
                     const double* in, double* out)
 {
     const long npix = (long)h * w;
+    /* output channels in parallel when the caller's image loop is not (one
+     * image); each output keeps its own summation order */
+#pragma omp parallel for schedule(static)
     for (int co = 0; co < co_n; ++co)
         for (int i = 0; i < h; ++i)
             for (int j = 0; j < w; ++j) {
@@ -156,7 +159,7 @@ void or_net_forward(int n, int h, int w, const double* theta, const double* x, i
     }
     memcpy(acts, x, sizeof(double) * n * cin_[0] * npix);
     round_vec(acts, (long)n * cin_[0] * npix, bf16);
-#pragma omp parallel for
+#pragma omp parallel for if (n > 1)
     for (int im = 0; im < n; ++im) {
         for (int l = 0; l < OR_NET_LAYERS; ++l) {
             const double* in = acts + aoff[l] + (long)im * cin_[l] * npix;

@@ -285,12 +285,25 @@ def apss(h, w, t, prm, st):
     lib().or_apss(h, w, t, C.byref(make_params(prm)), C.byref(st.c()))
 
 
+def plane(h, w, t, prm, st):
+    lib().or_plane(h, w, t, C.byref(make_params(prm)), C.byref(st.c()))
+
+
+def bilateral(h, w, t, prm, st):
+    lib().or_bilateral(h, w, t, C.byref(make_params(prm)), C.byref(st.c()))
+
+
 def int_lowpass(h, w, prm, st):
     lib().or_int_lowpass(h, w, C.byref(make_params(prm)), C.byref(st.c()))
 
 
 def bkg_lowpass(h, w, prm, b):
     lib().or_bkg_lowpass(h, w, C.byref(make_params(prm)), _ptr(b, C.c_double))
+
+
+def depth_denoise(h, w, t, prm, st):
+    """The depth block's denoiser selected by prm["depth_denoiser"]."""
+    lib().or_depth_denoise(int(h), int(w), int(t), C.byref(make_params(prm)), C.byref(st.c()))
 
 
 def palm(fr, irf, prm, st, n_iter):
@@ -310,6 +323,11 @@ def reconstruct(dense, irf: OIrf, prm: dict, gain=None) -> OState:
 
 def num_threads() -> int:
     return int(lib().or_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """Threads of the oracle's OpenMP loops in this process."""
+    lib().or_set_num_threads(int(n))
 
 
 # ---------------------------------------------------------------------------

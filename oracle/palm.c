@@ -9,12 +9,22 @@
  */
 #include "rt3d_oracle.h"
 
+/* The depth block's denoiser, by p->depth_denoiser: 0 none, 1 APSS (the
+ * paper's), 2 the learned network with its APSS fallback, 3 a local plane
+ * fit, 4 a bilateral depth filter (the last two: denoise.c). */
+void or_depth_denoise(int h, int w, int t, const or_params* p, or_state* s)
+{
+    if (p->depth_denoiser == 1) or_apss(h, w, t, p, s);
+    if (p->depth_denoiser == 2) or_learned_depth(h, w, t, p, s);
+    if (p->depth_denoiser == 3) or_plane(h, w, t, p, s);
+    if (p->depth_denoiser == 4) or_bilateral(h, w, t, p, s);
+}
+
 void or_palm(const or_frame* f, const or_irf* irf, const or_params* p, or_state* s, int n_iter)
 {
     for (int it = 0; it < n_iter; ++it) {
         or_t_step(f, irf, p, s);                         /* depth: gradient step */
-        if (p->depth_denoiser == 1) or_apss(f->h, f->w, f->t, p, s);   /* depth: APSS */
-        if (p->depth_denoiser == 2) or_learned_depth(f->h, f->w, f->t, p, s);   /* depth: learned */
+        or_depth_denoise(f->h, f->w, f->t, p, s);        /* depth: denoiser */
         or_r_step(f, irf, p, s);                         /* intensity: gradient step */
         or_int_lowpass(f->h, f->w, p, s);                /* intensity: low-pass + pruning */
         or_b_step(f, irf, p, s);                         /* background: gradient step */

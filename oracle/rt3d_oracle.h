@@ -107,6 +107,8 @@ void or_init(const uint16_t* dense, const double* gain, int h, int w, int t,
 /* ---- one PALM iteration, step by step ---- */
 void or_t_step(const or_frame* f, const or_irf* irf, const or_params* p, or_state* s);
 void or_apss(int h, int w, int t, const or_params* p, or_state* s);
+void or_plane(int h, int w, int t, const or_params* p, or_state* s);
+void or_bilateral(int h, int w, int t, const or_params* p, or_state* s);
 void or_r_step(const or_frame* f, const or_irf* irf, const or_params* p, or_state* s);
 void or_int_lowpass(int h, int w, const or_params* p, or_state* s);
 void or_b_step(const or_frame* f, const or_irf* irf, const or_params* p, or_state* s);
@@ -132,10 +134,12 @@ void or_adamw(double* theta, const double* g, double* m, double* v, int step, do
 void or_learned_depth(int h, int w, int t, const or_params* p, or_state* s);
 
 /* ---- whole method ---- */
+void or_depth_denoise(int h, int w, int t, const or_params* p, or_state* s);
 void or_palm(const or_frame* f, const or_irf* irf, const or_params* p, or_state* s, int n_iter);
 void or_reconstruct(const uint16_t* dense, const or_frame* f, const or_irf* irf,
                     const or_params* p, or_state* s);
 int or_num_threads(void);
+void or_set_num_threads(int n);
 
 #ifdef __cplusplus
 }

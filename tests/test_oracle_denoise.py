@@ -253,3 +253,120 @@ def test_intensity_lowpass_pruning_and_merge_on_a_generic_cloud(orc):
     tie.r[:] = 3.0
     orc.int_lowpass(1, 1, _params(k_max=2, r_min=0.5, merge_dist=12.0, intensity_denoiser=0), tie)
     assert tie.alive[:, 0, 0].tolist() == [1, 0] and tie.r[0, 0, 0] == 6.0
+
+
+def _generic_two_slot_cloud(orc, seed, h=13, w=15):
+    """A curved, noisy front surface with dead points plus a second slot's
+    partial layer inside the radius (the generic cloud of the lstsq pins)."""
+    rng = np.random.default_rng(seed)
+    i, j = np.meshgrid(np.arange(h, dtype=np.float64), np.arange(w, dtype=np.float64), indexing="ij")
+    front = 700 + 4.0 * j - 2.5 * i + 0.35 * (i - 6) ** 2 - 0.2 * (j - 7) * (i - 6) + rng.normal(0, 2.5, (h, w))
+    front[rng.random((h, w)) < 0.15] = np.inf
+    layer = front + 25.0 + rng.normal(0, 2.0, (h, w))
+    layer[rng.random((h, w)) < 0.7] = np.inf
+    return _cloud(orc, np.stack([front, layer]))
+
+
+def _window(src_t, src_a, k, a, b, prm, h, w):
+    """Neighbours of point (k, a, b) by their definition: (x, y, z, d2, weight, di, dj)."""
+    pitch, hh, R = prm["pixel_pitch"], prm["apss_radius"], prm["win_r"]
+    t0 = src_t[k, a, b]
+    out = []
+    for m in range(src_t.shape[0]):
+        for di in range(-R, R + 1):
+            for dj in range(-R, R + 1):
+                ii, jj = a + di, b + dj
+                if not (0 <= ii < h and 0 <= jj < w) or not src_a[m, ii, jj]:
+                    continue
+                x, y, z = pitch * dj / hh, pitch * di / hh, (src_t[m, ii, jj] - t0) / hh
+                d2 = x * x + y * y + z * z
+                if d2 < 1.0:
+                    out.append((x, y, z, d2, (1.0 - d2) ** 4, di, dj))
+    return np.array(out, np.float64).reshape(-1, 7)
+
+
+def test_plane_fit_matches_weighted_least_squares_plane_by_lstsq(orc):
+    """The plane-fit depth denoiser on a generic cloud against its definition
+    solved another way: the weighted least-squares plane u0 + u1 x + u2 y = -z
+    over the window's weighted neighbours by numpy's lstsq on the
+    square-root-weighted design, the point moved to z* = -u0 (within one
+    radius and the histogram); points with too few neighbours or collinear
+    pixel offsets stay."""
+    h, w, t = 13, 15, 2000
+    prm = _params(k_max=2)
+    st = _generic_two_slot_cloud(orc, 22, h, w)
+    src_t, src_a = st.t.copy(), st.alive.copy()
+    orc.plane(h, w, t, prm, st)
+    checked = 0
+    for k in range(2):
+        for a in range(h):
+            for b in range(w):
+                if not src_a[k, a, b]:
+                    continue
+                nb = _window(src_t, src_a, k, a, b, prm, h, w)
+                got, t0 = st.t[k, a, b], src_t[k, a, b]
+                if len(nb) < prm["apss_min_nb"] or np.linalg.matrix_rank(np.c_[np.ones(len(nb)), nb[:, 5:7]]) < 3:
+                    assert got == t0
+                    continue
+                sw = np.sqrt(nb[:, 4])
+                A = np.c_[np.ones(len(nb)), nb[:, 0], nb[:, 1]] * sw[:, None]
+                u0 = np.linalg.lstsq(A, -nb[:, 2] * sw, rcond=None)[0][0]
+                want = float(np.clip(t0 + prm["apss_radius"] * np.clip(-u0, -1, 1), 0, t - 1))
+                assert abs(got - want) < 1e-7, (k, a, b, got, want)
+                checked += 1
+    assert checked > 150
+
+
+def test_plane_fit_keeps_planes_but_not_spheres(orc):
+    """Exact planes are fixed points of the plane fit (as of APSS); an exact
+    sphere, which APSS keeps, is flattened: the sphere term is what the plane
+    fit drops."""
+    h, w = 15, 15
+    prm = _params(pixel_pitch=4.0, apss_radius=12.0)
+    i, j = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    plane = 500.0 + 1.3 * 4.0 * i - 0.6 * 4.0 * j
+    st = _cloud(orc, plane)
+    orc.plane(h, w, 2000, prm, st)
+    np.testing.assert_allclose(st.t[0], plane, atol=1e-9)
+    x, y = 4.0 * (j - 7.2), 4.0 * (i - 6.9)
+    sphere = 900.0 - np.sqrt(60.0 ** 2 - x ** 2 - y ** 2)
+    a, b = _cloud(orc, sphere), _cloud(orc, sphere)
+    orc.apss(h, w, 2000, prm, a)
+    orc.plane(h, w, 2000, prm, b)
+    np.testing.assert_allclose(a.t[0], sphere, atol=1e-9)
+    assert np.abs(b.t[0] - sphere)[3:-3, 3:-3].min() > 1e-3
+
+
+def test_bilateral_matches_weighted_mean_by_brute_force(orc):
+    """The bilateral depth denoiser on a generic cloud against its definition:
+    the point's depth offset becomes the weight-averaged offset of the
+    window's weighted neighbours (itself included); it commutes with a depth
+    shift and keeps a fronto-parallel plane."""
+    h, w, t = 13, 15, 2000
+    prm = _params(k_max=2)
+    st = _generic_two_slot_cloud(orc, 23, h, w)
+    src_t, src_a = st.t.copy(), st.alive.copy()
+    orc.bilateral(h, w, t, prm, st)
+    checked = 0
+    for k in range(2):
+        for a in range(h):
+            for b in range(w):
+                if not src_a[k, a, b]:
+                    continue
+                nb = _window(src_t, src_a, k, a, b, prm, h, w)
+                got, t0 = st.t[k, a, b], src_t[k, a, b]
+                if len(nb) < prm["apss_min_nb"]:
+                    assert got == t0
+                    continue
+                zs = float((nb[:, 4] * nb[:, 2]).sum() / nb[:, 4].sum())
+                want = float(np.clip(t0 + prm["apss_radius"] * zs, 0, t - 1))
+                assert abs(got - want) < 1e-7, (k, a, b, got, want)
+                checked += 1
+    assert checked > 150
+    shifted = _generic_two_slot_cloud(orc, 23, h, w)
+    shifted.t[:] = src_t + 37.5
+    orc.bilateral(h, w, t, prm, shifted)
+    np.testing.assert_allclose(shifted.t - 37.5, st.t, atol=1e-9)
+    flat = _cloud(orc, np.full((9, 9), 812.25))
+    orc.bilateral(9, 9, t, prm, flat)
+    assert np.all(flat.t[0] == 812.25)
