@@ -51,12 +51,16 @@ def parse():
     ap.add_argument("--latency-frames", type=int, default=64)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-frames", type=int, default=4)
+    ap.add_argument("--cpu-single-frames", type=int, default=1,
+                    help="frames of the single-thread oracle timing (0 = skip)")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--serve-seconds", type=float, default=3.0,
                     help="duration of the continuous-batching serving run (0 = skip)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the precision (tensor-core init) and learned forms")
     ap.add_argument("--form-steps", type=int, default=5)
+    ap.add_argument("--no-sweep", dest="sweep", action="store_false",
+                    help="skip the execution-time sweeps over pixels and active bins (Fig. 5)")
     return ap.parse_args()
 
 
@@ -90,8 +94,8 @@ def job_throughput(frames_per_rank_step: int, steps: int, world: int, t_max_ms: 
     return frames_per_rank_step * steps * world / (t_max_ms / 1000.0)
 
 
-def algorithmic_bytes(n_frames: int, nnz_total: int, k: int, fused_frac: float = 0.0) -> dict:
-    """Bytes each kernel class must move per launch for n frames of H x W x T
+def algorithmic_bytes(n_px: int, t: int, nnz_total: int, k: int, fused_frac: float = 0.0) -> dict:
+    """Bytes each kernel class must move per launch for n_px pixels of T bins
     (every array read or written once; halos counted once).  Per pixel:
       init    2T dense read + 8 seg + 9K state + 4 b written, + 4 per nonzero entry written
       phase A 8 seg + 4 b_half + K (4 t + 4 r + 1 alive_b + 1 alive + 4 t_half) + 4 b, + 4/entry
@@ -100,10 +104,10 @@ def algorithmic_bytes(n_frames: int, nnz_total: int, k: int, fused_frac: float =
               a launch that also runs the next iteration's depth step (fused_frac of
               them) writes K x 4 t_half + 4 b more
       final   K (1 alive_b + 1 alive) + 4 b_half + 4 b."""
-    px = n_frames * H * W
+    px = n_px
     e = 4 * nnz_total
     return {
-        "init": px * (2 * T + 8 + 9 * k + 4) + e,
+        "init": px * (2 * t + 8 + 9 * k + 4) + e,
         "phase_a": px * (8 + 4 + k * 14 + 4) + e,
         "phase_b": px * (8 + k * 17 + 4) + e,
         "phase_c": px * (8 + k * 14 + 8) + e + fused_frac * px * (4 * k + 4),
@@ -111,26 +115,68 @@ def algorithmic_bytes(n_frames: int, nnz_total: int, k: int, fused_frac: float =
     }
 
 
-def lateral_offsets(prm) -> int:
-    """Window offsets (di, dj) inside the APSS radius: the candidate pixels of a point."""
-    R, p, h = prm["win_r"], prm["pixel_pitch"], prm["apss_radius"]
-    return sum(1 for di in range(-R, R + 1) for dj in range(-R, R + 1)
-               if (p * di) ** 2 + (p * dj) ** 2 < h * h)
+LOOP_KERNELS = ("phase_a", "phase_b", "phase_c", "final")
 
 
-def algorithmic_flops(n_frames: int, nnz_total: int, n_points: int, k: int, prm,
-                      fused_frac: float = 0.0) -> dict:
-    """FP32 operations each loop kernel must execute per launch:
-      APSS         per alive point: (offsets in radius) x K candidates x 36 (distance,
-                   weight, 14 moment multiply-adds) + 60 (centred 3x3 solve, projection)
-      low-pass     per alive point: (offsets) x K x 12
-      gradient step per nonzero bin: K x 24 (cubic IRF value and slope, lambda, sums);
-      phase C launches that also run the next depth step (fused_frac) add its sums."""
-    off = lateral_offsets(prm)
-    grad = nnz_total * k * 24
-    return {"phase_a": grad,
-            "phase_b": n_points * (off * k * 36 + 60) + grad,
-            "phase_c": n_points * off * k * 12 + grad + fused_frac * grad}
+def loop_bytes_per_call(n_px: int, t: int, nnz_total: int, k: int, prm) -> float:
+    """Algorithmic bytes of a call's whole PALM loop (every launch of phases
+    A, B, C and the finaliser), from the per-launch table above and the
+    launch counts the library makes: with the identity background denoiser
+    one phase A, then n_iter x (B, C) with all but the last C also running
+    the next depth step; otherwise n_iter x (A, B, C); one finaliser."""
+    n = int(prm["n_iter"])
+    if n <= 0:
+        return 0.0
+    a = algorithmic_bytes(n_px, t, nnz_total, k, fused_fraction(prm))
+    n_a = n if prm.get("bkg_mode", 0) == 1 else 1
+    return n_a * a["phase_a"] + n * (a["phase_b"] + a["phase_c"]) + a["final"]
+
+
+def method_work(outs, nnz_px, prm, k):
+    """The FP32 work the method itself needs in one APSS + intensity-step pass
+    (phase B), counted on the final point clouds of the call's frames:
+      per alive point, per alive candidate in the window cells inside the
+      lateral radius: a distance test (4 FLOP: difference, scale, square-add,
+      compare);
+      per neighbour inside the 3-D radius: the weight and the 14 moment sums
+      (30 FLOP);
+      per point with a fit: the centred 3x3 solve and projection (60 FLOP);
+      the intensity step's bin sums: per nonzero bin and alive point of its
+      pixel, the cubic IRF value and slope, the point's share of lambda and the
+      sum (15 FLOP), and per bin lambda and its reciprocal (3 FLOP).
+    Returns (flop, counts)."""
+    R, pitch, hr = int(prm["win_r"]), float(prm["pixel_pitch"]), float(prm["apss_radius"])
+    cells = [(di, dj) for di in range(-R, R + 1) for dj in range(-R, R + 1)
+             if (pitch * di / hr) ** 2 + (pitch * dj / hr) ** 2 < 1.0]
+    tests = inwin = pts = 0
+    bin_slots = 0
+    for o, nz in zip(outs, nnz_px):
+        t = o["t"].cpu().numpy().astype(np.float64)
+        a = o["alive"].cpu().numpy().astype(bool)
+        kk, hh, ww = t.shape
+        pts += int(a.sum())
+        bin_slots += int((nz * a.sum(0)).sum())
+        for di, dj in cells:
+            i0, i1 = max(0, -di), min(hh, hh - di)
+            j0, j1 = max(0, -dj), min(ww, ww - dj)
+            if i0 >= i1 or j0 >= j1:
+                continue
+            r2 = (pitch * di / hr) ** 2 + (pitch * dj / hr) ** 2
+            for n in range(kk):
+                an = a[n, i0:i1, j0:j1]
+                tn = t[n, i0:i1, j0:j1]
+                for m in range(kk):
+                    am = a[m, i0 + di:i1 + di, j0 + dj:j1 + dj]
+                    both = an & am
+                    tests += int(both.sum())
+                    z = (t[m, i0 + di:i1 + di, j0 + dj:j1 + dj] - tn) / hr
+                    inwin += int((both & (r2 + z * z < 1.0)).sum())
+    nnz_total = int(sum(int(x.sum()) for x in nnz_px))
+    flop = 4 * tests + 30 * inwin + 60 * pts + 15 * bin_slots + 3 * nnz_total
+    return flop, {"alive_points": pts, "candidate_tests": tests, "in_window_neighbours": inwin,
+                  "nonzero_bins": nnz_total, "bin_point_pairs": bin_slots,
+                  "tests_per_point": round(tests / max(pts, 1), 2),
+                  "neighbours_per_point": round(inwin / max(pts, 1), 2)}
 
 
 def fused_fraction(prm) -> float:
@@ -209,6 +255,14 @@ def traffic_record(kernel: str):
     return rec.get("dram_bytes_per_launch_full")
 
 
+def bench_config(world: int) -> dict:
+    """The workload both arms name (the reference arm runs a bounded sample of it)."""
+    return {"workload": "net_object_wall 141x141x4096, K=3, gamma IRF (3,5), "
+                        "5 signal photons/px, SBR 1, 20 PALM iterations",
+            "l2": "inputs larger than L2 (dense histograms stream from HBM each step)",
+            "parallelism": f"replicas x{world}"}
+
+
 # --------------------------------------------------------------------------- our arm
 
 def run_ours(args, world, rank, local):
@@ -279,37 +333,52 @@ def run_ours(args, world, rank, local):
     t_max = max_over_ranks(ms_total, world, dev)
     value = job_throughput(nb, args.steps, world, t_max)
 
-    # ---------------- dominant kernel vs its roofline
-    n_points = int(sum(int(o["n_points"].item()) for o in outs))
+    # ---------------- the loop's own time: the same two-chain call with no
+    # PALM iteration (initialisation and finaliser only), subtracted
+    outs0 = [ctx.new_result(H, W, K) for _ in range(nb)]
+    ms_init_only = time_calls(ctx, dict(prm, n_iter=0), frames, outs0, max(3, min(args.steps, 10)))
+    del outs0
+    ms_loop = ms_total / args.steps - ms_init_only
+
+    # ---------------- rooflines (the path is HBM-bound)
+    n_px = nb * H * W
     ff = fused_fraction(prm)
-    alg = algorithmic_bytes(nb, nnz_total, K, ff)
-    flops = algorithmic_flops(nb, nnz_total, n_points, K, prm, ff)
+    alg = algorithmic_bytes(n_px, T, nnz_total, K, ff)
     peaks = measured_peaks()
     per_kernel = {}
     for name in KERNEL_NAMES:
         ms, n = ktimes[name]
         if n:
             sec = ms / n / 1000.0
-            d = dict(ms_total=ms, launches=n, ms_per_launch=ms / n,
-                     alg_bytes_per_launch=alg[name], gbs=alg[name] / sec / 1e9,
-                     hbm_frac=alg[name] / sec / 1e9 / peaks["hbm_gbs"])
-            if name in flops:
-                d.update(alg_flops_per_launch=flops[name], tflops=flops[name] / sec / 1e12,
-                         alu_frac=flops[name] / sec / 1e12 / peaks["fp32_tflops"])
-            per_kernel[name] = d
+            per_kernel[name] = dict(ms_total=ms, launches=n, ms_per_launch=ms / n,
+                                    alg_bytes_per_launch=alg[name], gbs=alg[name] / sec / 1e9,
+                                    hbm_frac=alg[name] / sec / 1e9 / peaks["hbm_gbs"])
     dom = max(per_kernel, key=lambda k: per_kernel[k]["ms_total"])
     d = per_kernel[dom]
-    if dom == "init" or dom == "final":
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": round(d["gbs"], 1),
-                    "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(d["hbm_frac"], 4),
-                    "peak_source": f"{peaks['source']} copy bandwidth (burst)",
-                    "traffic": traffic_record(dom)}
-    else:
-        roofline = {"bound": "alu", "kernel": dom, "achieved": round(d["tflops"], 2),
-                    "peak": round(peaks["fp32_tflops"], 1), "unit": "TFLOP/s",
-                    "frac": round(d["alu_frac"], 4),
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(d["gbs"], 1),
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": round(d["hbm_frac"], 4),
+                "peak_source": f"{peaks['source']} copy bandwidth (burst), of {peaks['source']}",
+                "alg_bytes_per_launch": int(d["alg_bytes_per_launch"]),
+                "ms_per_launch": round(d["ms_per_launch"], 5),
+                "traffic": traffic_record(dom)}
+    lb = loop_bytes_per_call(n_px, T, nnz_total, K, prm)
+    loop_roofline = {"bound": "hbm", "what": "all PALM-loop launches of a call (phases A, B, C, finaliser)",
+                     "alg_bytes_per_step": int(lb), "loop_ms_per_step": round(ms_loop, 4),
+                     "step_ms_without_iterations": round(ms_init_only, 4),
+                     "achieved": round(lb / (ms_loop * 1e-3) / 1e9, 1), "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": round(lb / (ms_loop * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                     "method": "loop time = two-chain step time minus the same call with n_iter = 0"}
+    # the ALU view of the dominant loop kernel, counting only the method's work
+    nnz_px = [torch.count_nonzero(dd.view(torch.int16), dim=2).cpu().numpy() for dd in dense]
+    flop_b, work = method_work(outs, nnz_px, prm, K)
+    alu_view = None
+    if "phase_b" in per_kernel:
+        sec_b = per_kernel["phase_b"]["ms_per_launch"] * 1e-3
+        alu_view = {"bound": "alu", "kernel": "phase_b", "alg_flop_per_launch": int(flop_b),
+                    "achieved": round(flop_b / sec_b / 1e12, 3), "peak": round(peaks["fp32_tflops"], 1),
+                    "unit": "TFLOP/s", "frac": round(flop_b / sec_b / 1e12 / peaks["fp32_tflops"], 4),
                     "peak_source": "FP32 FMA: 148 SMs x 128 lanes x 2 x max SM clock",
-                    "traffic": traffic_record(dom)}
+                    "work_counted_on_final_state": work}
 
     result = None
     if rank == 0:
@@ -347,23 +416,23 @@ def run_ours(args, world, rank, local):
             if not args.no_forms:
                 serving["learned"] = run_serving(args, local, learned_form=True)
 
+        # ---------------- execution time against pixels and active bins (Fig. 5)
+        sweep = run_fig5_sweep(args, local) if args.sweep else None
+
         # ---------------- the precision and learned forms
         forms = None
         if not args.no_forms:
             forms = {"tensor_core_init_on_this_workload": run_tc_headline(args, ctx, prm, frames, outs, peaks),
-                     "precision": run_precision_form(args, local, peaks),
-                     "learned": run_learned_form(args, local)}
+                     "precision": run_precision_form(args, local, peaks, with_oracle=not args.no_parity),
+                     "learned": run_learned_form(args, local, with_oracle=not args.no_parity)}
 
         result = {
             "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(t_max / args.steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 (matched filter int32)", "data": "synthetic (seeded Philox, device-resident)",
-            "config": {"workload": "net_object_wall 141x141x4096, K=3, gamma IRF (3,5), "
-                                   "5 signal photons/px, SBR 1, 20 PALM iterations",
-                       "frames_per_step": nb, "nnz_per_pixel": round(nnz_total / (nb * H * W), 2),
-                       "l2": "inputs larger than L2 (dense histograms stream from HBM each step)",
-                       "parallelism": f"replicas x{world}"},
+            "config": bench_config(world),
+            "frames_per_step": nb, "nnz_per_pixel": round(nnz_total / (nb * H * W), 2),
             "latency_ms": {"batch_step_p50": round(statistics.median(step_ms), 4),
                            "batch_step_p99": round(float(np.percentile(step_ms, 99)), 4),
                            "frame_p50": round(float(np.percentile(lat, 50)), 4),
@@ -372,6 +441,8 @@ def run_ours(args, world, rank, local):
             "e2e": e2e,
             "e2e_sparse": e2e_sparse,
             "roofline": roofline,
+            "loop_roofline": loop_roofline,
+            "alu_view": alu_view,
             "init_roofline": {"bound": "hbm", "achieved": round(per_kernel["init"]["gbs"], 1),
                               "peak": peaks["hbm_gbs"], "unit": "GB/s",
                               "frac": round(per_kernel["init"]["hbm_frac"], 4),
@@ -383,6 +454,7 @@ def run_ours(args, world, rank, local):
             "parity": parity,
             "serving": serving,
             "forms": forms,
+            "fig5_sweep": sweep,
             "cpu_baseline": cpu,
         }
     if world > 1:
@@ -419,6 +491,23 @@ def time_steps(ctx, prm, frames, outs, steps, warmup=2):
     return a.elapsed_time(b) / steps, {k: v[0] / v[1] for k, v in kt.items() if v[1]}
 
 
+def time_calls(ctx, prm, frames, outs, steps, warmup=2):
+    """Mean ms per batched call, timed with CUDA events on the current stream
+    (no per-kernel events: the library's production two-chain graph)."""
+    import torch
+    for _ in range(warmup):
+        ctx.reconstruct_batch(prm, frames, outs)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        ctx.reconstruct_batch(prm, frames, outs)
+    b.record()
+    b.synchronize()
+    return a.elapsed_time(b) / steps
+
+
 def init_bytes(n_px, t, k, nnz_total):
     """Algorithmic bytes of the initialisation (see algorithmic_bytes)."""
     return n_px * (2 * t + 8 + 9 * k + 4) + 4 * nnz_total
@@ -446,20 +535,21 @@ def run_tc_headline(args, ctx, prm, frames, outs, peaks) -> dict:
     return out
 
 
-def run_precision_form(args, device, peaks) -> dict:
+def run_precision_form(args, device, peaks, with_oracle=True) -> dict:
     """Precision form: 256 x 256 x 4096, two surfaces, SBR 0.1 (about 54
     photons per pixel), 8 frames per step; the matched filter on CUDA cores
     (integer) and on tensor cores (FP16 and BF16 operands, FP32 accumulation).
     The filter output is an exact integer in every mode, so the results are
-    bitwise equal and the depth error against the FP64 oracle is that of the
-    FP32 loop (stated by the parity tests)."""
+    bitwise equal; each mode's first frame is also compared with the FP64
+    oracle (depth error max / p99.9 / fraction within 1e-3 bins).  The loop's
+    HBM roofline fraction is reported for this workload too."""
     import torch
     from paper_1905_06700_b300 import rt3d as R
     h = w = 256
     t = 4096
     nb = 8
     base = scenes.two_layer(h, w, t)
-    prm = scenes.make_params(base)
+    prm = scenes.make_params(base, apss_fp64=1)        # this form solves APSS in FP64
     k = prm["k_max"]
     ctx = R.Context(h, w, t, k, base.irf.samples, base.irf.origin, max_batch=nb, device=device)
     dense = [ctx.synthesize(scenes.sampling_tables(scenes.two_layer(h, w, t, seed=1 + f))) for f in range(nb)]
@@ -467,33 +557,90 @@ def run_precision_form(args, device, peaks) -> dict:
     nnz = int(sum(int(torch.count_nonzero(d.view(torch.int16)).item()) for d in dense))
     frames = [dict(dense=d) for d in dense]
     outs = [ctx.new_result(h, w, k) for _ in range(nb)]
-    res = {"workload": "two_layer 256x256x4096, K=2, Gaussian IRF sigma 4, 5 signal photons/px, SBR 0.1, "
-                       "20 PALM iterations, 8 frames per step",
+    res = {"workload": "two_layer 256x256x4096, K=2, gamma IRF (3,5), 5 signal photons/px, SBR 0.1, "
+                       "20 PALM iterations, 8 frames per step; APSS normal equations solved in FP64 "
+                       "(integer_fp32_solve: the same in FP32)",
            "nnz_per_pixel": round(nnz / (nb * h * w), 1)}
+    oracle_runs = {}
+    if with_oracle:
+        import oracle
+        from oracle import compare
+        oracle.build()
+        z0 = dense[0].view(torch.int16).cpu().numpy().view(np.uint16)
+        oirf = oracle.OIrf(base.irf.samples, base.irf.origin)
+        oracle_runs = {1: compare.reconstruct_with_probes(z0, oirf, prm),
+                       0: compare.reconstruct_with_probes(z0, oirf, dict(prm, apss_fp64=0))}
     ref = None
-    for name, mode in (("integer", 0), ("fp16", 2), ("bf16", 1)):
-        ms, kt = time_steps(ctx, dict(prm, lmf_precision=mode), frames, outs, args.form_steps)
+    for name, mode, fp64 in (("integer", 0, 1), ("fp16", 2, 1), ("bf16", 1, 1), ("integer_fp32_solve", 0, 0)):
+        ms, kt = time_steps(ctx, dict(prm, lmf_precision=mode, apss_fp64=fp64), frames, outs, args.form_steps)
         init_ms = kt.get("init", 0.0) + kt.get("init_tc", 0.0)
         gbs = init_bytes(nb * h * w, t, k, nnz) / (init_ms * 1e-3) / 1e9
         entry = {"frames_per_s": round(nb / (ms / 1000), 2), "init_ms": round(init_ms, 4),
-                 "init_gbs": round(gbs, 1), "init_hbm_frac": round(gbs / peaks["hbm_gbs"], 4)}
+                 "init_gbs": round(gbs, 1), "init_hbm_frac": round(gbs / peaks["hbm_gbs"], 4),
+                 "phase_b_ms": round(kt.get("phase_b", 0.0), 4),
+                 "apss_solve": "fp64" if fp64 else "fp32"}
         if ref is None:
             ref = [{kk: v.clone() for kk, v in o.items()} for o in outs]
-        else:
+            # the loop's HBM roofline on this workload
+            ms0 = time_calls(ctx, dict(prm, n_iter=0), frames, [ctx.new_result(h, w, k) for _ in range(nb)],
+                             args.form_steps)
+            lb = loop_bytes_per_call(nb * h * w, t, nnz, k, prm)
+            loop_ms = ms - ms0
+            res["loop_roofline"] = {"bound": "hbm", "alg_bytes_per_step": int(lb),
+                                    "loop_ms_per_step": round(loop_ms, 4),
+                                    "achieved": round(lb / (loop_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+                                    "peak": peaks["hbm_gbs"],
+                                    "frac": round(lb / (loop_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)}
+        elif fp64:
             entry["bitwise_equal_to_integer_path"] = bool(all(
                 torch.equal(a[kk], b[kk]) for a, b in zip(ref, outs) for kk in ("t", "r", "alive", "b")))
+        if fp64 in oracle_runs:
+            from oracle import compare
+            o, probes = oracle_runs[fp64]
+            g = {kk: v.cpu().numpy() for kk, v in outs[0].items() if kk != "n_points"}
+            st = compare.cloud_stats(g, o, probes, t, 1e-3, 1e-4, r_min=prm["r_min"])
+            entry["vs_fp64_oracle_frame0"] = {
+                "points": st["points"], "alive_mismatch": st["all_alive_mismatch"],
+                "dt_max_bins": st["all_dt_max"], "dt_p999_bins": st["all_dt_p999"],
+                "frac_within_1e-3_bins": st["all_frac_within_tol"],
+                "ill_conditioned": st["ill"], "dt_max_bins_well_conditioned": st["dt_max"],
+                "dr_max_rel_well_conditioned": st["dr_max"],
+                "ill_conditioned_over_3x_probe_deviation": st["ill_over_bound"],
+                "ill_conditioned_worst_ratio_to_probe": st["ill_ratio_max"]}
         res[name] = entry
     assert ctx.device_status() == R.RT3D_OK
     ctx.close()
     return res
 
 
-def run_learned_form(args, device) -> dict:
-    """Learned form: 256 x 256 x 2048 random planes, spheres and boxes (1-20
-    signal photons/px, SBR 0.05-2), the committed network in place of APSS;
+def learned_oracle_error(sc, dense, out, prm, theta) -> dict:
+    """The learned form's error against the FP64 oracle running the same
+    network on the same frame (the stated error of the bf16 form)."""
+    import torch
+    import oracle
+    oracle.build()
+    z = dense.view(torch.int16).cpu().numpy().view(np.uint16)
+    o = oracle.reconstruct(z, oracle.OIrf(sc.irf.samples, sc.irf.origin),
+                           dict(prm, net_theta=np.asarray(theta, np.float64)))
+    g = {k: v.cpu().numpy() for k, v in out.items() if k != "n_points"}
+    ga, oa = g["alive"].astype(bool), o.alive.astype(bool)
+    both = ga & oa
+    dt = np.abs(g["t"].astype(np.float64) - o.t)[both]
+    dr = (np.abs(g["r"].astype(np.float64) - o.r) / np.maximum(o.r, 0.1))[both]
+    return {"points": int(oa.sum()), "alive_mismatch": int((ga != oa).sum()),
+            "dt_median_bins": float(np.median(dt)), "dt_p99_bins": float(np.percentile(dt, 99)),
+            "dt_p999_bins": float(np.percentile(dt, 99.9)), "dt_max_bins": float(dt.max()),
+            "frac_within_1e-3_bins": float((dt <= 1e-3).mean()),
+            "dr_median_rel": float(np.median(dr)), "dr_p99_rel": float(np.percentile(dr, 99))}
+
+
+def run_learned_form(args, device, with_oracle=True) -> dict:
+    """Learned form and the other plug-in depth denoisers: 256 x 256 x 2048
+    random planes, spheres and boxes (1-20 signal photons/px, SBR 0.05-2);
     throughput, single-frame latency and the inlier depth error against the
-    true surfaces (points within 5 IRF sigma) for no depth denoiser, APSS and
-    the learned form."""
+    true surfaces (points within 5 IRF sigma) for no depth denoiser, APSS,
+    the local plane fit, the bilateral depth filter and the learned form (the
+    committed network in place of APSS)."""
     import torch
     from paper_1905_06700_b300 import learned
     from paper_1905_06700_b300 import rt3d as R
@@ -519,7 +666,7 @@ def run_learned_form(args, device) -> dict:
     res = {"workload": "random_shapes 256x256x2048 (seeds 200000-200007), K=2, Gaussian IRF sigma 3, "
                        "20 PALM iterations, 8 frames per step",
            "checkpoint": {kk: head[kk] for kk in ("trained_on", "training") if kk in head}}
-    for name, den in (("none", 0), ("apss", 1), ("learned", 2)):
+    for name, den in (("none", 0), ("apss", 1), ("plane", 3), ("bilateral", 4), ("learned", 2)):
         p = dict(prm, depth_denoiser=den)
         ms, kt = time_steps(ctx, p, frames, outs, args.form_steps)
         errs = [learned.depth_errors(o, sc.depth, inlier) for o, sc in zip(outs, scs)]
@@ -534,6 +681,8 @@ def run_learned_form(args, device) -> dict:
             b.synchronize()
             if i >= 2:
                 lat.append(a.elapsed_time(b))
+        if den == 2 and with_oracle:
+            res["learned_vs_fp64_oracle_frame0"] = learned_oracle_error(scs[0], dense[0], outs[0], p, theta)
         res[name] = {"frames_per_s": round(nb / (ms / 1000), 2),
                      "frame_latency_ms_p50": round(float(np.percentile(lat, 50)), 3),
                      "frame_latency_ms_p99": round(float(np.percentile(lat, 99)), 3),
@@ -544,6 +693,62 @@ def run_learned_form(args, device) -> dict:
     assert ctx.device_status() == R.RT3D_OK
     ctx.close()
     return res
+
+
+def run_fig5_sweep(args, device) -> dict:
+    """Execution time per frame against (a) the pixel count at about four
+    active bins per pixel and (b) the mean number of active (nonzero) bins
+    per pixel at 141 x 141 pixels (Methods, Fig. 5), on head-like frames
+    (one surface per pixel, two at the head's rim; gamma IRF; 3 signal
+    photons per pixel, T = 4096, K = 2, 20 PALM iterations).  Per point: the
+    median over repeated single-frame calls (the paper's per-frame time, CUDA
+    events, inputs resident) and the per-frame time of 8-frame batched calls."""
+    import torch
+    from paper_1905_06700_b300 import rt3d as R
+    t = 4096
+    reps = 7
+
+    def measure(h, w, bkg_photons, nb=8):
+        scs = [scenes.head_like(h, w, t, seed=1 + f, bkg_photons=bkg_photons) for f in range(nb)]
+        prm = scenes.make_params(scs[0])
+        k = prm["k_max"]
+        exp_nnz = 4.0 + bkg_photons
+        ctx = R.Context(h, w, t, k, scs[0].irf.samples, scs[0].irf.origin, max_batch=nb, device=device,
+                        max_entries=int(nb * h * w * (2 * exp_nnz + 64)))
+        dense = [ctx.synthesize(scenes.sampling_tables(sc)) for sc in scs]
+        torch.cuda.synchronize()
+        nnz = float(np.mean([torch.count_nonzero(d.view(torch.int16)).item() / (h * w) for d in dense]))
+        one = ctx.new_result(h, w, k)
+        lat = []
+        for i in range(reps + 2):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            ctx.reconstruct(prm, dense=dense[i % nb], out=one)
+            b.record()
+            b.synchronize()
+            if i >= 2:
+                lat.append(a.elapsed_time(b))
+        outs = [ctx.new_result(h, w, k) for _ in range(nb)]
+        ms = time_calls(ctx, prm, [dict(dense=d) for d in dense], outs, 3)
+        assert ctx.device_status() == R.RT3D_OK
+        ctx.close()
+        del dense, outs
+        torch.cuda.empty_cache()
+        return {"pixels": h * w, "mean_active_bins": round(nnz, 2),
+                "frame_ms_single": round(float(np.median(lat)), 4),
+                "frame_ms_batched": round(ms / nb, 4)}
+
+    by_pixels = [dict(side=sd, **measure(sd, sd, 1.2)) for sd in (32, 64, 96, 141, 192, 256, 384, 512)]
+    by_bins = [dict(bkg_photons=bp, **measure(141, 141, bp)) for bp in (0.0, 1.0, 3.0, 8.0, 20.0, 50.0, 100.0, 200.0)]
+    x = np.array([r["mean_active_bins"] for r in by_bins])
+    y = np.array([r["frame_ms_single"] for r in by_bins])
+    slope, icpt = np.polyfit(x, y, 1)
+    return {"workload": "head_like frames, T=4096, K=2, gamma IRF (3,5), 3 signal photons/px, 20 iterations",
+            "time_vs_pixels_4_active_bins": by_pixels,
+            "time_vs_active_bins_141x141": by_bins,
+            "linear_fit_single_frame_ms_vs_active_bins": {"slope_ms_per_bin": round(float(slope), 5),
+                                                          "intercept_ms": round(float(icpt), 4)}}
 
 
 def _pinned(shape, dtype):
@@ -590,52 +795,40 @@ def run_e2e(args, ctx, prm, dense, R):
     return res
 
 
+def oracle_parity(z, irf_samples, irf_origin, prm, out, h, w, t) -> dict:
+    """Error of one reconstructed frame (`out`, the library's result tensors)
+    against the FP64 oracle on the same histogram `z`.  The oracle's probe
+    ensemble (oracle.compare: the oracle's loop with its state rounded after
+    every step as FP32 kernels round theirs, at three perturbation sizes)
+    marks the points the method itself moves under a perturbation of that
+    size; the error is reported over the other points, over all points, and
+    on the ill-conditioned ones against the probes' own deviation."""
+    import oracle
+    from oracle import compare
+    irf = oracle.OIrf(irf_samples, irf_origin)
+    o, probes = compare.reconstruct_with_probes(z, irf, prm)
+    g = {k: v.cpu().numpy() for k, v in out.items() if k != "n_points"}
+    st = compare.cloud_stats(g, o, probes, t, 1e-3, 1e-4, r_min=prm["r_min"])
+    return {"points": st["points"], "ill_conditioned": st["ill"],
+            "alive_mismatch_well_conditioned": st["flips"],
+            "dt_max_bins_well_conditioned": st["dt_max"],
+            "dt_p999_bins_well_conditioned": st["dt_p999"],
+            "dr_max_rel_well_conditioned": st["dr_max"],
+            "ill_conditioned_flips": st["ill_flips"],
+            "ill_conditioned_flips_no_probe_flips": st["ill_flips_unexplained"],
+            "ill_conditioned_over_3x_probe_deviation": st["ill_over_bound"],
+            "ill_conditioned_worst_ratio_to_probe": st["ill_ratio_max"],
+            "near_threshold_points": st.get("near_threshold", 0),
+            "alive_mismatch": st["all_alive_mismatch"],
+            "dt_max_bins": st["all_dt_max"], "dt_p999_bins": st["all_dt_p999"],
+            "frac_within_1e-3_bins": st["all_frac_within_tol"]}
+
+
 def _parity_of_frame(oracle, prm, seed, out) -> dict:
-    """Depth/intensity error of the benchmark's first frame against the FP64
-    oracle.  A second oracle run, its state rounded after every step as FP32
-    kernels round theirs (depths to float32, intensities and backgrounds to 20
-    significant bits), marks the points the method itself moves under a
-    perturbation of that size; the error is reported over the other points and
-    over all of them."""
+    """Parity of the benchmark's frame `seed` (its result `out`) against the oracle."""
     sc = scenes.net_object_wall(H, W, T, seed=seed)
     z = oracle.synthesize(scenes.sampling_tables(sc))
-    irf = oracle.OIrf(sc.irf.samples, sc.irf.origin)
-    o = oracle.reconstruct(z, irf, prm)
-    fr = oracle.OFrame(z)
-    q = oracle.init(z, None, irf, prm)
-
-    def rnd(s):
-        s.t[:] = s.t.astype(np.float32)
-        for a in (s.r, s.b):
-            m, e = np.frexp(a)
-            a[:] = np.ldexp(np.round(m * 2.0 ** 20) / 2.0 ** 20, e)
-    rnd(q)
-    for _ in range(prm["n_iter"]):
-        oracle.t_step(fr, irf, prm, q); rnd(q)
-        if prm["depth_denoiser"] == 1:
-            oracle.apss(H, W, T, prm, q); rnd(q)
-        oracle.r_step(fr, irf, prm, q); rnd(q)
-        oracle.int_lowpass(H, W, prm, q); rnd(q)
-        oracle.b_step(fr, irf, prm, q); rnd(q)
-        oracle.bkg_lowpass(H, W, prm, q.b); rnd(q)
-    oa, qa = o.alive.astype(bool), q.alive.astype(bool)
-    ill = (oa != qa) | (oa & qa & (np.abs(o.t - q.t) > 5e-4)) | \
-          (oa & qa & (np.abs(o.r - q.r) > 5e-5 * np.maximum(np.abs(o.r), 0.1)))
-    g = {k: v.cpu().numpy() for k, v in out.items()}
-    ga = g["alive"].astype(bool)
-    both = ga & oa
-    dt_all = np.abs(g["t"].astype(np.float64) - o.t)
-    dr_all = np.abs(g["r"].astype(np.float64) - o.r) / np.maximum(o.r, 0.1)
-    well = both & ~ill
-    return {"points": int(oa.sum()), "ill_conditioned": int(ill.sum()),
-            "alive_mismatch_well_conditioned": int(((ga != oa) & ~ill).sum()),
-            "dt_max_bins_well_conditioned": float(dt_all[well].max()),
-            "dr_max_rel_well_conditioned": float(dr_all[well].max()),
-            "alive_mismatch": int((ga != oa).sum()),
-            "dt_max_bins": float(dt_all[both].max()), "dt_p999_bins": float(np.percentile(dt_all[both], 99.9)),
-            "dt_median_bins": float(np.median(dt_all[both])),
-            "dr_p999_rel": float(np.percentile(dr_all[both], 99.9)),
-            "frac_within_1e-3_bins": float((dt_all[both] <= 1e-3).mean())}
+    return oracle_parity(z, sc.irf.samples, sc.irf.origin, prm, out, H, W, T)
 
 
 def cpu_baseline(args, prm, parity_frame=None):
@@ -656,6 +849,18 @@ def cpu_baseline(args, prm, parity_frame=None):
     base = {"value": round(len(zs) / dt, 4), "unit": UNIT, "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"{len(zs)} full 141x141x4096 frames (init + 20 iterations), FP64, OpenMP"}
+    if args.cpu_single_frames > 0:
+        # the same oracle on one host thread
+        cores = oracle.num_threads()
+        oracle.set_num_threads(1)
+        t0 = time.perf_counter()
+        for sc, z in zs[:args.cpu_single_frames]:
+            oracle.reconstruct(z, irf, prm)
+        dt1 = time.perf_counter() - t0
+        oracle.set_num_threads(cores)
+        base["single_thread"] = {"value": round(args.cpu_single_frames / dt1, 4), "unit": UNIT, "cores": 1,
+                                 "sample": f"{args.cpu_single_frames} full 141x141x4096 frame(s), FP64, "
+                                           f"one thread"}
     parity = _parity_of_frame(oracle, prm, *parity_frame) if parity_frame is not None else None
     return base, parity
 
@@ -749,8 +954,7 @@ def run_reference(args, world, rank):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(1000 * total / args.steps, 2), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "net_object_wall 141x141x4096, K=3, 20 PALM iterations",
-                       "frames_per_step": 1},
+            "config": bench_config(world), "frames_per_step": 1,
             "cpu_baseline": {"value": round(value, 4), "unit": UNIT, "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": round(value, 4), "unit": UNIT, "h2d_bytes_per_step": 0,

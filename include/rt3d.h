@@ -67,8 +67,19 @@ typedef enum {
 
 /* Matched-filter arithmetic (all exact for counts within range). */
 enum { RT3D_LMF_INT = 0, RT3D_LMF_BF16 = 1, RT3D_LMF_FP16 = 2 };
-/* Depth denoiser: none, APSS (the paper's), learned conv net (if loaded). */
-enum { RT3D_DEPTH_NONE = 0, RT3D_DEPTH_APSS = 1, RT3D_DEPTH_LEARNED = 2 };
+/* Depth denoiser: none, APSS (the paper's), learned conv net (if loaded), and
+ * two other plug-in point cloud denoisers (the Discussion's quality / speed
+ * trade-off) over the APSS neighbourhood, weights and radius:
+ *   RT3D_DEPTH_PLANE      weighted least-squares plane u0 + u1 x + u2 y + z = 0
+ *                         in the point's local coordinates, point moved along
+ *                         the line of sight onto it (APSS without the sphere
+ *                         term: planes are kept, spheres flattened);
+ *   RT3D_DEPTH_BILATERAL  the weight-averaged depth of the neighbours (itself
+ *                         included): a bilateral depth filter.
+ * Both leave a point unchanged with fewer than apss_min_nb weighted
+ * neighbours; the plane fit also with collinear neighbour pixels. */
+enum { RT3D_DEPTH_NONE = 0, RT3D_DEPTH_APSS = 1, RT3D_DEPTH_LEARNED = 2, RT3D_DEPTH_PLANE = 3,
+       RT3D_DEPTH_BILATERAL = 4 };
 /* Background denoiser: identity (bistatic) or periodic Gaussian (= FFT low-pass). */
 enum { RT3D_BKG_IDENTITY = 0, RT3D_BKG_LOWPASS = 1 };
 
@@ -143,6 +154,9 @@ typedef struct {
     float net_scale;               /* learned depth denoiser: depth scale of its features and output (bins), > 0 */
     float net_fallback;            /* learned depth denoiser: a point whose proposed move exceeds this (bins)
                                       takes the APSS update instead */
+    int32_t apss_fp64;             /* 1: the APSS fit's normal equations (centring, Cholesky, projection)
+                                      are solved in FP64 from the FP32 neighbourhood moments, for APSS
+                                      and the learned form's APSS fallback; 0: in FP32 */
 } rt3d_params;
 
 /* Output (and, with warm_start, input) point cloud: DEVICE buffers owned by
@@ -269,11 +283,23 @@ rt3d_status rt3d_phase(rt3d_ctx_t* ctx, int phase, int first, const rt3d_frame* 
                        const rt3d_params* p, rt3d_result* state, void* stream);
 
 /* Synchronise `stream`, then return and clear the device-side status word
- * (RT3D_OK, RT3D_E_CAPACITY or RT3D_E_RANGE). */
+ * (RT3D_OK, RT3D_E_TIMEOUT, RT3D_E_CAPACITY or RT3D_E_RANGE, in that order of
+ * precedence). */
 rt3d_status rt3d_device_status(rt3d_ctx_t* ctx, void* stream);
 
 /* Kernel launches made by this context since creation (all entry points). */
 int64_t rt3d_launch_count(rt3d_ctx_t* ctx);
+
+/* Bound, in nanoseconds, of every device-side wait of this context's
+ * tensor-core kernels (the BF16/FP16 matched filter and the learned
+ * denoiser's pipelined convolution); default 1e9.  It takes effect from the
+ * next call (it travels in the call record).  A kernel whose wait reaches the
+ * bound stops, awaits its copies and matrix operations in flight, frees its
+ * tensor memory and raises RT3D_E_TIMEOUT in rt3d_device_status(); that
+ * call's results are not valid, the context stays usable.  0 gives up at the
+ * first wait that has not already completed (a test of that path).
+ * RT3D_E_INVALID for ns < 0. */
+rt3d_status rt3d_set_wait_limit(rt3d_ctx_t* ctx, int64_t ns);
 
 /* Per-kernel timing with CUDA events recorded around each launch (off by
  * default).  rt3d_kernel_times synchronises and returns, for kernel class i

@@ -9,11 +9,13 @@ distance, the denoisers' neighbour cut-offs) and has steep regions (photons
 on the onset of a gamma IRF), so a perturbation of the size of single
 precision rounding can move some points by far more than the rounding.  A
 *probe* is the oracle's loop with its state rounded after every step the way
-single-precision kernels round theirs: depths to float32, intensities and
-backgrounds to `bits` significant bits (about the rounding of a float32 sum
-of ~100 terms).  Points where the oracle and its probe disagree beyond half
-the tolerance are ill-conditioned; the GPU is held there to a bound set by
-the probes' own deviation (cloud_stats).
+single-precision kernels perturb theirs: depths to `t_bits` significant bits
+(24 = float32 storage; 23 and 25 stand for one more or one less rounding of
+the depth arithmetic) and intensities and backgrounds to `rb_bits` (about the
+rounding of a float32 sum of ~100 terms).  Points where the oracle and any
+probe of the ensemble disagree beyond half the tolerance are ill-conditioned;
+the GPU is held there to a bound set by the probes' own deviation
+(cloud_stats).
 """
 from __future__ import annotations
 
@@ -21,7 +23,8 @@ import numpy as np
 
 from . import oracle as O
 
-PROBE_BITS = (20, 18, 22)     # the probe ensemble: perturbations of 2^-20, 2^-18, 2^-22
+# the probe ensemble: (depth bits, intensity/background bits)
+PROBE_BITS = ((24, 20), (24, 18), (23, 19), (25, 21), (24, 22))
 
 
 def round_bits(a, bits):
@@ -31,13 +34,15 @@ def round_bits(a, bits):
 
 
 def _rnd(st, bits):
-    st.t[:] = st.t.astype(np.float32)
-    st.r[:] = round_bits(st.r, bits)
-    st.b[:] = round_bits(st.b, bits)
+    t_bits, rb_bits = bits
+    st.t[:] = st.t.astype(np.float32) if t_bits == 24 else round_bits(st.t, t_bits)
+    st.r[:] = round_bits(st.r, rb_bits)
+    st.b[:] = round_bits(st.b, rb_bits)
 
 
 def probe_palm(fr, irf, prm, start, n_iter, bits):
-    """The oracle's PALM loop from `start` (copied), rounded after every step."""
+    """The oracle's PALM loop from `start` (copied), rounded after every step
+    (bits = (depth bits, intensity/background bits))."""
     st = start.copy()
     _rnd(st, bits)
     h, w, t = fr.hh, fr.ww, fr.tt
@@ -77,10 +82,11 @@ def ill_mask(o, probe, tol_t, tol_r):
     return ill
 
 
-def cloud_stats(gpu, o, probes, T, tol_t, tol_r, r_min=None, ratio=2.0):
+def cloud_stats(gpu, o, probes, T, tol_t, tol_r, r_min=None, ratio=3.0):
     """Statistics of a reconstruction `gpu` (dict of numpy arrays t, r, alive,
     b) against the oracle state `o`, with the ill-conditioned points taken
-    from the first probe.
+    from the probe ensemble (a point is ill-conditioned if any probe moves it
+    beyond half the tolerance, ill_mask).
 
     Well-conditioned points: flips (alive differs), depth error (bins),
     relative intensity error (floor 0.1 photon), background error relative to
@@ -99,7 +105,9 @@ def cloud_stats(gpu, o, probes, T, tol_t, tol_r, r_min=None, ratio=2.0):
     whose final intensity lies within 1e-5 r_min of r_min (counted only)."""
     ga = gpu["alive"].astype(bool)
     oa = o.alive.astype(bool)
-    ill = ill_mask(o, probes[0], tol_t, tol_r) if probes else np.zeros_like(oa)
+    ill = np.zeros_like(oa)
+    for p in probes:
+        ill |= ill_mask(o, p, tol_t, tol_r)
     ok = ~ill
     both = ga & oa
     dt_all = np.abs(gpu["t"].astype(np.float64) - o.t)

@@ -36,9 +36,10 @@
 //       +-sep test reads a two-tile ring of y in shared memory; candidates
 //       near a tile end wait for the next tile;
 //     - after the last tile: b0 and r0 from the entries, as the CUDA-core path.
-// Every wait is bounded (about one second); on expiry the CTA raises the
-// timeout status, the other roles drain, copies in flight are awaited and the
-// tensor memory is freed.
+// Every wait is bounded (KParams::wait_ns, one second by default); on expiry
+// the CTA raises the timeout status, the other roles leave their loops, the
+// copies and MMAs in flight are awaited (each drain bounded by kTcDrainNs)
+// and the tensor memory is freed.
 #pragma once
 #include "rt3d_device.cuh"
 
@@ -59,7 +60,8 @@ constexpr int kTcEpiWarps = 4;
 constexpr int kTcThreads = (kTcEpiWarps + 2) * 32;
 constexpr int kTcBarBytes = 1024;
 constexpr int kTcSmemLimit = 227 * 1024;
-constexpr unsigned long long kTcWaitNs = 1000000000ull;   // bound of every wait
+constexpr unsigned long long kTcWaitNs = 1000000000ull;   // default bound of every wait (KParams::wait_ns)
+constexpr unsigned long long kTcDrainNs = 1000000000ull;  // bound of the teardown drains (copies, MMAs)
 
 __host__ __device__ constexpr int tc_smem_bytes(int nd, int stages)
 {
@@ -124,19 +126,32 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parit
 }
 
 // Wait for the phase of `bar` with the given parity.  Gives up once the
-// CTA's abort flag is raised or after kTcWaitNs, raising the flag itself.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag)
+// CTA's abort flag is raised or after `limit` ns, raising the flag itself
+// (limit 0: gives up unless the phase has already completed).
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                          unsigned long long limit)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     while (true) {
-        if (mbar_try_wait_sleep(bar, parity)) return true;
         if (*abort_flag) return false;
-        if (global_ns() - t0 > kTcWaitNs) {
+        if (global_ns() - t0 >= limit) {
             *abort_flag = 1;
             return false;
         }
+        if (mbar_try_wait_sleep(bar, parity)) return true;
     }
+}
+
+// Wait for a phase regardless of the abort flag, bounded by kTcDrainNs: used
+// at teardown for copies and MMAs still in flight (after an abort).
+__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const unsigned long long t0 = global_ns();
+    while (!mbar_try_wait_sleep(bar, parity))
+        if (global_ns() - t0 > kTcDrainNs) return false;
+    return true;
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x,
@@ -210,6 +225,7 @@ __device__ __forceinline__ void tc_ld32(uint32_t taddr, uint32_t (&v)[32])
 
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+
 // ------------------------------------------------------------------ kernel
 
 // Candidate at tau (value yc, raw bits) passes the full +-sep test: strictly
@@ -275,11 +291,14 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
     int* ring = reinterpret_cast<int*>(gbase + (size_t)(nd + S) * kTcStageBytes);
     unsigned char* misc_g = gbase + (size_t)(nd + S) * kTcStageBytes + kTcRingBytes;
     const uint32_t misc = base + (uint32_t)(nd + S) * kTcStageBytes + kTcRingBytes;
-    // barriers: full[S], empty[S], acc_full[4], acc_empty[4]; then tmem base, abort flag
+    // barriers: full[S], empty[S], acc_full[4], acc_empty[4]; then tmem base,
+    // abort flag, the MMA drain barrier
     const uint32_t bar_full = misc, bar_empty = misc + 8 * kTcMaxStages;
     const uint32_t bar_accf = misc + 16 * kTcMaxStages, bar_acce = bar_accf + 8 * kTcAccBufs;
     volatile uint32_t* tmem_slot = reinterpret_cast<volatile uint32_t*>(misc_g + 16 * kTcMaxStages + 16 * kTcAccBufs);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(misc_g + 16 * kTcMaxStages + 16 * kTcAccBufs + 4);
+    const uint32_t bar_drain = misc + 16 * kTcMaxStages + 16 * kTcAccBufs + 8;
+    const unsigned long long wlim = P.wait_ns;
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -300,6 +319,7 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
             mbar_init(bar_accf + 8 * a, 1);
             mbar_init(bar_acce + 8 * a, kTcEpiWarps);
         }
+        mbar_init(bar_drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -329,7 +349,7 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
                 tmap_acquire(map);
                 for (int b = 0; b < nbk; ++b, ++g) {
                     const uint32_t s = g % (uint32_t)S;
-                    if (g >= (uint32_t)S && !mbar_wait(bar_empty + 8 * s, ((g / S) & 1u) ^ 1u, abort_flag)) {
+                    if (g >= (uint32_t)S && !mbar_wait(bar_empty + 8 * s, ((g / S) & 1u) ^ 1u, abort_flag, wlim)) {
                         stop = true;
                         break;
                     }
@@ -341,10 +361,7 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
             // each stage completes its full barrier
             for (uint32_t k = 0; k < (uint32_t)S && k < g; ++k) {
                 const uint32_t last = g - 1 - k;
-                const uint32_t s = last % (uint32_t)S;
-                const unsigned long long t0 = global_ns();
-                while (!mbar_try_wait(bar_full + 8 * s, (last / S) & 1u))
-                    if (global_ns() - t0 > kTcWaitNs) break;
+                mbar_drain(bar_full + 8 * (last % (uint32_t)S), (last / S) & 1u);
             }
         }
     } else if (warp == kTcEpiWarps + 1) {
@@ -355,7 +372,7 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
 #pragma unroll
             for (int di = 0; di < kTcMaxOff; ++di) ksmask[di] = P.tc_ksmask[di];
             uint32_t g0 = 0, acc_cnt = 0;
-            bool stop = false;
+            bool stop = false, issued = false;
             for (int tile = tc0 + (int)blockIdx.x; tile < tc1 && !stop; tile += gridDim.x) {
                 const FrameDesc& F = B.f[frame_of_tc_tile(B, tile)];
                 const int nbk = (F.nt + kTcBlk - 1) / kTcBlk;
@@ -363,7 +380,7 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
                 for (int j = 0; j < nbk && !stop; ++j, ++acc_cnt) {
                     const uint32_t a = acc_cnt % kTcAccBufs;
                     if (acc_cnt >= (uint32_t)kTcAccBufs &&
-                        !mbar_wait(bar_acce + 8 * a, ((acc_cnt / kTcAccBufs) & 1u) ^ 1u, abort_flag)) {
+                        !mbar_wait(bar_acce + 8 * a, ((acc_cnt / kTcAccBufs) & 1u) ^ 1u, abort_flag, wlim)) {
                         stop = true;
                         break;
                     }
@@ -379,7 +396,7 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
                         const uint32_t s = gb % (uint32_t)S;
                         // TMA completion is observed through the barrier; the MMA
                         // reads the stage in the same (async) proxy
-                        if (!mbar_wait(bar_full + 8 * s, (gb / S) & 1u, abort_flag)) {
+                        if (!mbar_wait(bar_full + 8 * s, (gb / S) & 1u, abort_flag, wlim)) {
                             stop = true;
                             break;
                         }
@@ -391,6 +408,7 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
                             tc_mma(dt, tc_desc_sw128(sA + s * kTcStageBytes + ks * 32),
                                    tc_desc_sw128(sB + di * kTcBBytes + ks * 32), idesc, accumulate);
                             accumulate = 1;
+                            issued = true;
                         }
                     }
                     if (stop) break;
@@ -400,6 +418,12 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
                     for (; rel <= hi; ++rel) tc_commit(bar_empty + 8 * ((g0 + (uint32_t)rel) % (uint32_t)S));
                 }
                 g0 += (uint32_t)nbk;
+            }
+            // every MMA has finished before the tensor memory is freed (after an
+            // abort some were issued without a commit the epilogue waited for)
+            if (issued) {
+                tc_commit(bar_drain);
+                mbar_drain(bar_drain, 0u);
             }
         }
     } else {
@@ -436,7 +460,8 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
             for (int j = 0; j < nbk; ++j, ++acc_cnt) {
                 const uint32_t a = acc_cnt % kTcAccBufs;
                 // lanes agree on every wait's outcome (warp-collective steps follow)
-                if (!__all_sync(0xffffffffu, mbar_wait(bar_accf + 8 * a, (acc_cnt / kTcAccBufs) & 1u, abort_flag))) {
+                if (!__all_sync(0xffffffffu,
+                                mbar_wait(bar_accf + 8 * a, (acc_cnt / kTcAccBufs) & 1u, abort_flag, wlim))) {
                     stop = true;
                     break;
                 }
@@ -464,7 +489,7 @@ k_init_tc(const CallRecord* __restrict__ rec, const Work W, const uint8_t* __res
                 for (; c_next <= chi; ++c_next) {
                     const uint32_t gb = g0 + (uint32_t)c_next;
                     const uint32_t s = gb % (uint32_t)S;
-                    if (!__all_sync(0xffffffffu, mbar_wait(bar_full + 8 * s, (gb / S) & 1u, abort_flag))) {
+                    if (!__all_sync(0xffffffffu, mbar_wait(bar_full + 8 * s, (gb / S) & 1u, abort_flag, wlim))) {
                         stop = true;
                         break;
                     }

@@ -456,19 +456,51 @@ __device__ __forceinline__ int win_fill(const unsigned* vote, int R, float px, i
     return __popc(v0) + __popc(v1) + __popc(v2);
 }
 
-// APSS projection of one point (Results, "Depth update"; Guennebaud & Gross):
-// weighted algebraic-sphere fit s(x) = u0 + u1 x + u2 y + z + u4 |x|^2 over
-// the window (local coordinates scaled by 1/h), solved in centred form --
-// the 3x3 normal equations of (x, y, |x|^2) against z, then u0 from the
-// weighted means -- and projection along the line of sight onto s = 0.
+// Depth denoiser variants of phase B (template argument V):
+constexpr int kDenApss = 0;       // APSS, solve in FP32
+constexpr int kDenApss64 = 1;     // APSS, solve in FP64
+constexpr int kDenPlane = 2;      // local plane fit
+constexpr int kDenBilateral = 3;  // bilateral depth filter
+
+// FP64 reciprocal and reciprocal square root for the FP64 solve: the
+// single-precision hardware approximation refined by one Newton-Raphson step
+// in double, y <- y (2 - x y) and y <- y (3 - x y^2) / 2, which squares the
+// seed's relative error (about 2^-22) to about 2^-44.
+__device__ __forceinline__ double rcp64(double x)
+{
+    const double y = (double)__frcp_rn((float)x);
+    return fma(y, fma(-x, y, 1.0), y);
+}
+
+__device__ __forceinline__ double rsqrt64(double x)
+{
+    const double y = (double)rsqrtf((float)x);
+    return y * fma(-0.5 * x, y * y, 1.5);
+}
+
+// Depth denoiser of one point (Results, "Depth update"), over the window
+// cells of the unit disk (win_fill's list; qc is the point's halo index).
 // Dead or absent slots hold a far sentinel depth, so their weight is exactly
 // zero; each thread accumulates only the slots inside the window (in slot
-// order) over the cells of the unit disk (win_fill's list; qc is the point's
-// halo index).
-template <int K>
+// order).  Local coordinates are scaled by 1/h and taken about the point
+// itself; weights (1 - d^2)^4.
+//   APSS (Guennebaud & Gross): the weighted algebraic-sphere fit
+//     s(x) = u0 + u1 x + u2 y + z + u4 |x|^2, solved as the 3x3 normal
+//     equations of (x, y, |x|^2) against z about the weighted means
+//     (covariances from the raw moments, E[ab] - E[a] E[b]), then u0 from the
+//     means; projection along the line of sight onto s = 0.  kDenApss64 takes
+//     the covariances, the Cholesky solve and the projection in FP64 from the
+//     FP32 moments.
+//   Plane fit: the same without the sphere term (2x2 system), z* = -u0.
+//   Bilateral: z* = sum w z / sum w.
+// A point with fewer than apss_min_nb weighted neighbours (or, for the fits,
+// collinear pixel offsets) keeps its depth.
+template <int K, int V>
 __device__ float apss_point(const float* st, const float4* wg, const uint4* wi, int n_off, int qc, float tn,
                             const KParams& P, int T)
 {
+    constexpr bool kSphere = V == kDenApss || V == kDenApss64;
+    constexpr bool kFit = V != kDenBilateral;
     const float inv_h = 1.0f / P.apss_h;
     float S0 = 0.f, Sx = 0.f, Sy = 0.f, Sz = 0.f, Sq = 0.f;
     float Sxx = 0.f, Sxy = 0.f, Syy = 0.f, Sxq = 0.f, Syq = 0.f, Sqq = 0.f;
@@ -503,11 +535,20 @@ __device__ float apss_point(const float* st, const float4* wg, const uint4* wi, 
             float w = 1.0f - d2;
             w *= w;
             w = w * w;
-            const float wx = w * x, wy = w * y, wq = w * d2;
-            S0 += w; Sx += wx; Sy += wy; Sz += w * z; Sq += wq;
-            Sxx += wx * x; Sxy += wx * y; Syy += wy * y;
-            Sxq += wx * d2; Syq += wy * d2; Sqq += wq * d2;
-            Sxz += wx * z; Syz += wy * z; Sqz += wq * z;
+            S0 += w;
+            Sz += w * z;
+            if constexpr (kFit) {
+                const float wx = w * x, wy = w * y;
+                Sx += wx; Sy += wy;
+                Sxx += wx * x; Sxy += wx * y; Syy += wy * y;
+                Sxz += wx * z; Syz += wy * z;
+                if constexpr (kSphere) {
+                    const float wq = w * d2;
+                    Sq += wq;
+                    Sxq += wx * d2; Syq += wy * d2; Sqq += wq * d2;
+                    Sqz += wq * z;
+                }
+            }
         }
         const uint4 pk = wi[o];
         ia += cnt * pk.x;
@@ -516,38 +557,86 @@ __device__ float apss_point(const float* st, const float4* wg, const uint4* wi, 
     }
     const long long n = (long long)(ic & 511u);
     if (n < P.apss_min_nb) return tn;
-    const long long si = (long long)(ia & 4095u) - 4 * n, sj = (long long)(ia >> 12) - 4 * n;
-    const long long sii = (long long)(ib & 8191u), sjj = (long long)(ib >> 13);
-    const long long sij = (long long)(ic >> 9) - 16 * n;
-    const long long vii = n * sii - si * si;
-    const long long vjj = n * sjj - sj * sj;
-    const long long vij = n * sij - si * sj;
-    if (vii * vjj - vij * vij == 0) return tn;      // collinear pixel offsets
-    const float iw = 1.0f / S0;
-    const float mx = Sx * iw, my = Sy * iw, mz = Sz * iw, mq = Sq * iw;
-    const float cxx = Sxx * iw - mx * mx, cxy = Sxy * iw - mx * my, cyy = Syy * iw - my * my;
-    const float cxq = Sxq * iw - mx * mq, cyq = Syq * iw - my * mq, cqq = Sqq * iw - mq * mq;
-    const float dx = Sxz * iw - mx * mz, dy = Syz * iw - my * mz, dq = Sqz * iw - mq * mz;
-    // Cholesky of the 3x3 covariance
-    if (!(cxx > 0.0f)) return tn;
-    const float l11 = sqrtf(cxx);
-    const float l21 = cxy / l11, l31 = cxq / l11;
-    const float d22 = cyy - l21 * l21;
-    if (!(d22 > 0.0f)) return tn;
-    const float l22 = sqrtf(d22);
-    const float l32 = (cyq - l31 * l21) / l22;
-    const float d33 = cqq - l31 * l31 - l32 * l32;
-    if (!(d33 > 0.0f)) return tn;
-    const float l33 = sqrtf(d33);
-    const float y1 = -dx / l11;
-    const float y2 = (-dy - l21 * y1) / l22;
-    const float y3 = (-dq - l31 * y1 - l32 * y2) / l33;
-    const float u4 = y3 / l33;
-    const float u2 = (y2 - l32 * u4) / l22;
-    const float u1 = (y1 - l21 * u2 - l31 * u4) / l11;
-    const float u0 = -mz - u1 * mx - u2 * my - u4 * mq;
-    const float disc = 1.0f - 4.0f * u0 * u4;
-    float zs = -2.0f * u0 / (1.0f + sqrtf(fmaxf(disc, 0.0f)));
+    float zs = 0.0f;
+    if constexpr (V == kDenBilateral) {
+        zs = Sz / S0;
+    } else {
+        const long long si = (long long)(ia & 4095u) - 4 * n, sj = (long long)(ia >> 12) - 4 * n;
+        const long long sii = (long long)(ib & 8191u), sjj = (long long)(ib >> 13);
+        const long long sij = (long long)(ic >> 9) - 16 * n;
+        const long long vii = n * sii - si * si;
+        const long long vjj = n * sjj - sj * sj;
+        const long long vij = n * sij - si * sj;
+        if (vii * vjj - vij * vij == 0) return tn;      // collinear pixel offsets
+        if constexpr (V == kDenApss64) {
+            const double iw = rcp64((double)S0);
+            const double mx = Sx * iw, my = Sy * iw, mz = Sz * iw, mq = Sq * iw;
+            const double cxx = fma((double)Sxx, iw, -mx * mx), cxy = fma((double)Sxy, iw, -mx * my);
+            const double cyy = fma((double)Syy, iw, -my * my), cxq = fma((double)Sxq, iw, -mx * mq);
+            const double cyq = fma((double)Syq, iw, -my * mq), cqq = fma((double)Sqq, iw, -mq * mq);
+            const double dx = fma((double)Sxz, iw, -mx * mz), dy = fma((double)Syz, iw, -my * mz);
+            const double dq = fma((double)Sqz, iw, -mq * mz);
+            // Cholesky of the 3x3 covariance, with the reciprocal pivots
+            if (!(cxx > 0.0)) return tn;
+            const double r11 = rsqrt64(cxx);
+            const double l21 = cxy * r11, l31 = cxq * r11;
+            const double d22 = cyy - l21 * l21;
+            if (!(d22 > 0.0)) return tn;
+            const double r22 = rsqrt64(d22);
+            const double l32 = (cyq - l31 * l21) * r22;
+            const double d33 = cqq - l31 * l31 - l32 * l32;
+            if (!(d33 > 0.0)) return tn;
+            const double r33 = rsqrt64(d33);
+            const double y1 = -dx * r11;
+            const double y2 = (-dy - l21 * y1) * r22;
+            const double y3 = (-dq - l31 * y1 - l32 * y2) * r33;
+            const double u4 = y3 * r33;
+            const double u2 = (y2 - l32 * u4) * r22;
+            const double u1 = (y1 - l21 * u2 - l31 * u4) * r11;
+            const double u0 = -mz - u1 * mx - u2 * my - u4 * mq;
+            const double disc = 1.0 - 4.0 * u0 * u4;
+            const double sq = disc > 0.0 ? disc * rsqrt64(disc) : 0.0;
+            double z64 = -2.0 * u0 * rcp64(1.0 + sq);
+            z64 = fmin(fmax(z64, -1.0), 1.0);
+            const double t64 = (double)tn + (double)P.apss_h * z64;
+            return (float)fmin(fmax(t64, 0.0), (double)(T - 1));
+        } else {
+            const float iw = 1.0f / S0;
+            const float mx = Sx * iw, my = Sy * iw, mz = Sz * iw;
+            const float cxx = Sxx * iw - mx * mx, cxy = Sxy * iw - mx * my, cyy = Syy * iw - my * my;
+            const float dx = Sxz * iw - mx * mz, dy = Syz * iw - my * mz;
+            if (!(cxx > 0.0f)) return tn;
+            const float l11 = sqrtf(cxx);
+            const float l21 = cxy / l11;
+            const float d22 = cyy - l21 * l21;
+            if (!(d22 > 0.0f)) return tn;
+            const float l22 = sqrtf(d22);
+            const float y1 = -dx / l11;
+            const float y2 = (-dy - l21 * y1) / l22;
+            if constexpr (kSphere) {
+                const float mq = Sq * iw;
+                const float cxq = Sxq * iw - mx * mq, cyq = Syq * iw - my * mq, cqq = Sqq * iw - mq * mq;
+                const float dq = Sqz * iw - mq * mz;
+                const float l31 = cxq / l11;
+                const float l32 = (cyq - l31 * l21) / l22;
+                const float d33 = cqq - l31 * l31 - l32 * l32;
+                if (!(d33 > 0.0f)) return tn;
+                const float l33 = sqrtf(d33);
+                const float y3 = (-dq - l31 * y1 - l32 * y2) / l33;
+                const float u4 = y3 / l33;
+                const float u2 = (y2 - l32 * u4) / l22;
+                const float u1 = (y1 - l21 * u2 - l31 * u4) / l11;
+                const float u0 = -mz - u1 * mx - u2 * my - u4 * mq;
+                const float disc = 1.0f - 4.0f * u0 * u4;
+                zs = -2.0f * u0 / (1.0f + sqrtf(fmaxf(disc, 0.0f)));
+            } else {
+                const float u2 = y2 / l22;
+                const float u1 = (y1 - l21 * u2) / l11;
+                const float u0 = -mz - u1 * mx - u2 * my;
+                zs = -u0;
+            }
+        }
+    }
     zs = clampf(zs, -1.0f, 1.0f);
     return clampf(tn + P.apss_h * zs, 0.0f, (float)(T - 1));
 }
@@ -633,10 +722,11 @@ __device__ __forceinline__ int compact_points(const float* st, int R, int K, boo
 }
 
 // ----------------------------------------------------------------------------
-// Phase B: APSS depth denoiser + intensity gradient step.  alive_from_b: the
-// previous phase C ran this iteration's depth step, so the alive flags are
-// still in alive_b; they land in the frame here (phase C reads them there).
-template <int K>
+// Phase B: depth denoiser (variant V of apss_point; the learned network with
+// V as its fallback) + intensity gradient step.  alive_from_b: the previous
+// phase C ran this iteration's depth step, so the alive flags are still in
+// alive_b; they land in the frame here (phase C reads them there).
+template <int K, int V>
 __global__ void __launch_bounds__(kTileThreads, 7)
 k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, int tile0)
 {
@@ -658,7 +748,7 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, in
     const int np = F.npix, S = W.stride, R = P.win_r;
     const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
     const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
-    const bool apss = P.depth_den == RT3D_DEPTH_APSS || P.depth_den == RT3D_DEPTH_LEARNED;
+    const bool apss = P.depth_den != RT3D_DEPTH_NONE;
     const float apss_px = P.pitch * (1.0f / P.apss_h);
     if (apss) win_vote(s_vote, R, apss_px);
     if (alive_from_b)
@@ -675,12 +765,12 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, in
         for (int k = 0; k < K; ++k) F.alive[(long long)k * np + lp] = st[k * kHalo + q0] != kDeadDepth ? 1 : 0;
     const int n_pts = compact_points(st, R, K, c.inb, c.li, c.lj, s_pts, s_warp);
     __syncthreads();
-    if (P.depth_den == RT3D_DEPTH_APSS) {
+    if (apss && P.depth_den != RT3D_DEPTH_LEARNED) {
         for (int i = threadIdx.x; i < n_pts; i += kTileThreads) {
             const int px = s_pts[i] >> 2, k = s_pts[i] & 3;
             const int ci = px / kTileW + R, cj = px % kTileW + R;
             const int qc = ci * hstride + cj;
-            s_tn[k][px] = apss_point<K>(st, s_wg, s_wi, n_off, qc, st[k * kHalo + qc], P, F.nt);
+            s_tn[k][px] = apss_point<K, V>(st, s_wg, s_wi, n_off, qc, st[k * kHalo + qc], P, F.nt);
         }
     } else if (P.depth_den == RT3D_DEPTH_LEARNED) {
         // the network's move where it stays within the fallback bound, APSS elsewhere
@@ -696,7 +786,7 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, in
                     continue;
                 }
             }
-            s_tn[k][px] = apss_point<K>(st, s_wg, s_wi, n_off, ci * hstride + cj, t0, P, F.nt);
+            s_tn[k][px] = apss_point<K, V>(st, s_wg, s_wi, n_off, ci * hstride + cj, t0, P, F.nt);
         }
     }
     __syncthreads();

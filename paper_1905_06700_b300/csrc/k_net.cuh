@@ -774,17 +774,6 @@ __host__ __device__ constexpr int net_pipe_smem(int ci, int co)
     return (kPipeRing + 1) * net_pipe_row_bytes(ci) + net_tc_b_bytes(ci, co);
 }
 
-// Wait for a phase regardless of the abort flag (bounded): used at teardown
-// for copies and MMAs still in flight.
-__device__ __forceinline__ bool mbar_drain(uint32_t bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    while (!mbar_try_wait_sleep(bar, parity))
-        if (global_ns() - t0 > kTcWaitNs) return false;
-    return true;
-}
-
 // Work items of the batch: per frame, ceil(w / 128) column strips x
 // ceil(h / kPipeRows) row blocks.  Item -> frame, first column, rows [g0, g1).
 __device__ __forceinline__ int net_pipe_items(const Batch& B)
@@ -818,8 +807,12 @@ __device__ __forceinline__ void net_pipe_item(const Batch& B, int item, int& fi,
 template <int CI, int CO, int MODE>
 __global__ void __launch_bounds__(kPipeThreads, 1)
 k_net_conv_pipe(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, const uint16_t* __restrict__ bimg,
-                const float* __restrict__ bias, void* __restrict__ out, int* __restrict__ status)
+                const float* __restrict__ bias, void* __restrict__ out, int* __restrict__ status,
+                const unsigned long long* __restrict__ wait_ns)
 {
+    // bound of every wait: read from device memory at run time (the launch
+    // sits in a replayed graph); the default without one
+    const unsigned long long wlim = wait_ns ? *wait_ns : kTcWaitNs;
     static_assert(CI % 8 == 0, "16-byte input rows");
     // NCS chunk planes per input row are stored, NC are read by the MMAs
     // (planes NCS..NC-1 stay zero: CI below 16)
@@ -893,7 +886,7 @@ k_net_conv_pipe(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, c
             const uint16_t* fbase = in + (long long)F.pix_base * CI;
             for (int r = max(g0 - 1, 0); r <= min(g1, F.h - 1); ++r, ++q) {
                 const uint32_t slot = q % R;
-                if (!__all_sync(0xffffffffu, mbar_wait(bar_empty + 8 * slot, ((q / R) & 1u) ^ 1u, abort_flag))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(bar_empty + 8 * slot, ((q / R) & 1u) ^ 1u, abort_flag, wlim))) {
                     stop = true;
                     break;
                 }
@@ -932,10 +925,10 @@ k_net_conv_pipe(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, c
                         rows3[ky] = zrow_addr;
                         if (r < 0 || r >= H) continue;
                         const uint32_t pos = q + (uint32_t)(r - r_first);
-                        if (!mbar_wait(bar_full + 8 * (pos % R), (pos / R) & 1u, abort_flag)) stop = true;
+                        if (!mbar_wait(bar_full + 8 * (pos % R), (pos / R) & 1u, abort_flag, wlim)) stop = true;
                         rows3[ky] = row_addr + (pos % R) * ROW;
                     }
-                    if (stop || !mbar_wait(bar_acce + 8 * a, ((k >> 1) & 1u) ^ 1u, abort_flag)) {
+                    if (stop || !mbar_wait(bar_acce + 8 * a, ((k >> 1) & 1u) ^ 1u, abort_flag, wlim)) {
                         stop = true;
                         break;
                     }
@@ -982,7 +975,7 @@ k_net_conv_pipe(const Batch* __restrict__ Bp, const uint16_t* __restrict__ in, c
             const FrameDesc& F = B.f[fi];
             for (int gi = g0; gi < g1; ++gi, ++k) {
                 const uint32_t a = k & 1u;
-                if (!__all_sync(0xffffffffu, mbar_wait(bar_accf + 8 * a, (k >> 1) & 1u, abort_flag))) {
+                if (!__all_sync(0xffffffffu, mbar_wait(bar_accf + 8 * a, (k >> 1) & 1u, abort_flag, wlim))) {
                     stop = true;
                     break;
                 }

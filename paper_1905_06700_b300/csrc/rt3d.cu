@@ -47,14 +47,14 @@ struct PendingTiming {
 struct GraphKey {
     int total_pix, total_tiles, n_iter, warm, init_warps, profiled;
     size_t init_smem;
-    int tc_tiles, tc_stages, tc_nd, any_int, learned, fused, split_tiles;
+    int tc_tiles, tc_stages, tc_nd, any_int, learned, fused, split_tiles, den_variant;
     bool operator<(const GraphKey& o) const
     {
         return std::tie(total_pix, total_tiles, n_iter, warm, init_warps, profiled, init_smem, tc_tiles,
-                        tc_stages, tc_nd, any_int, learned, fused, split_tiles) <
+                        tc_stages, tc_nd, any_int, learned, fused, split_tiles, den_variant) <
                std::tie(o.total_pix, o.total_tiles, o.n_iter, o.warm, o.init_warps, o.profiled,
                         o.init_smem, o.tc_tiles, o.tc_stages, o.tc_nd, o.any_int, o.learned, o.fused,
-                        o.split_tiles);
+                        o.split_tiles, o.den_variant);
     }
 };
 
@@ -104,6 +104,7 @@ struct rt3d_ctx {
     uint8_t* d_band = nullptr;
     std::vector<uint8_t> band_img, band_last;
     int n_sms = 0;
+    unsigned long long wait_ns = kTcWaitNs;   // bound of the tensor-core kernels' waits
     // learned depth denoiser: the attached network and the loop's inference buffers
     rt3d_net* net = nullptr;
     uint16_t* net_a0 = nullptr;     // [stride][8] (6 features, 2 zero)
@@ -229,7 +230,8 @@ bool params_ok(const rt3d_config* cfg, const rt3d_params* p)
     if (!(p->lmf_delta_rel > 0.0f)) return false;
     if (p->win_r < 0 || p->win_r > RT3D_MAX_WIN_R) return false;
     if (p->apss_min_nb < 0) return false;
-    if (p->depth_denoiser < 0 || p->depth_denoiser > 2) return false;
+    if (p->depth_denoiser < 0 || p->depth_denoiser > RT3D_DEPTH_BILATERAL) return false;
+    if (p->apss_fp64 < 0 || p->apss_fp64 > 1) return false;
     if (p->intensity_denoiser < 0 || p->intensity_denoiser > 1) return false;
     if (p->bkg_mode < 0 || p->bkg_mode > 1) return false;
     if (p->bkg_mode == RT3D_BKG_LOWPASS && !(p->bkg_sigma > 0.0f)) return false;
@@ -279,6 +281,7 @@ rt3d_status build_kparams(const rt3d_ctx* c, const rt3d_params* p, KParams* K)
     K->win_r = p->win_r;
     K->apss_min_nb = p->apss_min_nb;
     K->depth_den = p->depth_denoiser;
+    K->apss_fp64 = p->apss_fp64;
     K->int_den = p->intensity_denoiser;
     K->bkg_mode = p->bkg_mode;
     K->bkg_rad = p->bkg_radius;
@@ -288,6 +291,7 @@ rt3d_status build_kparams(const rt3d_ctx* c, const rt3d_params* p, KParams* K)
     K->peak_min_photons = p->peak_min_photons;
     K->net_scale = p->net_scale;
     K->net_fallback = p->net_fallback;
+    K->wait_ns = c->wait_ns;
     float fsum = 0.0f;
     double hmax = 0.0;
     for (int s = 0; s < c->irf_len; ++s) {
@@ -553,6 +557,11 @@ rt3d_status launch_init(rt3d_ctx* c, const KParams& K, const Batch& B, Work W, c
     // the tensor-core kernel takes the dense frames of a cold start; the
     // CUDA-core kernel the rest (it skips those frames)
     const bool tc = K.tc_mode != 0 && !compact_only && tc1 > tc0;
+    // every pixel's sparse segment starts empty: a tensor-core init that gives
+    // up at its wait bound leaves the pixels it did not reach with no entries
+    // (the loop then reads nothing for them)
+    if (tc && pix_end > pix0)
+        RT3D_CUDA(cudaMemsetAsync(W.seg + pix0, 0, sizeof(uint2) * (size_t)(pix_end - pix0), s));
     if (!tc || compact_only || batch_has_int(B) || B.tc_tiles == 0) {
         const size_t smem = init_smem(K, K.peak_sep);
         const int warps = init_warps(K.peak_sep);
@@ -613,7 +622,8 @@ rt3d_status launch_conv_tc(rt3d_ctx* c, int strips, const Batch* B, const uint16
 
 template <int CI, int CO, int MODE>
 rt3d_status launch_conv_pipe(rt3d_ctx* c, int strips, const Batch* B, const uint16_t* in, const uint16_t* img,
-                             const float* bias, void* out, int* status, cudaStream_t s)
+                             const float* bias, void* out, int* status, const unsigned long long* wait_ns,
+                             cudaStream_t s)
 {
     if (strips <= 0) return RT3D_OK;
     auto fn = k_net_conv_pipe<CI, CO, MODE>;
@@ -623,7 +633,7 @@ rt3d_status launch_conv_pipe(rt3d_ctx* c, int strips, const Batch* B, const uint
     RT3D_CUDA(cudaGetDevice(&dev));
     RT3D_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     LaunchScope ls(c, s, kcNet);
-    fn<<<sms, kPipeThreads, smem, s>>>(B, in, img, bias, out, status);
+    fn<<<sms, kPipeThreads, smem, s>>>(B, in, img, bias, out, status, wait_ns);
     return RT3D_OK;
 }
 
@@ -634,22 +644,22 @@ rt3d_status launch_conv_pipe(rt3d_ctx* c, int strips, const Batch* B, const uint
 // kernel with NHWC activations (the network's own training calls).
 rt3d_status net_forward_tiles(rt3d_ctx* c, const rt3d_net* net, int strips, const Batch* B, const uint16_t* a0,
                               uint16_t* a1, uint16_t* a2, uint16_t* a3, float* y, int* status, cudaStream_t s,
-                              bool pipelined = false)
+                              bool pipelined = false, const unsigned long long* wait_ns = nullptr)
 {
     if (pipelined) {
         // a0 holds 8 channels per pixel (the last two zero); the weights of
         // channels 6 and 7 are zero in the operand image
         rt3d_status st = launch_conv_pipe<8, 48, kConvHidden>(c, strips, B, a0, net->wtc + net_tcoff(0),
-                                                              net->theta + net_boff(0), a1, status, s);
+                                                              net->theta + net_boff(0), a1, status, wait_ns, s);
         if (st == RT3D_OK)
             st = launch_conv_pipe<48, 48, kConvHidden>(c, strips, B, a1, net->wtc + net_tcoff(1),
-                                                       net->theta + net_boff(1), a2, status, s);
+                                                       net->theta + net_boff(1), a2, status, wait_ns, s);
         if (st == RT3D_OK)
             st = launch_conv_pipe<48, 48, kConvHidden>(c, strips, B, a2, net->wtc + net_tcoff(2),
-                                                       net->theta + net_boff(2), a3, status, s);
+                                                       net->theta + net_boff(2), a3, status, wait_ns, s);
         if (st == RT3D_OK)
             st = launch_conv_pipe<48, 2, kConvOut>(c, strips, B, a3, net->wtc + net_tcoff(3),
-                                                   net->theta + net_boff(3), y, status, s);
+                                                   net->theta + net_boff(3), y, status, wait_ns, s);
         return st;
     }
     rt3d_status st = launch_conv_tc<6, 48, kConvHidden>(c, strips, B, a0, net->wtc + net_tcoff(0),
@@ -666,32 +676,49 @@ rt3d_status net_forward_tiles(rt3d_ctx* c, const rt3d_net* net, int strips, cons
     return st;
 }
 
-// One PALM phase kernel (0: A, 1: B, 2: C), instantiated for the slot count.
+// One PALM phase kernel (0: A, 1: B, 2: C), instantiated for the slot count
+// (and phase B for its depth-denoiser variant, den_variant).
 // flag: phase A -- first iteration; phase B -- alive flags still in alive_b;
 // phase C -- run the next iteration's depth step too.
 // (tiles [tile0, tile0 + tiles) of the batch)
-template <int K>
-void launch_phase_k(int phase, int flag, int tiles, cudaStream_t s, const CallRecord* rec, const Work& W,
-                    int tile0)
+int den_variant(const KParams& P)
 {
-    if (phase == 0)
-        k_phase_a<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag, tile0);
-    else if (phase == 1)
-        k_phase_b<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag, tile0);
-    else
-        k_phase_c<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag, tile0);
+    if (P.depth_den == RT3D_DEPTH_PLANE) return kDenPlane;
+    if (P.depth_den == RT3D_DEPTH_BILATERAL) return kDenBilateral;
+    return P.apss_fp64 ? kDenApss64 : kDenApss;
 }
 
-void launch_phase(int k, int phase, int flag, int tiles, cudaStream_t s, const CallRecord* rec, const Work& W,
-                  int tile0 = 0)
+template <int K>
+void launch_phase_k(int phase, int flag, int variant, int tiles, cudaStream_t s, const CallRecord* rec,
+                    const Work& W, int tile0)
+{
+    if (phase == 0) {
+        k_phase_a<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag, tile0);
+    } else if (phase == 1) {
+        switch (variant) {
+        case kDenApss64: k_phase_b<K, kDenApss64><<<tiles, kTileThreads, 0, s>>>(rec, W, flag, tile0); break;
+        case kDenPlane: k_phase_b<K, kDenPlane><<<tiles, kTileThreads, 0, s>>>(rec, W, flag, tile0); break;
+        case kDenBilateral:
+            k_phase_b<K, kDenBilateral><<<tiles, kTileThreads, 0, s>>>(rec, W, flag, tile0);
+            break;
+        default: k_phase_b<K, kDenApss><<<tiles, kTileThreads, 0, s>>>(rec, W, flag, tile0); break;
+        }
+    } else {
+        k_phase_c<K><<<tiles, kTileThreads, 0, s>>>(rec, W, flag, tile0);
+    }
+}
+
+void launch_phase(const KParams& P, int phase, int flag, int tiles, cudaStream_t s, const CallRecord* rec,
+                  const Work& W, int tile0 = 0)
 {
     static_assert(kMaxK == 4, "one instantiation per slot count");
     if (tiles <= 0) return;
-    switch (k) {
-    case 1: launch_phase_k<1>(phase, flag, tiles, s, rec, W, tile0); break;
-    case 2: launch_phase_k<2>(phase, flag, tiles, s, rec, W, tile0); break;
-    case 3: launch_phase_k<3>(phase, flag, tiles, s, rec, W, tile0); break;
-    default: launch_phase_k<4>(phase, flag, tiles, s, rec, W, tile0); break;
+    const int v = den_variant(P);
+    switch (P.k) {
+    case 1: launch_phase_k<1>(phase, flag, v, tiles, s, rec, W, tile0); break;
+    case 2: launch_phase_k<2>(phase, flag, v, tiles, s, rec, W, tile0); break;
+    case 3: launch_phase_k<3>(phase, flag, v, tiles, s, rec, W, tile0); break;
+    default: launch_phase_k<4>(phase, flag, v, tiles, s, rec, W, tile0); break;
     }
 }
 
@@ -712,7 +739,7 @@ rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter,
     for (int it = 0; it < n_iter; ++it) {
         if (it == 0 || !fused) {
             LaunchScope ls(c, s, kcA);
-            launch_phase(c->h_rec.P.k, 0, it == 0 ? 1 : 0, tiles, s, c->d_rec, c->W, tile0);
+            launch_phase(c->h_rec.P, 0, it == 0 ? 1 : 0, tiles, s, c->d_rec, c->W, tile0);
         }
         if (learned) {
             {
@@ -723,16 +750,16 @@ rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter,
             }
             const rt3d_status st = net_forward_tiles(
                 c, c->net, B.net_strips, &c->d_rec->B, c->net_a0, c->net_a1, c->net_a2, c->net_a1, c->net_y,
-                c->W.status, s, true);
+                c->W.status, s, true, &c->d_rec->P.wait_ns);
             if (st != RT3D_OK) return st;
         }
         {
             LaunchScope ls(c, s, kcB);
-            launch_phase(c->h_rec.P.k, 1, fused && it > 0 ? 1 : 0, tiles, s, c->d_rec, c->W, tile0);
+            launch_phase(c->h_rec.P, 1, fused && it > 0 ? 1 : 0, tiles, s, c->d_rec, c->W, tile0);
         }
         {
             LaunchScope ls(c, s, kcC);
-            launch_phase(c->h_rec.P.k, 2, fused && it + 1 < n_iter ? 1 : 0, tiles, s, c->d_rec, c->W, tile0);
+            launch_phase(c->h_rec.P, 2, fused && it + 1 < n_iter ? 1 : 0, tiles, s, c->d_rec, c->W, tile0);
         }
     }
     RT3D_CUDA(cudaGetLastError());
@@ -797,7 +824,8 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
     const GraphKey key{B.total_pix, B.total_tiles, p->n_iter, p->warm_start != 0,
                        init_warps(K.peak_sep), c->profiling ? 1 : 0, init_smem(K, K.peak_sep),
                        B.tc_tiles, K.tc_stages, K.tc_nd, batch_has_int(B) ? 1 : 0,
-                       K.depth_den == RT3D_DEPTH_LEARNED ? 1 : 0, fused_depth_step(K) ? 1 : 0, split_tiles};
+                       K.depth_den == RT3D_DEPTH_LEARNED ? 1 : 0, fused_depth_step(K) ? 1 : 0, split_tiles,
+                       den_variant(K)};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         // capture the launch sequence of this geometry once, on a private stream
@@ -926,6 +954,7 @@ rt3d_status rt3d_default_params(rt3d_params* p)
     p->warm_start = 0;
     p->net_scale = 3.0f;
     p->net_fallback = 6.0f;
+    p->apss_fp64 = 0;
     return RT3D_OK;
 }
 
@@ -1398,7 +1427,7 @@ rt3d_status rt3d_phase(rt3d_ctx_t* c, int phase, int first, const rt3d_frame* f,
         RT3D_CUDA(cudaMemcpyAsync(c->W.b_half, state->b, sizeof(float) * np, cudaMemcpyDeviceToDevice, s));
     {
         LaunchScope ls(c, s, phase == 0 ? kcA : (phase == 1 ? kcB : kcC));
-        launch_phase(K.k, phase, phase == 0 ? first : 0, B.total_tiles, s, c->d_rec, c->W);
+        launch_phase(K, phase, phase == 0 ? first : 0, B.total_tiles, s, c->d_rec, c->W);
     }
     RT3D_CUDA(cudaGetLastError());
     for (int k = 0; k < Kp; ++k) {
@@ -1433,6 +1462,13 @@ rt3d_status rt3d_device_status(rt3d_ctx_t* c, void* stream)
 }
 
 int64_t rt3d_launch_count(rt3d_ctx_t* c) { return c ? c->launches : -1; }
+
+rt3d_status rt3d_set_wait_limit(rt3d_ctx_t* c, int64_t ns)
+{
+    if (!c || ns < 0) return RT3D_E_INVALID;
+    c->wait_ns = (unsigned long long)ns;
+    return RT3D_OK;
+}
 
 rt3d_status rt3d_set_profiling(rt3d_ctx_t* c, int on)
 {
@@ -1858,6 +1894,7 @@ rt3d_status static_kparams(const rt3d_irf* irf, const rt3d_params* p, KParams* K
     K->win_r = p->win_r;
     K->apss_min_nb = p->apss_min_nb;
     K->depth_den = p->depth_denoiser;
+    K->apss_fp64 = p->apss_fp64;
     K->int_den = p->intensity_denoiser;
     K->bkg_mode = p->bkg_mode;
     K->bkg_rad = p->bkg_radius;
@@ -1867,6 +1904,7 @@ rt3d_status static_kparams(const rt3d_irf* irf, const rt3d_params* p, KParams* K
     K->peak_min_photons = p->peak_min_photons;
     K->net_scale = p->net_scale;
     K->net_fallback = p->net_fallback;
+    K->wait_ns = kTcWaitNs;
     float fsum = 0.0f;
     double hmax = 0.0;
     for (int s = 0; s < irf->len; ++s) {
@@ -1989,9 +2027,9 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     init_fn<<<(B.total_pix + warps - 1) / warps, warps * 32, smem, s>>>(d_rec, W, 0, B.total_pix);
     for (int it = 0; it < p->n_iter; ++it) {
         const bool fused = fused_depth_step(K);
-        if (it == 0 || !fused) launch_phase(K.k, 0, it == 0 ? 1 : 0, B.total_tiles, s, d_rec, W);
-        launch_phase(K.k, 1, fused && it > 0 ? 1 : 0, B.total_tiles, s, d_rec, W);
-        launch_phase(K.k, 2, fused && it + 1 < p->n_iter ? 1 : 0, B.total_tiles, s, d_rec, W);
+        if (it == 0 || !fused) launch_phase(K, 0, it == 0 ? 1 : 0, B.total_tiles, s, d_rec, W);
+        launch_phase(K, 1, fused && it > 0 ? 1 : 0, B.total_tiles, s, d_rec, W);
+        launch_phase(K, 2, fused && it + 1 < p->n_iter ? 1 : 0, B.total_tiles, s, d_rec, W);
     }
     k_final<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W, p->n_iter > 0 ? 1 : 0, 0);
     RT3D_CUDA(cudaGetLastError());

@@ -38,6 +38,7 @@ struct KParams {
     float pitch, apss_h, int_h, r_min, merge_dist;
     int win_r, apss_min_nb;
     int depth_den, int_den, bkg_mode, bkg_rad;
+    int apss_fp64;                  // APSS solve (and the learned form's fallback) in FP64
     int irf_len, irf_origin;
     float irf_sum;                  // sum of the float IRF samples (H in the interior)
     int peak_sep, peak_min_photons;
@@ -51,6 +52,7 @@ struct KParams {
     int tc_wmin_bits;               // float bits of peak_min_photons in accumulator units
     float tc_unit_inv;              // accumulator value * tc_unit_inv = exact integer
     float net_scale, net_fallback;  // learned depth denoiser: feature/output scale, APSS fallback threshold
+    unsigned long long wait_ns;     // bound of every device-side wait of the tensor-core kernels
     float irf[kMaxIrf];             // normalised IRF samples
     int lmf[kMaxIrf];               // quantised log-IRF K_s
     float bkg_ker[2 * kMaxBkgR + 1];

@@ -65,7 +65,7 @@ class Params(C.Structure):
                 ("lmf_delta_rel", C.c_float), ("lmf_frac_bits", C.c_int32),
                 ("peak_min_photons", C.c_int32), ("peak_sep", C.c_int32),
                 ("lmf_precision", C.c_int32), ("warm_start", C.c_int32),
-                ("net_scale", C.c_float), ("net_fallback", C.c_float)]
+                ("net_scale", C.c_float), ("net_fallback", C.c_float), ("apss_fp64", C.c_int32)]
 
 
 class AdamW(C.Structure):
@@ -134,6 +134,7 @@ def lib():
                                  C.POINTER(Result), _P]),
         "rt3d_device_status": (C.c_int, [_P, _P]),
         "rt3d_launch_count": (C.c_int64, [_P]),
+        "rt3d_set_wait_limit": (C.c_int, [_P, C.c_int64]),
         "rt3d_set_profiling": (C.c_int, [_P, C.c_int]),
         "rt3d_kernel_times": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                         C.c_int, C.c_int]),
@@ -355,6 +356,10 @@ class Context:
 
     def launch_count(self) -> int:
         return int(lib().rt3d_launch_count(self.handle))
+
+    def set_wait_limit(self, ns: int):
+        """Bound of the tensor-core kernels' device-side waits (rt3d_set_wait_limit)."""
+        check(lib().rt3d_set_wait_limit(self.handle, int(ns)), "rt3d_set_wait_limit")
 
     def set_profiling(self, on: bool):
         check(lib().rt3d_set_profiling(self.handle, int(on)), "rt3d_set_profiling")

@@ -252,6 +252,32 @@ def two_layer(h=256, w=256, t=4096, seed=1, mean_signal=5.0, sbr=0.1) -> Scene:
     return Scene(h, w, t, depth, sig, bkg, irf, seed, "two_layer")
 
 
+def head_like(h=141, w=141, t=4096, seed=1, mean_signal=3.0, bkg_photons=1.0) -> Scene:
+    """The shape of the paper's raster-scan head frame (141 x 141 pixels, a few
+    signal photons per pixel, mostly one surface per pixel and two at the
+    head's border): an ellipsoidal head in front of a back plane, its rim
+    pixels splitting their light between the two; gamma IRF (3, 5);
+    mean_signal signal photons and bkg_photons background photons per pixel
+    (uniform over the T bins).  Used for the execution-time sweeps of Fig. 5
+    (pixel count, mean active bins per pixel)."""
+    irf = gamma_irf(3.0, 5.0, 80)
+    rng = np.random.default_rng(seed)
+    sc = t / 4096.0
+    i, j = np.meshgrid(np.arange(h, dtype=np.float64), np.arange(w, dtype=np.float64), indexing="ij")
+    rho = np.sqrt(((i - 0.5 * (h - 1)) / (0.36 * h)) ** 2 + ((j - 0.5 * (w - 1)) / (0.27 * w)) ** 2)
+    inside = rho < 1.0
+    rim = inside & (rho > 0.92)
+    total = _reflectivity(rng, (h, w), mean_signal)
+    depth = np.full((2, h, w), np.nan)
+    sig = np.zeros((2, h, w))
+    depth[0] = np.where(inside, (2000.0 - 300.0 * np.sqrt(np.maximum(1.0 - rho ** 2, 0.0))) * sc, np.nan)
+    sig[0] = np.where(inside, np.where(rim, 0.5, 1.0) * total, 0.0)
+    depth[1] = np.where(~inside | rim, (2600.0 + 0.5 * (i - h / 2)) * sc, np.nan)
+    sig[1] = np.where(~inside, total, np.where(rim, 0.5 * total, 0.0))
+    bkg = np.full((h, w), bkg_photons / t)
+    return Scene(h, w, t, depth, sig, bkg, irf, seed, "head_like")
+
+
 def random_shapes(h=256, w=256, t=2048, seed=0) -> Scene:
     """Random planes, spheres and boxes (at most two surfaces per pixel), with
     1-20 signal photons per pixel and a signal-to-background ratio in 0.05-2."""
@@ -340,7 +366,7 @@ def make_params(scene: Scene, **over) -> dict:
         lmf_delta_rel=1e-3, lmf_frac_bits=5, peak_min_photons=2,
         peak_sep=max(2, int(math.ceil(2.0 * math.sqrt(var)))),
         lmf_precision=0, warm_start=0,
-        net_scale=math.sqrt(var), net_fallback=math.sqrt(var) / 3.0,
+        net_scale=math.sqrt(var), net_fallback=math.sqrt(var) / 3.0, apss_fp64=0,
     )
     p.update(over)
     return p

@@ -108,7 +108,7 @@ def test_validation_rejects_bad_frames(L, fr_kw):
 @pytest.mark.parametrize("field,value", [("n_iter", -1), ("k_max", 0), ("k_max", 4), ("t_step", 0.0),
                                          ("r_min", 0.0), ("win_r", 5), ("bkg_radius", 16),
                                          ("lmf_frac_bits", 13), ("peak_min_photons", 256),
-                                         ("depth_denoiser", 3), ("apss_radius", float("nan")),
+                                         ("depth_denoiser", 5), ("apss_fp64", 2), ("apss_radius", float("nan")),
                                          ("lmf_delta_rel", 0.0)])
 def test_validation_rejects_bad_params(L, field, value):
     p = R.rt3d_default_params()

@@ -1,6 +1,8 @@
 """Learned depth denoiser on the GPU (the library's own forward, backward and
 AdamW kernels) against the FP64 oracle, its place in the PALM loop, and what
 training it gains over the method without a depth denoiser."""
+import os
+
 import numpy as np
 import pytest
 
@@ -8,6 +10,11 @@ import scenes
 from gpu_util import make_ctx, np_of, oracle_irf, torch_mod, upload_u16, workload_params
 
 pytestmark = pytest.mark.gpu
+
+GRAD_RTOL = 2e-3      # element-wise relative tolerance of the network gradient
+GRAD_FLOOR = 2e-3     # plus this fraction of the block's rms gradient
+WEIGHTS = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "paper_1905_06700_b300", "weights", "learned_depth.bin")
 
 
 def _net(n=4, h=32, w=32):
@@ -87,11 +94,20 @@ def test_gradient_matches_oracle(orc):
     lo, dy = orc.net_loss(y, tg, m)
     want, _ = orc.net_backward(th.astype(np.float64), acts, dy, bf16_round=True)
     assert float(loss.cpu()[0]) == pytest.approx(lo, rel=1e-4)
+    # element by element: |g - g_oracle| <= GRAD_RTOL |g_oracle| + GRAD_FLOOR rms(block),
+    # per layer's weight block and bias block.  The floor covers entries whose
+    # sum over pixels nearly cancels: one layer input that FP32 and FP64 sums
+    # round to neighbouring bfloat16 values changes a term by 2^-8 of itself.
+    worst = []
     for l in range(4):
         for bias in (False, True):
             a, b = orc.net_offset(l, bias), (orc.net_offset(l, True) if not bias else orc.net_offset(l + 1, False))
-            rel = np.linalg.norm(g[a:b] - want[a:b]) / max(np.linalg.norm(want[a:b]), 1e-30)
-            assert rel <= 2e-3, (l, bias, rel)
+            w = want[a:b]
+            rms = float(np.sqrt(np.mean(w ** 2)))
+            excess = (np.abs(g[a:b] - w) - GRAD_RTOL * np.abs(w)) / max(rms, 1e-30)
+            worst.append((l, bias, float(excess.max()), float(np.median(np.abs(g[a:b] - w) / np.maximum(np.abs(w), 1e-30)))))
+            assert excess.max() <= GRAD_FLOOR, (l, bias, float(excess.max()), int(np.argmax(excess)))
+    print("gradient: worst (|dg| - %.0e |g|) / rms per block, median relative error:" % GRAD_RTOL, worst)
 
 
 def test_adamw_step_matches_oracle(orc):
@@ -224,3 +240,35 @@ def test_trained_network_gains_over_no_depth_denoiser():
           % (losses[:20].mean(), losses[-20:].mean(), none, fn, apss, fa, lrn, fl))
     assert losses[-20:].mean() < 0.7 * losses[:20].mean()
     assert lrn < 0.8 * none
+
+
+def test_learned_form_full_size_error_against_oracle(orc):
+    """The learned form's own configuration: a 256 x 256 x 2048 random-shapes
+    frame (held-out seed), the committed trained network in place of APSS,
+    20 PALM iterations, against the FP64 oracle running the same network.
+    The network's inputs are bfloat16 roundings of FP32 (GPU) or FP64
+    (oracle) feature sums, so a point whose feature straddles a bfloat16
+    rounding boundary takes a slightly different move, and the loop carries
+    that difference on; the error is stated (printed) and bounded."""
+    from paper_1905_06700_b300 import learned
+    th, _ = learned.load(WEIGHTS)
+    sc = scenes.random_shapes(256, 256, 2048, seed=200000)
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = dict(workload_params(sc), depth_denoiser=2)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    net = _net(1, sc.h, sc.w)
+    net.set_params(th)
+    ctx.set_depth_net(net)
+    g = _recon(ctx, prm, z)
+    o = orc.reconstruct(z, oracle_irf(orc, sc), dict(prm, net_theta=th.astype(np.float64)))
+    ga, oa = g["alive"].astype(bool), o.alive.astype(bool)
+    both = ga & oa
+    flips = int((ga != oa).sum())
+    dt = np.abs(g["t"].astype(np.float64) - o.t)[both]
+    dr = (np.abs(g["r"].astype(np.float64) - o.r) / np.maximum(o.r, 0.1))[both]
+    print("learned form 256x256x2048 vs FP64 oracle: points %d flips %d dt median %.2e p99 %.2e "
+          "p99.9 %.2e max %.2e, within 1e-3 bins %.4f; dr median %.2e p99 %.2e"
+          % (int(oa.sum()), flips, np.median(dt), np.percentile(dt, 99), np.percentile(dt, 99.9),
+             dt.max(), (dt <= 1e-3).mean(), np.median(dr), np.percentile(dr, 99)))
+    assert flips <= 0.02 * int(oa.sum())
+    assert np.median(dt) <= 2e-2 and np.percentile(dt, 99) <= 0.5

@@ -7,9 +7,9 @@ import numpy as np
 import pytest
 
 import scenes
-from gpu_util import (compare_clouds, ill_conditioned, make_ctx, np_of, oracle_irf,
-                      oracle_with_probe, state_f32_rounded, state_to_device, torch_mod, u16_np,
-                      upload_u16, workload_params)
+from gpu_util import (compare_clouds, make_ctx, np_of, oracle_irf, oracle_with_probes,
+                      state_f32_rounded, state_to_device, torch_mod, u16_np, upload_u16,
+                      workload_params)
 
 pytestmark = pytest.mark.gpu
 
@@ -139,10 +139,12 @@ def test_phase_a_depth_step(orc, idx, bkg_mode):
 
 
 @pytest.mark.parametrize("idx", [0, 1, 4])
-@pytest.mark.parametrize("den", [1, 0])
-def test_phase_b_apss_and_intensity_step(orc, idx, den):
+@pytest.mark.parametrize("den,fp64", [(1, 0), (0, 0), (1, 1), (3, 0), (4, 0)])
+def test_phase_b_apss_and_intensity_step(orc, idx, den, fp64):
+    """Phase B with each depth denoiser (none, APSS with its solve in FP32 or
+    FP64, plane fit, bilateral) then the intensity step, from identical inputs."""
     sc = _scenes_small()[idx]
-    z, prm, irf, st0, ctx, csr, fr = _phase_setup(orc, sc, depth_denoiser=den)
+    z, prm, irf, st0, ctx, csr, fr = _phase_setup(orc, sc, depth_denoiser=den, apss_fp64=fp64)
     # start from a state after one depth step so that APSS has work to do
     orc.t_step(fr, irf, prm, st0)
     st0 = state_f32_rounded(orc, st0)
@@ -150,10 +152,9 @@ def test_phase_b_apss_and_intensity_step(orc, idx, den):
     ctx.phase(1, 0, prm, csr, dev, shape=(sc.h, sc.w, sc.t))
     g = np_of(dev)
     o = st0.copy()
-    if den:
-        orc.apss(sc.h, sc.w, sc.t, prm, o)
+    orc.depth_denoise(sc.h, sc.w, sc.t, prm, o)
     orc.r_step(fr, irf, prm, o)
-    compare_clouds(g, o, sc.t, TOL_T, TOL_R, label="B")
+    compare_clouds(g, o, sc.t, TOL_T, TOL_R, label=f"B den={den} fp64={fp64}")
 
 
 @pytest.mark.parametrize("idx", [0, 1, 4])
@@ -181,14 +182,15 @@ def test_reconstruct_matches_oracle(orc, idx):
     prm = workload_params(sc)
     ctx = make_ctx(sc, k=prm["k_max"])
     g = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
-    o, probe = oracle_with_probe(orc, sc, z, prm)
-    ill = ill_conditioned(o, probe, TOL_T, TOL_R)
-    stats = compare_clouds(g, o, sc.t, TOL_T, TOL_R, ill=ill, max_ill_frac=0.02, label=sc.name)
+    o, probes = oracle_with_probes(orc, sc, z, prm)
+    stats = compare_clouds(g, o, sc.t, TOL_T, TOL_R, probes=probes, max_ill_frac=0.05,
+                           label=sc.name, r_min=prm["r_min"])
     assert g["n_points"] == int(g["alive"].sum())
     print(sc.name, stats)
 
 
 @pytest.mark.parametrize("over", [dict(bkg_mode=1), dict(depth_denoiser=0, intensity_denoiser=0),
+                                  dict(apss_fp64=1), dict(depth_denoiser=3), dict(depth_denoiser=4),
                                   dict(k_max=4), dict(k_max=1, win_r=1), dict(n_iter=0),
                                   dict(win_r=4, apss_radius=72.0, int_radius=72.0)])
 def test_reconstruct_options_match_oracle(orc, over):
@@ -197,9 +199,9 @@ def test_reconstruct_options_match_oracle(orc, over):
     prm = workload_params(sc, **over)
     ctx = make_ctx(sc, k=prm["k_max"])
     g = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
-    o, probe = oracle_with_probe(orc, sc, z, prm)
-    ill = ill_conditioned(o, probe, TOL_T, TOL_R)
-    stats = compare_clouds(g, o, sc.t, TOL_T, TOL_R, ill=ill, max_ill_frac=0.02, label=str(over))
+    o, probes = oracle_with_probes(orc, sc, z, prm)
+    stats = compare_clouds(g, o, sc.t, TOL_T, TOL_R, probes=probes, max_ill_frac=0.05,
+                           label=str(over), r_min=prm["r_min"])
     print(over, stats)
 
 
@@ -214,9 +216,9 @@ def test_reconstruct_with_gain_and_dead_pixels(orc):
     prm = workload_params(sc)
     ctx = make_ctx(sc, k=prm["k_max"])
     g = np_of(ctx.reconstruct(prm, dense=upload_u16(z), gain=torch.from_numpy(gain).cuda()))
-    o, probe = oracle_with_probe(orc, sc, z, prm, gain=gain.astype(np.float64))
-    ill = ill_conditioned(o, probe, TOL_T, TOL_R)
-    compare_clouds(g, o, sc.t, TOL_T, TOL_R, ill=ill, max_ill_frac=0.02, label="gain")
+    o, probes = oracle_with_probes(orc, sc, z, prm, gain=gain.astype(np.float64))
+    compare_clouds(g, o, sc.t, TOL_T, TOL_R, probes=probes, max_ill_frac=0.05, label="gain",
+                   r_min=prm["r_min"])
     assert not g["alive"][:, 3, 5].any() and not g["alive"][:, 10, 0].any()
 
 
@@ -381,9 +383,9 @@ def test_dense_pixels_init_and_reconstruct_match_oracle(orc):
         assert np.array_equal(e >> 16, fr.bin[fr.off[p]:fr.off[p + 1]])
         assert np.array_equal(e & 0xFFFF, fr.cnt[fr.off[p]:fr.off[p + 1]])
     g = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
-    o, probe = oracle_with_probe(orc, sc, z, prm)
-    ill = ill_conditioned(o, probe, TOL_T, TOL_R)
-    stats = compare_clouds(g, o, sc.t, TOL_T, TOL_R, ill=ill, max_ill_frac=0.02, label="dense pixels")
+    o, probes = oracle_with_probes(orc, sc, z, prm)
+    stats = compare_clouds(g, o, sc.t, TOL_T, TOL_R, probes=probes, max_ill_frac=0.05,
+                           label="dense pixels", r_min=prm["r_min"])
     print("dense pixels", stats)
 
 
@@ -398,12 +400,12 @@ def test_longest_histogram_and_irf_match_oracle(orc):
     assert np.array_equal(g["t"].astype(np.float64), o.t)
     np.testing.assert_allclose(g["r"], o.r, rtol=1e-5, atol=1e-6)
     g = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
-    o, probe = oracle_with_probe(orc, sc, z, prm)
+    o, probes = oracle_with_probes(orc, sc, z, prm)
     # depths near 16384 bins are FP32 numbers 2^-9 apart: the depth tolerance
     # is four of those spacings (1e-3 bins is below the format's resolution)
     tol_t = max(TOL_T, 4.0 * float(np.spacing(np.float32(sc.t))))
-    ill = ill_conditioned(o, probe, tol_t, TOL_R)
-    stats = compare_clouds(g, o, sc.t, tol_t, TOL_R, ill=ill, max_ill_frac=0.02, label="T=16384, L=256")
+    stats = compare_clouds(g, o, sc.t, tol_t, TOL_R, probes=probes, max_ill_frac=0.05,
+                           label="T=16384, L=256", r_min=prm["r_min"])
     print("T=16384, L=256", stats)
 
 
@@ -434,7 +436,6 @@ def test_warm_start_on_a_moving_scene_matches_oracle(orc):
     previous frame's cloud: the GPU's warm start against the oracle's loop run
     from the same state (every value rounded through float32, as the GPU
     holds it), with the same perturbation probe for ill-conditioned points."""
-    from gpu_util import _round_bits
     base = scenes.small_random(14, 23, 300, n_comp=2, seed=71)
     sc1, sc2 = scenes.moving_frame(base, 0), scenes.moving_frame(base, 1)
     z1 = orc.synthesize(scenes.sampling_tables(sc1))
@@ -449,25 +450,10 @@ def test_warm_start_on_a_moving_scene_matches_oracle(orc):
     start.alive[:] = a["alive"]
     start.b[:] = a["b"]
     g2 = np_of(ctx.reconstruct(dict(prm, warm_start=1), dense=upload_u16(z2), out=g1))
-    irf = oracle_irf(orc, base)
-    fr = orc.OFrame(z2)
-    o = start.copy()
-    orc.palm(fr, irf, prm, o, prm["n_iter"])
-    q = start.copy()
-
-    def rnd(st):
-        st.t[:] = st.t.astype(np.float32)
-        st.r[:] = _round_bits(st.r, 20)
-        st.b[:] = _round_bits(st.b, 20)
-    for _ in range(prm["n_iter"]):
-        orc.t_step(fr, irf, prm, q); rnd(q)
-        orc.apss(base.h, base.w, base.t, prm, q); rnd(q)
-        orc.r_step(fr, irf, prm, q); rnd(q)
-        orc.int_lowpass(base.h, base.w, prm, q); rnd(q)
-        orc.b_step(fr, irf, prm, q); rnd(q)
-        orc.bkg_lowpass(base.h, base.w, prm, q.b); rnd(q)
-    ill = ill_conditioned(o, q, TOL_T, TOL_R)
-    stats = compare_clouds(g2, o, base.t, TOL_T, TOL_R, ill=ill, max_ill_frac=0.02, label="warm start")
+    from oracle import compare
+    o, probes = compare.palm_with_probes(orc.OFrame(z2), oracle_irf(orc, base), prm, start, prm["n_iter"])
+    stats = compare_clouds(g2, o, base.t, TOL_T, TOL_R, probes=probes, max_ill_frac=0.05, label="warm start",
+                           r_min=prm["r_min"])
     print("warm start", stats)
 
 
@@ -489,7 +475,64 @@ def test_reconstruct_multisurface_full_size_matches_oracle(orc):
     prm = workload_params(sc)
     ctx = make_ctx(sc, k=prm["k_max"])
     g = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
-    o, probe = oracle_with_probe(orc, sc, z, prm)
-    ill = ill_conditioned(o, probe, TOL_T, TOL_R)
-    stats = compare_clouds(g, o, sc.t, TOL_T, TOL_R, ill=ill, max_ill_frac=0.02, label="full")
+    o, probes = oracle_with_probes(orc, sc, z, prm)
+    stats = compare_clouds(g, o, sc.t, TOL_T, TOL_R, probes=probes, max_ill_frac=0.05,
+                           label="full", r_min=prm["r_min"])
     print("141x141x4096", stats)
+
+
+@pytest.mark.parametrize("fp64", [1, 0])
+def test_two_layer_full_size_matches_oracle(orc, fp64):
+    """The precision form's workload at full size (256 x 256 x 4096, two
+    surfaces per pixel at a signal-to-background ratio of 0.1: ~54 nonzero
+    bins per pixel), every point compared with the FP64 oracle.  This form
+    solves the APSS normal equations in FP64 (apss_fp64 = 1) and is held to
+    the FP32 tolerance.  With the solve in FP32, the normal equations of a
+    few near-planar windows are ill-conditioned enough to move a point by
+    about 1e-3 bins more: that variant's error is stated (printed) and
+    bounded at 1e-2 bins.  The BF16 and FP16 tensor-core filters give the
+    integer path's results bit for bit (test_gpu_tc), so they inherit these
+    figures."""
+    sc = scenes.two_layer()
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc, apss_fp64=fp64)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    g = np_of(ctx.reconstruct(prm, dense=upload_u16(z)))
+    o, probes = oracle_with_probes(orc, sc, z, prm)
+    stats = compare_clouds(g, o, sc.t, TOL_T if fp64 else 1e-2, TOL_R, probes=probes, max_ill_frac=0.05,
+                           label=f"two_layer 256x256x4096 apss_fp64={fp64}", r_min=prm["r_min"])
+    print("256x256x4096 SBR 0.1, APSS solve in", "FP64" if fp64 else "FP32", stats)
+
+
+@pytest.mark.parametrize("den,fp64", [(1, 0), (1, 1), (3, 0), (4, 0)])
+def test_phase_b_full_frame_each_denoiser(orc, den, fp64):
+    """One phase B (depth denoiser, then the intensity step) on the full
+    141 x 141 x 4096 benchmark frame, from the oracle's own state after five
+    iterations (rounded to float32), for APSS (solve in FP32 and FP64), the
+    plane fit and the bilateral filter: every depth within a few float32
+    spacings of the oracle's step, every intensity within 1e-4."""
+    sc = scenes.net_object_wall()
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = workload_params(sc, depth_denoiser=den, apss_fp64=fp64)
+    irf = oracle_irf(orc, sc)
+    fr = orc.OFrame(z)
+    st = orc.init(z, None, irf, prm)
+    orc.palm(fr, irf, prm, st, 5)
+    orc.t_step(fr, irf, prm, st)
+    st = state_f32_rounded(orc, st)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    csr = ctx.compact(upload_u16(z))
+    dev = state_to_device(st)
+    ctx.phase(1, 0, prm, csr, dev, shape=(sc.h, sc.w, sc.t))
+    g = np_of(dev)
+    o = st.copy()
+    orc.depth_denoise(sc.h, sc.w, sc.t, prm, o)
+    orc.r_step(fr, irf, prm, o)
+    a = o.alive.astype(bool)
+    dt = np.abs(g["t"].astype(np.float64) - o.t)[a]
+    spacing = np.spacing(np.abs(o.t[a]).astype(np.float32)).astype(np.float64)
+    dr = (np.abs(g["r"].astype(np.float64) - o.r) / np.maximum(o.r, 0.1))[a]
+    print(f"phase B full frame den={den} fp64={fp64}: max |dt| {dt.max():.3e} bins "
+          f"({(dt / spacing).max():.2f} float32 spacings), max rel |dr| {dr.max():.2e}")
+    assert np.all(dt <= 4.0 * spacing)
+    assert dr.max() <= TOL_R
