@@ -56,11 +56,11 @@ def probe_palm(fr, irf, prm, start, n_iter, bits):
     return st
 
 
-def reconstruct_with_probes(dense, irf, prm, gain=None, bits_list=PROBE_BITS):
+def reconstruct_with_probes(dense, irf, prm, gain=None, bits_list=PROBE_BITS, irf_idx=None):
     """(oracle reconstruction, [probe reconstructions]) of one frame."""
-    o = O.reconstruct(dense, irf, prm, gain=gain)
-    fr = O.OFrame(dense, gain)
-    s0 = O.init(dense, gain, irf, prm)
+    o = O.reconstruct(dense, irf, prm, gain=gain, irf_idx=irf_idx)
+    fr = O.OFrame(dense, gain, irf_idx)
+    s0 = O.init(dense, gain, irf, prm, irf_idx=irf_idx)
     probes = [probe_palm(fr, irf, prm, s0, prm["n_iter"], b) for b in bits_list]
     return o, probes
 

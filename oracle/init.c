@@ -91,12 +91,22 @@ int or_peaks(const int64_t* y, const int64_t* wcount, int t, int sep, int min_ph
     return nbest;
 }
 
-void or_init(const uint16_t* dense, const double* gain, int h, int w, int t,
-             const or_irf* irf, const or_params* prm, or_state* s)
+/* Initialisation with per-pixel instrument responses: pixel p uses
+ * irf_set[irf_idx[p]] for its matched filter and windows (irf_idx NULL: every
+ * pixel uses irf_set[0]). */
+void or_init_idx(const uint16_t* dense, const double* gain, const uint8_t* irf_idx, int h, int w, int t,
+                 const or_irf* irf_set, const or_params* prm, or_state* s)
 {
     const int64_t npix = (int64_t)h * w;
-    int32_t* kern = (int32_t*)malloc(sizeof(int32_t) * irf->len);
-    or_lmf_kernel(irf, prm->lmf_delta_rel, prm->lmf_frac_bits, kern);
+    int n_irf = 1;
+    if (irf_idx)
+        for (int64_t p = 0; p < npix; ++p)
+            if (irf_idx[p] + 1 > n_irf) n_irf = irf_idx[p] + 1;
+    int32_t* kerns[256];
+    for (int i = 0; i < n_irf; ++i) {
+        kerns[i] = (int32_t*)malloc(sizeof(int32_t) * irf_set[i].len);
+        or_lmf_kernel(&irf_set[i], prm->lmf_delta_rel, prm->lmf_frac_bits, kerns[i]);
+    }
 #pragma omp parallel
     {
         int64_t* y = (int64_t*)malloc(sizeof(int64_t) * t);
@@ -106,6 +116,9 @@ void or_init(const uint16_t* dense, const double* gain, int h, int w, int t,
         for (int64_t p = 0; p < npix; ++p) {
             const uint16_t* z = dense + p * t;
             const double g = gain[p];
+            const int which = irf_idx ? irf_idx[p] : 0;
+            const or_irf* irf = &irf_set[which];
+            const int32_t* kern = kerns[which];
             int32_t taus[16];
             int n = 0;
             if (g > 0.0) {
@@ -154,5 +167,11 @@ void or_init(const uint16_t* dense, const double* gain, int h, int w, int t,
         free(wc);
         free(inwin);
     }
-    free(kern);
+    for (int i = 0; i < n_irf; ++i) free(kerns[i]);
+}
+
+void or_init(const uint16_t* dense, const double* gain, int h, int w, int t,
+             const or_irf* irf, const or_params* prm, or_state* s)
+{
+    or_init_idx(dense, gain, NULL, h, w, t, irf, prm, s);
 }

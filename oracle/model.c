@@ -40,6 +40,14 @@ void or_irf_eval(const or_irf* irf, double x, double* h, double* dh)
     *dh = 0.5 * (c1 + 2.0 * c2 * u + 3.0 * c3 * u * u);
 }
 
+/* The instrument response of pixel p: h_{i,j} of the likelihood equation is
+ * per pixel; `irf` is the array of responses and idx[p] picks one (NULL:
+ * every pixel uses irf[0]). */
+static const or_irf* irf_at(const or_irf* irf, const uint8_t* idx, int64_t p)
+{
+    return idx ? irf + idx[p] : irf;
+}
+
 /* Mean count of pixel p in bin t (likelihood equation):
  *   lambda = g (sum over alive points n of the pixel r_n h(t - t_n) + b),
  * floored at lam_floor so that the logarithm and 1/lambda exist. */
@@ -61,18 +69,24 @@ static double pixel_lambda(const or_state* s, int64_t p, int64_t npix, double g,
 /* g(t, r, b) = sum_{i,j,t} (lambda - z log lambda), the negative log-likelihood
  * of Results, "Observation model", without the constant log z! term.  Dense
  * over every bin: the reference the sparse gradients are checked against. */
-double or_nll_dense(int h, int w, int t, const double* z, const double* gain,
-                    const or_state* s, const or_irf* irf, double lam_floor)
+double or_nll_dense_idx(int h, int w, int t, const double* z, const double* gain, const uint8_t* irf_idx,
+                        const or_state* s, const or_irf* irf, double lam_floor)
 {
     const int64_t npix = (int64_t)h * w;
     double total = 0.0;
     for (int64_t p = 0; p < npix; ++p)
         for (int tb = 0; tb < t; ++tb) {
-            const double lam = pixel_lambda(s, p, npix, gain[p], irf, (double)tb, lam_floor);
+            const double lam = pixel_lambda(s, p, npix, gain[p], irf_at(irf, irf_idx, p), (double)tb, lam_floor);
             const double zz = z[p * t + tb];
             total += lam - (zz > 0.0 ? zz * log(lam) : 0.0);
         }
     return total;
+}
+
+double or_nll_dense(int h, int w, int t, const double* z, const double* gain,
+                    const or_state* s, const or_irf* irf, double lam_floor)
+{
+    return or_nll_dense_idx(h, w, t, z, gain, NULL, s, irf, lam_floor);
 }
 
 /* H_n = sum_{t in [0,T)} h(t - t_n) and H'_n = sum_t h'(t - t_n): the part of the
@@ -99,10 +113,11 @@ static void support_sums(const or_irf* irf, double tn, int t, double* H, double*
  * Methods and Fig. 5):
  *   sh[k]  = sum z h(t - t_k) / lambda,  sdh[k] = sum z h'(t - t_k) / lambda,
  *   *sz    = sum z / lambda. */
-static void pixel_sums(const or_frame* f, const or_state* s, const or_irf* irf,
+static void pixel_sums(const or_frame* f, const or_state* s, const or_irf* irf_set,
                        double lam_floor, int64_t p, double* sh, double* sdh, double* sz)
 {
     const int64_t npix = (int64_t)f->h * f->w;
+    const or_irf* irf = irf_at(irf_set, f->irf_idx, p);
     const double g = f->gain[p];
     for (int k = 0; k < s->k; ++k) sh[k] = sdh[k] = 0.0;
     *sz = 0.0;
@@ -142,7 +157,7 @@ void or_gradients(const or_frame* f, const or_state* s, const or_irf* irf,
                 continue;
             }
             double H, dH;
-            support_sums(irf, s->t[n], f->t, &H, &dH);
+            support_sums(irf_at(irf, f->irf_idx, p), s->t[n], f->t, &H, &dH);
             gt[n] = g * s->r[n] * (-dH + sdh[k]);
             gr[n] = g * (H - sh[k]);
         }
@@ -176,7 +191,7 @@ void or_t_step(const or_frame* f, const or_irf* irf, const or_params* prm, or_st
             newt[k] = s->t[n];
             if (!s->alive[n]) continue;
             double H, dH;
-            support_sums(irf, s->t[n], f->t, &H, &dH);
+            support_sums(irf_at(irf, f->irf_idx, p), s->t[n], f->t, &H, &dH);
             const double grad = g * s->r[n] * (-dH + sdh[k]);
             const double beta = prm->t_step / (g * s->r[n] + prm->eps_r);
             const double step = clampd(-beta * grad, -prm->dt_max, prm->dt_max);
@@ -204,7 +219,7 @@ void or_r_step(const or_frame* f, const or_irf* irf, const or_params* prm, or_st
             newr[k] = s->r[n];
             if (!s->alive[n]) continue;
             double H, dH;
-            support_sums(irf, s->t[n], f->t, &H, &dH);
+            support_sums(irf_at(irf, f->irf_idx, p), s->t[n], f->t, &H, &dH);
             const double v = s->r[n] - prm->r_step * (s->r[n] + prm->eps_r) * (H - sh[k]);
             newr[k] = v > 0.0 ? v : 0.0;
         }

@@ -46,7 +46,8 @@ class Irf(C.Structure):
 class Frame(C.Structure):
     _fields_ = [("h", C.c_int), ("w", C.c_int), ("t", C.c_int),
                 ("off", C.POINTER(C.c_int64)), ("bin", C.POINTER(C.c_int32)),
-                ("cnt", C.POINTER(C.c_double)), ("gain", C.POINTER(C.c_double))]
+                ("cnt", C.POINTER(C.c_double)), ("gain", C.POINTER(C.c_double)),
+                ("irf_idx", C.POINTER(C.c_uint8))]
 
 
 class State(C.Structure):
@@ -76,6 +77,7 @@ def lib():
         _lib = C.CDLL(build())
         _lib.or_poisson_fixed.restype = C.c_uint32
         _lib.or_nll_dense.restype = C.c_double
+        _lib.or_nll_dense_idx.restype = C.c_double
         _lib.or_peaks.restype = C.c_int
         _lib.or_num_threads.restype = C.c_int
         _lib.or_net_nparams.restype = C.c_long
@@ -154,10 +156,20 @@ class OIrf:
         return Irf(len(self.h), self.origin, _ptr(self.h, C.c_double))
 
 
-class OFrame:
-    """Per-pixel nonzero-bin lists of a histogram (integer or expected counts)."""
+def _irfs(irf):
+    """An OIrf, or a list of them (the per-pixel responses a frame's irf_idx
+    selects from), as the C array the oracle takes."""
+    lst = list(irf) if isinstance(irf, (list, tuple)) else [irf]
+    arr = (Irf * len(lst))(*[i.c() for i in lst])
+    arr._keep = lst
+    return arr
 
-    def __init__(self, z, gain=None):
+
+class OFrame:
+    """Per-pixel nonzero-bin lists of a histogram (integer or expected counts),
+    with an optional per-pixel index into a list of IRFs."""
+
+    def __init__(self, z, gain=None, irf_idx=None):
         z = np.asarray(z)
         self.hh, self.ww, self.tt = z.shape
         flat = z.reshape(-1, self.tt)
@@ -168,11 +180,14 @@ class OFrame:
         self.cnt = flat[rows, bins].astype(np.float64)
         g = np.ones((self.hh, self.ww)) if gain is None else np.asarray(gain, np.float64)
         self.gain = np.ascontiguousarray(g.reshape(self.hh, self.ww))
+        self.irf_idx = None if irf_idx is None else np.ascontiguousarray(
+            np.asarray(irf_idx, np.uint8).reshape(self.hh, self.ww))
 
     def c(self):
         return Frame(self.hh, self.ww, self.tt, _ptr(self.off, C.c_int64),
                      _ptr(self.bin, C.c_int32), _ptr(self.cnt, C.c_double),
-                     _ptr(self.gain, C.c_double))
+                     _ptr(self.gain, C.c_double),
+                     None if self.irf_idx is None else _ptr(self.irf_idx, C.c_uint8))
 
 
 # ---------------------------------------------------------------------------
@@ -212,12 +227,14 @@ def irf_eval(irf: OIrf, x):
     return h.value, dh.value
 
 
-def nll_dense(z, gain, st: OState, irf: OIrf, lam_floor):
+def nll_dense(z, gain, st: OState, irf, lam_floor, irf_idx=None):
     z = np.ascontiguousarray(z, np.float64)
     h, w, t = z.shape
     g = np.ascontiguousarray(np.ones((h, w)) if gain is None else gain, np.float64)
-    return lib().or_nll_dense(h, w, t, _ptr(z, C.c_double), _ptr(g, C.c_double),
-                              C.byref(st.c()), C.byref(irf.c()), C.c_double(lam_floor))
+    idx = None if irf_idx is None else np.ascontiguousarray(np.asarray(irf_idx, np.uint8).reshape(h, w))
+    return lib().or_nll_dense_idx(h, w, t, _ptr(z, C.c_double), _ptr(g, C.c_double),
+                                  None if idx is None else _ptr(idx, C.c_uint8),
+                                  C.byref(st.c()), _irfs(irf), C.c_double(lam_floor))
 
 
 def gradients(fr: OFrame, st: OState, irf: OIrf, prm: dict):
@@ -226,7 +243,7 @@ def gradients(fr: OFrame, st: OState, irf: OIrf, prm: dict):
     gr = np.zeros((k, h, w))
     gb = np.zeros((h, w))
     p = make_params(prm)
-    lib().or_gradients(C.byref(fr.c()), C.byref(st.c()), C.byref(irf.c()), C.byref(p),
+    lib().or_gradients(C.byref(fr.c()), C.byref(st.c()), _irfs(irf), C.byref(p),
                        _ptr(gt, C.c_double), _ptr(gr, C.c_double), _ptr(gb, C.c_double))
     return gt, gr, gb
 
@@ -258,27 +275,31 @@ def peaks(y, wc, sep, min_photons, kmax):
     return taus[:n].copy()
 
 
-def init(dense, gain, irf: OIrf, prm: dict) -> OState:
+def init(dense, gain, irf, prm: dict, irf_idx=None) -> OState:
+    """Initialisation; irf is an OIrf or a list of them with irf_idx [h][w]
+    selecting each pixel's."""
     dense = np.ascontiguousarray(dense, np.uint16)
     h, w, t = dense.shape
     g = np.ascontiguousarray(np.ones((h, w)) if gain is None else gain, np.float64)
+    idx = None if irf_idx is None else np.ascontiguousarray(np.asarray(irf_idx, np.uint8).reshape(h, w))
     st = new_state(prm["k_max"], h, w)
     p = make_params(prm)
-    lib().or_init(_ptr(dense, C.c_uint16), _ptr(g, C.c_double), h, w, t, C.byref(irf.c()),
-                  C.byref(p), C.byref(st.c()))
+    lib().or_init_idx(_ptr(dense, C.c_uint16), _ptr(g, C.c_double),
+                      None if idx is None else _ptr(idx, C.c_uint8), h, w, t, _irfs(irf),
+                      C.byref(p), C.byref(st.c()))
     return st
 
 
 def t_step(fr, irf, prm, st):
-    lib().or_t_step(C.byref(fr.c()), C.byref(irf.c()), C.byref(make_params(prm)), C.byref(st.c()))
+    lib().or_t_step(C.byref(fr.c()), _irfs(irf), C.byref(make_params(prm)), C.byref(st.c()))
 
 
 def r_step(fr, irf, prm, st):
-    lib().or_r_step(C.byref(fr.c()), C.byref(irf.c()), C.byref(make_params(prm)), C.byref(st.c()))
+    lib().or_r_step(C.byref(fr.c()), _irfs(irf), C.byref(make_params(prm)), C.byref(st.c()))
 
 
 def b_step(fr, irf, prm, st):
-    lib().or_b_step(C.byref(fr.c()), C.byref(irf.c()), C.byref(make_params(prm)), C.byref(st.c()))
+    lib().or_b_step(C.byref(fr.c()), _irfs(irf), C.byref(make_params(prm)), C.byref(st.c()))
 
 
 def apss(h, w, t, prm, st):
@@ -307,16 +328,18 @@ def depth_denoise(h, w, t, prm, st):
 
 
 def palm(fr, irf, prm, st, n_iter):
-    lib().or_palm(C.byref(fr.c()), C.byref(irf.c()), C.byref(make_params(prm)),
+    lib().or_palm(C.byref(fr.c()), _irfs(irf), C.byref(make_params(prm)),
                   C.byref(st.c()), int(n_iter))
 
 
-def reconstruct(dense, irf: OIrf, prm: dict, gain=None) -> OState:
+def reconstruct(dense, irf, prm: dict, gain=None, irf_idx=None) -> OState:
+    """The whole method; irf is an OIrf or a list of them with irf_idx [h][w]
+    selecting each pixel's."""
     dense = np.ascontiguousarray(dense, np.uint16)
     h, w, t = dense.shape
-    fr = OFrame(dense, gain)
+    fr = OFrame(dense, gain, irf_idx)
     st = new_state(prm["k_max"], h, w)
-    lib().or_reconstruct(_ptr(dense, C.c_uint16), C.byref(fr.c()), C.byref(irf.c()),
+    lib().or_reconstruct(_ptr(dense, C.c_uint16), C.byref(fr.c()), _irfs(irf),
                          C.byref(make_params(prm)), C.byref(st.c()))
     return st
 

@@ -35,6 +35,6 @@ void or_palm(const or_frame* f, const or_irf* irf, const or_params* p, or_state*
 void or_reconstruct(const uint16_t* dense, const or_frame* f, const or_irf* irf,
                     const or_params* p, or_state* s)
 {
-    or_init(dense, f->gain, f->h, f->w, f->t, irf, p, s);
+    or_init_idx(dense, f->gain, f->irf_idx, f->h, f->w, f->t, irf, p, s);
     or_palm(f, irf, p, s, p->n_iter);
 }

@@ -44,13 +44,17 @@ typedef struct {
 } or_irf;
 
 /* Sparse histogram: per pixel p the nonzero bins bin[off[p]..off[p+1]) with
- * their counts (double so that expected counts can be fed as well). */
+ * their counts (double so that expected counts can be fed as well).
+ * irf_idx: the likelihood's instrument response is per pixel (h_{i,j}); every
+ * function below that takes `irf` takes an array of responses, and pixel p
+ * uses irf[irf_idx[p]] (irf_idx NULL: every pixel uses irf[0]). */
 typedef struct {
     int h, w, t;
     const int64_t* off;       /* [h*w + 1] */
     const int32_t* bin;       /* [nnz] increasing within a pixel */
     const double* cnt;        /* [nnz] > 0 */
     const double* gain;       /* [h*w] */
+    const uint8_t* irf_idx;   /* [h*w] or NULL */
 } or_frame;
 
 /* Point cloud in K slots per pixel plus the background image. */
@@ -92,6 +96,8 @@ void or_synthesize(int h, int w, int t, int n_comp,
 void or_irf_eval(const or_irf* irf, double x, double* h, double* dh);
 double or_nll_dense(int h, int w, int t, const double* z, const double* gain,
                     const or_state* s, const or_irf* irf, double lam_floor);
+double or_nll_dense_idx(int h, int w, int t, const double* z, const double* gain, const uint8_t* irf_idx,
+                        const or_state* s, const or_irf* irf, double lam_floor);
 void or_gradients(const or_frame* f, const or_state* s, const or_irf* irf,
                   const or_params* p, double* gt, double* gr, double* gb);
 
@@ -103,6 +109,8 @@ int or_peaks(const int64_t* y, const int64_t* wcount, int t, int sep, int min_ph
              int kmax, int32_t* taus);
 void or_init(const uint16_t* dense, const double* gain, int h, int w, int t,
              const or_irf* irf, const or_params* p, or_state* s);
+void or_init_idx(const uint16_t* dense, const double* gain, const uint8_t* irf_idx, int h, int w, int t,
+                 const or_irf* irf, const or_params* p, or_state* s);
 
 /* ---- one PALM iteration, step by step ---- */
 void or_t_step(const or_frame* f, const or_irf* irf, const or_params* p, or_state* s);
