@@ -45,6 +45,7 @@ extern "C" {
 #define RT3D_VERSION 1
 #define RT3D_MAX_K 4          /* point slots per pixel */
 #define RT3D_MAX_IRF 256      /* samples of the instrument response */
+#define RT3D_MAX_IRFS 4       /* instrument responses a context holds (rt3d_set_irfs) */
 #define RT3D_MAX_BATCH 64     /* frames per batched call */
 #define RT3D_MAX_T 16384      /* histogram bins */
 #define RT3D_MAX_WIN_R 4      /* neighbourhood half-width of the denoisers, pixels */
@@ -107,17 +108,23 @@ typedef struct {
 /* One lidar frame, DEVICE pointers.  Give `dense`, or the sparse list
  * (csr_off, csr_ent), or both (then the sparse list is used by the loop and
  * the dense histogram by the initialisation).
- *   dense    [h][w][t] uint16 photon counts
- *   csr_off  [h*w + 1] offsets into csr_ent (pixel p owns off[p]..off[p+1])
- *   csr_ent  packed (bin << 16) | count, count >= 1, bins increasing per pixel;
- *            a photon list with repeated bins is NOT accepted -- merge first
- *   gain     [h][w] detector gain g_{i,j} (0 = dead pixel) or NULL for 1. */
+ *   dense     [h][w][t] uint16 photon counts
+ *   csr_off   [h*w + 1] offsets into csr_ent (pixel p owns off[p]..off[p+1])
+ *   csr_ent   packed (bin << 16) | count, count >= 1, bins increasing per pixel;
+ *             a photon list with repeated bins is NOT accepted -- merge first
+ *   gain      [h][w] detector gain g_{i,j} (0 = dead pixel) or NULL for 1
+ *   irf_index [h][w] the instrument response h_{i,j} of each pixel: an index
+ *             into the context's responses (rt3d_set_irfs; an index past the
+ *             last reads as the last), or NULL for response 0.  A frame with
+ *             an index is initialised by the CUDA-core matched filter (its
+ *             lmf_precision is not used). */
 typedef struct {
     int32_t h, w, t;
     const uint16_t* dense;
     const uint32_t* csr_off;
     const uint32_t* csr_ent;
     const float* gain;
+    const uint8_t* irf_index;
 } rt3d_frame;
 
 /* Every constant of the method.  Step sizes of the gradient steps (the paper's
@@ -202,6 +209,17 @@ rt3d_status rt3d_validate(const rt3d_config* cfg, const rt3d_frame* f, const rt3
  * (sparse-entry buffer, half-step state, counters).  *out is NULL on error. */
 rt3d_status rt3d_create(const rt3d_config* cfg, const rt3d_irf* irf, rt3d_ctx_t** out);
 void rt3d_destroy(rt3d_ctx_t* ctx);
+
+/* Per-pixel instrument responses (Results, "Observation model": the response
+ * h_{i,j} of the likelihood is per pixel).  Replaces the context's responses
+ * with n of them (HOST array, copied; 1..RT3D_MAX_IRFS); frames pick one per
+ * pixel with rt3d_frame.irf_index, and response 0 serves frames without an
+ * index (rt3d_create's IRF is the single response 0 until this is called).
+ * Each response is normalised as in rt3d_create.  Their samples must fit the
+ * kernels' tables: sum over responses of (len + 6) <= RT3D_MAX_IRF + 6.
+ * Takes effect from the next call.  RT3D_E_INVALID for a bad count, length,
+ * origin or sample (nothing changes then). */
+rt3d_status rt3d_set_irfs(rt3d_ctx_t* ctx, int n, const rt3d_irf* irfs);
 
 /* Photon synthesis (test/benchmark input, not the method): Poisson counts of
  * the observation model drawn with Philox4x32-10 (Salmon et al., SC'11),

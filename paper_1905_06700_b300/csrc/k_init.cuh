@@ -60,11 +60,13 @@ k_init(const CallRecord* __restrict__ rec, const Work W, int pix0, int pix_end)
     const KParams& P = rec->P;
     const Batch& B = rec->B;
     extern __shared__ __align__(16) unsigned char smem[];
-    int* sK = reinterpret_cast<int*>(smem);
-    const int L = P.irf_len, O = P.irf_origin, sep = P.peak_sep;
+    int* sK_all = reinterpret_cast<int*>(smem);
+    const int sep = P.peak_sep;
     const int min_photons = P.peak_min_photons;
-    const int k_bytes = (L * 4 + 15) & ~15;
-    for (int i = threadIdx.x; i < L; i += blockDim.x) sK[i] = P.lmf[i];
+    // every response's taps (a pixel uses its own response's)
+    const int n_taps = P.irf_offs[P.n_irf - 1] + P.irf_lens[P.n_irf - 1];
+    const int k_bytes = (n_taps * 4 + 15) & ~15;
+    for (int i = threadIdx.x; i < n_taps; i += blockDim.x) sK_all[i] = P.lmf[i];
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -78,6 +80,10 @@ k_init(const CallRecord* __restrict__ rec, const Work W, int pix0, int pix_end)
     const int T = F.nt;
     if (lp == 0 && lane == 0 && F.n_points) *F.n_points = 0;   // counted by the finaliser
     const float g = F.gain ? F.gain[lp] : 1.0f;
+    // the pixel's instrument response: taps, length and origin
+    const int which = pixel_irf(P, F, lp);
+    const int L = P.irf_lens[which], O = P.irf_origins[which];
+    const int* sK = sK_all + P.irf_offs[which];
 
     unsigned char* wbase = smem + k_bytes + warp * init_warp_bytes(sep);
     uint32_t* stage = reinterpret_cast<uint32_t*>(wbase);

@@ -41,16 +41,23 @@ __device__ __forceinline__ TileCtx tile_ctx(const Batch& B, int tile0)
     return c;
 }
 
+// The responses' samples with kIrfPad zeros on each side, one region per
+// response (IrfRef::pad_off).
 __device__ __forceinline__ void load_irf(float* pad, const KParams& P)
 {
-    for (int i = threadIdx.x; i < P.irf_len + 2 * kIrfPad; i += blockDim.x) {
-        const int k = i - kIrfPad;
-        pad[i] = (k >= 0 && k < P.irf_len) ? P.irf[k] : 0.0f;
+    for (int i = 0; i < P.n_irf; ++i) {
+        const IrfRef R = irf_ref(P, i);
+        const float* src = P.irf + P.irf_offs[i];
+        for (int q = threadIdx.x; q < R.len + 2 * kIrfPad; q += blockDim.x) {
+            const int k = q - kIrfPad;
+            pad[R.pad_off + q] = (k >= 0 && k < R.len) ? src[k] : 0.0f;
+        }
     }
 }
 
-// Catmull-Rom intervals of the IRF, for the bin sums.  Entry i holds the
-// interval that starts at sample k = i - 3,
+// Catmull-Rom intervals of the IRF, for the bin sums.  Entry i of a
+// response's region (IrfRef::coef_off) holds the interval that starts at
+// sample k = i - 3,
 //   h(k + u) = c.x + u (c.y + u (c.z + u c.w)),   h'(k + u) = c.y + u (2 c.z + 3 c.w u),
 // the interpolant of irf_eval with its factor 1/2 folded into the coefficients
 // (an exact scaling).  Entries 0 and L + 4 (k = -3 and k = L + 1) are zero: an
@@ -60,21 +67,25 @@ constexpr int kCoefLen = kMaxIrf + 5;
 __device__ __forceinline__ void load_irf_coef(float* pad, float4* coef, const KParams& P)
 {
     load_irf(pad, P);
-    const int L = P.irf_len;
-    for (int i = threadIdx.x; i < L + 5; i += blockDim.x) {
-        const int k = i - 3;
-        float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        if (k >= -2 && k <= L) {
-            const float pm = k - 1 >= 0 && k - 1 < L ? P.irf[k - 1] : 0.0f;
-            const float p0 = k >= 0 && k < L ? P.irf[k] : 0.0f;
-            const float p1 = k + 1 >= 0 && k + 1 < L ? P.irf[k + 1] : 0.0f;
-            const float p2 = k + 2 >= 0 && k + 2 < L ? P.irf[k + 2] : 0.0f;
-            const float c1 = p1 - pm;
-            const float c2 = 2.0f * pm - 5.0f * p0 + 4.0f * p1 - p2;
-            const float c3 = -pm + 3.0f * p0 - 3.0f * p1 + p2;
-            c = make_float4(p0, 0.5f * c1, 0.5f * c2, 0.5f * c3);
+    for (int r = 0; r < P.n_irf; ++r) {
+        const IrfRef R = irf_ref(P, r);
+        const int L = R.len;
+        const float* h = P.irf + P.irf_offs[r];
+        for (int i = threadIdx.x; i < L + 5; i += blockDim.x) {
+            const int k = i - 3;
+            float4 c = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+            if (k >= -2 && k <= L) {
+                const float pm = k - 1 >= 0 && k - 1 < L ? h[k - 1] : 0.0f;
+                const float p0 = k >= 0 && k < L ? h[k] : 0.0f;
+                const float p1 = k + 1 >= 0 && k + 1 < L ? h[k + 1] : 0.0f;
+                const float p2 = k + 2 >= 0 && k + 2 < L ? h[k + 2] : 0.0f;
+                const float c1 = p1 - pm;
+                const float c2 = 2.0f * pm - 5.0f * p0 + 4.0f * p1 - p2;
+                const float c3 = -pm + 3.0f * p0 - 3.0f * p1 + p2;
+                c = make_float4(p0, 0.5f * c1, 0.5f * c2, 0.5f * c3);
+            }
+            coef[R.coef_off + i] = c;
         }
-        coef[i] = c;
     }
 }
 
@@ -89,11 +100,12 @@ __device__ __forceinline__ void slot_frame(int origin, float t, int& base, float
     u = y0 - f;
 }
 
-// Per-pixel record of the bin sums: u[K], base[K], rr[K], b, g, packed in
+// Per-pixel record of the bin sums: u[K], base[K], rr[K], b, g and the
+// response's coefficient region (offset << 16 | last entry), packed in
 // 16-byte words.
 template <int K>
 struct PixRec {
-    static constexpr int NW = (3 * K + 2 + 3) / 4;
+    static constexpr int NW = (3 * K + 3 + 3) / 4;
     float4 q[NW];
 };
 
@@ -122,8 +134,8 @@ struct WarpSums {
 // so the result is deterministic and independent of the rest of the batch.
 template <int K, int MODE, int NSX>
 __device__ __forceinline__ void warp_pixel_sums(const uint32_t* __restrict__ ent, uint2 sg, bool on,
-                                                const float4* coef, const KParams& P, const float* tk,
-                                                const float* rr, float b, float g,
+                                                const float4* coef, const KParams& P, const IrfRef& ir,
+                                                const float* tk, const float* rr, float b, float g,
                                                 WarpSums<K, NSX>& S, float* out)
 {
     constexpr int NS = MODE == 2 ? 1 : K;
@@ -149,12 +161,13 @@ __device__ __forceinline__ void warp_pixel_sums(const uint32_t* __restrict__ ent
 #pragma unroll
         for (int k = 0; k < K; ++k) {
             int base;
-            slot_frame(P.irf_origin, tk[k], base, w[k]);
+            slot_frame(ir.origin, tk[k], base, w[k]);
             w[K + k] = __int_as_float(base);
             w[2 * K + k] = rr[k];
         }
         w[3 * K] = b;
         w[3 * K + 1] = g;
+        w[3 * K + 2] = __int_as_float((ir.coef_off << 16) | (ir.len + 4));
 #pragma unroll
         for (int i = 0; i < NW; ++i) S.rec[lane].q[i] = make_float4(w[4 * i], w[4 * i + 1], w[4 * i + 2], w[4 * i + 3]);
     }
@@ -164,7 +177,6 @@ __device__ __forceinline__ void warp_pixel_sums(const uint32_t* __restrict__ ent
     S.nextp[lane] = above ? __ffs(above) - 1 : 32;
     __syncwarp();
 
-    const unsigned cmax = (unsigned)(P.irf_len + 4);
     const float lam_floor = P.lam_floor;
     const int lo = (lane * E) >> 5, hi = ((lane + 1) * E) >> 5;
     if (lo < hi) {
@@ -175,6 +187,7 @@ __device__ __forceinline__ void warp_pixel_sums(const uint32_t* __restrict__ ent
             if (S.incl[p + s - 1] <= lo) p += s;
         float up[K], rp[K], bp, gp;
         int basep[K];
+        unsigned coffp, cmaxp;   // the pixel's coefficient region and its last (zero) entry
         auto load_pixel = [&](int q) {
             float w[4 * NW];
 #pragma unroll
@@ -193,6 +206,9 @@ __device__ __forceinline__ void warp_pixel_sums(const uint32_t* __restrict__ ent
             }
             bp = w[3 * K];
             gp = w[3 * K + 1];
+            const unsigned cw = __float_as_uint(w[3 * K + 2]);
+            coffp = cw >> 16;
+            cmaxp = cw & 0xffffu;
         };
         float part[NS];
         // a piece of pixel q ends: a lane's first piece of a pixel begun in an
@@ -231,7 +247,7 @@ __device__ __forceinline__ void warp_pixel_sums(const uint32_t* __restrict__ ent
             float acc = bp;
 #pragma unroll
             for (int k = 0; k < K; ++k) {
-                const float4 c = coef[min((unsigned)(tb + basep[k]), cmax)];
+                const float4 c = coef[coffp + min((unsigned)(tb + basep[k]), cmaxp)];
                 const float u = up[k];
                 hv[k] = c.x + u * (c.y + u * (c.z + u * c.w));
                 dv[k] = c.y + u * (2.0f * c.z + 3.0f * c.w * u);
@@ -308,16 +324,16 @@ __device__ __forceinline__ float bkg_filter(const KParams& P, const float* bh, i
 // gradient step on the negative log-likelihood, clamped to dt_max and to the
 // histogram) from its bin sums sdh[k] = sum z h'(t - t_k)/lambda.
 template <int K>
-__device__ __forceinline__ void depth_step(const float* pad, const KParams& P, int T, const float* tk,
-                                           const float* rk, const bool* ak, float g, const float* sdh,
-                                           float* t_half, long long stride)
+__device__ __forceinline__ void depth_step(const float* pad, const KParams& P, const IrfRef& ir, int T,
+                                           const float* tk, const float* rk, const bool* ak, float g,
+                                           const float* sdh, float* t_half, long long stride)
 {
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         float tn = tk[k];
         if (ak[k] && g > 0.0f) {
             float H, dH;
-            support_sums(pad, P, T, tk[k], H, dH);
+            support_sums(pad, ir, T, tk[k], H, dH);
             const float grad = g * rk[k] * (-dH + sdh[k]);
             const float beta = P.t_step / (g * rk[k] + P.eps_r);
             const float step = clampf(-beta * grad, -P.dt_max, P.dt_max);
@@ -346,6 +362,7 @@ k_phase_a(const CallRecord* __restrict__ rec, const Work W, int first, int tile0
     const int np = F.npix, S = W.stride;
     const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
     const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
+    const IrfRef ir = irf_ref(P, c.inb ? pixel_irf(P, F, lp) : 0);
     float b = 0.0f, g = 0.0f;
     float tk[K], rk[K], rr[K];
     bool ak[K];
@@ -377,9 +394,9 @@ k_phase_a(const CallRecord* __restrict__ rec, const Work W, int first, int tile0
 #pragma unroll
     for (int k = 0; k < K; ++k) rr[k] = ak[k] ? rk[k] : 0.0f;
     float sdh[K];
-    warp_pixel_sums<K, 0>(F.ent, sg, c.inb, coef, P, tk, rr, b, g, ws[threadIdx.x >> 5], sdh);
+    warp_pixel_sums<K, 0>(F.ent, sg, c.inb, coef, P, ir, tk, rr, b, g, ws[threadIdx.x >> 5], sdh);
     if (!c.inb) return;
-    depth_step<K>(pad, P, F.nt, tk, rk, ak, g, sdh, W.t_half + wp, S);
+    depth_step<K>(pad, P, ir, F.nt, tk, rk, ak, g, sdh, W.t_half + wp, S);
 }
 
 // ----------------------------------------------------------------------------
@@ -748,6 +765,7 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, in
     const int np = F.npix, S = W.stride, R = P.win_r;
     const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
     const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
+    const IrfRef ir = irf_ref(P, c.inb ? pixel_irf(P, F, lp) : 0);
     const bool apss = P.depth_den != RT3D_DEPTH_NONE;
     const float apss_px = P.pitch * (1.0f / P.apss_h);
     if (apss) win_vote(s_vote, R, apss_px);
@@ -812,14 +830,14 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, in
         for (int k = 0; k < K; ++k) F.t[(long long)k * np + lp] = tn[k];
     }
     float sh[K];
-    warp_pixel_sums<K, 1>(F.ent, sg, c.inb, coef, P, tk, rr, b, g, ws[threadIdx.x >> 5], sh);
+    warp_pixel_sums<K, 1>(F.ent, sg, c.inb, coef, P, ir, tk, rr, b, g, ws[threadIdx.x >> 5], sh);
     if (!c.inb) return;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
         float rn = rk[k];
         if (ak[k] && g > 0.0f) {
             float H, dH;
-            support_sums(pad, P, F.nt, tk[k], H, dH);
+            support_sums(pad, ir, F.nt, tk[k], H, dH);
             rn = fmaxf(rk[k] - P.r_step * (rk[k] + P.eps_r) * (H - sh[k]), 0.0f);
         }
         W.r_half[(long long)k * S + wp] = rn;
@@ -855,6 +873,7 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next, int t
     const int np = F.npix, S = W.stride, R = P.win_r;
     const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
     const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
+    const IrfRef ir = irf_ref(P, c.inb ? pixel_irf(P, F, lp) : 0);
     const float int_px = P.pitch * (1.0f / P.int_h);
     if (P.int_den) win_vote(s_vote, R, int_px);
     // own pixel state read with the halo (one memory round trip)
@@ -937,7 +956,7 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next, int t
     }
     const float g = g_own, b = b_own;
     float sz;
-    warp_pixel_sums<K, 2>(F.ent, sg, c.inb, coef, P, tk, rr, b, g, ws[threadIdx.x >> 5], &sz);
+    warp_pixel_sums<K, 2>(F.ent, sg, c.inb, coef, P, ir, tk, rr, b, g, ws[threadIdx.x >> 5], &sz);
     float bn = b;
     if (c.inb) {
         if (g > 0.0f) bn = fmaxf(b - P.b_step * (b + P.eps_b) * (1.0f - sz / (float)F.nt), P.b_floor);
@@ -958,9 +977,9 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next, int t
     }
     if (c.inb) F.b[lp] = bn;
     float sdh[K];
-    warp_pixel_sums<K, 0>(F.ent, sg, c.inb, coef, P, tka, rra, bn, g, ws[threadIdx.x >> 5], sdh);
+    warp_pixel_sums<K, 0>(F.ent, sg, c.inb, coef, P, ir, tka, rra, bn, g, ws[threadIdx.x >> 5], sdh);
     if (!c.inb) return;
-    depth_step<K>(pad, P, F.nt, tka, rka, aka, g, sdh, W.t_half + wp, S);
+    depth_step<K>(pad, P, ir, F.nt, tka, rka, aka, g, sdh, W.t_half + wp, S);
 }
 
 // ----------------------------------------------------------------------------

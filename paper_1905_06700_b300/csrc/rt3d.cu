@@ -91,8 +91,11 @@ struct rt3d_net {
 
 struct rt3d_ctx {
     rt3d_config cfg{};
-    std::vector<double> irf_norm;   // normalised in double, index order
-    int irf_len = 0, irf_origin = 0;
+    // instrument responses, each normalised in double in index order; frames
+    // pick one per pixel (response 0 without an index)
+    int n_irf = 1;
+    std::vector<double> irf_norm[kMaxIrfs];
+    int irf_len[kMaxIrfs] = {0}, irf_origin[kMaxIrfs] = {0};
     Work W{};
     long long stride = 0;           // workspace pixels = max_batch * max_h * max_w
     int* d_status = nullptr;
@@ -129,6 +132,7 @@ struct rt3d_ctx {
     uint32_t* s_ent = nullptr;
     long long s_ent_cap = 0;
     float* s_gain = nullptr;
+    uint8_t* s_idx = nullptr;
     float* s_t = nullptr;
     float* s_r = nullptr;
     float* s_b = nullptr;
@@ -259,6 +263,47 @@ bool config_ok(const rt3d_config* cfg)
 
 rt3d_status build_tc_params(const rt3d_params* p, KParams* K);
 
+// The instrument responses' per-call tables: float samples (concatenated),
+// their sums, the quantised log-IRF taps
+//   K_s = round(2^f log1p(h_s / (delta_rel max h)))
+// of each response (max h of that response), and response 0's fields for the
+// tensor-core init.  norms[i] holds lens[i] samples normalised in double.
+rt3d_status fill_irf_tables(KParams* K, int n, const double* const* norms, const int* lens,
+                            const int* origins, const rt3d_params* p)
+{
+    K->n_irf = n;
+    int off = 0, kmax = 0;
+    const double scale = std::ldexp(1.0, p->lmf_frac_bits);
+    for (int i = 0; i < n; ++i) {
+        K->irf_offs[i] = off;
+        K->irf_lens[i] = lens[i];
+        K->irf_origins[i] = origins[i];
+        float fsum = 0.0f;
+        double hmax = 0.0;
+        for (int s = 0; s < lens[i]; ++s) {
+            K->irf[off + s] = (float)norms[i][s];
+            fsum += K->irf[off + s];
+            if (norms[i][s] > hmax) hmax = norms[i][s];
+        }
+        K->irf_sums[i] = fsum;
+        const double delta = (double)p->lmf_delta_rel * hmax;
+        for (int s = 0; s < lens[i]; ++s) {
+            const double v = std::nearbyint(scale * std::log1p(norms[i][s] / delta));
+            if (v > 1e9) return RT3D_E_INVALID;
+            K->lmf[off + s] = (int)v;
+            if (K->lmf[off + s] > kmax) kmax = K->lmf[off + s];
+        }
+        off += lens[i];
+    }
+    K->irf_len = lens[0];
+    K->irf_origin = origins[0];
+    K->irf_sum = K->irf_sums[0];
+    K->lmf_kmax = kmax;
+    if (p->lmf_precision == RT3D_LMF_BF16 && kmax > 256) return RT3D_E_INVALID;
+    if (p->lmf_precision == RT3D_LMF_FP16 && kmax > 2048) return RT3D_E_INVALID;
+    return RT3D_OK;
+}
+
 // Per-call tables derived from the IRF and the parameters.
 rt3d_status build_kparams(const rt3d_ctx* c, const rt3d_params* p, KParams* K)
 {
@@ -285,34 +330,15 @@ rt3d_status build_kparams(const rt3d_ctx* c, const rt3d_params* p, KParams* K)
     K->int_den = p->intensity_denoiser;
     K->bkg_mode = p->bkg_mode;
     K->bkg_rad = p->bkg_radius;
-    K->irf_len = c->irf_len;
-    K->irf_origin = c->irf_origin;
     K->peak_sep = p->peak_sep;
     K->peak_min_photons = p->peak_min_photons;
     K->net_scale = p->net_scale;
     K->net_fallback = p->net_fallback;
     K->wait_ns = c->wait_ns;
-    float fsum = 0.0f;
-    double hmax = 0.0;
-    for (int s = 0; s < c->irf_len; ++s) {
-        K->irf[s] = (float)c->irf_norm[s];
-        fsum += K->irf[s];
-        if (c->irf_norm[s] > hmax) hmax = c->irf_norm[s];
-    }
-    K->irf_sum = fsum;
-    // quantised log-IRF: K_s = round(2^f log1p(h_s / (delta_rel max h)))
-    const double delta = (double)p->lmf_delta_rel * hmax;
-    const double scale = std::ldexp(1.0, p->lmf_frac_bits);
-    int kmax = 0;
-    for (int s = 0; s < c->irf_len; ++s) {
-        const double v = std::nearbyint(scale * std::log1p(c->irf_norm[s] / delta));
-        if (v > 1e9) return RT3D_E_INVALID;
-        K->lmf[s] = (int)v;
-        if (K->lmf[s] > kmax) kmax = K->lmf[s];
-    }
-    K->lmf_kmax = kmax;
-    if (p->lmf_precision == RT3D_LMF_BF16 && kmax > 256) return RT3D_E_INVALID;
-    if (p->lmf_precision == RT3D_LMF_FP16 && kmax > 2048) return RT3D_E_INVALID;
+    const double* norms[kMaxIrfs];
+    for (int i = 0; i < c->n_irf; ++i) norms[i] = c->irf_norm[i].data();
+    const rt3d_status st = fill_irf_tables(K, c->n_irf, norms, c->irf_len, c->irf_origin, p);
+    if (st != RT3D_OK) return st;
     if (p->bkg_mode == RT3D_BKG_LOWPASS) {
         const double sg = (double)p->bkg_sigma;
         double ks = 0.0;
@@ -468,13 +494,15 @@ rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3
         d.use_csr = f[i].csr_off != nullptr;
         d.ent = d.use_csr ? f[i].csr_ent : c->W.ent;
         d.gain = f[i].gain;
+        d.irf_index = f[i].irf_index;
         d.tc_tile_base = tc_tiles;
         d.net_strip_base = strips;
         strips += d.h * ((d.w + kStrip - 1) / kStrip);
         // tensor-core init of a dense frame whose rows TMA can address (16-byte
-        // aligned start and row stride); other frames take the CUDA-core path,
-        // which computes the identical integer filter
-        if (tc_init && !d.use_csr && f[i].t % 8 == 0 && ((uintptr_t)f[i].dense & 15) == 0) {
+        // aligned start and row stride) and whose pixels share response 0;
+        // other frames take the CUDA-core path, which computes the identical
+        // integer filter
+        if (tc_init && !d.use_csr && !f[i].irf_index && f[i].t % 8 == 0 && ((uintptr_t)f[i].dense & 15) == 0) {
             // each pixel's entries at a fixed offset (pixel x bins) of the
             // frame's region, so no allocation order is needed
             const long long cells = (long long)d.npix * f[i].t;
@@ -515,7 +543,8 @@ int init_warps(int sep)
 
 size_t init_smem(const KParams& K, int sep)
 {
-    return (size_t)((K.irf_len * 4 + 15) & ~15) + (size_t)init_warps(sep) * init_warp_bytes(sep);
+    const int n_taps = K.irf_offs[K.n_irf - 1] + K.irf_lens[K.n_irf - 1];
+    return (size_t)((n_taps * 4 + 15) & ~15) + (size_t)init_warps(sep) * init_warp_bytes(sep);
 }
 
 // One upload per call of the tables and frame descriptors the kernels read.
@@ -986,10 +1015,11 @@ rt3d_status rt3d_create(const rt3d_config* cfg, const rt3d_irf* irf, rt3d_ctx_t*
     rt3d_ctx* c = new (std::nothrow) rt3d_ctx();
     if (!c) return RT3D_E_NOMEM;
     c->cfg = *cfg;
-    c->irf_len = irf->len;
-    c->irf_origin = irf->origin;
-    c->irf_norm.resize(irf->len);
-    for (int s = 0; s < irf->len; ++s) c->irf_norm[s] = irf->samples[s] / sum;
+    c->n_irf = 1;
+    c->irf_len[0] = irf->len;
+    c->irf_origin[0] = irf->origin;
+    c->irf_norm[0].resize(irf->len);
+    for (int s = 0; s < irf->len; ++s) c->irf_norm[0][s] = irf->samples[s] / sum;
     c->stride = (long long)cfg->max_batch * cfg->max_h * cfg->max_w;
     long long cap = cfg->max_entries;
     if (cap == 0) cap = c->stride * cfg->max_t;
@@ -1023,13 +1053,42 @@ rt3d_status rt3d_create(const rt3d_config* cfg, const rt3d_irf* irf, rt3d_ctx_t*
     return RT3D_OK;
 }
 
+rt3d_status rt3d_set_irfs(rt3d_ctx_t* c, int n, const rt3d_irf* irfs)
+{
+    if (!c || !irfs || n < 1 || n > RT3D_MAX_IRFS) return RT3D_E_INVALID;
+    int room = 0;
+    for (int i = 0; i < n; ++i) {
+        const rt3d_irf& r = irfs[i];
+        if (!r.samples || r.len < 1 || r.len > RT3D_MAX_IRF || r.origin < 0 || r.origin >= r.len)
+            return RT3D_E_INVALID;
+        double sum = 0.0;
+        for (int s = 0; s < r.len; ++s) {
+            if (!(r.samples[s] >= 0.0) || !std::isfinite(r.samples[s])) return RT3D_E_INVALID;
+            sum += r.samples[s];
+        }
+        if (!(sum > 0.0)) return RT3D_E_INVALID;
+        room += r.len + 2 * kIrfPad;
+    }
+    if (room > RT3D_MAX_IRF + 2 * kIrfPad) return RT3D_E_INVALID;
+    c->n_irf = n;
+    for (int i = 0; i < n; ++i) {
+        double sum = 0.0;
+        for (int s = 0; s < irfs[i].len; ++s) sum += irfs[i].samples[s];
+        c->irf_len[i] = irfs[i].len;
+        c->irf_origin[i] = irfs[i].origin;
+        c->irf_norm[i].resize(irfs[i].len);
+        for (int s = 0; s < irfs[i].len; ++s) c->irf_norm[i][s] = irfs[i].samples[s] / sum;
+    }
+    return RT3D_OK;
+}
+
 void rt3d_destroy(rt3d_ctx_t* c)
 {
     if (!c) return;
     cudaSetDevice(c->cfg.device);
     void* ptrs[] = {c->W.seg, c->W.ent, c->d_count, c->W.t_half, c->W.r_half, c->W.b_half,
                     c->W.alive_b, c->d_status, c->d_tmp, c->d_rec, c->s_dense, c->s_off, c->s_ent,
-                    c->s_gain, c->s_t, c->s_r, c->s_b, c->s_alive, c->s_np, c->s_batch, c->d_band,
+                    c->s_gain, c->s_idx, c->s_t, c->s_r, c->s_b, c->s_alive, c->s_np, c->s_batch, c->d_band,
                     c->net_a0, c->net_a1, c->net_a2, c->net_y};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1198,6 +1257,7 @@ rt3d_status rt3d_reconstruct_host(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d
         RT3D_CUDA(cudaMalloc((void**)&c->s_dense, sizeof(uint16_t) * mpix * c->cfg.max_t));
         RT3D_CUDA(cudaMalloc((void**)&c->s_off, sizeof(uint32_t) * (mpix + 1)));
         RT3D_CUDA(cudaMalloc((void**)&c->s_gain, sizeof(float) * mpix));
+        RT3D_CUDA(cudaMalloc((void**)&c->s_idx, (size_t)mpix));
         RT3D_CUDA(cudaMalloc((void**)&c->s_t, sizeof(float) * K * mpix));
         RT3D_CUDA(cudaMalloc((void**)&c->s_r, sizeof(float) * K * mpix));
         RT3D_CUDA(cudaMalloc((void**)&c->s_b, sizeof(float) * mpix));
@@ -1231,6 +1291,10 @@ rt3d_status rt3d_reconstruct_host(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d
     if (f->gain) {
         RT3D_CUDA(cudaMemcpyAsync(c->s_gain, f->gain, sizeof(float) * npix, cudaMemcpyHostToDevice, s));
         df.gain = c->s_gain;
+    }
+    if (f->irf_index) {
+        RT3D_CUDA(cudaMemcpyAsync(c->s_idx, f->irf_index, (size_t)npix, cudaMemcpyHostToDevice, s));
+        df.irf_index = c->s_idx;
     }
     rt3d_result dr{c->s_t, c->s_r, c->s_alive, c->s_b, c->s_np};
     const int Kp = p->k_max;
@@ -1269,7 +1333,7 @@ rt3d_status rt3d_reconstruct_batch_host(rt3d_ctx_t* c, int n, const rt3d_frame* 
     const int Kp = p->k_max;
     auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
     // one staging area: every frame's inputs, then every frame's results
-    struct Span { size_t dense, off, ent, gain, t, r, a, b, np; long long npix, nent; };
+    struct Span { size_t dense, off, ent, gain, idx, t, r, a, b, np; long long npix, nent; };
     std::vector<Span> sp(n);
     size_t bytes = 0;
     for (int i = 0; i < n; ++i) {
@@ -1284,6 +1348,8 @@ rt3d_status rt3d_reconstruct_batch_host(rt3d_ctx_t* c, int n, const rt3d_frame* 
         if (f[i].csr_off) bytes += al(sizeof(uint32_t) * (x.nent > 0 ? x.nent : 1));
         x.gain = bytes;
         if (f[i].gain) bytes += al(sizeof(float) * x.npix);
+        x.idx = bytes;
+        if (f[i].irf_index) bytes += al((size_t)x.npix);
         x.t = bytes;
         bytes += al(sizeof(float) * Kp * x.npix);
         x.r = bytes;
@@ -1346,6 +1412,10 @@ rt3d_status rt3d_reconstruct_batch_host(rt3d_ctx_t* c, int n, const rt3d_frame* 
         if (f[i].gain) {
             df[i].gain = reinterpret_cast<const float*>(base + x.gain);
             RT3D_CUDA(cudaMemcpyAsync(base + x.gain, f[i].gain, sizeof(float) * x.npix, cudaMemcpyHostToDevice, cs));
+        }
+        if (f[i].irf_index) {
+            df[i].irf_index = base + x.idx;
+            RT3D_CUDA(cudaMemcpyAsync(base + x.idx, f[i].irf_index, (size_t)x.npix, cudaMemcpyHostToDevice, cs));
         }
         dr[i] = rt3d_result{reinterpret_cast<float*>(base + x.t), reinterpret_cast<float*>(base + x.r),
                             base + x.a, reinterpret_cast<float*>(base + x.b),
@@ -1898,33 +1968,14 @@ rt3d_status static_kparams(const rt3d_irf* irf, const rt3d_params* p, KParams* K
     K->int_den = p->intensity_denoiser;
     K->bkg_mode = p->bkg_mode;
     K->bkg_rad = p->bkg_radius;
-    K->irf_len = irf->len;
-    K->irf_origin = irf->origin;
     K->peak_sep = p->peak_sep;
     K->peak_min_photons = p->peak_min_photons;
     K->net_scale = p->net_scale;
     K->net_fallback = p->net_fallback;
     K->wait_ns = kTcWaitNs;
-    float fsum = 0.0f;
-    double hmax = 0.0;
-    for (int s = 0; s < irf->len; ++s) {
-        K->irf[s] = (float)hn[s];
-        fsum += K->irf[s];
-        if (hn[s] > hmax) hmax = hn[s];
-    }
-    K->irf_sum = fsum;
-    const double delta = (double)p->lmf_delta_rel * hmax;
-    const double scale = std::ldexp(1.0, p->lmf_frac_bits);
-    int kmax = 0;
-    for (int s = 0; s < irf->len; ++s) {
-        const double v = std::nearbyint(scale * std::log1p(hn[s] / delta));
-        if (v > 1e9) return RT3D_E_INVALID;
-        K->lmf[s] = (int)v;
-        if (K->lmf[s] > kmax) kmax = K->lmf[s];
-    }
-    K->lmf_kmax = kmax;
-    if (p->lmf_precision == RT3D_LMF_BF16 && kmax > 256) return RT3D_E_INVALID;
-    if (p->lmf_precision == RT3D_LMF_FP16 && kmax > 2048) return RT3D_E_INVALID;
+    const double* norms[1] = {hn};
+    const rt3d_status st = fill_irf_tables(K, 1, norms, &irf->len, &irf->origin, p);
+    if (st != RT3D_OK) return st;
     if (p->bkg_mode == RT3D_BKG_LOWPASS) {
         const double sg = (double)p->bkg_sigma;
         double ks = 0.0;
@@ -1963,6 +2014,7 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     cfg.max_batch = 1;
     if (!params_ok(&cfg, p)) return RT3D_E_INVALID;
     if (p->depth_denoiser == RT3D_DEPTH_LEARNED) return RT3D_E_UNIMPL;
+    if (f->irf_index) return RT3D_E_UNIMPL;      // one response: `irf`
 
     int device = 0;
     RT3D_CUDA(cudaGetDevice(&device));

@@ -18,6 +18,7 @@ namespace rt3d {
 
 constexpr int kMaxK = RT3D_MAX_K;
 constexpr int kMaxIrf = RT3D_MAX_IRF;
+constexpr int kMaxIrfs = RT3D_MAX_IRFS;
 constexpr int kMaxBatch = RT3D_MAX_BATCH;
 constexpr int kMaxWinR = RT3D_MAX_WIN_R;
 constexpr int kMaxBkgR = RT3D_MAX_BKG_R;
@@ -39,8 +40,13 @@ struct KParams {
     int win_r, apss_min_nb;
     int depth_den, int_den, bkg_mode, bkg_rad;
     int apss_fp64;                  // APSS solve (and the learned form's fallback) in FP64
-    int irf_len, irf_origin;
+    int irf_len, irf_origin;        // response 0 (the tensor-core init's)
     float irf_sum;                  // sum of the float IRF samples (H in the interior)
+    // instrument responses a pixel picks from (FrameDesc::irf_index): samples
+    // of response i at irf[irf_offs[i]], lmf taps at lmf[irf_offs[i]]
+    int n_irf;
+    int irf_lens[kMaxIrfs], irf_origins[kMaxIrfs], irf_offs[kMaxIrfs];
+    float irf_sums[kMaxIrfs];
     int peak_sep, peak_min_photons;
     int lmf_kmax;                   // largest quantised log-IRF value
     // tensor-core matched filter (dense frames, lmf_precision BF16 / FP16)
@@ -53,8 +59,8 @@ struct KParams {
     float tc_unit_inv;              // accumulator value * tc_unit_inv = exact integer
     float net_scale, net_fallback;  // learned depth denoiser: feature/output scale, APSS fallback threshold
     unsigned long long wait_ns;     // bound of every device-side wait of the tensor-core kernels
-    float irf[kMaxIrf];             // normalised IRF samples
-    int lmf[kMaxIrf];               // quantised log-IRF K_s
+    float irf[kMaxIrf];             // normalised IRF samples (all responses, concatenated)
+    int lmf[kMaxIrf];               // quantised log-IRF K_s (same offsets)
     float bkg_ker[2 * kMaxBkgR + 1];
 };
 
@@ -67,6 +73,7 @@ struct FrameDesc {
     const uint32_t* csr_off;
     const uint32_t* ent;            // entries the loop reads (caller's or workspace)
     const float* gain;
+    const uint8_t* irf_index;       // [h][w] response of each pixel, or null (response 0)
     int tc;                         // cold start of this frame runs in the tensor-core init
     int tc_tile_base;               // its first 128-pixel tile there
     int net_strip_base;             // first 128-pixel row strip of the frame (learned denoiser)
@@ -141,6 +148,33 @@ __device__ __forceinline__ int frame_of_pixel(const Batch& B, int pix)
     return lo;
 }
 
+// A pixel's instrument response h_{i,j} (the likelihood's response is per
+// pixel): its length, origin and sample sum, and where its padded samples and
+// its interval coefficients start in the kernels' shared tables (each
+// response padded by kIrfPad zeros on both sides; L + 5 coefficient entries).
+struct IrfRef {
+    int pad_off, coef_off, len, origin;
+    float sum;
+};
+
+__device__ __forceinline__ IrfRef irf_ref(const KParams& P, int which)
+{
+    IrfRef r;
+    r.len = P.irf_lens[which];
+    r.origin = P.irf_origins[which];
+    r.sum = P.irf_sums[which];
+    r.pad_off = P.irf_offs[which] + 2 * kIrfPad * which;
+    r.coef_off = P.irf_offs[which] + 5 * which;
+    return r;
+}
+
+// Response index of local pixel lp (an index past the last response reads as
+// the last).
+__device__ __forceinline__ int pixel_irf(const KParams& P, const FrameDesc& F, int lp)
+{
+    return F.irf_index ? min((int)F.irf_index[lp], P.n_irf - 1) : 0;
+}
+
 // Catmull-Rom (Keys a = -1/2) interpolation of the IRF samples and its
 // derivative at offset x from a point's depth.  `pad` holds the samples with
 // kIrfPad zeros on each side, so pad[k + kIrfPad] = h_k for k in [-3, L+2].
@@ -164,16 +198,17 @@ __device__ __forceinline__ void irf_eval(const float* pad, int L, int origin, fl
     dh = 0.5f * (c1 + u * (2.0f * c2 + 3.0f * c3 * u));
 }
 
-// H = sum_{t in [0,T)} h(t - tn) and H' = sum h'(t - tn).  In the interior the
-// Catmull-Rom interpolant reproduces constants: H = sum of samples, H' = 0;
-// near the histogram ends the sums are taken explicitly.
-__device__ __forceinline__ void support_sums(const float* pad, const KParams& P, int T,
-                                             float tn, float& H, float& dH)
+// H = sum_{t in [0,T)} h(t - tn) and H' = sum h'(t - tn) for the response R
+// (its padded samples at pad + R.pad_off).  In the interior the Catmull-Rom
+// interpolant reproduces constants: H = sum of samples, H' = 0; near the
+// histogram ends the sums are taken explicitly.
+__device__ __forceinline__ void support_sums(const float* pad, const IrfRef& R, int T, float tn, float& H,
+                                             float& dH)
 {
-    const int base = (int)floorf(tn) - P.irf_origin;
-    int lo = base - 3, hi = base + P.irf_len + 2;
+    const int base = (int)floorf(tn) - R.origin;
+    int lo = base - 3, hi = base + R.len + 2;
     if (lo >= 0 && hi <= T - 1) {
-        H = P.irf_sum;
+        H = R.sum;
         dH = 0.0f;
         return;
     }
@@ -182,7 +217,7 @@ __device__ __forceinline__ void support_sums(const float* pad, const KParams& P,
     float sh = 0.0f, sdh = 0.0f;
     for (int tb = lo; tb <= hi; ++tb) {
         float hv, dv;
-        irf_eval(pad, P.irf_len, P.irf_origin, (float)tb - tn, hv, dv);
+        irf_eval(pad + R.pad_off, R.len, R.origin, (float)tb - tn, hv, dv);
         sh += hv;
         sdh += dv;
     }

@@ -49,7 +49,7 @@ class Irf(C.Structure):
 class Frame(C.Structure):
     _fields_ = [("h", C.c_int32), ("w", C.c_int32), ("t", C.c_int32),
                 ("dense", C.c_void_p), ("csr_off", C.c_void_p), ("csr_ent", C.c_void_p),
-                ("gain", C.c_void_p)]
+                ("gain", C.c_void_p), ("irf_index", C.c_void_p)]
 
 
 class Params(C.Structure):
@@ -135,6 +135,7 @@ def lib():
         "rt3d_device_status": (C.c_int, [_P, _P]),
         "rt3d_launch_count": (C.c_int64, [_P]),
         "rt3d_set_wait_limit": (C.c_int, [_P, C.c_int64]),
+        "rt3d_set_irfs": (C.c_int, [_P, C.c_int, C.POINTER(Irf)]),
         "rt3d_set_profiling": (C.c_int, [_P, C.c_int]),
         "rt3d_kernel_times": (C.c_int, [_P, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                         C.c_int, C.c_int]),
@@ -237,13 +238,24 @@ class Context:
             pass
 
     # -- frames / results -------------------------------------------------------
-    def frame(self, dense=None, csr=None, gain=None, shape=None) -> Frame:
+    def frame(self, dense=None, csr=None, gain=None, shape=None, irf_index=None) -> Frame:
         if dense is not None:
             h, w, t = dense.shape
         else:
             h, w, t = shape
         off, ent = (csr if csr is not None else (None, None))
-        return Frame(h, w, t, _ptr(dense), _ptr(off), _ptr(ent), _ptr(gain))
+        return Frame(h, w, t, _ptr(dense), _ptr(off), _ptr(ent), _ptr(gain), _ptr(irf_index))
+
+    def set_irfs(self, irfs):
+        """rt3d_set_irfs: irfs = [(samples, origin), ...], response i for
+        pixels whose irf_index is i."""
+        arr = (Irf * len(irfs))()
+        keep = []
+        for i, (samples, origin) in enumerate(irfs):
+            a = np.ascontiguousarray(samples, np.float64)
+            keep.append(a)
+            arr[i] = Irf(a.ctypes.data_as(C.POINTER(C.c_double)), len(a), int(origin))
+        check(lib().rt3d_set_irfs(self.handle, len(irfs), arr), "rt3d_set_irfs")
 
     def new_result(self, h, w, k=None):
         torch = self.torch
@@ -306,8 +318,9 @@ class Context:
         check(lib().rt3d_lmf(self.handle, C.byref(fr), C.byref(p), _ptr(y), _stream(stream)), "rt3d_lmf")
         return y
 
-    def init(self, params, dense=None, csr=None, gain=None, shape=None, out=None, stream=None):
-        fr = self.frame(dense, csr, gain, shape)
+    def init(self, params, dense=None, csr=None, gain=None, shape=None, out=None, stream=None,
+             irf_index=None):
+        fr = self.frame(dense, csr, gain, shape, irf_index)
         p = params_from(params)
         out = out or self.new_result(fr.h, fr.w, p.k_max)
         rs = self.result_struct(out)
@@ -315,8 +328,9 @@ class Context:
               "rt3d_init")
         return out
 
-    def reconstruct(self, params, dense=None, csr=None, gain=None, shape=None, out=None, stream=None):
-        fr = self.frame(dense, csr, gain, shape)
+    def reconstruct(self, params, dense=None, csr=None, gain=None, shape=None, out=None, stream=None,
+             irf_index=None):
+        fr = self.frame(dense, csr, gain, shape, irf_index)
         p = params_from(params)
         out = out or self.new_result(fr.h, fr.w, p.k_max)
         rs = self.result_struct(out)
@@ -329,7 +343,7 @@ class Context:
         n = len(frames)
         fa = (Frame * n)()
         for i, f in enumerate(frames):
-            fa[i] = self.frame(f.get("dense"), f.get("csr"), f.get("gain"), f.get("shape"))
+            fa[i] = self.frame(f.get("dense"), f.get("csr"), f.get("gain"), f.get("shape"), f.get("irf_index"))
         if outs is None:
             outs = [self.new_result(fa[i].h, fa[i].w, p.k_max) for i in range(n)]
         ra = (Result * n)(*[self.result_struct(o) for o in outs])
@@ -337,8 +351,9 @@ class Context:
               "rt3d_reconstruct_batch")
         return outs
 
-    def phase(self, phase: int, first: int, params, csr, state: dict, gain=None, shape=None, stream=None):
-        fr = self.frame(None, csr, gain, shape)
+    def phase(self, phase: int, first: int, params, csr, state: dict, gain=None, shape=None, stream=None,
+              irf_index=None):
+        fr = self.frame(None, csr, gain, shape, irf_index)
         p = params_from(params)
         rs = self.result_struct(state)
         check(lib().rt3d_phase(self.handle, int(phase), int(first), C.byref(fr), C.byref(p),
@@ -386,17 +401,19 @@ def _host_ptr(a):
 
 
 def reconstruct_host(ctx: Context, params, dense: np.ndarray, gain: Optional[np.ndarray] = None,
-                     csr: Optional[tuple] = None, out: Optional[dict] = None, stream=None) -> dict:
+                     csr: Optional[tuple] = None, out: Optional[dict] = None, stream=None,
+                     irf_index: Optional[np.ndarray] = None) -> dict:
     """rt3d_reconstruct_host: HOST numpy buffers in and out (copies inside the call)."""
     p = params_from(params)
     h, w, t = dense.shape if dense is not None else csr[2]
     dense = None if dense is None else np.ascontiguousarray(dense, np.uint16)
     gain = None if gain is None else np.ascontiguousarray(gain, np.float32)
+    irf_index = None if irf_index is None else np.ascontiguousarray(irf_index, np.uint8)
     off = ent = None
     if csr is not None:
         off = np.ascontiguousarray(csr[0], np.uint32)
         ent = np.ascontiguousarray(csr[1], np.uint32)
-    fr = Frame(h, w, t, _host_ptr(dense), _host_ptr(off), _host_ptr(ent), _host_ptr(gain))
+    fr = Frame(h, w, t, _host_ptr(dense), _host_ptr(off), _host_ptr(ent), _host_ptr(gain), _host_ptr(irf_index))
     k = p.k_max
     if out is None:
         out = dict(t=np.zeros((k, h, w), np.float32), r=np.zeros((k, h, w), np.float32),
@@ -414,7 +431,8 @@ def reconstruct_batch_host(ctx: Context, params, frames: Sequence[dict], outs: O
     """rt3d_reconstruct_batch_host: n frames of HOST numpy buffers in, HOST
     results out, one batched reconstruction.  Each frame dict holds `dense`
     ([h][w][t] uint16) and/or `csr` ((offsets, entries, (h, w, t))), and
-    optionally `gain`; page-locked arrays give full link bandwidth."""
+    optionally `gain` and `irf_index`; page-locked arrays give full link
+    bandwidth."""
     p = params_from(params)
     k = p.k_max
     keep, frs, rss = [], [], []
@@ -425,12 +443,14 @@ def reconstruct_batch_host(ctx: Context, params, frames: Sequence[dict], outs: O
         h, w, t = dense.shape if dense is not None else csr[2]
         dense = None if dense is None else np.ascontiguousarray(dense, np.uint16)
         gain = None if f.get("gain") is None else np.ascontiguousarray(f["gain"], np.float32)
+        idx = None if f.get("irf_index") is None else np.ascontiguousarray(f["irf_index"], np.uint8)
         off = ent = None
         if csr is not None:
             off = np.ascontiguousarray(csr[0], np.uint32)
             ent = np.ascontiguousarray(csr[1], np.uint32)
-        keep += [dense, gain, off, ent]
-        frs.append(Frame(h, w, t, _host_ptr(dense), _host_ptr(off), _host_ptr(ent), _host_ptr(gain)))
+        keep += [dense, gain, off, ent, idx]
+        frs.append(Frame(h, w, t, _host_ptr(dense), _host_ptr(off), _host_ptr(ent), _host_ptr(gain),
+                         _host_ptr(idx)))
         if outs[i] is None:
             outs[i] = dict(t=np.zeros((k, h, w), np.float32), r=np.zeros((k, h, w), np.float32),
                            alive=np.zeros((k, h, w), np.uint8), b=np.zeros((h, w), np.float32),

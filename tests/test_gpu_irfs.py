@@ -1,0 +1,112 @@
+"""Per-pixel instrument responses h_{i,j} (Results, "Observation model") on the
+GPU against the FP64 oracle, through the C ABI: a context holds several
+responses (rt3d_set_irfs) and a frame names each pixel's (irf_index)."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import scenes
+from gpu_util import compare_clouds, make_ctx, np_of, torch_mod, upload_u16, workload_params
+
+pytestmark = pytest.mark.gpu
+
+TOL_T = 1e-3
+TOL_R = 1e-4
+
+
+def _two_response_frame(orc, seed, h=19, w=23, t=300):
+    """A scene observed through two responses: each pixel's histogram drawn
+    with its own response (two syntheses of the same scene, picked per pixel
+    in 4 x 4-pixel blocks, so the denoisers' windows see both)."""
+    base = scenes.small_random(h, w, t, n_comp=2, seed=seed)
+    ia, ib = scenes.gaussian_irf(3.0, 12), scenes.gamma_irf(3.0, 2.0, 30)
+    za = orc.synthesize(scenes.sampling_tables(dataclasses.replace(base, irf=ia)))
+    zb = orc.synthesize(scenes.sampling_tables(dataclasses.replace(base, irf=ib)))
+    rng = np.random.default_rng(seed)
+    blocks = rng.integers(0, 2, size=((h + 3) // 4, (w + 3) // 4))
+    idx = np.kron(blocks, np.ones((4, 4), np.int64))[:h, :w].astype(np.uint8)
+    z = np.where(idx[..., None] == 1, zb, za)
+    base = dataclasses.replace(base, irf=ia)
+    return base, (ia, ib), idx, z
+
+
+def _ctx(base, irfs, prm, **kw):
+    ctx = make_ctx(base, k=prm["k_max"], **kw)
+    ctx.set_irfs([(i.samples, i.origin) for i in irfs])
+    return ctx
+
+
+def _oirfs(orc, irfs):
+    return [orc.OIrf(i.samples, i.origin) for i in irfs]
+
+
+def test_per_pixel_responses_init_bit_exact(orc):
+    torch = torch_mod()
+    base, irfs, idx, z = _two_response_frame(orc, 91)
+    prm = workload_params(base)
+    ctx = _ctx(base, irfs, prm)
+    g = np_of(ctx.init(prm, dense=upload_u16(z), irf_index=torch.from_numpy(idx).cuda()))
+    o = orc.init(z, None, _oirfs(orc, irfs), prm, irf_idx=idx)
+    assert np.array_equal(g["alive"], o.alive)
+    assert np.array_equal(g["t"].astype(np.float64), o.t)       # integer peak bins
+    np.testing.assert_allclose(g["r"], o.r, rtol=1e-5, atol=1e-6)
+    np.testing.assert_allclose(g["b"], o.b, rtol=1e-5, atol=1e-12)
+
+
+@pytest.mark.parametrize("over", [dict(), dict(bkg_mode=1), dict(depth_denoiser=0, intensity_denoiser=0)])
+def test_per_pixel_responses_match_oracle(orc, over):
+    torch = torch_mod()
+    from oracle import compare
+    base, irfs, idx, z = _two_response_frame(orc, 92)
+    prm = workload_params(base, **over)
+    ctx = _ctx(base, irfs, prm)
+    g = np_of(ctx.reconstruct(prm, dense=upload_u16(z), irf_index=torch.from_numpy(idx).cuda()))
+    o, probes = compare.reconstruct_with_probes(z, _oirfs(orc, irfs), prm, irf_idx=idx)
+    st = compare_clouds(g, o, base.t, TOL_T, TOL_R, probes=probes, max_ill_frac=0.05,
+                        label=f"two responses {over}", r_min=prm["r_min"])
+    print("two responses", over, st)
+
+
+def test_per_pixel_responses_in_batches_and_host_entry(orc):
+    """A batch mixing a two-response frame, a frame without an index and a
+    frame whose index names response 1 everywhere gives each frame's single
+    results bit for bit; the host-buffer entry point gives the device
+    path's; a frame with an index in a tensor-core precision mode (which
+    takes the CUDA-core filter) gives the integer path's."""
+    torch = torch_mod()
+    from paper_1905_06700_b300 import rt3d as R
+    base, irfs, idx, z = _two_response_frame(orc, 93)
+    prm = workload_params(base)
+    ctx = _ctx(base, irfs, prm, max_batch=3)
+    other = orc.synthesize(scenes.sampling_tables(scenes.small_random(11, 17, 300, n_comp=2, seed=94,
+                                                                      irf=irfs[0])))
+    ones = np.ones((11, 17), np.uint8)
+    frames = [dict(dense=upload_u16(z), irf_index=torch.from_numpy(idx).cuda()),
+              dict(dense=upload_u16(other)),
+              dict(dense=upload_u16(other), irf_index=torch.from_numpy(ones).cuda())]
+    batch = [np_of(o) for o in ctx.reconstruct_batch(prm, frames)]
+    singles = [np_of(ctx.reconstruct(prm, **f)) for f in frames]
+    for a, b in zip(batch, singles):
+        for k in ("t", "r", "alive", "b", "n_points"):
+            assert np.array_equal(np.asarray(a[k]), np.asarray(b[k])), k
+    assert not np.array_equal(singles[1]["t"], singles[2]["t"])      # response 1 differs
+    host = R.reconstruct_host(ctx, prm, z, irf_index=idx)
+    for k in ("t", "r", "alive", "b"):
+        assert np.array_equal(singles[0][k], host[k]), k
+    tc = np_of(ctx.reconstruct(dict(prm, lmf_precision=2), **frames[0]))
+    for k in ("t", "r", "alive", "b"):
+        assert np.array_equal(singles[0][k], tc[k]), k
+    assert ctx.device_status() == R.RT3D_OK
+
+
+def test_set_irfs_validates():
+    from paper_1905_06700_b300 import rt3d as R
+    base = scenes.small_random(4, 4, 64, n_comp=1, seed=1)
+    ctx = make_ctx(base)
+    g = scenes.gaussian_irf(3.0, 12)
+    for bad in ([], [(g.samples, g.origin)] * 5, [(np.zeros(5), 2)], [(g.samples, 99)],
+                [(np.ones(200), 0), (np.ones(60), 0)]):
+        with pytest.raises(R.Rt3dError):
+            ctx.set_irfs(bad)
+    ctx.set_irfs([(np.ones(59), 0)] * 4)          # 4 x (59 + 6) = 260 <= 262
