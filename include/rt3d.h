@@ -50,7 +50,7 @@ extern "C" {
 #define RT3D_MAX_T 16384      /* histogram bins */
 #define RT3D_MAX_WIN_R 4      /* neighbourhood half-width of the denoisers, pixels */
 #define RT3D_MAX_BKG_R 15     /* background filter half-width, pixels */
-#define RT3D_MAX_SYNTH_COMP 8 /* surfaces per pixel in rt3d_synthesize */
+#define RT3D_MAX_SYNTH_COMP 64 /* surfaces per pixel in rt3d_synthesize */
 
 /* Opaque context: owns the device workspace of one CUDA device. */
 typedef struct rt3d_ctx rt3d_ctx_t;

@@ -45,12 +45,13 @@ def probe_palm(fr, irf, prm, start, n_iter, bits):
     (bits = (depth bits, intensity/background bits))."""
     st = start.copy()
     _rnd(st, bits)
+    up = int(prm.get("upsample", 1))
     h, w, t = fr.hh, fr.ww, fr.tt
     for _ in range(n_iter):
         O.t_step(fr, irf, prm, st); _rnd(st, bits)
-        O.depth_denoise(h, w, t, prm, st); _rnd(st, bits)
+        O.depth_denoise(h * up, w * up, t, prm, st); _rnd(st, bits)
         O.r_step(fr, irf, prm, st); _rnd(st, bits)
-        O.int_lowpass(h, w, prm, st); _rnd(st, bits)
+        O.int_lowpass(h * up, w * up, prm, st); _rnd(st, bits)
         O.b_step(fr, irf, prm, st); _rnd(st, bits)
         O.bkg_lowpass(h, w, prm, st.b); _rnd(st, bits)
     return st
@@ -114,8 +115,13 @@ def cloud_stats(gpu, o, probes, T, tol_t, tol_r, r_min=None, ratio=3.0):
     rfl = np.maximum(np.abs(o.r), 0.1)
     dr_all = np.abs(gpu["r"].astype(np.float64) - o.r) / rfl
     well = both & ok
-    ill_px = ill.any(0)
-    rate = o.b + (o.r * oa).sum(0) / T
+    # background: per pixel (with super-resolution the points sit on a finer
+    # grid; a pixel's rate sums its block's points)
+    up = o.t.shape[1] // o.b.shape[0]
+    kk, hh, ww = o.t.shape
+    blk = lambda a: a.reshape(kk, hh // up, up, ww // up, up).sum(axis=(0, 2, 4))
+    ill_px = blk(ill.astype(np.int64)) > 0
+    rate = o.b + blk(o.r * oa) / T
     db = (np.abs(gpu["b"].astype(np.float64) - o.b) / np.maximum(rate, 1e-12))[~ill_px]
 
     # envelope of the probes' own deviations

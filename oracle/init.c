@@ -98,6 +98,8 @@ void or_init_idx(const uint16_t* dense, const double* gain, const uint8_t* irf_i
                  const or_irf* irf_set, const or_params* prm, or_state* s)
 {
     const int64_t npix = (int64_t)h * w;
+    const int up = prm->upsample > 1 ? prm->upsample : 1;
+    const int64_t wnpix = npix * up * up;
     int n_irf = 1;
     if (irf_idx)
         for (int64_t p = 0; p < npix; ++p)
@@ -144,22 +146,30 @@ void or_init_idx(const uint16_t* dense, const double* gain, const uint8_t* irf_i
                 b0 = v > prm->b_floor ? v : prm->b_floor;
             }
             s->b[p] = b0;
-            for (int k = 0; k < s->k; ++k) {
-                const int64_t idx = (int64_t)k * npix + p;
-                if (k < n) {
-                    int win = 0;
-                    for (int sidx = 0; sidx < irf->len; ++sidx) {
-                        const int tb = taus[k] + sidx - irf->origin;
-                        if (tb >= 0 && tb < t) ++win;
+            /* with super-resolution (upsample u > 1) every world pixel of the
+             * lidar pixel's u x u block starts from the pixel's peaks, each with
+             * 1/u^2 of the intensity (reading: the block's points then give the
+             * pixel the same lambda as the peaks) */
+            const int64_t pi = p / w, pj = p % w, ww = (int64_t)w * up;
+            for (int a = 0; a < up * up; ++a) {
+                const int64_t q = (pi * up + a / up) * ww + (pj * up + a % up);
+                for (int k = 0; k < s->k; ++k) {
+                    const int64_t idx = (int64_t)k * wnpix + q;
+                    if (k < n) {
+                        int win = 0;
+                        for (int sidx = 0; sidx < irf->len; ++sidx) {
+                            const int tb = taus[k] + sidx - irf->origin;
+                            if (tb >= 0 && tb < t) ++win;
+                        }
+                        const double r0 = (double)wc[taus[k]] / g - b0 * win;
+                        s->t[idx] = (double)taus[k];
+                        s->r[idx] = (r0 > prm->r_min ? r0 : prm->r_min) / (up * up);
+                        s->alive[idx] = 1;
+                    } else {
+                        s->t[idx] = 0.0;
+                        s->r[idx] = 0.0;
+                        s->alive[idx] = 0;
                     }
-                    const double r0 = (double)wc[taus[k]] / g - b0 * win;
-                    s->t[idx] = (double)taus[k];
-                    s->r[idx] = r0 > prm->r_min ? r0 : prm->r_min;
-                    s->alive[idx] = 1;
-                } else {
-                    s->t[idx] = 0.0;
-                    s->r[idx] = 0.0;
-                    s->alive[idx] = 0;
                 }
             }
         }

@@ -68,7 +68,7 @@ class Params(C.Structure):
                 ("lmf_delta_rel", C.c_double), ("lmf_frac_bits", C.c_int),
                 ("peak_min_photons", C.c_int), ("peak_sep", C.c_int),
                 ("net_theta", C.POINTER(C.c_double)), ("net_scale", C.c_double),
-                ("net_fallback", C.c_double)]
+                ("net_fallback", C.c_double), ("upsample", C.c_int)]
 
 
 def lib():
@@ -115,6 +115,8 @@ def make_params(d: dict) -> Params:
             continue
         if name in ("net_scale", "net_fallback") and name not in d:
             v = 1.0
+        elif name == "upsample" and name not in d:
+            v = 1
         else:
             v = d[name]
         setattr(p, name, int(v) if ctype is C.c_int else _f32(v))
@@ -136,8 +138,11 @@ class OState:
                      _ptr(self.alive, C.c_uint8), _ptr(self.b, C.c_double))
 
 
-def new_state(k, h, w) -> OState:
-    return OState(np.zeros((k, h, w)), np.zeros((k, h, w)), np.zeros((k, h, w), np.uint8),
+def new_state(k, h, w, up=1) -> OState:
+    """A state for an h x w frame: points on the world grid (up times finer
+    with super-resolution), the background per pixel."""
+    hh, ww = h * up, w * up
+    return OState(np.zeros((k, hh, ww)), np.zeros((k, hh, ww)), np.zeros((k, hh, ww), np.uint8),
                   np.zeros((h, w)))
 
 
@@ -227,21 +232,20 @@ def irf_eval(irf: OIrf, x):
     return h.value, dh.value
 
 
-def nll_dense(z, gain, st: OState, irf, lam_floor, irf_idx=None):
+def nll_dense(z, gain, st: OState, irf, lam_floor, irf_idx=None, up=1):
     z = np.ascontiguousarray(z, np.float64)
     h, w, t = z.shape
     g = np.ascontiguousarray(np.ones((h, w)) if gain is None else gain, np.float64)
     idx = None if irf_idx is None else np.ascontiguousarray(np.asarray(irf_idx, np.uint8).reshape(h, w))
     return lib().or_nll_dense_idx(h, w, t, _ptr(z, C.c_double), _ptr(g, C.c_double),
-                                  None if idx is None else _ptr(idx, C.c_uint8),
+                                  None if idx is None else _ptr(idx, C.c_uint8), int(up),
                                   C.byref(st.c()), _irfs(irf), C.c_double(lam_floor))
 
 
-def gradients(fr: OFrame, st: OState, irf: OIrf, prm: dict):
-    k, h, w = st.t.shape
-    gt = np.zeros((k, h, w))
-    gr = np.zeros((k, h, w))
-    gb = np.zeros((h, w))
+def gradients(fr: OFrame, st: OState, irf, prm: dict):
+    gt = np.zeros(st.t.shape)
+    gr = np.zeros(st.t.shape)
+    gb = np.zeros((fr.hh, fr.ww))
     p = make_params(prm)
     lib().or_gradients(C.byref(fr.c()), C.byref(st.c()), _irfs(irf), C.byref(p),
                        _ptr(gt, C.c_double), _ptr(gr, C.c_double), _ptr(gb, C.c_double))
@@ -282,7 +286,7 @@ def init(dense, gain, irf, prm: dict, irf_idx=None) -> OState:
     h, w, t = dense.shape
     g = np.ascontiguousarray(np.ones((h, w)) if gain is None else gain, np.float64)
     idx = None if irf_idx is None else np.ascontiguousarray(np.asarray(irf_idx, np.uint8).reshape(h, w))
-    st = new_state(prm["k_max"], h, w)
+    st = new_state(prm["k_max"], h, w, int(prm.get("upsample", 1)))
     p = make_params(prm)
     lib().or_init_idx(_ptr(dense, C.c_uint16), _ptr(g, C.c_double),
                       None if idx is None else _ptr(idx, C.c_uint8), h, w, t, _irfs(irf),
@@ -338,7 +342,7 @@ def reconstruct(dense, irf, prm: dict, gain=None, irf_idx=None) -> OState:
     dense = np.ascontiguousarray(dense, np.uint16)
     h, w, t = dense.shape
     fr = OFrame(dense, gain, irf_idx)
-    st = new_state(prm["k_max"], h, w)
+    st = new_state(prm["k_max"], h, w, int(prm.get("upsample", 1)))
     lib().or_reconstruct(_ptr(dense, C.c_uint16), C.byref(fr.c()), _irfs(irf),
                          C.byref(make_params(prm)), C.byref(st.c()))
     return st

@@ -22,11 +22,15 @@ void or_depth_denoise(int h, int w, int t, const or_params* p, or_state* s)
 
 void or_palm(const or_frame* f, const or_irf* irf, const or_params* p, or_state* s, int n_iter)
 {
+    /* the point cloud's denoisers run on the world grid (u times finer than
+     * the pixels with super-resolution), the background's on the pixels */
+    const int up = p->upsample > 1 ? p->upsample : 1;
+    const int wh = f->h * up, ww = f->w * up;
     for (int it = 0; it < n_iter; ++it) {
         or_t_step(f, irf, p, s);                         /* depth: gradient step */
-        or_depth_denoise(f->h, f->w, f->t, p, s);        /* depth: denoiser */
+        or_depth_denoise(wh, ww, f->t, p, s);            /* depth: denoiser */
         or_r_step(f, irf, p, s);                         /* intensity: gradient step */
-        or_int_lowpass(f->h, f->w, p, s);                /* intensity: low-pass + pruning */
+        or_int_lowpass(wh, ww, p, s);                    /* intensity: low-pass + pruning */
         or_b_step(f, irf, p, s);                         /* background: gradient step */
         or_bkg_lowpass(f->h, f->w, p, s->b);             /* background: denoiser */
     }

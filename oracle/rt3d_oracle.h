@@ -81,6 +81,10 @@ typedef struct {
      * and output depth scale (bins), per-point APSS fallback threshold (bins) */
     const double* net_theta;
     double net_scale, net_fallback;
+    /* point-to-cube mapping f: super-resolution factor u (1 = off).  The
+     * state's t, r, alive are then [K][u h][u w] on the world grid, whose
+     * u x u blocks map to the h x w lidar pixels; b stays [h][w]. */
+    int upsample;
 } or_params;
 
 /* ---- synthetic photons (input generation, not the method) ---- */
@@ -97,7 +101,7 @@ void or_irf_eval(const or_irf* irf, double x, double* h, double* dh);
 double or_nll_dense(int h, int w, int t, const double* z, const double* gain,
                     const or_state* s, const or_irf* irf, double lam_floor);
 double or_nll_dense_idx(int h, int w, int t, const double* z, const double* gain, const uint8_t* irf_idx,
-                        const or_state* s, const or_irf* irf, double lam_floor);
+                        int up, const or_state* s, const or_irf* irf, double lam_floor);
 void or_gradients(const or_frame* f, const or_state* s, const or_irf* irf,
                   const or_params* p, double* gt, double* gr, double* gb);
 

@@ -278,6 +278,69 @@ def head_like(h=141, w=141, t=4096, seed=1, mean_signal=3.0, bkg_photons=1.0) ->
     return Scene(h, w, t, depth, sig, bkg, irf, seed, "head_like")
 
 
+def super_resolved(world_depth: np.ndarray, world_signal: np.ndarray, bkg: np.ndarray, t: int, irf: Irf,
+                   up: int, seed: int, name: str = "super_resolved") -> Scene:
+    """A lidar frame observing a world-resolution scene through the point-to-
+    cube mapping f of Results, "Observation model", with super-resolution:
+    each lidar pixel (i, j) sees the u x u world pixels (u i + a, u j + c).
+    world_depth / world_signal are [S][u h][u w] (NaN / 0 where a surface is
+    absent); sub-pixel a u + c and surface s become component (a u + c) S + s
+    of the lidar pixel, so the sampler draws each world point's photons."""
+    S, hu, wu = world_depth.shape
+    h, w = hu // up, wu // up
+    depth = np.full((up * up * S, h, w), np.nan)
+    sig = np.zeros((up * up * S, h, w))
+    for a in range(up * up):
+        ai, aj = divmod(a, up)
+        for s in range(S):
+            depth[a * S + s] = world_depth[s, ai::up, aj::up]
+            sig[a * S + s] = world_signal[s, ai::up, aj::up]
+    return Scene(h, w, t, depth, sig, np.asarray(bkg, np.float64), irf, seed, name)
+
+
+def camouflage_people(h=32, w=32, t=153, up=3, seed=1, signal=450.0, bkg_photons=450.0, frame=0):
+    """The paper's dynamic-scene shape (Results, "3D Dynamic scenes"): a
+    32 x 32-pixel array with T = 153 bins observing, on a 3x finer world grid,
+    a camouflage net in front, two people walking behind it and a backplane;
+    about 450 signal and 450 background photons per pixel.  Most world pixels
+    see two surfaces (the net's holes show one), and a lidar pixel on a
+    person's contour mixes up to three depths.  Returns (scene, world_depth
+    [2][u h][u w]).  `frame` moves the people 1 world pixel sideways per frame."""
+    rng = np.random.default_rng(seed)
+    hu, wu = h * up, w * up
+    i, j = np.meshgrid(np.arange(hu, dtype=np.float64), np.arange(wu, dtype=np.float64), indexing="ij")
+    # the net: a smooth random field thresholded to ~55 % cover
+    field = np.zeros((hu, wu))
+    for _ in range(6):
+        fi, fj, ph = rng.uniform(0.15, 0.5), rng.uniform(0.15, 0.5), rng.uniform(0, 2 * np.pi)
+        field += np.sin(fi * i + ph) * np.cos(fj * j + 0.7 * ph)
+    net = field > np.quantile(field, 0.45)
+    net_depth = 0.30 * t + 0.02 * t * (j / wu)
+    # two people: upright ellipses with a head, at different depths
+    person = np.zeros((hu, wu), bool)
+    p_depth = np.full((hu, wu), np.nan)
+    for cx, d0, ww_ in ((0.33 * wu + frame, 0.55 * t, 0.09 * wu), (0.68 * wu - frame, 0.60 * t, 0.08 * wu)):
+        body = (((j - cx) / ww_) ** 2 + ((i - 0.62 * hu) / (0.30 * hu)) ** 2) < 1.0
+        head = ((j - cx) ** 2 + (i - 0.25 * hu) ** 2) < (0.45 * ww_) ** 2
+        m = (body | head) & ~person
+        p_depth = np.where(m, d0 - 2.0 * np.sqrt(np.maximum(1.0 - ((j - cx) / ww_) ** 2, 0.0)), p_depth)
+        person |= m
+    wall_depth = 0.78 * t + 0.01 * t * (i / hu)
+    depth = np.full((2, hu, wu), np.nan)
+    sig = np.zeros((2, hu, wu))
+    per_world = signal / (up * up)
+    refl = rng.uniform(0.6, 1.0, (hu, wu))
+    refl *= 1.0 / refl.mean()
+    depth[0] = np.where(net, net_depth, np.nan)
+    sig[0] = np.where(net, 0.4 * per_world * refl, 0.0)
+    depth[1] = np.where(person, p_depth, wall_depth)
+    sig[1] = np.where(net, 0.6, 1.0) * per_world * refl
+    irf = gaussian_irf(1.0, 4)
+    sc = super_resolved(depth, sig, np.full((h, w), bkg_photons / t), t, irf, up,
+                        seed * 1_000_003 + frame, "camouflage_people")
+    return sc, depth
+
+
 def random_shapes(h=256, w=256, t=2048, seed=0) -> Scene:
     """Random planes, spheres and boxes (at most two surfaces per pixel), with
     1-20 signal photons per pixel and a signal-to-background ratio in 0.05-2."""
@@ -366,7 +429,7 @@ def make_params(scene: Scene, **over) -> dict:
         lmf_delta_rel=1e-3, lmf_frac_bits=5, peak_min_photons=2,
         peak_sep=max(2, int(math.ceil(2.0 * math.sqrt(var)))),
         lmf_precision=0, warm_start=0,
-        net_scale=math.sqrt(var), net_fallback=math.sqrt(var) / 3.0, apss_fp64=0,
+        net_scale=math.sqrt(var), net_fallback=math.sqrt(var) / 3.0, apss_fp64=0, upsample=1,
     )
     p.update(over)
     return p
