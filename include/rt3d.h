@@ -46,6 +46,7 @@ extern "C" {
 #define RT3D_MAX_K 4          /* point slots per pixel */
 #define RT3D_MAX_IRF 256      /* samples of the instrument response */
 #define RT3D_MAX_IRFS 4       /* instrument responses a context holds (rt3d_set_irfs) */
+#define RT3D_MAX_UPSAMPLE 4   /* super-resolution factor of rt3d_params.upsample */
 #define RT3D_MAX_BATCH 64     /* frames per batched call */
 #define RT3D_MAX_T 16384      /* histogram bins */
 #define RT3D_MAX_WIN_R 4      /* neighbourhood half-width of the denoisers, pixels */
@@ -164,11 +165,26 @@ typedef struct {
     int32_t apss_fp64;             /* 1: the APSS fit's normal equations (centring, Cholesky, projection)
                                       are solved in FP64 from the FP32 neighbourhood moments, for APSS
                                       and the learned form's APSS fallback; 0: in FP32 */
+    int32_t upsample;              /* super-resolution factor u of the point-to-cube mapping f (Results,
+                                      "Observation model"; "3D Dynamic scenes"), 1..RT3D_MAX_UPSAMPLE:
+                                      the point cloud lives on a world grid u times finer than the
+                                      pixels, lidar pixel (i, j) observing the points of world pixels
+                                      (u i + a, u j + c), 0 <= a, c < u.  The result's t, r, alive are
+                                      then [k_max][u h][u w] (b stays [h][w]); pixel_pitch and the
+                                      denoisers' radii are in world pixels; the initialisation gives
+                                      each world pixel its lidar pixel's peaks with 1/u^2 of the
+                                      intensity.  1 = off.  With u > 1: rt3d_reconstruct,
+                                      rt3d_reconstruct_batch and rt3d_init only (the other entry points
+                                      return RT3D_E_UNIMPL), not with the learned denoiser
+                                      (RT3D_E_UNIMPL), the matched filter on CUDA cores whatever
+                                      lmf_precision says, and the frames' world pixels must fit the
+                                      context's max_batch x max_h x max_w (else RT3D_E_INVALID). */
 } rt3d_params;
 
 /* Output (and, with warm_start, input) point cloud: DEVICE buffers owned by
- * the caller.  t, r, alive: [params.k_max][h][w]; b: [h][w]; n_points: one
- * int32 (number of alive points) or NULL. */
+ * the caller.  t, r, alive: [params.k_max][h][w] ([k_max][u h][u w] with
+ * params.upsample = u); b: [h][w]; n_points: one int32 (number of alive
+ * points) or NULL. */
 typedef struct {
     float* t;
     float* r;
@@ -336,21 +352,40 @@ rt3d_status rt3d_kernel_times(rt3d_ctx_t* ctx, double* ms, int64_t* launches, in
  * reserve all memory at start-up for a fixed footprint, plugins whose host
  * framework owns the device memory, processes under a strict memory quota.
  * The kernels' scratch (sparse entries, half-step state, counters) lives in
- * one static device array of about 8.8 MiB that the library reserves on every
- * GPU that loads it, until the process exits.  Limits, checked on the host
+ * one static device array of about 8.8 MiB, held by every GPU on which the
+ * library's module has been loaded, until the process exits.  Under CUDA's
+ * lazy module loading (the default since CUDA 12.2) the module -- and the
+ * array -- is loaded on a device at the first call there, and each kernel's
+ * code at its first launch: a caller that then reserves the rest of the
+ * device's memory should first make one call of every form it will use
+ * (cold and warm start; dense or sparse input) on each device, or load
+ * modules eagerly (CUDA_MODULE_LOADING=EAGER).  Limits, checked on the host
  * before anything is launched (RT3D_E_INVALID otherwise): h*w <= 16384
- * pixels; with a dense histogram also h*w*t <= 2^21 bins; k_max <= RT3D_MAX_K.
- * `irf` is a HOST pointer (normalised per call); frame and result pointers
- * are DEVICE pointers owned by the caller; the work is enqueued on `stream`
- * on the current CUDA device.  The first call on a device looks the array's
- * device address up once (cudaGetSymbolAddress), so make that first call
- * before any stream capture.  Every call shares the one array and reuses it
- * from the previous call (the counters are cleared each call): calls whose
- * work overlaps on the GPU -- on different streams, or from several threads
- * -- race on it and must be ordered by the caller.  No cudaMalloc, cudaFree
- * or other allocating routine is called. */
+ * pixels; with a dense histogram also h*w*t <= 2^21 bins; k_max <=
+ * RT3D_MAX_K.  `irf` is a HOST pointer (normalised per call); frame and
+ * result pointers are DEVICE pointers owned by the caller; the work is
+ * enqueued on `stream` on the current CUDA device.  The matched filter runs
+ * on CUDA cores whatever params.lmf_precision says (its integers are the same).
+ * The learned depth denoiser, a per-pixel irf_index and upsample > 1 return
+ * RT3D_E_UNIMPL.  The first call on a device looks the array's device address
+ * up once (cudaGetSymbolAddress), so make that first call before any stream
+ * capture; no call may be made while `stream` is being captured (the call
+ * record goes up from a pageable host copy; RT3D_E_INVALID then).  Every call
+ * shares the one array and reuses it from the previous call (the counters
+ * and the device status word are cleared each call): calls whose work
+ * overlaps on the GPU -- on different streams, or from several threads --
+ * race on it and must be ordered by the caller.  Errors found on the device
+ * (capacity, exact-arithmetic range) are read with rt3d_noalloc_status.  No
+ * cudaMalloc, cudaFree or other allocating routine is called. */
 rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_frame* f,
                                      const rt3d_params* p, rt3d_result* out, void* stream);
+
+/* The device status word of the last rt3d_reconstruct_noalloc call on the
+ * current device (no counterpart in the paper; allocation-free like that
+ * entry point): synchronises `stream`, returns RT3D_OK, RT3D_E_CAPACITY or
+ * RT3D_E_RANGE (pixels whose counts exceed the exact-arithmetic range keep no
+ * points) and clears the word. */
+rt3d_status rt3d_noalloc_status(void* stream);
 
 /* Copy the sparse representation built by the last initialisation out to
  * HOST buffers, for inspection: seg[p] = (start, count) per pixel of the

@@ -73,10 +73,11 @@ k_init(const CallRecord* __restrict__ rec, const Work W, int pix0, int pix_end)
     // this launch covers the batch's pixels [pix0, pix_end)
     const int pix = pix0 + (int)blockIdx.x * (int)(blockDim.x >> 5) + warp;
     if (pix >= pix_end) return;
-    const FrameDesc& F = B.f[frame_of_pixel(B, pix)];
+    // lidar pixels: the histograms' grid
+    const FrameDesc& F = B.f[frame_of_lpixel(B, pix)];
     // frames whose cold start runs in the tensor-core init
     if (!kCompactOnly && F.tc) return;
-    const int lp = pix - F.pix_base;
+    const int lp = pix - F.lpix_base;
     const int T = F.nt;
     if (lp == 0 && lane == 0 && F.n_points) *F.n_points = 0;   // counted by the finaliser
     const float g = F.gain ? F.gain[lp] : 1.0f;
@@ -396,9 +397,12 @@ k_init(const CallRecord* __restrict__ rec, const Work W, int pix0, int pix_end)
     if (g > 0.0f && t_out > 0) b0 = fmaxf((float)n_out / ((float)t_out * g), P.b_floor);
     if (!active) nsel = 0;
 
-    const int np = F.npix;
-    if (lane < K) {
-        const int k = lane;
+    // the points: with super-resolution (u > 1) every world pixel of the
+    // lidar pixel's u x u block starts from the pixel's peaks, each with
+    // 1/u^2 of the intensity; lanes over (world pixel a, slot k)
+    const int np = F.npix, up = P.up;
+    for (int e = lane; e < K * up * up; e += 32) {
+        const int k = e % K, a = e / K;
         float tt = 0.0f, rr = 0.0f;
         uint8_t al = 0;
 #pragma unroll
@@ -408,9 +412,15 @@ k_init(const CallRecord* __restrict__ rec, const Work W, int pix0, int pix_end)
                 rr = fmaxf((float)wsum[q] / g - b0 * (float)winlen[q], P.r_min);
                 al = 1;
             }
-        F.t[(long long)k * np + lp] = tt;
-        F.r[(long long)k * np + lp] = rr;
-        F.alive[(long long)k * np + lp] = al;
+        long long wq = lp;
+        if (up > 1) {
+            const int i = lp / F.lw, j = lp - (lp / F.lw) * F.lw;
+            wq = (long long)(i * up + a / up) * F.w + (j * up + a % up);
+            rr /= (float)(up * up);
+        }
+        F.t[(long long)k * np + wq] = tt;
+        F.r[(long long)k * np + wq] = rr;
+        F.alive[(long long)k * np + wq] = al;
     }
     if (lane == 0) F.b[lp] = b0;
 }

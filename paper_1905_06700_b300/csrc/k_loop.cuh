@@ -764,8 +764,11 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, in
     const FrameDesc& F = B.f[c.fi];
     const int np = F.npix, S = W.stride, R = P.win_r;
     const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
-    const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
-    const IrfRef ir = irf_ref(P, c.inb ? pixel_irf(P, F, lp) : 0);
+    // with super-resolution this kernel runs the depth denoiser on the world
+    // grid only (the intensity step is per lidar pixel: k_sr_step)
+    const bool sres = P.up > 1;
+    const uint2 sg = c.inb && !sres ? W.seg[wp] : make_uint2(0u, 0u);
+    const IrfRef ir = irf_ref(P, c.inb && !sres ? pixel_irf(P, F, lp) : 0);
     const bool apss = P.depth_den != RT3D_DEPTH_NONE;
     const float apss_px = P.pitch * (1.0f / P.apss_h);
     if (apss) win_vote(s_vote, R, apss_px);
@@ -824,11 +827,12 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, in
         if (c.inb && !ak[k]) tn[k] = W.t_half[(long long)k * S + wp];
     }
     if (c.inb) {
-        g = F.gain ? F.gain[lp] : 1.0f;
-        b = F.b[lp];
+        g = F.gain && !sres ? F.gain[lp] : 1.0f;
+        b = sres ? 0.0f : F.b[lp];
 #pragma unroll
         for (int k = 0; k < K; ++k) F.t[(long long)k * np + lp] = tn[k];
     }
+    if (sres) return;
     float sh[K];
     warp_pixel_sums<K, 1>(F.ent, sg, c.inb, coef, P, ir, tk, rr, b, g, ws[threadIdx.x >> 5], sh);
     if (!c.inb) return;
@@ -872,16 +876,19 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next, int t
     const FrameDesc& F = B.f[c.fi];
     const int np = F.npix, S = W.stride, R = P.win_r;
     const int lp = c.inb ? c.gi * F.w + c.gj : 0, wp = F.pix_base + lp;
-    const uint2 sg = c.inb ? W.seg[wp] : make_uint2(0u, 0u);
-    const IrfRef ir = irf_ref(P, c.inb ? pixel_irf(P, F, lp) : 0);
+    // with super-resolution this kernel runs the intensity denoiser on the
+    // world grid only (the background step is per lidar pixel: k_sr_step)
+    const bool sres = P.up > 1;
+    const uint2 sg = c.inb && !sres ? W.seg[wp] : make_uint2(0u, 0u);
+    const IrfRef ir = irf_ref(P, c.inb && !sres ? pixel_irf(P, F, lp) : 0);
     const float int_px = P.pitch * (1.0f / P.int_h);
     if (P.int_den) win_vote(s_vote, R, int_px);
     // own pixel state read with the halo (one memory round trip)
     float r_own[K];
 #pragma unroll
     for (int k = 0; k < K; ++k) r_own[k] = c.inb ? F.r[(long long)k * np + lp] : 0.0f;
-    const float g_own = c.inb ? (F.gain ? F.gain[lp] : 1.0f) : 0.0f;
-    const float b_own = c.inb ? F.b[lp] : 0.0f;
+    const float g_own = c.inb && !sres ? (F.gain ? F.gain[lp] : 1.0f) : 0.0f;
+    const float b_own = c.inb && !sres ? F.b[lp] : 0.0f;
     load_halo<K, true>(c, F, R, F.t, np, 0, F.alive, np, st, W.r_half, S, F.pix_base, sr);
     __syncthreads();
     const int hstride = kTileW + 2 * R;
@@ -945,6 +952,7 @@ k_phase_c(const CallRecord* __restrict__ rec, const Work W, int fuse_next, int t
             W.alive_b[(long long)k * S + wp] = s_an[k][threadIdx.x];
         }
     }
+    if (sres) return;
     __syncthreads();
 
     float tk[K], rr[K];
@@ -1008,7 +1016,15 @@ k_final(const CallRecord* __restrict__ rec, const Work W, int ran, int tile0)
             }
             mine += a;
         }
-        if (ran) F.b[lp] = bkg_filter(P, W.b_half + F.pix_base, F.h, F.w, c.gi, c.gj);
+        if (ran) {
+            if (P.up == 1) {
+                F.b[lp] = bkg_filter(P, W.b_half + F.pix_base, F.h, F.w, c.gi, c.gj);
+            } else if (c.gi % P.up == 0 && c.gj % P.up == 0) {
+                // one world pixel per lidar pixel writes that pixel's background
+                const int i = c.gi / P.up, j = c.gj / P.up;
+                F.b[i * F.lw + j] = bkg_filter(P, W.b_half + F.lpix_base, F.lh, F.lw, i, j);
+            }
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);

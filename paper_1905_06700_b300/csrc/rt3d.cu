@@ -24,6 +24,7 @@
 #include "k_init_tc.cuh"
 #include "k_net.cuh"
 #include "k_loop.cuh"
+#include "k_sr.cuh"
 #include "k_compact.cuh"
 
 using namespace rt3d;
@@ -47,14 +48,14 @@ struct PendingTiming {
 struct GraphKey {
     int total_pix, total_tiles, n_iter, warm, init_warps, profiled;
     size_t init_smem;
-    int tc_tiles, tc_stages, tc_nd, any_int, learned, fused, split_tiles, den_variant;
+    int tc_tiles, tc_stages, tc_nd, any_int, learned, fused, split_tiles, den_variant, up;
     bool operator<(const GraphKey& o) const
     {
         return std::tie(total_pix, total_tiles, n_iter, warm, init_warps, profiled, init_smem, tc_tiles,
-                        tc_stages, tc_nd, any_int, learned, fused, split_tiles, den_variant) <
+                        tc_stages, tc_nd, any_int, learned, fused, split_tiles, den_variant, up) <
                std::tie(o.total_pix, o.total_tiles, o.n_iter, o.warm, o.init_warps, o.profiled,
                         o.init_smem, o.tc_tiles, o.tc_stages, o.tc_nd, o.any_int, o.learned, o.fused,
-                        o.split_tiles, o.den_variant);
+                        o.split_tiles, o.den_variant, o.up);
     }
 };
 
@@ -236,6 +237,7 @@ bool params_ok(const rt3d_config* cfg, const rt3d_params* p)
     if (p->apss_min_nb < 0) return false;
     if (p->depth_denoiser < 0 || p->depth_denoiser > RT3D_DEPTH_BILATERAL) return false;
     if (p->apss_fp64 < 0 || p->apss_fp64 > 1) return false;
+    if (p->upsample < 1 || p->upsample > RT3D_MAX_UPSAMPLE) return false;
     if (p->intensity_denoiser < 0 || p->intensity_denoiser > 1) return false;
     if (p->bkg_mode < 0 || p->bkg_mode > 1) return false;
     if (p->bkg_mode == RT3D_BKG_LOWPASS && !(p->bkg_sigma > 0.0f)) return false;
@@ -327,6 +329,7 @@ rt3d_status build_kparams(const rt3d_ctx* c, const rt3d_params* p, KParams* K)
     K->apss_min_nb = p->apss_min_nb;
     K->depth_den = p->depth_denoiser;
     K->apss_fp64 = p->apss_fp64;
+    K->up = p->upsample;
     K->int_den = p->intensity_denoiser;
     K->bkg_mode = p->bkg_mode;
     K->bkg_rad = p->bkg_radius;
@@ -470,24 +473,30 @@ rt3d_status encode_histogram_map(const rt3d_frame* f, CUtensorMap* map)
 
 // Batch descriptors for n frames whose results go to out[i].
 rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_result* out,
-                        Batch* B, CallRecord* rec = nullptr, bool tc_init = false)
+                        Batch* B, CallRecord* rec = nullptr, bool tc_init = false, int up = 1)
 {
     std::memset(B, 0, sizeof(Batch));
     B->n = n;
-    int tiles = 0, pix = 0, tmax = 0;
+    int tiles = 0, pix = 0, lpix = 0, tmax = 0;
     int tc_tiles = 0, strips = 0;
     long long tc_ent = 0;
     for (int i = 0; i < n; ++i) {
         FrameDesc& d = B->f[i];
-        d.h = f[i].h;
-        d.w = f[i].w;
+        // the point cloud's grid: up times finer than the pixels with super-resolution
+        d.h = f[i].h * up;
+        d.w = f[i].w * up;
         d.nt = f[i].t;
-        d.npix = f[i].h * f[i].w;
-        d.tiles_w = (f[i].w + kTileW - 1) / kTileW;
+        d.npix = d.h * d.w;
+        d.lh = f[i].h;
+        d.lw = f[i].w;
+        d.lnpix = f[i].h * f[i].w;
+        d.tiles_w = (d.w + kTileW - 1) / kTileW;
         d.tile_base = tiles;
         d.pix_base = pix;
-        tiles += d.tiles_w * ((f[i].h + kTileH - 1) / kTileH);
+        d.lpix_base = lpix;
+        tiles += d.tiles_w * ((d.h + kTileH - 1) / kTileH);
         pix += d.npix;
+        lpix += d.lnpix;
         tmax = f[i].t > tmax ? f[i].t : tmax;
         d.dense = f[i].dense;
         d.csr_off = f[i].csr_off;
@@ -502,7 +511,8 @@ rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3
         // aligned start and row stride) and whose pixels share response 0;
         // other frames take the CUDA-core path, which computes the identical
         // integer filter
-        if (tc_init && !d.use_csr && !f[i].irf_index && f[i].t % 8 == 0 && ((uintptr_t)f[i].dense & 15) == 0) {
+        if (tc_init && up == 1 && !d.use_csr && !f[i].irf_index && f[i].t % 8 == 0 &&
+            ((uintptr_t)f[i].dense & 15) == 0) {
             // each pixel's entries at a fixed offset (pixel x bins) of the
             // frame's region, so no allocation order is needed
             const long long cells = (long long)d.npix * f[i].t;
@@ -531,6 +541,7 @@ rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3
     B->net_strips = strips;
     B->total_tiles = tiles;
     B->total_pix = pix;
+    B->total_lpix = lpix;
     B->max_t = tmax;
     return RT3D_OK;
 }
@@ -581,7 +592,7 @@ bool batch_has_int(const Batch& B)
 rt3d_status launch_init(rt3d_ctx* c, const KParams& K, const Batch& B, Work W, cudaStream_t s,
                         bool dump, bool compact_only, int pix0 = 0, int pix_end = -1, int tc0 = 0, int tc1 = -1)
 {
-    if (pix_end < 0) pix_end = B.total_pix;
+    if (pix_end < 0) pix_end = B.total_lpix;    // the init runs per lidar pixel
     if (tc1 < 0) tc1 = B.tc_tiles;
     // the tensor-core kernel takes the dense frames of a cold start; the
     // CUDA-core kernel the rest (it skips those frames)
@@ -795,6 +806,53 @@ rt3d_status launch_loop(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter,
     return RT3D_OK;
 }
 
+// The super-resolved iteration (upsample u > 1): the gradient steps per lidar
+// pixel (k_sr_step), the denoisers on the world grid (phases B and C, which
+// skip their per-pixel steps then):
+//   depth step -> APSS -> intensity step -> intensity low-pass, pruning,
+//   merge -> background step; the background denoiser runs at the head of the
+//   next depth step (and in the finaliser).
+template <int K>
+void launch_sr_step(int mode, int first, int lpix, cudaStream_t s, const CallRecord* rec, const Work& W)
+{
+    const int grid = (lpix + kSrWarps - 1) / kSrWarps;
+    if (mode == 0)
+        k_sr_step<K, 0><<<grid, kSrWarps * 32, 0, s>>>(rec, W, first, 0, lpix);
+    else if (mode == 1)
+        k_sr_step<K, 1><<<grid, kSrWarps * 32, 0, s>>>(rec, W, first, 0, lpix);
+    else
+        k_sr_step<K, 2><<<grid, kSrWarps * 32, 0, s>>>(rec, W, first, 0, lpix);
+}
+
+rt3d_status launch_loop_sr(rt3d_ctx* c, const Batch& B, cudaStream_t s, int n_iter)
+{
+    const KParams& P = c->h_rec.P;
+    auto step = [&](int mode, int first) {
+        LaunchScope ls(c, s, mode == 0 ? kcA : (mode == 1 ? kcB : kcC));
+        switch (P.k) {
+        case 1: launch_sr_step<1>(mode, first, B.total_lpix, s, c->d_rec, c->W); break;
+        case 2: launch_sr_step<2>(mode, first, B.total_lpix, s, c->d_rec, c->W); break;
+        case 3: launch_sr_step<3>(mode, first, B.total_lpix, s, c->d_rec, c->W); break;
+        default: launch_sr_step<4>(mode, first, B.total_lpix, s, c->d_rec, c->W); break;
+        }
+    };
+    for (int it = 0; it < n_iter; ++it) {
+        step(0, it == 0 ? 1 : 0);
+        {
+            LaunchScope ls(c, s, kcB);
+            launch_phase(P, 1, 0, B.total_tiles, s, c->d_rec, c->W);
+        }
+        step(1, 0);
+        {
+            LaunchScope ls(c, s, kcC);
+            launch_phase(P, 2, 0, B.total_tiles, s, c->d_rec, c->W);
+        }
+        step(2, 0);
+    }
+    RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}
+
 rt3d_status launch_final(rt3d_ctx* c, const Batch& B, cudaStream_t s, int ran, int tile0 = 0, int tiles = -1)
 {
     if (tiles < 0) tiles = B.total_tiles;
@@ -817,6 +875,13 @@ rt3d_status check_common(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_par
         if (out && (!out[i].t || !out[i].r || !out[i].alive || !out[i].b)) return RT3D_E_INVALID;
     }
     if (p->depth_denoiser == RT3D_DEPTH_LEARNED && !c->net) return RT3D_E_INVALID;
+    if (p->upsample > 1) {
+        // the world grid's pixels share the workspace with the batch's pixels
+        long long world = 0;
+        for (int i = 0; i < n; ++i) world += (long long)f[i].h * f[i].w * p->upsample * p->upsample;
+        if (world > c->stride) return RT3D_E_INVALID;
+        if (p->depth_denoiser == RT3D_DEPTH_LEARNED) return RT3D_E_UNIMPL;
+    }
     return RT3D_OK;
 }
 
@@ -830,7 +895,7 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
     st = build_kparams(c, p, &K);
     if (st != RT3D_OK) return st;
     Batch& B = c->h_rec.B;
-    st = build_batch(c, n, f, out, &B, &c->h_rec, K.tc_mode != 0 && !p->warm_start);
+    st = build_batch(c, n, f, out, &B, &c->h_rec, K.tc_mode != 0 && !p->warm_start, p->upsample);
     if (st != RT3D_OK) return st;
     st = upload_record(c, s);
     if (st != RT3D_OK) return st;
@@ -841,20 +906,20 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
     // batch) and while kernel times are recorded (so each kernel's duration is
     // its own).
     int n0 = 0, split_tiles = 0, split_pix = 0, split_tc = 0;
-    if (n >= 2 && K.depth_den != RT3D_DEPTH_LEARNED && !c->profiling) {
+    if (n >= 2 && K.depth_den != RT3D_DEPTH_LEARNED && !c->profiling && K.up == 1) {
         // first chain: the frames whose tiles end by half the batch's tiles (at least one)
         auto tiles_end = [&](int i) { return i + 1 < n ? B.f[i + 1].tile_base : B.total_tiles; };
         while (n0 < n - 1 && 2 * tiles_end(n0) <= B.total_tiles) ++n0;
         if (n0 == 0) n0 = 1;
         split_tiles = B.f[n0].tile_base;
-        split_pix = B.f[n0].pix_base;
+        split_pix = B.f[n0].lpix_base;
         split_tc = B.f[n0].tc_tile_base;
     }
     const GraphKey key{B.total_pix, B.total_tiles, p->n_iter, p->warm_start != 0,
                        init_warps(K.peak_sep), c->profiling ? 1 : 0, init_smem(K, K.peak_sep),
                        B.tc_tiles, K.tc_stages, K.tc_nd, batch_has_int(B) ? 1 : 0,
                        K.depth_den == RT3D_DEPTH_LEARNED ? 1 : 0, fused_depth_step(K) ? 1 : 0, split_tiles,
-                       den_variant(K)};
+                       den_variant(K), K.up};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         // capture the launch sequence of this geometry once, on a private stream
@@ -875,7 +940,9 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
             const bool warm = p->warm_start != 0;
             if (split_tiles == 0) {
                 if (e == cudaSuccess) cst = launch_init(c, K, B, c->W, c->cap_stream, false, warm);
-                if (e == cudaSuccess && cst == RT3D_OK) cst = launch_loop(c, B, c->cap_stream, p->n_iter);
+                if (e == cudaSuccess && cst == RT3D_OK)
+                    cst = K.up > 1 ? launch_loop_sr(c, B, c->cap_stream, p->n_iter)
+                                   : launch_loop(c, B, c->cap_stream, p->n_iter);
                 if (e == cudaSuccess && cst == RT3D_OK) cst = launch_final(c, B, c->cap_stream, ran);
             } else {
                 // the tensor-core init holds most of an SM's shared memory, so it
@@ -890,7 +957,7 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
                 if (e == cudaSuccess && cst == RT3D_OK && !tc_init)
                     cst = launch_init(c, K, B, c->W, c->cap_stream, false, warm, 0, split_pix, 0, split_tc);
                 if (e == cudaSuccess && cst == RT3D_OK && !tc_init)
-                    cst = launch_init(c, K, B, c->W, c->cap_stream2, false, warm, split_pix, B.total_pix, split_tc,
+                    cst = launch_init(c, K, B, c->W, c->cap_stream2, false, warm, split_pix, B.total_lpix, split_tc,
                                       B.tc_tiles);
                 if (e == cudaSuccess && cst == RT3D_OK) cst = launch_loop(c, B, c->cap_stream, p->n_iter, 0, split_tiles);
                 if (e == cudaSuccess && cst == RT3D_OK)
@@ -984,6 +1051,7 @@ rt3d_status rt3d_default_params(rt3d_params* p)
     p->net_scale = 3.0f;
     p->net_fallback = 6.0f;
     p->apss_fp64 = 0;
+    p->upsample = 1;
     return RT3D_OK;
 }
 
@@ -1219,7 +1287,7 @@ rt3d_status rt3d_init(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d_params* p, 
     st = build_kparams(c, p, &K);
     if (st != RT3D_OK) return st;
     Batch& B = c->h_rec.B;
-    st = build_batch(c, 1, f, out, &B, &c->h_rec, K.tc_mode != 0);
+    st = build_batch(c, 1, f, out, &B, &c->h_rec, K.tc_mode != 0, p->upsample);
     if (st != RT3D_OK) return st;
     st = upload_record(c, s);
     if (st != RT3D_OK) return st;
@@ -1249,6 +1317,7 @@ rt3d_status rt3d_reconstruct_host(rt3d_ctx_t* c, const rt3d_frame* f, const rt3d
     if (!c || !f || !p || !out) return RT3D_E_INVALID;
     rt3d_status st = check_common(c, 1, f, p, out);
     if (st != RT3D_OK) return st;
+    if (p->upsample > 1) return RT3D_E_UNIMPL;
     RT3D_CUDA(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     const long long mpix = (long long)c->cfg.max_h * c->cfg.max_w;
@@ -1328,6 +1397,7 @@ rt3d_status rt3d_reconstruct_batch_host(rt3d_ctx_t* c, int n, const rt3d_frame* 
     if (!c || !f || !p || !out || n < 1) return RT3D_E_INVALID;
     rt3d_status st = check_common(c, n, f, p, out);
     if (st != RT3D_OK) return st;
+    if (p->upsample > 1) return RT3D_E_UNIMPL;
     RT3D_CUDA(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     const int Kp = p->k_max;
@@ -1466,6 +1536,7 @@ rt3d_status rt3d_phase(rt3d_ctx_t* c, int phase, int first, const rt3d_frame* f,
     rt3d_status st = check_common(c, 1, f, p, state);
     if (st != RT3D_OK) return st;
     if (!f->csr_off) return RT3D_E_INVALID;
+    if (p->upsample > 1) return RT3D_E_UNIMPL;
     RT3D_CUDA(cudaSetDevice(c->cfg.device));
     cudaStream_t s = (cudaStream_t)stream;
     KParams& K = c->h_rec.P;
@@ -1622,11 +1693,16 @@ rt3d_status net_batch(rt3d_net* net, int n, int h, int w, cudaStream_t s)
         d.tiles_w = tw;
         d.tile_base = i * tw * th;
         d.pix_base = i * h * w;
+        d.lh = h;
+        d.lw = w;
+        d.lnpix = h * w;
+        d.lpix_base = d.pix_base;
         d.net_strip_base = i * h * ((w + kStrip - 1) / kStrip);
     }
     B.net_strips = n * h * ((w + kStrip - 1) / kStrip);
     B.total_tiles = n * tw * th;
     B.total_pix = n * h * w;
+    B.total_lpix = B.total_pix;
     RT3D_CUDA(cudaMemcpyAsync(net->d_batch, &B, sizeof(Batch), cudaMemcpyHostToDevice, s));
     return RT3D_OK;
 }
@@ -1886,9 +1962,12 @@ rt3d_status rt3d_set_depth_net(rt3d_ctx_t* c, rt3d_net_t* net)
 // Reconstruction without any allocation (rt3d_reconstruct_noalloc).
 //
 // Callers that must not allocate device memory after start-up get the whole
-// method with its scratch in one file-scope device array, reserved when the
-// library is loaded and held by every GPU that loads it until the process
-// exits.  Its size bounds the frames this entry point accepts:
+// method with its scratch in one file-scope device array, held by every GPU
+// that has loaded the library's module until the process exits.  Under CUDA's
+// lazy module loading (the default) the module -- and with it the array -- is
+// loaded on a device at the first use there (the first call's address
+// look-up), and each kernel's code at its first launch.  Its size bounds the
+// frames this entry point accepts:
 //   pixels h*w <= kStaticMaxPixels, and for a dense histogram h*w*t <=
 //   kStaticMaxEntries (so that even a histogram with every bin nonzero fits
 //   the sparse-entry area; a caller's own sparse list needs no entry area).
@@ -1965,6 +2044,7 @@ rt3d_status static_kparams(const rt3d_irf* irf, const rt3d_params* p, KParams* K
     K->apss_min_nb = p->apss_min_nb;
     K->depth_den = p->depth_denoiser;
     K->apss_fp64 = p->apss_fp64;
+    K->up = 1;
     K->int_den = p->intensity_denoiser;
     K->bkg_mode = p->bkg_mode;
     K->bkg_rad = p->bkg_radius;
@@ -2015,6 +2095,13 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     if (!params_ok(&cfg, p)) return RT3D_E_INVALID;
     if (p->depth_denoiser == RT3D_DEPTH_LEARNED) return RT3D_E_UNIMPL;
     if (f->irf_index) return RT3D_E_UNIMPL;      // one response: `irf`
+    if (p->upsample > 1) return RT3D_E_UNIMPL;
+
+    // the call record goes up from a pageable stack copy, which a stream
+    // capture would record by address: not while `stream` is being captured
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    RT3D_CUDA(cudaStreamIsCapturing((cudaStream_t)stream, &cap));
+    if (cap != cudaStreamCaptureStatusNone) return RT3D_E_INVALID;
 
     int device = 0;
     RT3D_CUDA(cudaGetDevice(&device));
@@ -2050,6 +2137,10 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     d.tiles_w = (f->w + kTileW - 1) / kTileW;
     d.tile_base = 0;
     d.pix_base = 0;
+    d.lh = f->h;
+    d.lw = f->w;
+    d.lnpix = (int)npix;
+    d.lpix_base = 0;
     d.dense = f->dense;
     d.csr_off = f->csr_off;
     d.use_csr = has_csr;
@@ -2062,6 +2153,7 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     d.n_points = out->n_points;
     B.total_tiles = d.tiles_w * ((f->h + kTileH - 1) / kTileH);
     B.total_pix = (int)npix;
+    B.total_lpix = (int)npix;
     B.max_t = f->t;
 
     cudaStream_t s = (cudaStream_t)stream;
@@ -2085,5 +2177,23 @@ extern "C" rt3d_status rt3d_reconstruct_noalloc(const rt3d_irf* irf, const rt3d_
     }
     k_final<<<B.total_tiles, kTileThreads, 0, s>>>(d_rec, W, p->n_iter > 0 ? 1 : 0, 0);
     RT3D_CUDA(cudaGetLastError());
+    return RT3D_OK;
+}
+
+extern "C" rt3d_status rt3d_noalloc_status(void* stream)
+{
+    int device = 0;
+    RT3D_CUDA(cudaGetDevice(&device));
+    unsigned char* base = nullptr;
+    const rt3d_status st = static_scratch(device, &base);
+    if (st != RT3D_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int h = 0;
+    RT3D_CUDA(cudaMemcpyAsync(&h, base + kStaticOffStatus, sizeof(int), cudaMemcpyDeviceToHost, s));
+    RT3D_CUDA(cudaMemsetAsync(base + kStaticOffStatus, 0, sizeof(int), s));
+    RT3D_CUDA(cudaStreamSynchronize(s));
+    if (h & kStatusTimeout) return RT3D_E_TIMEOUT;
+    if (h & kStatusCapacity) return RT3D_E_CAPACITY;
+    if (h & kStatusRange) return RT3D_E_RANGE;
     return RT3D_OK;
 }

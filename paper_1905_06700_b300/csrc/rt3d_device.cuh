@@ -40,6 +40,7 @@ struct KParams {
     int win_r, apss_min_nb;
     int depth_den, int_den, bkg_mode, bkg_rad;
     int apss_fp64;                  // APSS solve (and the learned form's fallback) in FP64
+    int up;                         // super-resolution factor u of the mapping f (1 = off)
     int irf_len, irf_origin;        // response 0 (the tensor-core init's)
     float irf_sum;                  // sum of the float IRF samples (H in the interior)
     // instrument responses a pixel picks from (FrameDesc::irf_index): samples
@@ -65,9 +66,11 @@ struct KParams {
 };
 
 struct FrameDesc {
-    int h, w, nt, npix;             // nt = histogram bins
+    int h, w, nt, npix;             // point-cloud (world) grid; nt = histogram bins
+    int lh, lw, lnpix;              // lidar pixels (= h, w, npix without super-resolution)
     int tiles_w, tile_base;         // tile grid of the loop kernels
-    int pix_base;                   // first pixel of this frame in the batch workspace
+    int pix_base;                   // first world pixel of this frame in the batch workspace
+    int lpix_base;                  // first lidar pixel (sparse segments, backgrounds)
     int use_csr;                    // loop reads the caller's sparse list
     const uint16_t* dense;
     const uint32_t* csr_off;
@@ -86,6 +89,7 @@ struct FrameDesc {
 
 struct Batch {
     int n, total_tiles, total_pix, max_t;
+    int total_lpix;                 // lidar pixels of all frames
     int tc_tiles;                   // 128-pixel tiles of the tensor-core init
     long long tc_entries;           // entries reserved for its frames (pixels x bins)
     long long ent_base_int;         // the CUDA-core init allocates entries from here on
@@ -144,6 +148,16 @@ __device__ __forceinline__ int frame_of_pixel(const Batch& B, int pix)
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (B.f[mid].pix_base <= pix) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int frame_of_lpixel(const Batch& B, int lpix)
+{
+    int lo = 0, hi = B.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (B.f[mid].lpix_base <= lpix) lo = mid; else hi = mid - 1;
     }
     return lo;
 }

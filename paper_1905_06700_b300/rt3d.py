@@ -65,7 +65,8 @@ class Params(C.Structure):
                 ("lmf_delta_rel", C.c_float), ("lmf_frac_bits", C.c_int32),
                 ("peak_min_photons", C.c_int32), ("peak_sep", C.c_int32),
                 ("lmf_precision", C.c_int32), ("warm_start", C.c_int32),
-                ("net_scale", C.c_float), ("net_fallback", C.c_float), ("apss_fp64", C.c_int32)]
+                ("net_scale", C.c_float), ("net_fallback", C.c_float), ("apss_fp64", C.c_int32),
+                ("upsample", C.c_int32)]
 
 
 class AdamW(C.Structure):
@@ -143,6 +144,7 @@ def lib():
                                       C.POINTER(C.c_int64), _P]),
         "rt3d_reconstruct_noalloc": (C.c_int, [C.POINTER(Irf), C.POINTER(Frame),
                                                C.POINTER(Params), C.POINTER(Result), _P]),
+        "rt3d_noalloc_status": (C.c_int, [_P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(L, name)
@@ -257,13 +259,15 @@ class Context:
             arr[i] = Irf(a.ctypes.data_as(C.POINTER(C.c_double)), len(a), int(origin))
         check(lib().rt3d_set_irfs(self.handle, len(irfs), arr), "rt3d_set_irfs")
 
-    def new_result(self, h, w, k=None):
+    def new_result(self, h, w, k=None, up=1):
+        """Result tensors of an h x w frame: points on the world grid (up times
+        finer with super-resolution), background per pixel."""
         torch = self.torch
         k = k or self.k_max
         d = self.device
-        return dict(t=torch.zeros((k, h, w), dtype=torch.float32, device=d),
-                    r=torch.zeros((k, h, w), dtype=torch.float32, device=d),
-                    alive=torch.zeros((k, h, w), dtype=torch.uint8, device=d),
+        return dict(t=torch.zeros((k, h * up, w * up), dtype=torch.float32, device=d),
+                    r=torch.zeros((k, h * up, w * up), dtype=torch.float32, device=d),
+                    alive=torch.zeros((k, h * up, w * up), dtype=torch.uint8, device=d),
                     b=torch.zeros((h, w), dtype=torch.float32, device=d),
                     n_points=torch.zeros(1, dtype=torch.int32, device=d))
 
@@ -322,7 +326,7 @@ class Context:
              irf_index=None):
         fr = self.frame(dense, csr, gain, shape, irf_index)
         p = params_from(params)
-        out = out or self.new_result(fr.h, fr.w, p.k_max)
+        out = out or self.new_result(fr.h, fr.w, p.k_max, p.upsample)
         rs = self.result_struct(out)
         check(lib().rt3d_init(self.handle, C.byref(fr), C.byref(p), C.byref(rs), _stream(stream)),
               "rt3d_init")
@@ -332,7 +336,7 @@ class Context:
              irf_index=None):
         fr = self.frame(dense, csr, gain, shape, irf_index)
         p = params_from(params)
-        out = out or self.new_result(fr.h, fr.w, p.k_max)
+        out = out or self.new_result(fr.h, fr.w, p.k_max, p.upsample)
         rs = self.result_struct(out)
         check(lib().rt3d_reconstruct(self.handle, C.byref(fr), C.byref(p), C.byref(rs),
                                      _stream(stream)), "rt3d_reconstruct")
@@ -345,7 +349,7 @@ class Context:
         for i, f in enumerate(frames):
             fa[i] = self.frame(f.get("dense"), f.get("csr"), f.get("gain"), f.get("shape"), f.get("irf_index"))
         if outs is None:
-            outs = [self.new_result(fa[i].h, fa[i].w, p.k_max) for i in range(n)]
+            outs = [self.new_result(fa[i].h, fa[i].w, p.k_max, p.upsample) for i in range(n)]
         ra = (Result * n)(*[self.result_struct(o) for o in outs])
         check(lib().rt3d_reconstruct_batch(self.handle, n, fa, C.byref(p), ra, _stream(stream)),
               "rt3d_reconstruct_batch")
@@ -475,6 +479,12 @@ def rt3d_reconstruct_noalloc(irf_samples, irf_origin: int, frame: Frame, params,
     p = params_from(params)
     return lib().rt3d_reconstruct_noalloc(C.byref(irf), C.byref(frame), C.byref(p),
                                           C.byref(result), _stream(stream))
+
+
+def rt3d_noalloc_status(stream=None) -> int:
+    """Device status of the last allocation-free call on the current device
+    (synchronises; clears the word)."""
+    return lib().rt3d_noalloc_status(_stream(stream))
 
 
 class Net:
