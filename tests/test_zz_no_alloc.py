@@ -73,3 +73,53 @@ def test_noalloc_rejects_frames_beyond_its_static_scratch():
     wide = R.Frame(200, 100, 8, R._ptr(big), None, None, None)              # 20000 px > 16384
     assert R.rt3d_reconstruct_noalloc(np.ones(9), 4, wide, prm,
                                       R.Context.result_struct(out)) == R.RT3D_E_INVALID
+
+
+def test_noalloc_sparse_input_warm_start_and_gain_match_context(orc):
+    """The other branches of the allocation-free call: the caller's own
+    sparse list (no entry area of the static array), a warm start from the
+    previous result (the caller's buffers read back), and a gain map; each
+    against the context entry point."""
+    from paper_1905_06700_b300 import rt3d as R
+    torch = torch_mod()
+    sc = scenes.small_random(19, 23, 300, n_comp=2, seed=61)
+    z, prm = _frame_and_params(orc, sc)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    dense = upload_u16(z)
+    off, ent = ctx.compact(dense)
+    gain = torch.from_numpy(np.random.default_rng(2).uniform(0.6, 1.4, (sc.h, sc.w)).astype(np.float32)).cuda()
+    k = prm["k_max"]
+
+    def run(fr, p, out):
+        st = R.rt3d_reconstruct_noalloc(sc.irf.samples, sc.irf.origin, fr, p, R.Context.result_struct(out))
+        assert st == R.RT3D_OK, R.status_str(st)
+        torch.cuda.synchronize()
+        return np_of(out)
+
+    # sparse list
+    out = ctx.new_result(sc.h, sc.w, k)
+    got = run(R.Frame(sc.h, sc.w, sc.t, None, R._ptr(off), R._ptr(ent), None), prm, out)
+    _close(got, np_of(ctx.reconstruct(prm, csr=(off, ent), shape=z.shape)))
+    # warm start from that result, dense input with a gain map
+    warm = dict(prm, warm_start=1)
+    want_dev = ctx.new_result(sc.h, sc.w, k)
+    for key in out:
+        want_dev[key].copy_(out[key])
+    want = np_of(ctx.reconstruct(warm, dense=dense, gain=gain, out=want_dev))
+    got = run(R.Frame(sc.h, sc.w, sc.t, R._ptr(dense), None, None, R._ptr(gain)), warm, out)
+    _close(got, want)
+    assert R.rt3d_noalloc_status() == R.RT3D_OK
+
+
+def test_noalloc_status_reports_the_exact_range_guard(orc):
+    """A pixel whose photons times the largest filter tap reach 2^31 cannot
+    be filtered exactly: the allocation-free call keeps no point there and
+    its status query reports RT3D_E_RANGE (then reads clean)."""
+    from paper_1905_06700_b300 import rt3d as R
+    sc = scenes.small_random(6, 7, 512, n_comp=2, seed=43)
+    z, prm = _frame_and_params(orc, sc)
+    z[2, 3, :] = 65535
+    got = _call_noalloc(sc, upload_u16(z), prm, R)
+    assert R.rt3d_noalloc_status() == R.RT3D_E_RANGE
+    assert R.rt3d_noalloc_status() == R.RT3D_OK
+    assert not got["alive"][:, 2, 3].any()
