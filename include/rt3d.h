@@ -90,8 +90,12 @@ typedef struct {
     int32_t max_h, max_w, max_t;   /* largest frame */
     int32_t k_max;                 /* point slots per pixel, 1..RT3D_MAX_K */
     int32_t max_batch;             /* frames per batched call, 1..RT3D_MAX_BATCH */
-    int64_t max_entries;           /* nonzero-bin capacity per call; 0 = max_batch*max_h*max_w*max_t */
+    int64_t max_entries;           /* nonzero-bin capacity per call; 0 = max_batch*max_h*max_w*max_t,
+                                      or with mem_budget > 0 the largest the budget leaves */
     int32_t device;                /* CUDA device ordinal */
+    int64_t mem_budget;            /* bytes of device memory the workspace may take (0 = no limit):
+                                      rt3d_create returns RT3D_E_NOMEM if the per-pixel state and the
+                                      entry capacity do not fit it (see rt3d_workspace_bytes) */
 } rt3d_config;
 
 /* Instrument response h_{i,j}(.) of the likelihood equation, shared by all
@@ -220,6 +224,15 @@ rt3d_status rt3d_default_params(rt3d_params* p);
 /* Host-only validation of a frame and parameters against a configuration.
  * Touches no device; frame pointers are only checked for NULL-ness. */
 rt3d_status rt3d_validate(const rt3d_config* cfg, const rt3d_frame* f, const rt3d_params* p);
+
+/* Device bytes the workspace of rt3d_create(cfg) takes: per pixel of the
+ * batch 16 + 9 k_max bytes (sparse segments, half-step state, pruning flags,
+ * a scan buffer), 4 bytes per sparse entry, and the call record.  With
+ * max_entries = 0 and mem_budget > 0, the entry capacity is the largest that
+ * keeps this within the budget; *entries (may be NULL) receives it.  Host
+ * only.  RT3D_E_INVALID for a bad configuration, RT3D_E_NOMEM if the budget
+ * does not hold the per-pixel state (or the given max_entries). */
+rt3d_status rt3d_workspace_bytes(const rt3d_config* cfg, int64_t* bytes, int64_t* entries);
 
 /* Create a context on cfg->device: copies the IRF, allocates the workspace
  * (sparse-entry buffer, half-step state, counters).  *out is NULL on error. */

@@ -53,7 +53,12 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane)
     return v;
 }
 
-template <bool kDumpY, bool kCompactOnly>
+// Variants (kVar bits): kInitIdx -- some frame of the launch names a response
+// per pixel (rt3d_frame.irf_index); kInitUp -- super-resolution (the points
+// go to the world grid).
+constexpr int kInitIdx = 1, kInitUp = 2;
+
+template <bool kDumpY, bool kCompactOnly, int kVar = 0>
 __global__ void __launch_bounds__(kInitWarps * 32, 20)
 k_init(const CallRecord* __restrict__ rec, const Work W, int pix0, int pix_end)
 {
@@ -64,7 +69,8 @@ k_init(const CallRecord* __restrict__ rec, const Work W, int pix0, int pix_end)
     const int sep = P.peak_sep;
     const int min_photons = P.peak_min_photons;
     // every response's taps (a pixel uses its own response's)
-    const int n_taps = P.irf_offs[P.n_irf - 1] + P.irf_lens[P.n_irf - 1];
+    constexpr bool kIdx = (kVar & kInitIdx) != 0;
+    const int n_taps = kIdx ? P.irf_offs[P.n_irf - 1] + P.irf_lens[P.n_irf - 1] : P.irf_len;
     const int k_bytes = (n_taps * 4 + 15) & ~15;
     for (int i = threadIdx.x; i < n_taps; i += blockDim.x) sK_all[i] = P.lmf[i];
     __syncthreads();
@@ -81,10 +87,11 @@ k_init(const CallRecord* __restrict__ rec, const Work W, int pix0, int pix_end)
     const int T = F.nt;
     if (lp == 0 && lane == 0 && F.n_points) *F.n_points = 0;   // counted by the finaliser
     const float g = F.gain ? F.gain[lp] : 1.0f;
-    // the pixel's instrument response: taps, length and origin
-    const int which = pixel_irf(P, F, lp);
-    const int L = P.irf_lens[which], O = P.irf_origins[which];
-    const int* sK = sK_all + P.irf_offs[which];
+    // the pixel's instrument response: taps, length and origin (response 0
+    // unless the frame names one per pixel)
+    const int which = kIdx ? pixel_irf(P, F, lp) : 0;
+    const int L = kIdx ? P.irf_lens[which] : P.irf_len, O = kIdx ? P.irf_origins[which] : P.irf_origin;
+    const int* sK = kIdx ? sK_all + P.irf_offs[which] : sK_all;
 
     unsigned char* wbase = smem + k_bytes + warp * init_warp_bytes(sep);
     uint32_t* stage = reinterpret_cast<uint32_t*>(wbase);
@@ -400,9 +407,11 @@ k_init(const CallRecord* __restrict__ rec, const Work W, int pix0, int pix_end)
     // the points: with super-resolution (u > 1) every world pixel of the
     // lidar pixel's u x u block starts from the pixel's peaks, each with
     // 1/u^2 of the intensity; lanes over (world pixel a, slot k)
-    const int np = F.npix, up = P.up;
-    for (int e = lane; e < K * up * up; e += 32) {
-        const int k = e % K, a = e / K;
+    const int np = F.npix;
+    const int up = (kVar & kInitUp) ? P.up : 1;
+    if (lane < K * up * up) {
+        // lane = a K + k: world pixel a of the block (a = 0 without super-resolution), slot k
+        const int k = up == 1 ? lane : lane % K, a = up == 1 ? 0 : lane / K;
         float tt = 0.0f, rr = 0.0f;
         uint8_t al = 0;
 #pragma unroll
@@ -414,13 +423,34 @@ k_init(const CallRecord* __restrict__ rec, const Work W, int pix0, int pix_end)
             }
         long long wq = lp;
         if (up > 1) {
-            const int i = lp / F.lw, j = lp - (lp / F.lw) * F.lw;
+            const int i = lp / F.lw, j = lp - i * F.lw;
             wq = (long long)(i * up + a / up) * F.w + (j * up + a % up);
             rr /= (float)(up * up);
         }
         F.t[(long long)k * np + wq] = tt;
         F.r[(long long)k * np + wq] = rr;
         F.alive[(long long)k * np + wq] = al;
+    }
+    if ((kVar & kInitUp) && up > 2) {
+        // blocks of more than 32 points: the rest (u = 3, 4 with K > 3 or u = 4)
+        for (int e = lane + 32; e < K * up * up; e += 32) {
+            const int k = e % K, a = e / K;
+            float tt = 0.0f, rr = 0.0f;
+            uint8_t al = 0;
+#pragma unroll
+            for (int q = 0; q < kMaxK; ++q)
+                if (q == k && q < nsel) {
+                    tt = (float)sel[q];
+                    rr = fmaxf((float)wsum[q] / g - b0 * (float)winlen[q], P.r_min);
+                    al = 1;
+                }
+            const int i = lp / F.lw, j = lp - i * F.lw;
+            const long long wq = (long long)(i * up + a / up) * F.w + (j * up + a % up);
+            rr /= (float)(up * up);
+            F.t[(long long)k * np + wq] = tt;
+            F.r[(long long)k * np + wq] = rr;
+            F.alive[(long long)k * np + wq] = al;
+        }
     }
     if (lane == 0) F.b[lp] = b0;
 }

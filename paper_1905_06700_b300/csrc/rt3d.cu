@@ -48,14 +48,14 @@ struct PendingTiming {
 struct GraphKey {
     int total_pix, total_tiles, n_iter, warm, init_warps, profiled;
     size_t init_smem;
-    int tc_tiles, tc_stages, tc_nd, any_int, learned, fused, split_tiles, den_variant, up;
+    int tc_tiles, tc_stages, tc_nd, any_int, learned, fused, split_tiles, den_variant, up, init_var;
     bool operator<(const GraphKey& o) const
     {
         return std::tie(total_pix, total_tiles, n_iter, warm, init_warps, profiled, init_smem, tc_tiles,
-                        tc_stages, tc_nd, any_int, learned, fused, split_tiles, den_variant, up) <
+                        tc_stages, tc_nd, any_int, learned, fused, split_tiles, den_variant, up, init_var) <
                std::tie(o.total_pix, o.total_tiles, o.n_iter, o.warm, o.init_warps, o.profiled,
                         o.init_smem, o.tc_tiles, o.tc_stages, o.tc_nd, o.any_int, o.learned, o.fused,
-                        o.split_tiles, o.den_variant, o.up);
+                        o.split_tiles, o.den_variant, o.up, o.init_var);
     }
 };
 
@@ -257,7 +257,7 @@ bool config_ok(const rt3d_config* cfg)
     if (cfg->max_h < 1 || cfg->max_w < 1 || cfg->max_t < 1 || cfg->max_t > RT3D_MAX_T) return false;
     if (cfg->k_max < 1 || cfg->k_max > RT3D_MAX_K) return false;
     if (cfg->max_batch < 1 || cfg->max_batch > RT3D_MAX_BATCH) return false;
-    if (cfg->max_entries < 0) return false;
+    if (cfg->max_entries < 0 || cfg->mem_budget < 0) return false;
     const long long pix = (long long)cfg->max_batch * cfg->max_h * cfg->max_w;
     if (pix > (1ll << 30)) return false;
     return cfg->device >= 0;
@@ -546,6 +546,14 @@ rt3d_status build_batch(const rt3d_ctx* c, int n, const rt3d_frame* f, const rt3
     return RT3D_OK;
 }
 
+// The init kernel's variant: per-pixel responses in the batch, super-resolution.
+int init_variant(const KParams& K, const Batch& B)
+{
+    bool any_idx = false;
+    for (int i = 0; i < B.n; ++i) any_idx |= B.f[i].irf_index != nullptr;
+    return (any_idx ? kInitIdx : 0) | (K.up > 1 ? kInitUp : 0);
+}
+
 int init_warps(int sep)
 {
     int w = kInitSmemBudget / init_warp_bytes(sep);
@@ -607,7 +615,14 @@ rt3d_status launch_init(rt3d_ctx* c, const KParams& K, const Batch& B, Work W, c
         const int warps = init_warps(K.peak_sep);
         const int grid = (pix_end - pix0 + warps - 1) / warps;
         if (grid > 0) {
-            auto fn = dump ? k_init<true, false> : (compact_only ? k_init<false, true> : k_init<false, false>);
+            const int var = init_variant(K, B);
+            const bool any_idx = (var & kInitIdx) != 0;
+            auto fn = dump ? (any_idx ? k_init<true, false, kInitIdx> : k_init<true, false, 0>)
+                           : compact_only ? k_init<false, true, 0>
+                           : var == 0 ? k_init<false, false, 0>
+                           : var == kInitIdx ? k_init<false, false, kInitIdx>
+                           : var == kInitUp ? k_init<false, false, kInitUp>
+                           : k_init<false, false, kInitIdx | kInitUp>;
             RT3D_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
             {
                 LaunchScope ls(c, s, kcInit);
@@ -919,7 +934,7 @@ rt3d_status run_batch(rt3d_ctx* c, int n, const rt3d_frame* f, const rt3d_params
                        init_warps(K.peak_sep), c->profiling ? 1 : 0, init_smem(K, K.peak_sep),
                        B.tc_tiles, K.tc_stages, K.tc_nd, batch_has_int(B) ? 1 : 0,
                        K.depth_den == RT3D_DEPTH_LEARNED ? 1 : 0, fused_depth_step(K) ? 1 : 0, split_tiles,
-                       den_variant(K), K.up};
+                       den_variant(K), K.up, init_variant(K, B)};
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
         // capture the launch sequence of this geometry once, on a private stream
@@ -1063,6 +1078,30 @@ rt3d_status rt3d_validate(const rt3d_config* cfg, const rt3d_frame* f, const rt3
     return RT3D_OK;
 }
 
+rt3d_status rt3d_workspace_bytes(const rt3d_config* cfg, int64_t* bytes, int64_t* entries)
+{
+    if (!config_ok(cfg) || !bytes) return RT3D_E_INVALID;
+    const long long stride = (long long)cfg->max_batch * cfg->max_h * cfg->max_w;
+    const int K = cfg->k_max;
+    // seg 8, t_half and r_half 4 K each, b_half 4, alive_b K, scan buffer 4 (+ 4 once)
+    const long long fixed = (long long)stride * (16 + 9 * K) + 4 + sizeof(unsigned long long) + sizeof(int) +
+                            sizeof(CallRecord);
+    long long cap = cfg->max_entries;
+    if (cap == 0) {
+        cap = stride * cfg->max_t;
+        if (cfg->mem_budget > 0) {
+            const long long room = (cfg->mem_budget - fixed) / 4;
+            if (room < 1) return RT3D_E_NOMEM;
+            if (room < cap) cap = room;
+        }
+    }
+    const long long total = fixed + 4 * cap;
+    if (cfg->mem_budget > 0 && total > cfg->mem_budget) return RT3D_E_NOMEM;
+    *bytes = total;
+    if (entries) *entries = cap;
+    return RT3D_OK;
+}
+
 rt3d_status rt3d_create(const rt3d_config* cfg, const rt3d_irf* irf, rt3d_ctx_t** out)
 {
     if (!out) return RT3D_E_INVALID;
@@ -1089,8 +1128,14 @@ rt3d_status rt3d_create(const rt3d_config* cfg, const rt3d_irf* irf, rt3d_ctx_t*
     c->irf_norm[0].resize(irf->len);
     for (int s = 0; s < irf->len; ++s) c->irf_norm[0][s] = irf->samples[s] / sum;
     c->stride = (long long)cfg->max_batch * cfg->max_h * cfg->max_w;
-    long long cap = cfg->max_entries;
-    if (cap == 0) cap = c->stride * cfg->max_t;
+    int64_t ws_bytes = 0, cap = 0;
+    {
+        const rt3d_status wst = rt3d_workspace_bytes(cfg, &ws_bytes, &cap);
+        if (wst != RT3D_OK) {
+            rt3d_destroy(c);
+            return wst;
+        }
+    }
     const int K = cfg->k_max;
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** ptr, size_t bytes) {

@@ -39,7 +39,7 @@ class Rt3dError(RuntimeError):
 class Config(C.Structure):
     _fields_ = [("max_h", C.c_int32), ("max_w", C.c_int32), ("max_t", C.c_int32),
                 ("k_max", C.c_int32), ("max_batch", C.c_int32), ("max_entries", C.c_int64),
-                ("device", C.c_int32)]
+                ("device", C.c_int32), ("mem_budget", C.c_int64)]
 
 
 class Irf(C.Structure):
@@ -108,6 +108,7 @@ def lib():
         "rt3d_default_params": (C.c_int, [C.POINTER(Params)]),
         "rt3d_validate": (C.c_int, [C.POINTER(Config), C.POINTER(Frame), C.POINTER(Params)]),
         "rt3d_create": (C.c_int, [C.POINTER(Config), C.POINTER(Irf), C.POINTER(_P)]),
+        "rt3d_workspace_bytes": (C.c_int, [C.POINTER(Config), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "rt3d_net_create": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(_P)]),
         "rt3d_net_destroy": (None, [_P]),
         "rt3d_net_set_params": (C.c_int, [_P, _P]),
@@ -201,6 +202,14 @@ def _stream(stream):
     return C.c_void_p(s.cuda_stream)
 
 
+def workspace_bytes(cfg: Config):
+    """(bytes, entry capacity) of the workspace rt3d_create(cfg) would take."""
+    b = C.c_int64()
+    e = C.c_int64()
+    check(lib().rt3d_workspace_bytes(C.byref(cfg), C.byref(b), C.byref(e)), "rt3d_workspace_bytes")
+    return int(b.value), int(e.value)
+
+
 def params_from(d) -> Params:
     """Params from a dict (missing keys take the library defaults)."""
     if isinstance(d, Params):
@@ -220,11 +229,11 @@ class Context:
     """A library context plus torch-tensor marshalling for its entry points."""
 
     def __init__(self, max_h: int, max_w: int, max_t: int, k_max: int, irf_samples, irf_origin: int,
-                 max_batch: int = 1, max_entries: int = 0, device: int = 0):
+                 max_batch: int = 1, max_entries: int = 0, device: int = 0, mem_budget: int = 0):
         import torch
         self.torch = torch
         self.device = torch.device("cuda", device)
-        self.cfg = Config(max_h, max_w, max_t, k_max, max_batch, max_entries, device)
+        self.cfg = Config(max_h, max_w, max_t, k_max, max_batch, max_entries, device, mem_budget)
         self.k_max = k_max
         self.handle = rt3d_create(self.cfg, irf_samples, irf_origin)
 

@@ -12,8 +12,12 @@ the device.  Admission rules:
     later ones warm);
   * frames join a batch only while the slot's workspace holds them -- the
     batch's pixels within the context's pixel capacity and its worst-case
-    nonzero bins within the context's sparse-entry capacity (admission by
-    memory).
+    nonzero bins within the context's sparse-entry capacity;
+  * with a device-memory budget for frame data (SlotLimits.mem_budget), a
+    batch is admitted only while the bytes of the frames in flight (their
+    dense histograms) plus the streams' device-resident point clouds stay
+    within it (admission by memory: frames wait in the queue, not on the
+    device).
 
 The device work is behind a small backend interface so that the scheduling
 logic can be exercised without a GPU.  Host logic only: every step of the
@@ -57,6 +61,19 @@ class SlotLimits:
     max_h: int
     max_w: int
     max_t: int
+    mem_budget: int = 0        # device bytes for frame data over all slots (0 = no limit)
+    k_max: int = 3             # point slots per pixel (size of a stream's point cloud)
+
+
+def input_bytes(req: "Request") -> int:
+    """Device bytes of a frame's dense histogram while it is in flight."""
+    return 2 * req.pixels * req.t
+
+
+def state_bytes(req: "Request", k_max: int) -> int:
+    """Device bytes of a stream's resident point cloud (t, r float32 and an
+    alive byte per slot and pixel, a float32 background per pixel)."""
+    return req.pixels * (9 * k_max + 4)
 
 
 class Backend:
@@ -79,12 +96,17 @@ class Server:
     def __init__(self, backend: Backend, clock: Callable[[], float] = time.perf_counter):
         self.backend = backend
         self.clock = clock
-        self.queue: deque = deque()
+        # queued frames per stream, in frame order (a stream's frames run in
+        # order, one at a time, so only each stream's oldest can join a batch)
+        self.queues: Dict[int, deque] = {}
         self.busy_streams: Dict[int, Request] = {}
         self.started_streams: set = set()
         self.inflight: Dict[int, List[Request]] = {}
         self.completed: List[Request] = []
         self.batches: List[List[Request]] = []
+        self.inflight_bytes = 0            # dense inputs of the frames on the device
+        self.resident_bytes = 0            # the streams' point clouds
+        self.peak_bytes = 0
         self.t0 = clock()
 
     def now(self) -> float:
@@ -93,20 +115,26 @@ class Server:
     def submit(self, req: Request) -> None:
         lim = self.backend.limits()
         if req.h > lim.max_h or req.w > lim.max_w or req.t > lim.max_t \
-                or req.pixels > lim.max_pixels or req.pixels * req.t > lim.max_entries:
-            # a frame that cannot fit a slot on its own would wait forever
+                or req.pixels > lim.max_pixels or req.pixels * req.t > lim.max_entries \
+                or (lim.mem_budget and input_bytes(req) + state_bytes(req, lim.k_max) > lim.mem_budget):
+            # a frame that cannot fit a slot (or the memory budget) on its own would wait forever
             raise ValueError(f"frame {req.h}x{req.w}x{req.t} exceeds the server's slot capacity")
-        self.queue.append(req)
+        self.queues.setdefault(req.stream, deque()).append(req)
+
+    def queued(self) -> int:
+        return sum(len(q) for q in self.queues.values())
 
     def _form_batch(self) -> Optional[List[Request]]:
         lim = self.backend.limits()
         batch: List[Request] = []
         warm = None
         pixels = entries = 0
-        in_batch = set()
-        for req in list(self.queue):
-            if req.stream in self.busy_streams or req.stream in in_batch:
-                continue
+        mem = self.inflight_bytes + self.resident_bytes
+        # candidates: the oldest queued frame of every stream with none in flight,
+        # in arrival order
+        heads = [q[0] for st, q in self.queues.items() if q and st not in self.busy_streams]
+        heads.sort(key=lambda r: (r.arrival, r.stream, r.index))
+        for req in heads:
             # the first frame of a stream starts cold
             req_warm = req.stream in self.started_streams
             if warm is None:
@@ -115,20 +143,19 @@ class Server:
                 continue
             if pixels + req.pixels > lim.max_pixels or entries + req.pixels * req.t > lim.max_entries:
                 continue
-            # frames of one stream run in order: skip later frames of a stream
-            # whose earlier frame is still queued
-            if any(q.stream == req.stream and q.index < req.index for q in self.queue):
+            need = input_bytes(req) + (0 if req.stream in self.started_streams else state_bytes(req, lim.k_max))
+            if lim.mem_budget and mem + need > lim.mem_budget:
                 continue
             batch.append(req)
-            in_batch.add(req.stream)
             pixels += req.pixels
             entries += req.pixels * req.t
+            mem += need
             if len(batch) >= lim.max_frames:
                 break
         if not batch:
             return None
         for req in batch:
-            self.queue.remove(req)
+            self.queues[req.stream].popleft()
         self._warm = bool(warm)
         return batch
 
@@ -143,6 +170,7 @@ class Server:
                     req.done = t
                     self.busy_streams.pop(req.stream, None)
                     self.completed.append(req)
+                    self.inflight_bytes -= input_bytes(req)
                     finished += 1
         for slot in range(self.backend.n_slots()):
             if slot in self.inflight:
@@ -151,9 +179,14 @@ class Server:
             if batch is None:
                 break
             t = self.now()
+            lim = self.backend.limits()
             for req in batch:
                 req.admitted = t
                 self.busy_streams[req.stream] = req
+                self.inflight_bytes += input_bytes(req)
+                if req.stream not in self.started_streams:
+                    self.resident_bytes += state_bytes(req, lim.k_max)
+            self.peak_bytes = max(self.peak_bytes, self.inflight_bytes + self.resident_bytes)
             self.backend.launch(slot, batch, self._warm)
             for req in batch:
                 self.started_streams.add(req.stream)

@@ -16,14 +16,14 @@ steady-state launch.  Cases:
                 of 256x256 random features (the register-staged convolution
                 of the network's own training calls)
 
-Usage: python paper_1905_06700_b300/profile_cases.py CASE
+Usage: python profile_cases.py CASE
 """
 from __future__ import annotations
 
 import os
 import sys
 
-ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
@@ -32,7 +32,7 @@ from paper_1905_06700_b300 import build as B  # noqa: E402
 from paper_1905_06700_b300 import learned  # noqa: E402
 from paper_1905_06700_b300 import rt3d as R  # noqa: E402
 
-WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights", "learned_depth.bin")
+WEIGHTS = os.path.join(ROOT, "paper_1905_06700_b300", "weights", "learned_depth.bin")
 
 
 def case(name: str):

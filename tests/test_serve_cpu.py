@@ -1,5 +1,7 @@
 """Continuous-batching scheduler: admission, ordering and overlap, with a fake
 device backend and a manual clock (no GPU)."""
+import dataclasses
+
 import pytest
 
 from paper_1905_06700_b300.serve import Backend, Request, Server, SlotLimits, poisson_arrivals, summarize
@@ -145,3 +147,31 @@ def test_oversized_frames_are_rejected_at_submission():
     with pytest.raises(ValueError):
         srv.submit(Request(0, 0, 64, 64, 2048, 0.0))        # beyond the sparse capacity
     srv.submit(Request(0, 0, 64, 64, 1024, 0.0))
+
+
+def test_admission_by_device_memory_budget():
+    """With a device-memory budget for frame data, the frames in flight (their
+    dense histograms) plus the streams' resident point clouds never exceed it;
+    frames wait in the queue instead, every frame completes, and a frame that
+    cannot fit the budget on its own is refused at submission."""
+    from paper_1905_06700_b300.serve import input_bytes, state_bytes
+    clock = FakeClock()
+    arrivals = _arrivals(n_streams=6, rate=4000.0, duration=0.05, seed=3)
+    big = max(input_bytes(r) for r in arrivals)
+    states = sum(state_bytes(r, 3) for r in {r.stream: r for r in arrivals}.values())
+    budget = states + big                         # one of the largest frames in flight at a time
+    lim = SlotLimits(max_frames=4, max_pixels=3 * 64 * 64, max_entries=10 ** 8, max_h=256, max_w=256,
+                     max_t=4096, mem_budget=budget, k_max=3)
+    be = FakeBackend(clock, n_slots=3, limits=lim)
+    server = Server(be, clock=clock)
+    done = drive(server, clock, arrivals)
+    assert len(done) == len(arrivals)
+    assert 0 < server.peak_bytes <= budget and server.inflight_bytes == 0
+    # the same arrivals without the budget hold more on the device at once
+    clock2 = FakeClock()
+    free = Server(FakeBackend(clock2, n_slots=3, limits=dataclasses.replace(lim, mem_budget=0)), clock=clock2)
+    drive(free, clock2, _arrivals(n_streams=6, rate=4000.0, duration=0.05, seed=3))
+    assert free.peak_bytes > budget
+    with pytest.raises(ValueError):
+        Server(FakeBackend(clock, limits=SlotLimits(4, 10 ** 6, 10 ** 9, 256, 256, 4096, mem_budget=1000)),
+               clock=clock).submit(Request(0, 0, 64, 64, 1024, 0.0))
