@@ -552,19 +552,19 @@ __device__ float apss_point(const float* st, const float4* wg, const uint4* wi, 
             float w = 1.0f - d2;
             w *= w;
             w = w * w;
-            S0 += w;
-            Sz += w * z;
-            if constexpr (kFit) {
+            if constexpr (kSphere) {
+                const float wx = w * x, wy = w * y, wq = w * d2;
+                S0 += w; Sx += wx; Sy += wy; Sz += w * z; Sq += wq;
+                Sxx += wx * x; Sxy += wx * y; Syy += wy * y;
+                Sxq += wx * d2; Syq += wy * d2; Sqq += wq * d2;
+                Sxz += wx * z; Syz += wy * z; Sqz += wq * z;
+            } else if constexpr (kFit) {
                 const float wx = w * x, wy = w * y;
-                Sx += wx; Sy += wy;
+                S0 += w; Sx += wx; Sy += wy; Sz += w * z;
                 Sxx += wx * x; Sxy += wx * y; Syy += wy * y;
                 Sxz += wx * z; Syz += wy * z;
-                if constexpr (kSphere) {
-                    const float wq = w * d2;
-                    Sq += wq;
-                    Sxq += wx * d2; Syq += wy * d2; Sqq += wq * d2;
-                    Sqz += wq * z;
-                }
+            } else {
+                S0 += w; Sz += w * z;
             }
         }
         const uint4 pk = wi[o];
@@ -617,7 +617,34 @@ __device__ float apss_point(const float* st, const float4* wg, const uint4* wi, 
             z64 = fmin(fmax(z64, -1.0), 1.0);
             const double t64 = (double)tn + (double)P.apss_h * z64;
             return (float)fmin(fmax(t64, 0.0), (double)(T - 1));
+        } else if constexpr (kSphere) {
+            const float iw = 1.0f / S0;
+            const float mx = Sx * iw, my = Sy * iw, mz = Sz * iw, mq = Sq * iw;
+            const float cxx = Sxx * iw - mx * mx, cxy = Sxy * iw - mx * my, cyy = Syy * iw - my * my;
+            const float cxq = Sxq * iw - mx * mq, cyq = Syq * iw - my * mq, cqq = Sqq * iw - mq * mq;
+            const float dx = Sxz * iw - mx * mz, dy = Syz * iw - my * mz, dq = Sqz * iw - mq * mz;
+            // Cholesky of the 3x3 covariance
+            if (!(cxx > 0.0f)) return tn;
+            const float l11 = sqrtf(cxx);
+            const float l21 = cxy / l11, l31 = cxq / l11;
+            const float d22 = cyy - l21 * l21;
+            if (!(d22 > 0.0f)) return tn;
+            const float l22 = sqrtf(d22);
+            const float l32 = (cyq - l31 * l21) / l22;
+            const float d33 = cqq - l31 * l31 - l32 * l32;
+            if (!(d33 > 0.0f)) return tn;
+            const float l33 = sqrtf(d33);
+            const float y1 = -dx / l11;
+            const float y2 = (-dy - l21 * y1) / l22;
+            const float y3 = (-dq - l31 * y1 - l32 * y2) / l33;
+            const float u4 = y3 / l33;
+            const float u2 = (y2 - l32 * u4) / l22;
+            const float u1 = (y1 - l21 * u2 - l31 * u4) / l11;
+            const float u0 = -mz - u1 * mx - u2 * my - u4 * mq;
+            const float disc = 1.0f - 4.0f * u0 * u4;
+            zs = -2.0f * u0 / (1.0f + sqrtf(fmaxf(disc, 0.0f)));
         } else {
+            // plane: the 2x2 covariance of (x, y) against z
             const float iw = 1.0f / S0;
             const float mx = Sx * iw, my = Sy * iw, mz = Sz * iw;
             const float cxx = Sxx * iw - mx * mx, cxy = Sxy * iw - mx * my, cyy = Syy * iw - my * my;
@@ -630,28 +657,10 @@ __device__ float apss_point(const float* st, const float4* wg, const uint4* wi, 
             const float l22 = sqrtf(d22);
             const float y1 = -dx / l11;
             const float y2 = (-dy - l21 * y1) / l22;
-            if constexpr (kSphere) {
-                const float mq = Sq * iw;
-                const float cxq = Sxq * iw - mx * mq, cyq = Syq * iw - my * mq, cqq = Sqq * iw - mq * mq;
-                const float dq = Sqz * iw - mq * mz;
-                const float l31 = cxq / l11;
-                const float l32 = (cyq - l31 * l21) / l22;
-                const float d33 = cqq - l31 * l31 - l32 * l32;
-                if (!(d33 > 0.0f)) return tn;
-                const float l33 = sqrtf(d33);
-                const float y3 = (-dq - l31 * y1 - l32 * y2) / l33;
-                const float u4 = y3 / l33;
-                const float u2 = (y2 - l32 * u4) / l22;
-                const float u1 = (y1 - l21 * u2 - l31 * u4) / l11;
-                const float u0 = -mz - u1 * mx - u2 * my - u4 * mq;
-                const float disc = 1.0f - 4.0f * u0 * u4;
-                zs = -2.0f * u0 / (1.0f + sqrtf(fmaxf(disc, 0.0f)));
-            } else {
-                const float u2 = y2 / l22;
-                const float u1 = (y1 - l21 * u2) / l11;
-                const float u0 = -mz - u1 * mx - u2 * my;
-                zs = -u0;
-            }
+            const float u2 = y2 / l22;
+            const float u1 = (y1 - l21 * u2) / l11;
+            const float u0 = -mz - u1 * mx - u2 * my;
+            zs = -u0;
         }
     }
     zs = clampf(zs, -1.0f, 1.0f);

@@ -137,3 +137,26 @@ def test_bad_irf_is_rejected_before_any_device_call(L):
         with pytest.raises(R.Rt3dError) as e:
             R.rt3d_create(_cfg(), samples, origin)
         assert e.value.status == R.RT3D_E_INVALID
+
+
+def test_workspace_bytes_and_memory_budget(L):
+    """rt3d_workspace_bytes: 16 + 9K bytes per pixel of the batch plus 4 per
+    sparse entry (and the call record); with max_entries = 0 a budget sets the
+    entry capacity to the largest that fits; a budget below the per-pixel
+    state, or below an explicit entry capacity, is refused."""
+    cfg = _cfg()
+    full, ent = R.workspace_bytes(cfg)
+    stride = cfg.max_batch * cfg.max_h * cfg.max_w
+    assert ent == stride * cfg.max_t
+    fixed = full - 4 * ent
+    assert fixed >= stride * (16 + 9 * cfg.k_max) and fixed < stride * (16 + 9 * cfg.k_max) + (1 << 20)
+    budget = fixed + 4 * 100_000 + 3
+    b, e = R.workspace_bytes(_cfg(mem_budget=budget))
+    assert e == 100_000 and b <= budget
+    for bad in (_cfg(mem_budget=fixed // 2), _cfg(mem_budget=budget, max_entries=200_000)):
+        with pytest.raises(R.Rt3dError) as err:
+            R.workspace_bytes(bad)
+        assert err.value.status == R.RT3D_E_NOMEM
+    with pytest.raises(R.Rt3dError) as err:
+        R.workspace_bytes(_cfg(mem_budget=-1))
+    assert err.value.status == R.RT3D_E_INVALID
