@@ -48,7 +48,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--batch", type=int, default=16)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--latency-frames", type=int, default=64)
+    ap.add_argument("--latency-frames", type=int, default=128)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-frames", type=int, default=4)
     ap.add_argument("--cpu-single-frames", type=int, default=1,
