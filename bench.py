@@ -39,6 +39,9 @@ UNIT = "frames/s"
 H, W, T, K = 141, 141, 4096, 3
 KERNEL_NAMES = ["init", "phase_a", "phase_b", "phase_c", "final"]
 WEIGHTS = os.path.join(ROOT, "paper_1905_06700_b300", "weights", "learned_depth.bin")
+# the same network trained toward the synthetic scenes' true surfaces instead
+# of the plain method's output (reported beside the default checkpoint)
+WEIGHTS_TRUTH = os.path.join(ROOT, "paper_1905_06700_b300", "weights", "learned_depth_truth.bin")
 
 
 def parse():
@@ -646,7 +649,9 @@ def run_learned_form(args, device, with_oracle=True) -> dict:
     throughput, single-frame latency and the inlier depth error against the
     true surfaces (points within 5 IRF sigma) for no depth denoiser, APSS,
     the local plane fit, the bilateral depth filter and the learned form (the
-    committed network in place of APSS)."""
+    committed network in place of APSS, trained on the plain method's output;
+    and, as `learned_truth_target`, the same network trained toward the true
+    surfaces)."""
     import torch
     from paper_1905_06700_b300 import learned
     from paper_1905_06700_b300 import rt3d as R
@@ -672,7 +677,15 @@ def run_learned_form(args, device, with_oracle=True) -> dict:
     res = {"workload": "random_shapes 256x256x2048 (seeds 200000-200007), K=2, Gaussian IRF sigma 3, "
                        "20 PALM iterations, 8 frames per step",
            "checkpoint": {kk: head[kk] for kk in ("trained_on", "training") if kk in head}}
-    for name, den in (("none", 0), ("apss", 1), ("plane", 3), ("bilateral", 4), ("learned", 2)):
+    forms = [("none", 0), ("apss", 1), ("plane", 3), ("bilateral", 4), ("learned", 2)]
+    if os.path.exists(WEIGHTS_TRUTH):
+        forms.append(("learned_truth_target", 2))
+    for name, den in forms:
+        if name == "learned_truth_target":
+            theta_t, head_t = learned.load(WEIGHTS_TRUTH)
+            net_t = R.Net(1, h, w, device=device)
+            net_t.set_params(theta_t)
+            ctx.set_depth_net(net_t)
         p = dict(prm, depth_denoiser=den)
         ms, kt = time_steps(ctx, p, frames, outs, args.form_steps)
         errs = [learned.depth_errors(o, sc.depth, inlier) for o, sc in zip(outs, scs)]
@@ -687,7 +700,7 @@ def run_learned_form(args, device, with_oracle=True) -> dict:
             b.synchronize()
             if i >= 2:
                 lat.append(a.elapsed_time(b))
-        if den == 2 and with_oracle:
+        if name == "learned" and with_oracle:
             res["learned_vs_fp64_oracle_frame0"] = learned_oracle_error(scs[0], dense[0], outs[0], p, theta)
         res[name] = {"frames_per_s": round(nb / (ms / 1000), 2),
                      "frame_latency_ms_p50": round(float(np.percentile(lat, 50)), 3),
@@ -696,6 +709,8 @@ def run_learned_form(args, device, with_oracle=True) -> dict:
                      "depth_step_ms_per_iteration": round(kt.get("phase_b", 0.0) + 5 * kt.get("net", 0.0), 4),
                      "inlier_depth_rmse_bins": round(float(np.mean([e[0] for e in errs])), 4),
                      "inlier_fraction": round(float(np.mean([e[1] for e in errs])), 4)}
+        if name == "learned_truth_target":
+            res[name]["checkpoint"] = {kk: head_t[kk] for kk in ("trained_on", "training") if kk in head_t}
     assert ctx.device_status() == R.RT3D_OK
     ctx.close()
     return res

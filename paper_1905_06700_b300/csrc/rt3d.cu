@@ -1991,9 +1991,18 @@ rt3d_status rt3d_set_depth_net(rt3d_ctx_t* c, rt3d_net_t* net)
         alloc((void**)&c->net_y, sizeof(float) * 2 * c->stride);
         if (e != cudaSuccess) return cuda_fail(e);
         c->W.net_y = c->net_y;
-        // graphs captured before hold the old Work descriptor
-        for (auto& kv : c->graphs)
+    }
+    if (net != c->net) {
+        // captured graphs hold the launch arguments of the network they were
+        // captured with (its weights and scratch) and the Work descriptor
+        // from before the network buffers existed
+        for (auto& kv : c->graphs) {
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+            for (auto& pt : kv.second.timing) {
+                cudaEventDestroy(pt.a);
+                cudaEventDestroy(pt.b);
+            }
+        }
         c->graphs.clear();
         c->pending_graphs.clear();
     }

@@ -5,8 +5,11 @@ Host orchestration only: features, network passes, losses and AdamW steps run
 in the library (rt3d_net_*), the plain method's steps in its loop kernels
 (rt3d_phase).  A training pair is taken at every PALM iteration of a frame:
 the features of the point cloud after the depth gradient step (the input the
-depth denoiser sees) and, as target, the move the APSS denoiser then makes,
-divided by the depth scale, on the alive points of the first two slots.
+depth denoiser sees) and a target move, divided by the depth scale, on the
+alive points of the first two slots.  The target is the move to the nearest
+true surface of the pixel (synthetic scenes know it) on the points within
+`inlier` bins of one, or, without the scene's truth, the move the APSS
+denoiser makes (a network trained so imitates APSS and cannot do better).
 
 Checkpoint format: `<path>` holds the RT3D_NET_PARAMS float32 parameters
 (little endian, the library's flat order), `<path>.json` a header with the
@@ -42,10 +45,14 @@ def init_params(seed: int = 0) -> np.ndarray:
 
 
 def frame_pairs(ctx: "R.Context", net: "R.Net", dense, params: dict,
-                keep: Optional[Sequence[int]] = None) -> List[Tuple]:
+                keep: Optional[Sequence[int]] = None, truth: Optional[np.ndarray] = None,
+                inlier: Optional[float] = None) -> List[Tuple]:
     """(x [1][6][h][w], target [1][2][h][w], mask [1][2][h][w]) for every
     iteration of the plain method (APSS depth denoiser) on one dense frame
-    (or the iterations listed in `keep`)."""
+    (or the iterations listed in `keep`).  With `truth` (the scene's true
+    depths [S][h][w], NaN where a surface is absent) the target is the move to
+    the nearest true surface, masked to the points within `inlier` bins of it;
+    without, the APSS move on every alive point."""
     torch = ctx.torch
     prm = dict(params, depth_denoiser=1, warm_start=0)   # the plain method: APSS
     h, w, t = dense.shape
@@ -53,6 +60,11 @@ def frame_pairs(ctx: "R.Context", net: "R.Net", dense, params: dict,
     csr = ctx.compact(dense)
     st = ctx.init(prm, dense=dense)
     K = int(prm["k_max"])
+    tru = None
+    if truth is not None:
+        if inlier is None:
+            raise ValueError("a truth target needs the inlier band")
+        tru = torch.from_numpy(np.where(np.isfinite(truth), truth, 1e9).astype(np.float32)).to(ctx.device)
     pairs = []
     for it in range(int(prm["n_iter"])):
         ctx.phase(0, 1 if it == 0 else 0, prm, csr, st, shape=(h, w, t))
@@ -63,8 +75,14 @@ def frame_pairs(ctx: "R.Context", net: "R.Net", dense, params: dict,
         target = torch.zeros((1, 2, h, w), dtype=torch.float32, device=ctx.device)
         mask = torch.zeros((1, 2, h, w), dtype=torch.uint8, device=ctx.device)
         for k in range(min(K, 2)):
-            target[0, k] = (st["t"][k] - t_half[k]) / scale
-            mask[0, k] = alive[k]
+            if tru is None:
+                target[0, k] = (st["t"][k] - t_half[k]) / scale
+                mask[0, k] = alive[k]
+            else:
+                diff = tru - t_half[k][None]
+                near = torch.gather(diff, 0, diff.abs().argmin(0, keepdim=True))[0]
+                mask[0, k] = ((near.abs() < inlier) & (alive[k] > 0)).to(torch.uint8)
+                target[0, k] = near / scale
         target *= mask
         if keep is None or it in keep:
             pairs.append((x, target, mask))

@@ -5,8 +5,11 @@ Scenes: seeded random planes, spheres and boxes (at most two surfaces per
 pixel, 1-20 signal photons per pixel, SBR 0.05-2, Gaussian IRF sigma 3 bins),
 256 x 256 pixels x 2048 bins by default.  For each training scene the plain
 method runs on the device and a pair (features before the depth denoiser, the
-APSS move) is kept at a few iterations; the network is then trained with the
-library's own kernels (masked MSE, AdamW, cosine learning-rate decay).  The
+APSS move: a target from the plain method's output) is kept at a few
+iterations; the network is then trained with the library's own kernels (masked
+MSE, AdamW, cosine learning-rate decay).  `--target truth` takes instead the
+move to the nearest true surface of the synthetic scene, on the points within
+the inlier band of one.  The
 held-out scenes report the inlier depth RMSE against the true surfaces for no
 depth denoiser, APSS and the learned form; the report goes into the
 checkpoint header.
@@ -54,6 +57,7 @@ def main():
     ap.add_argument("--bins", type=int, default=2048)
     ap.add_argument("--keep", type=str, default="0,2,5,10,15", help="iterations whose pairs are kept")
     ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--target", choices=["apss", "truth"], default="apss")
     ap.add_argument("--batch", type=int, default=8)
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--weight-decay", type=float, default=1e-4)
@@ -68,6 +72,7 @@ def main():
     base = scenes.random_shapes(h, w, t, seed=0)
     prm = scenes.make_params(base)
     keep = [int(v) for v in args.keep.split(",")]
+    inlier = 5.0 * float(np.sqrt(base.irf.variance()))
     ctx = R.Context(h, w, t, prm["k_max"], base.irf.samples, base.irf.origin)
     net = R.Net(args.batch, h, w)
     t0 = time.time()
@@ -75,7 +80,8 @@ def main():
     for s in range(args.scenes):
         sc = scenes.random_shapes(h, w, t, seed=s)
         d = ctx.synthesize(scenes.sampling_tables(sc))
-        pairs += learned.frame_pairs(ctx, net, d, prm, keep=keep)
+        pairs += learned.frame_pairs(ctx, net, d, prm, keep=keep,
+                                     truth=sc.depth if args.target == "truth" else None, inlier=inlier)
     t_pairs = time.time() - t0
     net.set_params(learned.init_params(args.seed))
     t0 = time.time()
@@ -85,11 +91,11 @@ def main():
     t_train = time.time() - t0
     del pairs
     ctx.set_depth_net(net)
-    inlier = 5.0 * float(np.sqrt(base.irf.variance()))
     report = evaluate(ctx, prm, h, w, t, range(100000, 100000 + args.validate), inlier)
     theta = net.get_params()
     meta = dict(trained_on=dict(generator="random_shapes", scenes=args.scenes, size=[h, w, t],
-                                iterations_kept=keep, seeds=[0, args.scenes - 1]),
+                                iterations_kept=keep, seeds=[0, args.scenes - 1], target=args.target,
+                                inlier_bins=inlier),
                 training=dict(steps=args.steps, batch=args.batch, lr=args.lr, weight_decay=args.weight_decay,
                               loss_first=float(losses[:50].mean()), loss_last=float(losses[-50:].mean()),
                               seconds_pairs=round(t_pairs, 1), seconds_train=round(t_train, 1)),

@@ -204,6 +204,41 @@ def test_loop_with_a_network_matches_oracle(orc, n_iter):
         assert np.median(dt) <= 2e-2 and np.percentile(dt, 99) <= 0.2
 
 
+def test_attaching_another_network_runs_that_network(orc):
+    """A context replays captured call graphs; after another network is
+    attached, a call must run that network (bit for bit what a fresh context
+    with it gives), and new parameters set on the attached network must be
+    used by the next call without attaching it again."""
+    sc = scenes.small_random(21, 19, 256, n_comp=2, seed=14)
+    z = orc.synthesize(scenes.sampling_tables(sc))
+    prm = dict(workload_params(sc), depth_denoiser=2)
+    keys = ("t", "r", "alive", "b", "n_points")
+
+    def fresh(theta):
+        c = make_ctx(sc, k=prm["k_max"])
+        n = _net(1, sc.h, sc.w)
+        n.set_params(theta)
+        c.set_depth_net(n)
+        return _recon(c, prm, z)
+
+    ref_a, ref_b = fresh(_theta(3)), fresh(_theta(4))
+    assert any(not np.array_equal(np.asarray(ref_a[k]), np.asarray(ref_b[k])) for k in keys)
+    ctx = make_ctx(sc, k=prm["k_max"])
+    net_a, net_b = _net(1, sc.h, sc.w), _net(1, sc.h, sc.w)
+    net_a.set_params(_theta(3))
+    net_b.set_params(_theta(4))
+    ctx.set_depth_net(net_a)
+    got_a = _recon(ctx, prm, z)
+    ctx.set_depth_net(net_b)
+    got_b = _recon(ctx, prm, z)
+    net_b.set_params(_theta(3))            # same network object, new parameters
+    got_b_as_a = _recon(ctx, prm, z)
+    for k in keys:
+        assert np.array_equal(np.asarray(got_a[k]), np.asarray(ref_a[k])), k
+        assert np.array_equal(np.asarray(got_b[k]), np.asarray(ref_b[k])), k
+        assert np.array_equal(np.asarray(got_b_as_a[k]), np.asarray(ref_a[k])), k
+
+
 def test_trained_network_gains_over_no_depth_denoiser():
     """Train on pairs the plain method makes on random-shape scenes, then on
     held-out scenes the learned form's depth error is below the method's
