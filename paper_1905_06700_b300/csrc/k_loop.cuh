@@ -444,10 +444,11 @@ __device__ __forceinline__ void win_vote(unsigned* vote, int R, float px)
 // packed indicator words -- (di+4) | (dj+4) << 12, di^2 | dj^2 << 13 and
 // 1 | (di dj + 16) << 9 -- whose multiples by a slot count sum, field by field
 // and without carries (at most 4 slots x 81 cells), to the exact pixel-offset
-// moments of the weighted neighbours.  Low-pass: {r2, halo offset}.
+// moments of the weighted neighbours, then the cell's depth bound
+// h sqrt(1 - r2) (bins) of the window test.  Low-pass: {r2, halo offset}.
 template <bool kApss>
 __device__ __forceinline__ int win_fill(const unsigned* vote, int R, float px, int hstride, float4* g4,
-                                        uint4* ind, float2* g2)
+                                        uint4* ind, float2* g2, float h = 0.0f)
 {
     const unsigned v0 = vote[0], v1 = vote[1], v2 = vote[2];
     const int t = threadIdx.x;
@@ -464,7 +465,8 @@ __device__ __forceinline__ int win_fill(const unsigned* vote, int R, float px, i
                 g4[rank] = make_float4(x, y, r2, __int_as_float(q));
                 ind[rank] = make_uint4((unsigned)(di + 4) | ((unsigned)(dj + 4) << 12),
                                        (unsigned)(di * di) | ((unsigned)(dj * dj) << 13),
-                                       1u | ((unsigned)(di * dj + 16) << 9), 0u);
+                                       1u | ((unsigned)(di * dj + 16) << 9),
+                                       __float_as_uint(h * sqrtf(1.0f - r2)));
             } else {
                 g2[rank] = make_float2(r2, __int_as_float(q));
             }
@@ -528,27 +530,29 @@ __device__ float apss_point(const float* st, const float4* wg, const uint4* wi, 
         const float4 gc = wg[o];
         const float x = gc.x, y = gc.y, r2 = gc.z;
         const int q = qc + __float_as_int(gc.w);
-        float zk[K], d2k[K];
+        const uint4 pk = wi[o];
+        // inside the window iff d^2 = r2 + (dt / h)^2 < 1, i.e. |dt| < h sqrt(1 - r2),
+        // the cell's depth bound: one subtraction and one compare per slot;
+        // only the slots inside accumulate, the others have weight exactly
+        // zero and would leave every sum unchanged
+        const float dlim = __uint_as_float(pk.w);
+        float dk[K];
         unsigned in = 0u;
 #pragma unroll
         for (int m = 0; m < K; ++m) {
-            zk[m] = (st[m * kHalo + q] - tn) * inv_h;
-            d2k[m] = r2 + zk[m] * zk[m];
-            if (d2k[m] < 1.0f) in |= 1u << m;
+            dk[m] = st[m * kHalo + q] - tn;
+            if (fabsf(dk[m]) < dlim) in |= 1u << m;
         }
         const unsigned cnt = __popc(in);
-        // only the slots inside the window: the others have weight exactly
-        // zero and would leave every sum unchanged
         while (in) {
             const int m = __ffs(in) - 1;
             in &= in - 1u;
-            float z = zk[0], d2 = d2k[0];
+            float dd = dk[0];
 #pragma unroll
             for (int j = 1; j < K; ++j)
-                if (m == j) {
-                    z = zk[j];
-                    d2 = d2k[j];
-                }
+                if (m == j) dd = dk[j];
+            const float z = dd * inv_h;
+            const float d2 = r2 + z * z;
             float w = 1.0f - d2;
             w *= w;
             w = w * w;
@@ -567,7 +571,6 @@ __device__ float apss_point(const float* st, const float4* wg, const uint4* wi, 
                 S0 += w; Sz += w * z;
             }
         }
-        const uint4 pk = wi[o];
         ia += cnt * pk.x;
         ib += cnt * pk.y;
         ic += cnt * pk.z;
@@ -789,7 +792,7 @@ k_phase_b(const CallRecord* __restrict__ rec, const Work W, int alive_from_b, in
     __syncthreads();
     const int hstride = kTileW + 2 * R;
     const int q0 = (c.li + R) * hstride + (c.lj + R);
-    const int n_off = apss ? win_fill<true>(s_vote, R, apss_px, hstride, s_wg, s_wi, nullptr) : 0;
+    const int n_off = apss ? win_fill<true>(s_vote, R, apss_px, hstride, s_wg, s_wi, nullptr, P.apss_h) : 0;
     for (int k = 0; k < K; ++k) s_tn[k][threadIdx.x] = st[k * kHalo + q0];
     if (alive_from_b && c.inb)
         for (int k = 0; k < K; ++k) F.alive[(long long)k * np + lp] = st[k * kHalo + q0] != kDeadDepth ? 1 : 0;
