@@ -465,8 +465,9 @@ rt3d_status rt3d_net_train_step(rt3d_net_t* net, int n, int h, int w, const floa
 /* The network a context's loop uses when params.depth_denoiser is
  * RT3D_DEPTH_LEARNED (NULL detaches).  The network must outlive its use; the
  * context allocates its inference buffers here.  Attaching a different
- * network drops the context's captured call graphs (they hold the previous
- * network's buffers), so the next call of each shape captures again; new
+ * network waits for the device to finish its work and drops the context's
+ * captured call graphs (they hold the previous network's buffers), so the
+ * next call of each shape captures again; new
  * parameters set on the attached network (rt3d_net_set_params, training
  * steps) are seen by the next call without that. */
 rt3d_status rt3d_set_depth_net(rt3d_ctx_t* ctx, rt3d_net_t* net);

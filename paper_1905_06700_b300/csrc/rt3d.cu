@@ -1995,7 +1995,9 @@ rt3d_status rt3d_set_depth_net(rt3d_ctx_t* c, rt3d_net_t* net)
     if (net != c->net) {
         // captured graphs hold the launch arguments of the network they were
         // captured with (its weights and scratch) and the Work descriptor
-        // from before the network buffers existed
+        // from before the network buffers existed; a launch of one may still
+        // run on a caller's stream, so the device finishes its work first
+        if (!c->graphs.empty()) RT3D_CUDA(cudaDeviceSynchronize());
         for (auto& kv : c->graphs) {
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
             for (auto& pt : kv.second.timing) {
