@@ -110,3 +110,19 @@ def test_set_irfs_validates():
         with pytest.raises(R.Rt3dError):
             ctx.set_irfs(bad)
     ctx.set_irfs([(np.ones(59), 0)] * 4)          # 4 x (59 + 6) = 260 <= 262
+
+
+def test_index_past_the_last_response_reads_as_the_last(orc):
+    """rt3d_frame.irf_index: an index past the context's last response reads
+    as the last one (the header's contract), bit for bit."""
+    torch = torch_mod()
+    base, irfs, idx, z = _two_response_frame(orc, 95)
+    prm = workload_params(base)
+    ctx = _ctx(base, irfs, prm)
+    zd = upload_u16(z)
+    ones = torch.from_numpy(np.ones_like(idx)).cuda()
+    ref = np_of(ctx.reconstruct(prm, dense=zd, irf_index=ones))
+    for big in (7, 255):
+        got = np_of(ctx.reconstruct(prm, dense=zd, irf_index=torch.from_numpy(np.full_like(idx, big)).cuda()))
+        for k in ("t", "r", "alive", "b", "n_points"):
+            assert np.array_equal(np.asarray(ref[k]), np.asarray(got[k])), (big, k)
