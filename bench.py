@@ -579,6 +579,12 @@ def run_precision_form(args, device, peaks, with_oracle=True) -> dict:
         oirf = oracle.OIrf(base.irf.samples, base.irf.origin)
         oracle_runs = {1: compare.reconstruct_with_probes(z0, oirf, prm),
                        0: compare.reconstruct_with_probes(z0, oirf, dict(prm, apss_fp64=0))}
+        # the FP64 oracle's own time on this workload (one frame, the host's cores)
+        t0 = time.perf_counter()
+        oracle.reconstruct(z0, oirf, prm)
+        sec = time.perf_counter() - t0
+        res["cpu_fp64_oracle"] = {"frames_per_s": round(1.0 / sec, 4), "cores": oracle.num_threads(), "kind": "oracle",
+                                  "sample": "frame 0 of the workload (init + 20 iterations, FP64 APSS solve), OpenMP"}
     ref = None
     for name, mode, fp64 in (("integer", 0, 1), ("fp16", 2, 1), ("bf16", 1, 1), ("integer_fp32_solve", 0, 0)):
         ms, kt = time_steps(ctx, dict(prm, lmf_precision=mode, apss_fp64=fp64), frames, outs, args.form_steps)
