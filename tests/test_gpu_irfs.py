@@ -126,3 +126,32 @@ def test_index_past_the_last_response_reads_as_the_last(orc):
         got = np_of(ctx.reconstruct(prm, dense=zd, irf_index=torch.from_numpy(np.full_like(idx, big)).cuda()))
         for k in ("t", "r", "alive", "b", "n_points"):
             assert np.array_equal(np.asarray(ref[k]), np.asarray(got[k])), (big, k)
+
+
+def test_per_pixel_responses_with_gain_and_sparse_input_match_oracle(orc):
+    """Per-pixel responses together with a gain map holding dead pixels, first
+    from the dense histograms against the FP64 oracle, then from the same
+    photons as a sparse list (bit for bit the dense path's)."""
+    torch = torch_mod()
+    from oracle import compare
+    base, irfs, idx, z = _two_response_frame(orc, 96)
+    prm = workload_params(base)
+    rng = np.random.default_rng(96)
+    gain = rng.uniform(0.6, 1.4, (base.h, base.w)).astype(np.float32)
+    gain[2, 3] = 0.0
+    gain[11, 20] = 0.0
+    ctx = _ctx(base, irfs, prm)
+    zd = upload_u16(z)
+    gd = torch.from_numpy(gain).cuda()
+    ix = torch.from_numpy(idx).cuda()
+    g = np_of(ctx.reconstruct(prm, dense=zd, gain=gd, irf_index=ix))
+    o, probes = compare.reconstruct_with_probes(z, _oirfs(orc, irfs), prm, gain=gain.astype(np.float64),
+                                                irf_idx=idx)
+    st = compare_clouds(g, o, base.t, TOL_T, TOL_R, probes=probes, max_ill_frac=0.05,
+                        label="two responses, gain map", r_min=prm["r_min"])
+    assert not g["alive"][:, 2, 3].any() and not g["alive"][:, 11, 20].any()
+    csr = ctx.compact(zd)
+    s = np_of(ctx.reconstruct(prm, csr=csr, shape=z.shape, gain=gd, irf_index=ix))
+    for k in ("t", "r", "alive", "b", "n_points"):
+        assert np.array_equal(np.asarray(g[k]), np.asarray(s[k])), k
+    print("two responses, gain map", st)

@@ -90,3 +90,22 @@ def test_sr_batch_equals_single_frames_and_unsupported_paths_say_so(orc):
         ctx.reconstruct_batch(dict(prm, upsample=4), frames)
     assert e.value.status == R.RT3D_E_INVALID
     assert ctx.device_status() == R.RT3D_OK
+
+
+def test_sr_with_gain_map_matches_oracle(orc):
+    """Super-resolution with a detector gain map (a dead lidar pixel: its
+    block of world pixels keeps no points) against the FP64 oracle."""
+    torch = torch_mod()
+    from oracle import compare
+    sc, z = _frame(orc, 12, 10, seed=8)
+    prm = sr_params(sc)
+    rng = np.random.default_rng(8)
+    gain = rng.uniform(0.7, 1.3, (sc.h, sc.w)).astype(np.float32)
+    gain[4, 6] = 0.0
+    ctx = make_ctx(sc, k=2, max_h=3 * sc.h, max_w=3 * sc.w)
+    g = np_of(ctx.reconstruct(prm, dense=upload_u16(z), gain=torch.from_numpy(gain).cuda()))
+    o, probes = compare.reconstruct_with_probes(z, oracle_irf(orc, sc), prm, gain=gain.astype(np.float64))
+    st = compare_clouds(g, o, sc.t, TOL_T, TOL_R, probes=probes, max_ill_frac=0.05,
+                        label="super-resolution, gain map", r_min=prm["r_min"])
+    assert not g["alive"][:, 12:15, 18:21].any()
+    print("super-resolution, gain map", st)
