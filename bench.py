@@ -621,7 +621,10 @@ def run_precision_form(args, device, peaks, with_oracle=True) -> dict:
                 "ill_conditioned": st["ill"], "dt_max_bins_well_conditioned": st["dt_max"],
                 "dr_max_rel_well_conditioned": st["dr_max"],
                 "ill_conditioned_over_3x_probe_deviation": st["ill_over_bound"],
-                "ill_conditioned_worst_ratio_to_probe": st["ill_ratio_max"]}
+                "ill_conditioned_worst_ratio_to_probe": st["ill_ratio_max"],
+                "db_max_rel_well_conditioned": st["db_max"],
+                "ill_conditioned_backgrounds": st["ill_background_pixels"],
+                "ill_backgrounds_over_3x_probe_deviation": st["ill_background_over_bound"]}
         res[name] = entry
     assert ctx.device_status() == R.RT3D_OK
     ctx.close()
@@ -904,6 +907,9 @@ def oracle_parity(z, irf_samples, irf_origin, prm, out, h, w, t) -> dict:
             "ill_conditioned_flips_no_probe_flips": st["ill_flips_unexplained"],
             "ill_conditioned_over_3x_probe_deviation": st["ill_over_bound"],
             "ill_conditioned_worst_ratio_to_probe": st["ill_ratio_max"],
+            "db_max_rel_well_conditioned": st["db_max"],
+            "ill_conditioned_backgrounds": st["ill_background_pixels"],
+            "ill_backgrounds_over_3x_probe_deviation": st["ill_background_over_bound"],
             "near_threshold_points": st.get("near_threshold", 0),
             "alive_mismatch": st["all_alive_mismatch"],
             "dt_max_bins": st["all_dt_max"], "dt_p999_bins": st["all_dt_p999"],

@@ -91,7 +91,8 @@ def cloud_stats(gpu, o, probes, T, tol_t, tol_r, r_min=None, ratio=3.0):
 
     Well-conditioned points: flips (alive differs), depth error (bins),
     relative intensity error (floor 0.1 photon), background error relative to
-    the pixel's mean count rate b + sum r / T (pixels without ill points).
+    the pixel's mean count rate b + sum r / T (pixels without ill points whose
+    background no probe moves beyond half the tolerance).
 
     Ill-conditioned points: each must satisfy, against the probe ensemble's
     envelope env = max over probes of |probe - oracle| (infinite where a probe
@@ -101,6 +102,14 @@ def cloud_stats(gpu, o, probes, T, tol_t, tol_r, r_min=None, ratio=3.0):
         relative intensity.
     `ill_ratio_max` is the largest |gpu - oracle| / env over the ill points
     whose error exceeds the tolerance (0 if none does).
+
+    Backgrounds the same way: the background step is multiplicative in
+    (b + eps) (Methods, background update), so a pixel whose background starts
+    at the floor with photons its points do not explain grows it by orders of
+    magnitude and amplifies rounding.  A pixel whose background some probe
+    moves beyond half the tolerance, or that holds an ill point, is held to
+    |b_gpu - b_o| / rate <= max(tol_r, ratio * env_b) (`ill_background_pixels`,
+    `ill_background_over_bound`).
 
     Near-threshold points (the parity definition's exemption): oracle points
     whose final intensity lies within 1e-5 r_min of r_min (counted only)."""
@@ -121,8 +130,14 @@ def cloud_stats(gpu, o, probes, T, tol_t, tol_r, r_min=None, ratio=3.0):
     kk, hh, ww = o.t.shape
     blk = lambda a: a.reshape(kk, hh // up, up, ww // up, up).sum(axis=(0, 2, 4))
     ill_px = blk(ill.astype(np.int64)) > 0
-    rate = o.b + blk(o.r * oa) / T
-    db = (np.abs(gpu["b"].astype(np.float64) - o.b) / np.maximum(rate, 1e-12))[~ill_px]
+    rate = np.maximum(o.b + blk(o.r * oa) / T, 1e-12)
+    db_all = np.abs(gpu["b"].astype(np.float64) - o.b) / rate
+    env_b = np.zeros_like(o.b)
+    for p in probes:
+        env_b = np.maximum(env_b, np.abs(p.b - o.b) / rate)
+    ill_b = ill_px | (env_b > 0.5 * tol_r)
+    db = db_all[~ill_b]
+    b_over = ill_b & (db_all > np.maximum(tol_r, ratio * env_b))
 
     # envelope of the probes' own deviations
     env_t = np.zeros_like(o.t)
@@ -154,6 +169,8 @@ def cloud_stats(gpu, o, probes, T, tol_t, tol_r, r_min=None, ratio=3.0):
               dt_p999=float(np.percentile(dtw, 99.9)) if dtw.size else 0.0,
               dr_max=float(dr_all[well].max()) if well.any() else 0.0,
               db_max=float(db.max()) if db.size else 0.0,
+              ill_background_pixels=int((ill_b & ~ill_px).sum()),
+              ill_background_over_bound=int(b_over.sum()),
               ill_flips=int(ill_flips.sum()),
               ill_flips_unexplained=int(ill_flip_unexplained.sum()),
               ill_over_bound=int(ill_over.sum()),

@@ -77,7 +77,10 @@ def compare_clouds(gpu, orc_state, T, tol_t=1e-3, tol_r=1e-4, probes=None, max_i
     ill-conditioned are held instead to the ensemble's own deviation
     (oracle.compare.cloud_stats): a flip only where a probe flips the point,
     an error within max(tolerance, ratio x the probes' deviation); their
-    count is bounded by max_ill_frac of the points.  Returns statistics."""
+    count is bounded by max_ill_frac of the points.  Backgrounds likewise: a
+    pixel whose background a probe moves beyond half the tolerance is held to
+    the ensemble's deviation, and such pixels are at most max_ill_frac of the
+    pixels.  Returns statistics."""
     from oracle import compare
     st = compare.cloud_stats(gpu, orc_state, probes or [], T, tol_t, tol_r, r_min=r_min, ratio=ratio)
     n_pts = max(1, st["points"])
@@ -88,6 +91,8 @@ def compare_clouds(gpu, orc_state, T, tol_t=1e-3, tol_r=1e-4, probes=None, max_i
     assert st["db_max"] <= tol_r, (label, st)
     assert st["ill_flips_unexplained"] == 0, (label, st)
     assert st["ill_over_bound"] == 0, (label, st)
+    assert st["ill_background_over_bound"] == 0, (label, st)
+    assert st["ill_background_pixels"] <= max_ill_frac * orc_state.b.size, (label, "ill backgrounds", st)
     return st
 
 

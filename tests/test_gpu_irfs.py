@@ -155,3 +155,42 @@ def test_per_pixel_responses_with_gain_and_sparse_input_match_oracle(orc):
     for k in ("t", "r", "alive", "b", "n_points"):
         assert np.array_equal(np.asarray(g[k]), np.asarray(s[k])), k
     print("two responses, gain map", st)
+
+
+def test_warm_start_with_per_pixel_responses_matches_oracle(orc):
+    """A stream's next frame (the scene moved by one bin) observed through two
+    responses and started from the previous frame's cloud: the GPU's warm
+    start against the oracle's loop run from the same (float32) state."""
+    torch = torch_mod()
+    from oracle import compare
+    base = scenes.small_random(15, 21, 300, n_comp=2, seed=97)
+    ia, ib = scenes.gaussian_irf(3.0, 12), scenes.gamma_irf(3.0, 2.0, 30)
+    rng = np.random.default_rng(97)
+    blocks = rng.integers(0, 2, size=((base.h + 3) // 4, (base.w + 3) // 4))
+    idx = np.kron(blocks, np.ones((4, 4), np.int64))[:base.h, :base.w].astype(np.uint8)
+
+    def frame(k):
+        sk = scenes.moving_frame(base, k)
+        za = orc.synthesize(scenes.sampling_tables(dataclasses.replace(sk, irf=ia)))
+        zb = orc.synthesize(scenes.sampling_tables(dataclasses.replace(sk, irf=ib)))
+        return np.where(idx[..., None] == 1, zb, za)
+
+    z1, z2 = frame(0), frame(1)
+    irfs = (ia, ib)
+    b0 = dataclasses.replace(base, irf=ia)
+    prm = workload_params(b0)
+    ctx = _ctx(b0, irfs, prm)
+    ix = torch.from_numpy(idx).cuda()
+    g1 = ctx.reconstruct(prm, dense=upload_u16(z1), irf_index=ix)
+    a = np_of(g1)
+    start = orc.new_state(prm["k_max"], base.h, base.w)
+    start.t[:] = a["t"]
+    start.r[:] = a["r"]
+    start.alive[:] = a["alive"]
+    start.b[:] = a["b"]
+    g2 = np_of(ctx.reconstruct(dict(prm, warm_start=1), dense=upload_u16(z2), out=g1, irf_index=ix))
+    o, probes = compare.palm_with_probes(orc.OFrame(z2, None, irf_idx=idx), _oirfs(orc, irfs), prm, start,
+                                         prm["n_iter"])
+    st = compare_clouds(g2, o, base.t, TOL_T, TOL_R, probes=probes, max_ill_frac=0.05,
+                        label="two responses, warm start", r_min=prm["r_min"])
+    print("two responses, warm start", st)

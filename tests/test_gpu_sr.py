@@ -42,7 +42,7 @@ def test_sr_init_spreads_peaks_bit_exact(orc):
 
 
 @pytest.mark.parametrize("over", [dict(), dict(bkg_mode=1), dict(depth_denoiser=0), dict(depth_denoiser=3),
-                                  dict(n_iter=1)])
+                                  dict(n_iter=1), dict(apss_fp64=1)])
 def test_sr_reconstruct_matches_oracle(orc, over):
     from oracle import compare
     sc, z = _frame(orc)
