@@ -194,3 +194,30 @@ def test_warm_start_with_per_pixel_responses_matches_oracle(orc):
     st = compare_clouds(g2, o, base.t, TOL_T, TOL_R, probes=probes, max_ill_frac=0.05,
                         label="two responses, warm start", r_min=prm["r_min"])
     print("two responses, warm start", st)
+
+
+def test_learned_form_with_per_pixel_responses_matches_oracle(orc):
+    """The learned depth denoiser in a frame with two responses, against the
+    FP64 oracle running the same network (its bfloat16 inputs: the bounds of
+    the learned form's own parity test)."""
+    torch = torch_mod()
+    from paper_1905_06700_b300 import learned
+    from paper_1905_06700_b300 import rt3d as R
+    base, irfs, idx, z = _two_response_frame(orc, 98)
+    prm = dict(workload_params(base), depth_denoiser=2)
+    th = learned.init_params(9).astype(np.float64)
+    th += np.random.default_rng(16).normal(0, 0.02, th.size)
+    th = th.astype(np.float32)
+    ctx = _ctx(base, irfs, prm)
+    net = R.Net(1, base.h, base.w)
+    net.set_params(th)
+    ctx.set_depth_net(net)
+    g = np_of(ctx.reconstruct(prm, dense=upload_u16(z), irf_index=torch.from_numpy(idx).cuda()))
+    o = orc.reconstruct(z, _oirfs(orc, irfs), dict(prm, net_theta=th.astype(np.float64)), irf_idx=idx)
+    both = g["alive"].astype(bool) & o.alive.astype(bool)
+    flips = int((g["alive"].astype(bool) != o.alive.astype(bool)).sum())
+    dt = np.abs(g["t"].astype(np.float64) - o.t)[both]
+    print("learned form, two responses: points", int(o.alive.sum()), "flips", flips,
+          "dt median %.2e p99 %.2e max %.2e" % (np.median(dt), np.percentile(dt, 99), dt.max()))
+    assert flips <= 0.01 * max(1, int(o.alive.sum()))
+    assert np.median(dt) <= 2e-2 and np.percentile(dt, 99) <= 0.2
