@@ -344,7 +344,7 @@ def run_ours(args, world, rank, local):
     del outs0
     ms_loop = ms_total / args.steps - ms_init_only
 
-    # ---------------- rooflines (the path is HBM-bound)
+    # ---------------- rooflines (the path is HBM-bound: algorithmic bytes per launch / time)
     n_px = nb * H * W
     ff = fused_fraction(prm)
     alg = algorithmic_bytes(n_px, T, nnz_total, K, ff)
